@@ -1,0 +1,701 @@
+/*
+ * ft_oracle.c -- plain CPU oracle for the FastTrack tracking hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).  Shares no code
+ * with the CUDA library.  Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared.
+ *
+ * Steps, in the paper's order:
+ *   stereo matching, pinhole (sections II-B, IV-C)
+ *     a1  row-band index of right keypoints
+ *     a2  best Hamming match per left keypoint inside its band
+ *     a3  SAD refinement over +-L pixel shifts at the keypoint's level
+ *     a4  parabola sub-pixel fit, disparity and depth
+ *     a5  median-based outlier rejection over the frame's matches
+ *   stereo matching, fisheye (sections II-B, IV-C)
+ *     a6  brute force over the right overlap keypoints, best/second best + ratio
+ *   search of local points by projection (sections II-D, IV-E)
+ *     a7  64x48 keypoint grid
+ *     a8  frustum test, FP32 projection, predicted scale level
+ *     a9  cell-window gather, best/second-best Hamming, ratio test
+ *     a10 a keypoint claimed by several map points keeps the smallest
+ *         (distance, map point index); map points are searched independently
+ *         as the paper states (section IV-E).
+ * The paper prints none of the constants; each is a parameter (orc_params).
+ */
+#include "ft_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Hamming distance: XOR byte by byte, count bits with a 256-entry table.   */
+/* The table is built by counting the bits of each byte value one by one.   */
+/* ------------------------------------------------------------------------ */
+static int bit_count_table[256];
+static int bit_count_ready = 0;
+
+static void build_bit_count_table(void)
+{
+    for (int v = 0; v < 256; ++v) {
+        int c = 0;
+        for (int b = 0; b < 8; ++b) c += (v >> b) & 1;
+        bit_count_table[v] = c;
+    }
+    bit_count_ready = 1;
+}
+
+int orc_hamming(const uint8_t *a, const uint8_t *b)
+{
+    if (!bit_count_ready) build_bit_count_table();
+    int d = 0;
+    for (int i = 0; i < ORC_DESC_BYTES; ++i) d += bit_count_table[a[i] ^ b[i]];
+    return d;
+}
+
+/* Scale of level l: s^l accumulated in FP32, and its reciprocal. */
+void orc_scale_table(int nlevels, float s, float *sc, float *isc)
+{
+    sc[0] = 1.0f;
+    for (int l = 1; l < nlevels; ++l) sc[l] = sc[l - 1] * s;
+    for (int l = 0; l < nlevels; ++l) isc[l] = 1.0f / sc[l];
+}
+
+/* ------------------------------------------------------------------------ */
+/* atan2 on the first quadrant, written from the mathematics:               */
+/*   atan2(y, x) = atan(y/x) if y <= x, else pi/2 - atan(x/y);             */
+/*   for t in [0, 1]: atan(t) = pi/4 + atan((t-1)/(t+1)) if t > tan(pi/8); */
+/*   for |a| <= tan(pi/8): the Taylor series sum_k (-1)^k a^(2k+1)/(2k+1), */
+/*   truncated after k = 8 (remainder below 3e-9 for |a| <= 0.4143).       */
+/* Coefficients are 1/(2k+1) divided out in FP32; Horner in a^2.           */
+/* ------------------------------------------------------------------------ */
+#define ORC_ATAN_TERMS 9
+
+static float atan_small(float a)
+{
+    float c[ORC_ATAN_TERMS];
+    for (int k = 0; k < ORC_ATAN_TERMS; ++k) {
+        float inv = 1.0f / (float)(2 * k + 1);
+        c[k] = (k & 1) ? -inv : inv;
+    }
+    float a2 = a * a;
+    float p = c[ORC_ATAN_TERMS - 1];
+    for (int k = ORC_ATAN_TERMS - 2; k >= 0; --k) p = c[k] + a2 * p;
+    return a * p;
+}
+
+static float atan_unit(float t)   /* t in [0, 1] */
+{
+    const float tan_pi_8 = 0.41421356237309504880f;
+    const float pi_4 = 0.78539816339744830962f;
+    if (t > tan_pi_8) return pi_4 + atan_small((t - 1.0f) / (t + 1.0f));
+    return atan_small(t);
+}
+
+float orc_atan2_pos(float y, float x)
+{
+    const float pi_2 = 1.57079632679489661923f;
+    if (y == 0.0f) return 0.0f;                 /* includes y = x = 0 */
+    if (y <= x) return atan_unit(y / x);
+    return pi_2 - atan_unit(x / y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a1: row-band index.  Right keypoint j covers image rows                  */
+/* floor(y_j - r) .. ceil(y_j + r) with r = 2*scale[oct_j], clamped to the  */
+/* image; each row lists its keypoints in ascending j (CSR).                */
+/* Returns the number of entries, or -1 if it exceeds cap.                  */
+/* ------------------------------------------------------------------------ */
+static void band_rows(float y, float r, int H, int *lo, int *hi)
+{
+    int a = (int)floorf(y - r);
+    int b = (int)ceilf(y + r);
+    if (a < 0) a = 0;
+    if (b > H - 1) b = H - 1;
+    *lo = a;
+    *hi = b;
+}
+
+int orc_row_index(int nr, const float *yr, const int8_t *octr, const float *sc,
+                  int H, int *row_ptr, int *row_idx, int cap)
+{
+    int *count = (int *)calloc((size_t)H + 1, sizeof(int));
+    for (int j = 0; j < nr; ++j) {
+        int lo, hi;
+        band_rows(yr[j], 2.0f * sc[octr[j]], H, &lo, &hi);
+        for (int row = lo; row <= hi; ++row) count[row]++;
+    }
+    row_ptr[0] = 0;
+    for (int row = 0; row < H; ++row) row_ptr[row + 1] = row_ptr[row] + count[row];
+    int total = row_ptr[H];
+    if (total > cap) {
+        free(count);
+        return -1;
+    }
+    for (int row = 0; row < H; ++row) count[row] = row_ptr[row];
+    for (int j = 0; j < nr; ++j) {
+        int lo, hi;
+        band_rows(yr[j], 2.0f * sc[octr[j]], H, &lo, &hi);
+        for (int row = lo; row <= hi; ++row) row_idx[count[row]++] = j;
+    }
+    free(count);
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a2: for left keypoint i, scan the row list of row (int)y_i.  A right     */
+/* keypoint j is a candidate if its octave is within one of i's and its x   */
+/* lies in [x_i - maxD, x_i - minD], with minD = 0 and maxD = bf / b (the   */
+/* nearest depth is one baseline).  Best = smallest (d, j).  dist[i] is     */
+/* that smallest d (-1 without candidates); best_r[i] = j if d < th_stereo. */
+/* ------------------------------------------------------------------------ */
+void orc_stereo_best(const orc_params *p, const orc_pinhole *cam,
+                     const orc_keypoints *L, const orc_keypoints *R,
+                     const int *row_ptr, const int *row_idx,
+                     int32_t *best_r, int32_t *dist)
+{
+    const float minZ = cam->b;
+    const float minD = 0.0f;
+    const float maxD = cam->bf / minZ;
+    for (int i = 0; i < L->n; ++i) {
+        best_r[i] = -1;
+        dist[i] = -1;
+        if (L->y[i] < 0.0f) continue;
+        int row = (int)L->y[i];
+        if (row >= cam->height) continue;
+        if (row_ptr[row + 1] == row_ptr[row]) continue;
+        const float minU = L->x[i] - maxD;
+        const float maxU = L->x[i] - minD;
+        if (maxU < 0.0f) continue;
+        const int levelL = L->oct[i];
+        int bestd = 1 << 30, bestj = -1;
+        for (int e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
+            int j = row_idx[e];
+            if (R->oct[j] < levelL - 1 || R->oct[j] > levelL + 1) continue;
+            if (R->x[j] < minU || R->x[j] > maxU) continue;
+            int d = orc_hamming(L->desc + (size_t)i * ORC_DESC_BYTES,
+                                R->desc + (size_t)j * ORC_DESC_BYTES);
+            if (d < bestd || (d == bestd && j < bestj)) {
+                bestd = d;
+                bestj = j;
+            }
+        }
+        if (bestj < 0) continue;
+        dist[i] = bestd;
+        if (bestd < p->th_stereo) best_r[i] = bestj;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a3: SAD of the (2w+1)x(2w+1) left patch centred on (ul, vl) against the  */
+/* right patches centred on (ur0 + k, vl), k = -L..L, at pyramid level      */
+/* `level`.  Every patch first has its own centre pixel subtracted.         */
+/* Returns 0 (sad untouched) unless the left window and all right windows   */
+/* lie inside the level images.                                             */
+/* ------------------------------------------------------------------------ */
+int orc_sad_vector(const orc_params *p, const orc_pyramid *pl, const orc_pyramid *pr,
+                   int level, int ul, int vl, int ur0, int32_t *sad)
+{
+    const int w = p->sad_w, L = p->sad_L;
+    const int wl = pl->width[level], hl = pl->height[level];
+    const int wr = pr->width[level], hr = pr->height[level];
+    if (vl - w < 0 || vl + w > hl - 1 || vl + w > hr - 1) return 0;
+    if (ul - w < 0 || ul + w > wl - 1) return 0;
+    if (ur0 - L - w < 0 || ur0 + L + w > wr - 1) return 0;
+
+    const uint8_t *IL = pl->data[level];
+    const uint8_t *IR = pr->data[level];
+    const int sl = pl->pitch[level], sr = pr->pitch[level];
+    const int cL = IL[(size_t)vl * sl + ul];
+    for (int k = -L; k <= L; ++k) {
+        const int cR = IR[(size_t)vl * sr + (ur0 + k)];
+        int s = 0;
+        for (int dy = -w; dy <= w; ++dy) {
+            for (int dx = -w; dx <= w; ++dx) {
+                int a = IL[(size_t)(vl + dy) * sl + (ul + dx)] - cL;
+                int b = IR[(size_t)(vl + dy) * sr + (ur0 + k + dx)] - cR;
+                s += abs(a - b);
+            }
+        }
+        sad[k + L] = s;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a4: parabola through (k*-1, k*, k*+1) of the SAD curve, vertex offset    */
+/* delta = (S- - S+) / (2 (S- + S+ - 2 S0)); right coordinate              */
+/* uR = scale * (ur0 + k* + delta); disparity = xl - uR must lie in        */
+/* [0, maxD); a disparity of exactly 0 is replaced by 0.01 px; depth =     */
+/* bf / disparity.  Returns 1 if accepted.                                  */
+/* ------------------------------------------------------------------------ */
+int orc_subpixel(const int32_t *sad, int L, int kbest, int ur0, float scale, float xl,
+                 float bf, float maxD, float *u_right, float *depth, float *delta)
+{
+    const float minD = 0.0f;
+    const float dist1 = (float)sad[kbest + L - 1];
+    const float dist2 = (float)sad[kbest + L];
+    const float dist3 = (float)sad[kbest + L + 1];
+    const float deltaR = (dist1 - dist3) / (2.0f * (dist1 + dist3 - 2.0f * dist2));
+    *delta = deltaR;
+    if (deltaR < -1.0f || deltaR > 1.0f) return 0;   /* unreachable: |deltaR| <= 0.5 */
+    float bestuR = scale * ((float)ur0 + (float)kbest + deltaR);
+    float disparity = xl - bestuR;
+    if (!(disparity >= minD && disparity < maxD)) return 0;
+    if (disparity <= 0.0f) {
+        disparity = 0.01f;
+        bestuR = xl - 0.01f;
+    }
+    *depth = bf / disparity;
+    *u_right = bestuR;
+    return 1;
+}
+
+/* ascending integer sort (insertion sort; n is a few thousand at most) */
+static void sort_ints(int *v, int n)
+{
+    for (int i = 1; i < n; ++i) {
+        int x = v[i], j = i - 1;
+        while (j >= 0 && v[j] > x) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = x;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a5: over the accepted matches (sad_best >= 0), median = element n/2 of   */
+/* the ascending sort; every match with SAD >= factor * median loses its    */
+/* u_right and depth (set to -1).  Nothing happens when n = 0.             */
+/* ------------------------------------------------------------------------ */
+void orc_median_reject(int n_kp, const int32_t *sad_best, float factor, float *u_right,
+                       float *depth)
+{
+    int n = 0;
+    for (int i = 0; i < n_kp; ++i)
+        if (sad_best[i] >= 0) ++n;
+    if (n == 0) return;
+    int *v = (int *)malloc(sizeof(int) * (size_t)n);
+    int m = 0;
+    for (int i = 0; i < n_kp; ++i)
+        if (sad_best[i] >= 0) v[m++] = sad_best[i];
+    sort_ints(v, n);
+    const int median = v[n / 2];
+    const float thDist = factor * (float)median;
+    for (int i = 0; i < n_kp; ++i) {
+        if (sad_best[i] >= 0 && (float)sad_best[i] >= thDist) {
+            u_right[i] = -1.0f;
+            depth[i] = -1.0f;
+        }
+    }
+    free(v);
+}
+
+void orc_stereo_pinhole(const orc_params *p, const orc_pinhole *cam,
+                        const orc_keypoints *L, const orc_keypoints *R,
+                        const orc_pyramid *pl, const orc_pyramid *pr,
+                        int32_t *best_r, int32_t *dist, int32_t *sad_shift,
+                        int32_t *sad_best, float *u_right, float *depth)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
+
+    /* a1 */
+    const int H = cam->height;
+    int *row_ptr = (int *)malloc(sizeof(int) * ((size_t)H + 1));
+    int cap = 0;
+    for (int j = 0; j < R->n; ++j) {
+        int lo, hi;
+        band_rows(R->y[j], 2.0f * sc[R->oct[j]], H, &lo, &hi);
+        if (hi >= lo) cap += hi - lo + 1;
+    }
+    int *row_idx = (int *)malloc(sizeof(int) * ((size_t)cap + 1));
+    orc_row_index(R->n, R->y, R->oct, sc, H, row_ptr, row_idx, cap);
+
+    /* a2 */
+    orc_stereo_best(p, cam, L, R, row_ptr, row_idx, best_r, dist);
+
+    const float maxD = cam->bf / cam->b;
+    const int Ls = p->sad_L;
+    int32_t sad[2 * 64 + 1];
+
+    for (int i = 0; i < L->n; ++i) {
+        sad_shift[i] = ORC_NO_SHIFT;
+        sad_best[i] = -1;
+        u_right[i] = -1.0f;
+        depth[i] = -1.0f;
+        const int j = best_r[i];
+        if (j < 0) continue;
+
+        /* a3: level coordinates, SAD vector, first strict minimum */
+        const int l = L->oct[i];
+        const int ul = (int)roundf(L->x[i] * isc[l]);
+        const int vl = (int)roundf(L->y[i] * isc[l]);
+        const int ur0 = (int)roundf(R->x[j] * isc[l]);
+        if (!orc_sad_vector(p, pl, pr, l, ul, vl, ur0, sad)) continue;
+        int kbest = -Ls;
+        for (int k = -Ls + 1; k <= Ls; ++k)
+            if (sad[k + Ls] < sad[kbest + Ls]) kbest = k;
+        sad_shift[i] = kbest;
+        if (kbest == -Ls || kbest == Ls) continue;
+
+        /* a4 */
+        float delta;
+        if (orc_subpixel(sad, Ls, kbest, ur0, sc[l], L->x[i], cam->bf, maxD, &u_right[i],
+                         &depth[i], &delta))
+            sad_best[i] = sad[kbest + Ls];
+    }
+
+    /* a5 */
+    orc_median_reject(L->n, sad_best, p->median_factor, u_right, depth);
+    free(row_ptr);
+    free(row_idx);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a6: fisheye.  Left keypoints with x in [lap_l0, lap_l1] are matched by   */
+/* brute force against right keypoints with x in [lap_r0, lap_r1].  d1, d2  */
+/* are the two smallest (d, j); d2 = 256 if only one right keypoint exists. */
+/* Accept j1 if (float)d1 < ratio * (float)d2.  Left keypoints outside the  */
+/* overlap (or without candidates) get r_idx = d1 = d2 = -1.                */
+/* ------------------------------------------------------------------------ */
+void orc_stereo_fisheye(const orc_params *p, const orc_keypoints *L, const orc_keypoints *R,
+                        float lap_l0, float lap_l1, float lap_r0, float lap_r1,
+                        int32_t *r_idx, int32_t *d1, int32_t *d2)
+{
+    for (int i = 0; i < L->n; ++i) {
+        r_idx[i] = -1;
+        d1[i] = -1;
+        d2[i] = -1;
+        if (!(L->x[i] >= lap_l0 && L->x[i] <= lap_l1)) continue;
+        int bd = 0, bj = -1, sd = 0, sj = -1;
+        for (int j = 0; j < R->n; ++j) {
+            if (!(R->x[j] >= lap_r0 && R->x[j] <= lap_r1)) continue;
+            int d = orc_hamming(L->desc + (size_t)i * ORC_DESC_BYTES,
+                                R->desc + (size_t)j * ORC_DESC_BYTES);
+            /* keep the two smallest (d, j) pairs */
+            if (bj < 0 || d < bd || (d == bd && j < bj)) {
+                sd = bd;
+                sj = bj;
+                bd = d;
+                bj = j;
+            } else if (sj < 0 || d < sd || (d == sd && j < sj)) {
+                sd = d;
+                sj = j;
+            }
+        }
+        if (bj < 0) continue;
+        d1[i] = bd;
+        d2[i] = (sj >= 0) ? sd : 256;
+        if ((float)d1[i] < p->fisheye_ratio * (float)d2[i]) r_idx[i] = bj;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a7: grid cell of a keypoint: round((x - min_x) * 64 / (max_x - min_x)),  */
+/* same in y with 48 rows.  Returns 0 if the cell lies outside the grid.    */
+/* ------------------------------------------------------------------------ */
+int orc_grid_cell(float x, float y, float min_x, float max_x, float min_y, float max_y,
+                  int *cx, int *cy)
+{
+    const float iw = (float)ORC_GRID_COLS / (max_x - min_x);
+    const float ih = (float)ORC_GRID_ROWS / (max_y - min_y);
+    *cx = (int)roundf((x - min_x) * iw);
+    *cy = (int)roundf((y - min_y) * ih);
+    if (*cx < 0 || *cx >= ORC_GRID_COLS || *cy < 0 || *cy >= ORC_GRID_ROWS) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a8: frustum test and projection.  A point needs camera z > 0 (a point on */
+/* the camera plane has no pinhole projection).  Shared part (after the     */
+/* image test):                                                             */
+/* distance to the camera centre within [dist_lo*dmin, dist_hi*dmax],      */
+/* viewing cosine with the mean normal >= view_cos_min, predicted level =   */
+/* smallest l with scale[l] >= dmax / dist (else S-1).                     */
+/* out4 = (u, v, u_right, viewing cosine).  Returns 1 if in view.          */
+/* ------------------------------------------------------------------------ */
+static void transform(const float *R, const float *t, const float *P, float *Pc)
+{
+    Pc[0] = R[0] * P[0] + R[1] * P[1] + R[2] * P[2] + t[0];
+    Pc[1] = R[3] * P[0] + R[4] * P[1] + R[5] * P[2] + t[1];
+    Pc[2] = R[6] * P[0] + R[7] * P[1] + R[8] * P[2] + t[2];
+}
+
+static int distance_and_scale(const orc_params *p, const float *O, const float *Pw,
+                              const float *nrm, float dmin, float dmax,
+                              float *view_cos, int *level)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
+    const float PO[3] = {Pw[0] - O[0], Pw[1] - O[1], Pw[2] - O[2]};
+    const float dist = sqrtf(PO[0] * PO[0] + PO[1] * PO[1] + PO[2] * PO[2]);
+    const float maxDistance = p->dist_hi * dmax;
+    const float minDistance = p->dist_lo * dmin;
+    if (dist < minDistance || dist > maxDistance) return 0;
+    const float vc = (PO[0] * nrm[0] + PO[1] * nrm[1] + PO[2] * nrm[2]) / dist;
+    if (vc < p->view_cos_min) return 0;
+    const float ratio = dmax / dist;
+    int lv = p->nlevels - 1;
+    for (int l = 0; l < p->nlevels; ++l) {
+        if (sc[l] >= ratio) {
+            lv = l;
+            break;
+        }
+    }
+    *view_cos = vc;
+    *level = lv;
+    return 1;
+}
+
+int orc_project_pinhole(const orc_params *p, const orc_pinhole *cam, const orc_pose *T,
+                        const float *Pw, const float *nrm, float dmin, float dmax,
+                        float *out4, int *level)
+{
+    float Pc[3];
+    transform(T->R, T->t, Pw, Pc);
+    if (!(Pc[2] > 0.0f)) return 0;   /* behind, on the camera plane, or NaN */
+    const float invz = 1.0f / Pc[2];
+    const float u = cam->fx * Pc[0] * invz + cam->cx;
+    const float v = cam->fy * Pc[1] * invz + cam->cy;
+    if (u < cam->min_x || u > cam->max_x) return 0;
+    if (v < cam->min_y || v > cam->max_y) return 0;
+    const float ur = u - cam->bf * invz;
+    float vc;
+    if (!distance_and_scale(p, T->O, Pw, nrm, dmin, dmax, &vc, level)) return 0;
+    out4[0] = u;
+    out4[1] = v;
+    out4[2] = ur;
+    out4[3] = vc;
+    return 1;
+}
+
+/* Kannala-Brandt (equidistant, 4 coefficients):                           */
+/*   rho = |(x, y)|, theta = atan2(rho, z),                                */
+/*   theta_d = theta * (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8) */
+/*   (Horner in theta^2), u = fx * theta_d * x / rho + cx (rho = 0: u = cx). */
+static void kb8_project(const orc_kb8 *cam, const float *Pc, float *u, float *v)
+{
+    const float rho = sqrtf(Pc[0] * Pc[0] + Pc[1] * Pc[1]);
+    if (rho == 0.0f) {
+        *u = cam->cx;
+        *v = cam->cy;
+        return;
+    }
+    const float theta = orc_atan2_pos(rho, Pc[2]);
+    const float t2 = theta * theta;
+    float poly = cam->k[3];
+    poly = cam->k[2] + t2 * poly;
+    poly = cam->k[1] + t2 * poly;
+    poly = cam->k[0] + t2 * poly;
+    poly = 1.0f + t2 * poly;
+    const float thetad = theta * poly;
+    *u = cam->fx * thetad * Pc[0] / rho + cam->cx;
+    *v = cam->fy * thetad * Pc[1] / rho + cam->cy;
+}
+
+int orc_project_kb8(const orc_params *p, const orc_kb8 *cam, const float *R, const float *t,
+                    const float *O, const float *Pw, const float *nrm, float dmin, float dmax,
+                    float *out4, int *level)
+{
+    float Pc[3];
+    transform(R, t, Pw, Pc);
+    if (!(Pc[2] > 0.0f)) return 0;   /* behind, on the camera plane, or NaN */
+    float u, v;
+    kb8_project(cam, Pc, &u, &v);
+    if (u < cam->min_x || u > cam->max_x) return 0;
+    if (v < cam->min_y || v > cam->max_y) return 0;
+    float vc;
+    if (!distance_and_scale(p, O, Pw, nrm, dmin, dmax, &vc, level)) return 0;
+    out4[0] = u;
+    out4[1] = v;
+    out4[2] = -1.0f;
+    out4[3] = vc;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a9 + a10 for one camera.  For each map point in view (level >= 0):      */
+/*   radius = (narrow if cos > view_cos_narrow else wide) * th * scale[lv];  */
+/*   cells [floor((u-min_x-r)*iw), ceil((u-min_x+r)*iw)] clamped to the     */
+/*   grid (same in y); keep keypoints of those cells with octave in         */
+/*   [lv-1, lv], |x-u| < r, |y-v| < r, not taken, and (if u_right is given) */
+/*   u_right <= 0 or |ur - u_right| <= r.  d1/d2 = two smallest (d, k);     */
+/*   accept k1 if d1 <= th_search and not (ratio applies and                */
+/*   d1 > nn_ratio * d2), where the ratio applies when both share an octave */
+/*   (or always with ratio_any_octave).                                     */
+/*   a10: each keypoint keeps the smallest (d1, m) among the map points     */
+/*   that accepted it; the others get mp_kp = -1.                           */
+/* ------------------------------------------------------------------------ */
+void orc_search_camera(const orc_params *p, float min_x, float max_x, float min_y, float max_y,
+                       const orc_keypoints *K, const float *u_right, const uint8_t *taken,
+                       int M, const uint8_t *mp_desc, const int8_t *level, const float *proj,
+                       int32_t *mp_kp, int32_t *mp_d1, int32_t *mp_d2, int32_t *kp_mp)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
+    const float iw = (float)ORC_GRID_COLS / (max_x - min_x);
+    const float ih = (float)ORC_GRID_ROWS / (max_y - min_y);
+
+    /* a7: cell lists, cells in column-major order (ix, then iy), keypoints in
+     * ascending index inside a cell */
+    const int ncell = ORC_GRID_COLS * ORC_GRID_ROWS;
+    int *cell_ptr = (int *)calloc((size_t)ncell + 1, sizeof(int));
+    int *cell_idx = (int *)malloc(sizeof(int) * ((size_t)K->n + 1));
+    int *kcell = (int *)malloc(sizeof(int) * ((size_t)K->n + 1));
+    for (int k = 0; k < K->n; ++k) {
+        int cx, cy;
+        kcell[k] = -1;
+        if (orc_grid_cell(K->x[k], K->y[k], min_x, max_x, min_y, max_y, &cx, &cy)) {
+            kcell[k] = cx * ORC_GRID_ROWS + cy;
+            cell_ptr[kcell[k] + 1]++;
+        }
+    }
+    for (int c = 0; c < ncell; ++c) cell_ptr[c + 1] += cell_ptr[c];
+    int *fill = (int *)malloc(sizeof(int) * (size_t)ncell);
+    for (int c = 0; c < ncell; ++c) fill[c] = cell_ptr[c];
+    for (int k = 0; k < K->n; ++k)
+        if (kcell[k] >= 0) cell_idx[fill[kcell[k]]++] = k;
+
+    int64_t *owner = (int64_t *)malloc(sizeof(int64_t) * ((size_t)K->n + 1));
+    for (int k = 0; k < K->n; ++k) owner[k] = -1;
+
+    for (int m = 0; m < M; ++m) {
+        mp_kp[m] = -1;
+        mp_d1[m] = -1;
+        mp_d2[m] = -1;
+        const int lv = level[m];
+        if (lv < 0) continue;
+        const float u = proj[4 * m + 0], v = proj[4 * m + 1];
+        const float ur = proj[4 * m + 2], vc = proj[4 * m + 3];
+        float r = (vc > p->view_cos_narrow) ? p->radius_narrow : p->radius_wide;
+        r = r * p->search_th;
+        r = r * sc[lv];
+        const int minLevel = lv - 1, maxLevel = lv;
+
+        int x0 = (int)floorf((u - min_x - r) * iw);
+        if (x0 < 0) x0 = 0;
+        int x1 = (int)ceilf((u - min_x + r) * iw);
+        if (x1 > ORC_GRID_COLS - 1) x1 = ORC_GRID_COLS - 1;
+        int y0 = (int)floorf((v - min_y - r) * ih);
+        if (y0 < 0) y0 = 0;
+        int y1 = (int)ceilf((v - min_y + r) * ih);
+        if (y1 > ORC_GRID_ROWS - 1) y1 = ORC_GRID_ROWS - 1;
+        if (x0 >= ORC_GRID_COLS || x1 < 0 || y0 >= ORC_GRID_ROWS || y1 < 0) continue;
+
+        int bd = 0, bk = -1, sd = 0, sk = -1;
+        for (int ix = x0; ix <= x1; ++ix) {
+            for (int iy = y0; iy <= y1; ++iy) {
+                const int c = ix * ORC_GRID_ROWS + iy;
+                for (int e = cell_ptr[c]; e < cell_ptr[c + 1]; ++e) {
+                    const int k = cell_idx[e];
+                    if (K->oct[k] < minLevel || K->oct[k] > maxLevel) continue;
+                    const float distx = K->x[k] - u;
+                    const float disty = K->y[k] - v;
+                    if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
+                    if (taken && taken[k]) continue;
+                    if (u_right && u_right[k] > 0.0f) {
+                        const float er = fabsf(ur - u_right[k]);
+                        if (er > r) continue;
+                    }
+                    const int d = orc_hamming(mp_desc + (size_t)m * ORC_DESC_BYTES,
+                                              K->desc + (size_t)k * ORC_DESC_BYTES);
+                    if (bk < 0 || d < bd || (d == bd && k < bk)) {
+                        sd = bd;
+                        sk = bk;
+                        bd = d;
+                        bk = k;
+                    } else if (sk < 0 || d < sd || (d == sd && k < sk)) {
+                        sd = d;
+                        sk = k;
+                    }
+                }
+            }
+        }
+        if (bk < 0) continue;
+        mp_d1[m] = bd;
+        mp_d2[m] = (sk >= 0) ? sd : 256;
+        if (bd > p->th_search) continue;
+        const int oct1 = K->oct[bk];
+        const int oct2 = (sk >= 0) ? K->oct[sk] : -1;
+        if ((p->ratio_any_octave || oct1 == oct2) &&
+            (float)bd > p->nn_ratio * (float)mp_d2[m])
+            continue;
+        /* a10: claim keypoint bk with key (d1, m); the smaller key wins */
+        const int64_t key = ((int64_t)bd << 32) | (int64_t)m;
+        if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;
+        mp_kp[m] = bk;
+    }
+    for (int k = 0; k < K->n; ++k) kp_mp[k] = (owner[k] < 0) ? -1 : (int32_t)(owner[k] & 0xffffffff);
+    for (int m = 0; m < M; ++m)
+        if (mp_kp[m] >= 0 && kp_mp[mp_kp[m]] != m) mp_kp[m] = -1;
+    free(owner);
+    free(fill);
+    free(kcell);
+    free(cell_idx);
+    free(cell_ptr);
+}
+
+void orc_search_pinhole(const orc_params *p, const orc_pinhole *cam, const orc_pose *T,
+                        const orc_keypoints *K, const float *u_right, const uint8_t *taken,
+                        int M, const float *pos, const float *nrm, const uint8_t *mp_desc,
+                        const uint8_t *skip, int8_t *level, float *proj,
+                        int32_t *mp_kp, int32_t *mp_d1, int32_t *mp_d2, int32_t *kp_mp)
+{
+    for (int m = 0; m < M; ++m) {
+        level[m] = -1;
+        proj[4 * m + 0] = proj[4 * m + 1] = proj[4 * m + 2] = proj[4 * m + 3] = 0.0f;
+        if (skip && skip[m]) continue;
+        int lv;
+        if (orc_project_pinhole(p, cam, T, pos + 4 * m, nrm + 4 * m, pos[4 * m + 3],
+                                nrm[4 * m + 3], proj + 4 * m, &lv))
+            level[m] = (int8_t)lv;
+        else
+            proj[4 * m + 0] = proj[4 * m + 1] = proj[4 * m + 2] = proj[4 * m + 3] = 0.0f;
+    }
+    orc_search_camera(p, cam->min_x, cam->max_x, cam->min_y, cam->max_y, K, u_right, taken,
+                      M, mp_desc, level, proj, mp_kp, mp_d1, mp_d2, kp_mp);
+}
+
+void orc_search_fisheye(const orc_params *p, const orc_kb8 *camL, const orc_kb8 *camR,
+                        const float *R_rl, const float *t_rl, const orc_pose *T,
+                        const float *O_right,
+                        const orc_keypoints *KL, const uint8_t *takenL,
+                        const orc_keypoints *KR, const uint8_t *takenR,
+                        int M, const float *pos, const float *nrm, const uint8_t *mp_desc,
+                        const uint8_t *skip,
+                        int8_t *level_l, float *proj_l, int32_t *mp_kp_l, int32_t *mp_d1_l,
+                        int32_t *mp_d2_l, int32_t *kp_mp_l,
+                        int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
+                        int32_t *mp_d2_r, int32_t *kp_mp_r)
+{
+    /* right camera: T_rw = T_rl * T_lw, composed in FP32 in this order */
+    float Rr[9], tr[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            Rr[3 * i + j] = R_rl[3 * i + 0] * T->R[0 + j] + R_rl[3 * i + 1] * T->R[3 + j] +
+                            R_rl[3 * i + 2] * T->R[6 + j];
+        tr[i] = R_rl[3 * i + 0] * T->t[0] + R_rl[3 * i + 1] * T->t[1] +
+                R_rl[3 * i + 2] * T->t[2] + t_rl[i];
+    }
+    for (int m = 0; m < M; ++m) {
+        int lv;
+        level_l[m] = level_r[m] = -1;
+        for (int c = 0; c < 4; ++c) proj_l[4 * m + c] = proj_r[4 * m + c] = 0.0f;
+        if (skip && skip[m]) continue;
+        const float *Pw = pos + 4 * m, *n = nrm + 4 * m;
+        if (orc_project_kb8(p, camL, T->R, T->t, T->O, Pw, n, Pw[3], n[3], proj_l + 4 * m, &lv))
+            level_l[m] = (int8_t)lv;
+        else
+            for (int c = 0; c < 4; ++c) proj_l[4 * m + c] = 0.0f;
+        if (orc_project_kb8(p, camR, Rr, tr, O_right, Pw, n, Pw[3], n[3], proj_r + 4 * m, &lv))
+            level_r[m] = (int8_t)lv;
+        else
+            for (int c = 0; c < 4; ++c) proj_r[4 * m + c] = 0.0f;
+    }
+    orc_search_camera(p, camL->min_x, camL->max_x, camL->min_y, camL->max_y, KL, NULL, takenL,
+                      M, mp_desc, level_l, proj_l, mp_kp_l, mp_d1_l, mp_d2_l, kp_mp_l);
+    orc_search_camera(p, camR->min_x, camR->max_x, camR->min_y, camR->max_y, KR, NULL, takenR,
+                      M, mp_desc, level_r, proj_r, mp_kp_r, mp_d1_r, mp_d2_r, kp_mp_r);
+}

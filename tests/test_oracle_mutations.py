@@ -1,0 +1,77 @@
+"""The oracle's pins must catch plausible mistakes.  Each case plants one
+mistake in a copy of the oracle source (on the CPU), builds it, and runs the
+oracle pin suite against that copy: the suite has to fail."""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ft_oracle.c")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("hamming_short", "i < ORC_DESC_BYTES; ++i) d +=", "i < ORC_DESC_BYTES - 1; ++i) d +="),
+    ("band_ceil", "int b = (int)ceilf(y + r);", "int b = (int)floorf(y + r);"),
+    ("tie_last_j", "if (d < bestd || (d == bestd && j < bestj)) {", "if (d <= bestd) {"),
+    ("octave_window", "R->oct[j] > levelL + 1", "R->oct[j] > levelL"),
+    ("disparity_sign", "const float minU = L->x[i] - maxD;", "const float minU = L->x[i] + maxD;"),
+    ("threshold_le", "if (bestd < p->th_stereo)", "if (bestd <= p->th_stereo + 10)"),
+    ("centre_right", "int b = IR[(size_t)(vl + dy) * sr + (ur0 + k + dx)] - cR;",
+     "int b = IR[(size_t)(vl + dy) * sr + (ur0 + k + dx)] - cL;"),
+    ("shift_sign", "(ur0 + k + dx)] - cR;", "(ur0 - k + dx)] - cR;"),
+    ("sad_bounds", "ur0 + L + w > wr - 1", "ur0 + w > wr - 1"),
+    ("parabola_sign", "(dist1 - dist3) / (2.0f", "(dist3 - dist1) / (2.0f"),
+    ("parabola_factor", "/ (2.0f * (dist1 + dist3 - 2.0f * dist2))", "/ ((dist1 + dist3 - 2.0f * dist2))"),
+    ("median_index", "const int median = v[n / 2];", "const int median = v[(n - 1) / 2];"),
+    ("median_strict", "(float)sad_best[i] >= thDist", "(float)sad_best[i] > thDist"),
+    ("fisheye_overlap", "if (!(R->x[j] >= lap_r0 && R->x[j] <= lap_r1)) continue;", ""),
+    ("fisheye_second", "d2[i] = (sj >= 0) ? sd : 256;", "d2[i] = (sj >= 0) ? sd : 255;"),
+    ("transpose_R", "Pc[0] = R[0] * P[0] + R[1] * P[1] + R[2] * P[2] + t[0];",
+     "Pc[0] = R[0] * P[0] + R[3] * P[1] + R[6] * P[2] + t[0];"),
+    ("ur_sign", "const float ur = u - cam->bf * invz;", "const float ur = u + cam->bf * invz;"),
+    ("level_table", "if (sc[l] >= ratio) {", "if (sc[l] > ratio * 1.1f) {"),
+    ("viewcos_strict", "if (vc < p->view_cos_min) return 0;", "if (vc <= p->view_cos_min) return 0;"),
+    ("window_no_radius", "int x0 = (int)floorf((u - min_x - r) * iw);", "int x0 = (int)floorf((u - min_x) * iw);"),
+    ("cell_index", "const int c = ix * ORC_GRID_ROWS + iy;", "const int c = iy * ORC_GRID_ROWS + ix;"),
+    ("y_test_uses_x", "fabsf(distx) < r && fabsf(disty) < r", "fabsf(distx) < r && fabsf(distx) < r"),
+    ("ratio_octave", "(p->ratio_any_octave || oct1 == oct2)", "(p->ratio_any_octave || oct1 != oct2)"),
+    ("conflict_max", "if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;",
+     "if (owner[bk] < 0 || key > owner[bk]) owner[bk] = key;"),
+    ("stereo_check", "if (er > r) continue;", "if (er > 2.0f * r) continue;"),
+    ("kb8_horner", "float poly = cam->k[3];", "float poly = cam->k[0];"),
+    ("atan_reduction", "return pi_4 + atan_small", "return pi_4 - atan_small"),
+    ("taken_ignored", "if (taken && taken[k]) continue;", ""),
+]
+
+
+def _run_mutant(tmp, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation {name}: text not found"
+    mut = src.replace(old, new, 1)
+    cdir = os.path.join(tmp, name)
+    os.makedirs(cdir)
+    cpath = os.path.join(cdir, "ft_oracle.c")
+    open(cpath, "w").write(mut)
+    hsrc = os.path.join(ROOT, "oracle", "ft_oracle.h")
+    open(os.path.join(cdir, "ft_oracle.h"), "w").write(open(hsrc).read())
+    so = os.path.join(cdir, "libmut.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", so,
+                    cpath, "-lm"], check=True)
+    env = dict(os.environ, FT_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_stereo.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_search.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode
+
+
+def test_every_planted_mistake_is_caught():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+            results = list(ex.map(lambda m: _run_mutant(tmp, *m), MUTANTS))
+    survivors = [name for name, rc in results if rc == 0]
+    assert not survivors, f"pins missed planted mistakes: {survivors}"

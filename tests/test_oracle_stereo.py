@@ -1,0 +1,376 @@
+"""Pins of the CPU oracle's stereo steps (a1-a6) against facts that do not come
+from the oracle itself: bit-by-bit counting, brute force over all pairs,
+closed forms of hand-built images, hand-worked parabola values, and the
+generator's ground-truth disparities."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2509_10757_gb300 import scenes
+
+
+def bitcount(a, b):
+    return int(np.unpackbits(np.bitwise_xor(a, b)).sum())
+
+
+# --------------------------------------------------------------------------
+# Hamming, scale table
+# --------------------------------------------------------------------------
+def test_hamming_equals_bit_by_bit_count():
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        a = rng.integers(0, 256, 32, dtype=np.uint8)
+        b = rng.integers(0, 256, 32, dtype=np.uint8)
+        assert orc.hamming(a, b) == bitcount(a, b)
+    a = rng.integers(0, 256, 32, dtype=np.uint8)
+    assert orc.hamming(a, a) == 0
+    assert orc.hamming(a, np.bitwise_not(a)) == 256
+
+
+def test_scale_table_is_powers_of_the_scale():
+    sc, isc = orc.scale_table(8, 1.2)
+    for l in range(8):
+        assert abs(float(sc[l]) - 1.2 ** l) <= (l + 1) * 2.0 ** -23 * 1.2 ** l
+        assert abs(float(sc[l]) * float(isc[l]) - 1.0) < 2e-7
+
+
+def test_atan2_first_quadrant_against_double():
+    ys = np.concatenate([np.linspace(0, 3, 301), np.geomspace(1e-6, 1e4, 200)])
+    xs = np.concatenate([np.linspace(3, 0, 301), np.geomspace(1e4, 1e-6, 200)])
+    worst = 0.0
+    for y in ys:
+        for x in (xs[::25]):
+            y32, x32 = float(np.float32(y)), float(np.float32(x))
+            got = orc.atan2_pos(y32, x32)
+            ref = math.atan2(y32, x32)
+            err = abs(got - ref)
+            worst = max(worst, err / max(abs(ref), 1e-30) if ref > 1e-3 else err)
+            assert err <= 4 * np.spacing(np.float32(max(ref, 1e-30))) + 1e-9
+    assert orc.atan2_pos(0.0, 5.0) == 0.0
+    assert orc.atan2_pos(0.0, 0.0) == 0.0
+    assert abs(orc.atan2_pos(1.0, 1.0) - math.pi / 4) <= np.spacing(np.float32(math.pi / 4))
+    assert abs(orc.atan2_pos(3.0, 0.0) - math.pi / 2) <= np.spacing(np.float32(math.pi / 2))
+
+
+# --------------------------------------------------------------------------
+# a1: band membership  <=>  |y_j - row| < 1 + r_j  (exact arithmetic)
+# --------------------------------------------------------------------------
+def test_row_index_membership_is_distance_to_row(params):
+    rng = np.random.default_rng(2)
+    H = 40
+    n = 300
+    y = ((rng.integers(0, 4 * H, n) + 0.5) / 4.0).astype(np.float32)   # odd multiples of 1/8
+    oct_ = rng.integers(0, 8, n).astype(np.int8)
+    row_ptr, row_idx = orc.row_index(params, y, oct_, H)
+    assert row_ptr[0] == 0 and row_ptr[-1] == len(row_idx)
+    for row in range(H):
+        lst = row_idx[row_ptr[row]:row_ptr[row + 1]]
+        assert np.all(np.diff(lst) > 0), "row lists ascend in j"
+        expect = []
+        for j in range(n):
+            r = 2.0 * 1.2 ** int(oct_[j])
+            gap = abs(float(y[j]) - row) - (1.0 + r)
+            assert abs(gap) > 1e-3   # odd eighths stay clear of every 1 + 2*1.2^l
+            if gap < 0:
+                expect.append(j)
+        assert list(lst) == expect
+
+
+# --------------------------------------------------------------------------
+# a2: brute force over all left/right pairs
+# --------------------------------------------------------------------------
+def _tiny_pair_scene(seed, nl=40, nr=60, W=96, H=24, pool=4, flip=0.15):
+    rng = np.random.default_rng(seed)
+    base = rng.integers(0, 256, (pool, 32), dtype=np.uint8)
+    def descs(n):
+        d = base[rng.integers(0, pool, n)]
+        return scenes.flip_bits(rng, d, flip) if flip > 0 else d.copy()
+    left = scenes.Keypoints(x=(rng.integers(0, 4 * W, nl) / 4.0).astype(np.float32),
+                            y=((rng.integers(0, 4 * H, nl) + 0.5) / 4.0).astype(np.float32),
+                            oct=rng.integers(0, 8, nl).astype(np.int8), desc=descs(nl))
+    right = scenes.Keypoints(x=(rng.integers(0, 4 * W, nr) / 4.0).astype(np.float32),
+                             y=((rng.integers(0, 4 * H, nr) + 0.5) / 4.0).astype(np.float32),
+                             oct=rng.integers(0, 8, nr).astype(np.int8), desc=descs(nr))
+    cam = scenes.pinhole_camera(W, H, fx=30.0, b=0.2)
+    return cam, left, right
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_stereo_best_equals_brute_force(params, seed):
+    # seeds 6, 7: one or two distinct descriptors, so equal distances (ties) abound
+    pool = {6: 1, 7: 2}.get(seed, 3 if seed % 2 else 6)
+    cam, L, R = _tiny_pair_scene(seed, pool=pool, flip=0.0 if seed in (4, 6, 7) else 0.15)
+    best_r, dist = orc.stereo_best(params, cam, L, R)
+    maxD = float(np.float32(np.float32(cam.bf) / np.float32(cam.b)))
+    for i in range(L.n):
+        row = int(L.y[i])
+        cands = []
+        for j in range(R.n):
+            r = 2.0 * 1.2 ** int(R.oct[j])
+            if not abs(float(R.y[j]) - row) < 1.0 + r:
+                continue
+            if abs(int(R.oct[j]) - int(L.oct[i])) > 1:
+                continue
+            if not (float(L.x[i]) - maxD <= float(R.x[j]) <= float(L.x[i])):
+                continue
+            cands.append((bitcount(L.desc[i], R.desc[j]), j))
+        if not cands:
+            assert dist[i] == -1 and best_r[i] == -1
+            continue
+        d, j = min(cands)
+        assert dist[i] == d
+        assert best_r[i] == (j if d < params["th_stereo"] else -1)
+
+
+# --------------------------------------------------------------------------
+# a3: SAD of centre-subtracted patches, closed forms
+# --------------------------------------------------------------------------
+def _pyr(img):
+    return [np.ascontiguousarray(img)]
+
+
+def test_sad_bright_dot_closed_form(params):
+    # left: one pixel of value 100 on black; right: the dot s pixels right of ur0.
+    # Centre-subtracted left patch: -100 everywhere but 0 at the centre.
+    # Right patch at shift k: if k == s it equals the left patch (SAD 0);
+    # else it is 0 everywhere except +100 where the dot is (if inside).
+    # So SAD = 119*100 + 200 = 12100 when the dot is in the window, else 120*100.
+    H, W = 32, 64
+    ul, vl, ur0 = 30, 15, 28
+    for s in range(-4, 5):
+        IL = np.zeros((H, W), np.uint8)
+        IR = np.zeros((H, W), np.uint8)
+        IL[vl, ul] = 100
+        IR[vl, ur0 + s] = 100
+        sad = orc.sad_vector(params, _pyr(IL), _pyr(IR), 0, ul, vl, ur0)
+        for k in range(-5, 6):
+            if k == s:
+                expect = 0
+            elif abs(s - k) <= 5:
+                expect = 12100
+            else:
+                expect = 12000
+            assert sad[k + 5] == expect, (s, k)
+
+
+def test_sad_ignores_brightness_offset_and_finds_planted_shift(params):
+    rng = np.random.default_rng(3)
+    H, W = 40, 80
+    tex = rng.integers(20, 200, (H, W)).astype(np.int32)
+    ul, vl = 40, 20
+    for s in range(-4, 5):
+        IL = tex.astype(np.uint8)
+        IR = np.zeros_like(tex)
+        # right(x) = left(x - s) + 37, so the patch at ur0 + s equals the left one
+        ur0 = ul - 3
+        for x in range(W):
+            IR[:, x] = tex[:, min(max(x - (ur0 + s - ul), 0), W - 1)] + 37
+        sad = orc.sad_vector(params, _pyr(IL), _pyr(IR.astype(np.uint8)), 0, ul, vl, ur0)
+        assert sad[s + 5] == 0
+        assert np.all(np.delete(sad, s + 5) > 0)
+
+
+def test_sad_window_must_lie_inside_level(params):
+    H, W = 30, 50
+    img = np.full((H, W), 9, np.uint8)
+    P = _pyr(img)
+    assert orc.sad_vector(params, P, P, 0, 5, 5, 10) is not None     # all windows inside
+    assert orc.sad_vector(params, P, P, 0, 4, 5, 10) is None         # left window at x=-1
+    assert orc.sad_vector(params, P, P, 0, 5, 4, 10) is None         # rows above the image
+    assert orc.sad_vector(params, P, P, 0, 5, H - 6, 10) is not None
+    assert orc.sad_vector(params, P, P, 0, 5, H - 5, 10) is None
+    assert orc.sad_vector(params, P, P, 0, 5, 5, 9) is None          # right window at x=-1
+    assert orc.sad_vector(params, P, P, 0, 5, 5, W - 11) is not None
+    assert orc.sad_vector(params, P, P, 0, 5, 5, W - 10) is None
+
+
+# --------------------------------------------------------------------------
+# a4: parabola, hand-worked
+# --------------------------------------------------------------------------
+def test_parabola_hand_worked_values():
+    sad = np.array([50, 40, 30, 20, 10, 4, 6, 30, 40, 50, 60], np.int32)   # min at k=0
+    ok, ur, depth, delta = orc.subpixel(sad, 5, 0, 100, 1.0, 120.0, 40.0, 60.0)
+    # delta = (10 - 6) / (2 (10 + 6 - 8)) = 0.25
+    assert ok and delta == 0.25 and ur == 100.25 and depth == np.float32(40.0 / np.float32(19.75))
+    sad = np.array([50, 40, 30, 20, 6, 4, 10, 30, 40, 50, 60], np.int32)
+    ok, ur, depth, delta = orc.subpixel(sad, 5, 0, 100, 1.0, 120.0, 40.0, 60.0)
+    assert ok and delta == -0.25 and ur == 99.75
+    sad = np.array([50, 40, 30, 20, 8, 2, 8, 30, 40, 50, 60], np.int32)
+    ok, ur, depth, delta = orc.subpixel(sad, 5, 0, 100, 1.2, 130.0, 40.0, 60.0)
+    assert ok and delta == 0.0 and ur == np.float32(1.2) * np.float32(100.0)
+    # shift k* = +2 at level scale 2: uR = 2 * (50 + 2 + 0.25)
+    sad = np.array([9, 9, 9, 9, 9, 9, 10, 4, 6, 9, 9], np.int32)
+    ok, ur, _, delta = orc.subpixel(sad, 5, 2, 50, 2.0, 200.0, 40.0, 500.0)
+    assert ok and delta == 0.25 and ur == 104.5
+
+
+def test_parabola_disparity_range_and_clamp():
+    sad = np.array([9, 9, 9, 9, 8, 2, 8, 9, 9, 9, 9], np.int32)        # delta = 0
+    ok, ur, depth, _ = orc.subpixel(sad, 5, 0, 100, 1.0, 100.0, 40.0, 60.0)
+    assert ok and ur == np.float32(100.0 - 0.01) and depth == np.float32(40.0 / np.float32(0.01))
+    ok, *_ = orc.subpixel(sad, 5, 0, 100, 1.0, 99.5, 40.0, 60.0)         # negative disparity
+    assert not ok
+    ok, *_ = orc.subpixel(sad, 5, 0, 100, 1.0, 160.0, 40.0, 60.0)        # disparity == maxD
+    assert not ok
+    ok, ur, depth, _ = orc.subpixel(sad, 5, 0, 100, 1.0, 159.5, 40.0, 60.0)
+    assert ok and ur == 100.0 and depth == np.float32(40.0 / 59.5)
+
+
+def test_subpixel_recovers_planted_fraction(params):
+    # smooth texture shifted by s + f with linear interpolation: the parabola
+    # vertex lands within 0.2 px of the planted shift and on the right side
+    rng = np.random.default_rng(4)
+    H, W = 40, 120
+    tex = scenes.band_limited_noise(rng, H, W, sigma=3.0).astype(np.float64)
+    ul, vl, ur0 = 60, 20, 52
+    for s in (-2, 0, 3):
+        for f in (-0.35, -0.2, 0.2, 0.35):
+            xs = np.arange(W) - (ur0 + s + f - ul)
+            x0 = np.clip(np.floor(xs).astype(int), 0, W - 2)
+            fr = xs - np.floor(xs)
+            IR = tex[:, x0] * (1 - fr) + tex[:, x0 + 1] * fr
+            IRu8 = np.clip(np.rint(IR), 0, 255).astype(np.uint8)
+            sad = orc.sad_vector(params, _pyr(tex.astype(np.uint8)), _pyr(IRu8), 0, ul, vl, ur0)
+            k = int(np.argmin(sad)) - 5
+            ok, ur, _, delta = orc.subpixel(sad, 5, k, ur0, 1.0, 100.0, 10.0, 90.0)
+            assert ok
+            assert abs(ur - (ur0 + s + f)) < 0.2, (s, f, ur)
+            assert np.sign(ur - (ur0 + s)) == np.sign(f)
+
+
+# --------------------------------------------------------------------------
+# a5: median rejection, hand lists
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("sad,rejected", [
+    ([10, 20, 30, 100], [100]),             # median v[2] = 30, threshold 63
+    ([5, 5, 5, 5], []),                     # threshold 10.5
+    ([1, 2, 3, 4, 5, 100, 200], [100, 200]),  # median 4, threshold 8.4
+    ([7], []),                              # threshold 14.7
+    ([0], [0]),                             # threshold 0: 0 >= 0
+    ([3, 1, 2], []),                        # median 2, threshold 4.2
+    ([10, 21, 20], []),                     # median 20, threshold 42
+    ([10, 90, 20, 86, 41], [90]),           # median 41, threshold 86.1: 86 stays
+    ([10, 20, 30, 50], []),                 # n even: median is v[n/2] = 30, threshold 63
+    ([20, 9, 4, 10], []),                   # median v[2] = 10, threshold 21
+
+])
+def test_median_reject_hand_lists(params, sad, rejected):
+    n = len(sad)
+    sb = np.array(sad + [-1, -1], np.int32)
+    ur = np.arange(n + 2, dtype=np.float32) + 10
+    dp = np.arange(n + 2, dtype=np.float32) + 1
+    ur2, dp2 = orc.median_reject(sb, ur, dp, params["median_factor"])
+    for i in range(n + 2):
+        gone = i < n and sad[i] in rejected
+        assert (ur2[i] == -1.0) == gone and (dp2[i] == -1.0) == gone
+        if not gone:
+            assert ur2[i] == ur[i] and dp2[i] == dp[i]
+
+
+def test_median_reject_empty_is_noop(params):
+    sb = np.full(5, -1, np.int32)
+    ur = np.ones(5, np.float32)
+    dp = np.ones(5, np.float32)
+    ur2, dp2 = orc.median_reject(sb, ur, dp, params["median_factor"])
+    assert np.all(ur2 == 1) and np.all(dp2 == 1)
+
+
+# --------------------------------------------------------------------------
+# a1-a5 together: planted disparity from a mirror-symmetric scene is exact
+# --------------------------------------------------------------------------
+def test_planted_disparity_recovered_exactly(params):
+    # one bright dot per keypoint; at level l the right dot sits D_l level pixels
+    # left and is dimmer (150 vs 200).  The SAD curve is symmetric about the
+    # planted shift (6000 there, 24150 at the other shifts that still see the
+    # dot), so the parabola offset is 0 and u_right = scale_l * (x_l - D_l)
+    # with no rounding error.
+    W, H = 200, 120
+    cam = scenes.pinhole_camera(W, H, fx=60.0, b=0.5)
+    sc = scenes.level_scales32()
+    sizes = scenes.level_sizes(W, H)
+    pyrL = [np.zeros((h, w), np.uint8) for (w, h) in sizes]
+    pyrR = [np.zeros((h, w), np.uint8) for (w, h) in sizes]
+    desc = np.random.default_rng(5).integers(0, 256, (8, 32), dtype=np.uint8)
+    lx, ly, lo, rx, ry, ro = [], [], [], [], [], []
+    plan = [(0, 40, 30, 7), (1, 60, 50, 4), (2, 90, 20, 11), (3, 100, 60, 2), (0, 150, 90, 15)]
+    for l, u, v, D in plan:
+        pyrL[l][v, u] = 200
+        pyrR[l][v, u - D] = 150
+        lx.append(np.float32(u) * sc[l]); ly.append(np.float32(v) * sc[l]); lo.append(l)
+        # right keypoint detected 1 level pixel off the true spot
+        rx.append(np.float32(u - D + 1) * sc[l]); ry.append(np.float32(v) * sc[l]); ro.append(l)
+    n = len(plan)
+    L = scenes.Keypoints(np.array(lx, np.float32), np.array(ly, np.float32),
+                         np.array(lo, np.int8), desc[:n])
+    R = scenes.Keypoints(np.array(rx, np.float32), np.array(ry, np.float32),
+                         np.array(ro, np.int8), desc[:n].copy())
+    out = orc.stereo_pinhole(params, cam, L, R, pyrL, pyrR)
+    assert list(out["best_r"]) == list(range(n))
+    assert list(out["dist"]) == [0] * n
+    assert list(out["sad_shift"]) == [-1] * n
+    assert list(out["sad_best"]) == [6000] * n
+    for i, (l, u, v, D) in enumerate(plan):
+        expect_ur = np.float32(sc[l] * np.float32(u - D))
+        assert out["u_right"][i] == expect_ur
+        disp = np.float32(L.x[i] - expect_ur)
+        assert out["depth"][i] == np.float32(np.float32(cam.bf) / disp)
+
+
+def test_stereo_generated_scene_recovers_ground_truth(params):
+    f = scenes.single_pinhole(0)
+    out = orc.stereo_frame(params, f)
+    tr = f.truth["true_r"]
+    good = (out["u_right"] >= 0) & (tr >= 0)
+    assert good.sum() > 0.5 * f.left.n
+    # matches hit the planted right keypoint and the planted disparity
+    assert np.mean(out["best_r"][good] == tr[good]) > 0.97
+    err = np.abs((f.left.x[good] - out["u_right"][good]) - f.truth["disparity"][good])
+    assert np.mean(err < 1.0) > 0.9
+    # rejected or unmatched keypoints carry the -1 markers together
+    assert np.all((out["u_right"] < 0) == (out["depth"] < 0))
+
+
+# --------------------------------------------------------------------------
+# a6: fisheye brute force
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(5))
+def test_fisheye_equals_brute_force(params, seed):
+    cam, L, R = _tiny_pair_scene(100 + seed, nl=30, nr=45, pool=3 if seed < 3 else 8,
+                                 flip=0.0 if seed == 0 else 0.1)
+    rig = scenes.FisheyeRig(left=None, right=None, R_rl=None, t_rl=None, b=0.1,
+                            lap_l0=20.0, lap_l1=80.0, lap_r0=10.0, lap_r1=70.0)
+    out = orc.stereo_fisheye(params, rig, L, R)
+    for i in range(L.n):
+        if not (20.0 <= L.x[i] <= 80.0):
+            assert out["r_idx"][i] == -1 and out["d1"][i] == -1 and out["d2"][i] == -1
+            continue
+        c = sorted((bitcount(L.desc[i], R.desc[j]), j) for j in range(R.n)
+                   if 10.0 <= R.x[j] <= 70.0)
+        if not c:
+            assert out["d1"][i] == -1
+            continue
+        d1, j1 = c[0]
+        d2 = c[1][0] if len(c) > 1 else 256
+        assert out["d1"][i] == d1 and out["d2"][i] == d2
+        accept = np.float32(d1) < np.float32(0.7) * np.float32(d2)
+        assert out["r_idx"][i] == (j1 if accept else -1)
+
+
+def test_fisheye_single_candidate_uses_256(params):
+    rng = np.random.default_rng(21)
+    d = rng.integers(0, 256, (3, 32), dtype=np.uint8)
+    L = scenes.Keypoints(x=np.array([50.0, 50.0], np.float32), y=np.array([5.0, 6.0], np.float32),
+                         oct=np.array([0, 0], np.int8), desc=d[:2].copy())
+    # one right keypoint inside the overlap, one outside
+    R = scenes.Keypoints(x=np.array([40.0, 90.0], np.float32), y=np.array([5.0, 5.0], np.float32),
+                         oct=np.array([0, 0], np.int8), desc=d[1:3].copy())
+    rig = scenes.FisheyeRig(left=None, right=None, R_rl=None, t_rl=None, b=0.1,
+                            lap_l0=20.0, lap_l1=80.0, lap_r0=10.0, lap_r1=70.0)
+    out = orc.stereo_fisheye(params, rig, L, R)
+    assert list(out["d2"]) == [256, 256]
+    assert out["d1"][1] == 0 and out["r_idx"][1] == 0
+    d0 = bitcount(d[0], d[1])
+    assert out["d1"][0] == d0
+    assert out["r_idx"][0] == (0 if np.float32(d0) < np.float32(0.7) * np.float32(256) else -1)
