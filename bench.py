@@ -1,0 +1,411 @@
+"""Benchmark of the tracking hot path on GB300.
+
+Default workload (N=1): the batched pinhole workload: 64 frames per fused
+launch, 752x480 stereo pairs, 1000-1500 left keypoints and 2000-5000 local
+map points per frame, seeded synthetic scenes; a step is one ft_track_batch
+call (stereo matching then local-map search for all 64 frames), replayed
+through a CUDA graph with tile shapes from the autotuner.
+
+metric: matched keypoints/s + map-point searches/s, i.e. (left keypoints
+stereo-matched + map points searched) per second, whole job over all ranks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs its own 64-frame batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "matched keypoints/sec + map-point searches/sec on 1 GB300; p50/p99 frame latency, served vs plain"
+UNIT = "keypoints+map points/s"
+WORKLOAD = ("batched pinhole stereo + local-map search: 64 frames per fused launch, 752x480, "
+            "1000-1500 left keypoints, 2000-5000 map points per frame")
+FRAMES = 64
+L2_FLUSH_BYTES = 256 << 20
+PATCH_BYTES = 121 + 231          # left 11x11 patch + right 11x21 strip per refined match
+KP_BYTES = 4 + 4 + 1 + 32        # x, y, octave, descriptor
+MP_BYTES = 16 + 16 + 32 + 1      # pos+dmin, normal+dmax, descriptor, skip flag
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard_seed(base_seed: int, rank: int) -> int:
+    """Each rank gets its own independent batch of frames (weak scaling)."""
+    return base_seed + 1000 * rank
+
+
+def units_of(frames) -> tuple[int, int]:
+    """(left keypoints stereo-matched, map points searched) of a frame list."""
+    return sum(f.left.n for f in frames), sum(f.map.n for f in frames)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- measurement helpers
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("ft_kernels.cu", "ft_internal.h"):
+        with open(os.path.join(ROOT, "paper_2509_10757_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic() -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fused_kernel_batched_pinhole64.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(pb) -> int:
+    """Bytes the fused launch must move at minimum: every keypoint record,
+    taken flag and map record once, one left patch + right strip per refined
+    match, and every output once."""
+    total = pb.out_bytes
+    for f, fr in enumerate(pb.frames):
+        out = pb.outputs(f)
+        total += KP_BYTES * (fr.left.n + fr.right.n) + fr.left.n + MP_BYTES * fr.map.n
+        if fr.camera == "pinhole":
+            total += PATCH_BYTES * int(np.count_nonzero(out["sad_shift"] != -128))
+    return total
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+def time_oracle(frames, budget_s: float) -> dict:
+    """The oracle as it stands, single-threaded, on a bounded sample of frames."""
+    import oracle as orc
+    from paper_2509_10757_gb300.scenes import DEFAULT_PARAMS
+    orc.build()
+    p = dict(DEFAULT_PARAMS)
+    units, done = 0, 0
+    t0 = time.perf_counter()
+    for fr in frames:
+        orc.track_frame(p, fr)
+        units += fr.left.n + fr.map.n
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {len(frames)} frames of the batched workload, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, timed on host cores."""
+    if rank != 0:
+        return
+    from paper_2509_10757_gb300 import scenes
+    frames = scenes.pinhole_batch(seed=shard_seed(0, 0), n_frames=FRAMES)
+    per_step = max(1, min(FRAMES, 4))
+    import oracle as orc
+    orc.build()
+    p = dict(scenes.DEFAULT_PARAMS)
+    for i in range(args.warmup):
+        orc.track_frame(p, frames[i % FRAMES])
+    times, units = [], 0
+    for s in range(args.steps):
+        sample = [frames[(s * per_step + i) % FRAMES] for i in range(per_step)]
+        t0 = time.perf_counter()
+        for fr in sample:
+            orc.track_frame(p, fr)
+        times.append(time.perf_counter() - t0)
+        units += sum(fr.left.n + fr.map.n for fr in sample)
+    total = sum(times)
+    value = units / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32/f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_step": f"{per_step} frames through the CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} frames per step, {args.steps} steps, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import ctypes as C
+
+    import torch
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300 import build as B
+    from paper_2509_10757_gb300 import scenes
+    from paper_2509_10757_gb300.batch import (Context, PackedBatch, run_batch, run_search,
+                                              run_stereo, stream_handle)
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B.build()
+    frames = scenes.pinhole_batch(seed=shard_seed(0, rank), n_frames=FRAMES)
+    kp_units, mp_units = units_of(frames)
+    pb = PackedBatch(frames, device=dev)
+    pb.upload()
+    ctx = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES, use_graphs=True)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    best = L.ft_tuning()
+    with torch.cuda.stream(stream):
+        b = pb.batch()
+        L.check(ctx.lib.ft_autotune(ctx.ptr, stream_handle(stream), None, C.byref(b), 3, C.byref(best)),
+                "ft_autotune")
+    torch.cuda.synchronize(dev)
+
+    def step():
+        run_batch(ctx, pb, stream=stream)
+
+    # warm-up (graph capture happens on the first call)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    assert ctx.sync_status() == 0
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    launches0 = ctx.launches()
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)                  # evict L2 (256 MB write) between steps
+            starts[i].record(stream)
+            step()
+            stops[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    launches = ctx.launches() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    assert ctx.sync_status() == 0
+    local_s = sum(step_ms) / 1e3
+    job_s = max_over_ranks(local_s, world, dev)
+    units = sum_over_ranks(float(args.steps * (kp_units + mp_units)), world, dev)
+    value = units / job_s
+    ms_per_step = 1e3 * job_s / args.steps
+
+    # outputs of the last step, for the algorithmic byte count
+    pb.download()
+    alg_bytes = algorithmic_bytes(pb)
+    peaks = measured_peaks()
+    avg_launch_s = statistics.mean(step_ms) / 1e3
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = profiled_traffic()
+
+    # end to end through the C ABI: host -> device copy of the inputs, the
+    # fused launch, device -> host copy of the outputs, all inside each call
+    e2e_ms = []
+    for i in range(max(3, args.steps // 2)):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            run_batch(ctx, pb, stream=stream, stage=True)
+            s1.record(stream)
+        s1.synchronize()
+        e2e_ms.append(s0.elapsed_time(s1))
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, world, dev)
+    e2e_units = sum_over_ranks(float(len(e2e_ms) * (kp_units + mp_units)), world, dev)
+
+    # the plain form: one frame per call sequence (stereo, then search), synchronous
+    plain_ms = []
+    nplain = min(len(frames), 32)
+    for f in range(nplain):
+        with torch.cuda.stream(stream):
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            run_stereo(ctx, pb, f, stream=stream)
+            run_search(ctx, pb, f, stream=stream)
+            p1.record(stream)
+        p1.synchronize()
+        plain_ms.append(p0.elapsed_time(p1))
+    plain_units = sum(frames[f].left.n + frames[f].map.n for f in range(nplain))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(frames, budget_s=15.0)
+    ctx_tuning = {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
+                  "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm}
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32/f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_launch": FRAMES, "global_batch": FRAMES * world,
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+                   "cuda_graph": True, "tuning": ctx_tuning},
+        "components": {"stereo_keypoints_per_s": kp_units * world * args.steps / job_s,
+                       "map_point_searches_per_s": mp_units * world * args.steps / job_s},
+        "latency_ms": {"batch_p50": float(np.percentile(step_ms, 50)),
+                       "batch_p99": float(np.percentile(step_ms, 99)),
+                       "frame_p50_in_batch": float(np.percentile(step_ms, 50)),
+                       "frame_p99_in_batch": float(np.percentile(step_ms, 99))},
+        "plain": {"value": plain_units / (sum(plain_ms) / 1e3), "unit": UNIT,
+                  "frame_p50_ms": float(np.percentile(plain_ms, 50)),
+                  "frame_p99_ms": float(np.percentile(plain_ms, 99)),
+                  "form": "one frame per call sequence (ft_stereo_match_pinhole + ft_search_local_points)"},
+        "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": pb.in_bytes,
+                "d2h_bytes_per_step": pb.out_bytes,
+                "path": "ft_track_batch with host staging (pinned inputs incl. both pyramids)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "ft_fused_kernel"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

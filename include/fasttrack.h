@@ -1,0 +1,335 @@
+/*
+ * fasttrack.h -- C ABI of libfasttrack.so: the data-parallel core of visual
+ * SLAM tracking from "FastTrack: GPU-Accelerated Tracking for Visual SLAM",
+ * as hand-written CUDA for GB300 (sm_103a).
+ *
+ * Two operations of the tracking thread run here:
+ *   - stereo matching (sections II-B and IV-C): for every left keypoint, the
+ *     best right keypoint.  Pinhole cameras search a band along the epipolar
+ *     row, then refine the match over nearby pixels (SAD + parabola) and drop
+ *     outliers against the frame's median SAD.  Fisheye cameras brute-force
+ *     the right keypoints of the left/right overlap region.
+ *   - search of local map points by projection (sections II-D and IV-E):
+ *     every local map point is projected into the frame independently and
+ *     matched to the keypoints near its projection.
+ *
+ * Conventions for every entry point:
+ *   - Pointers inside the view structs are DEVICE pointers (unless a call
+ *     says otherwise) owned by the caller; the library never frees them.
+ *     Outputs are written in full (every element gets a value).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL is the legacy default stream).  FT_OK means "enqueued".
+ *   - All argument checks (NULL pointers, sizes, 16-byte alignment, level
+ *     sizes) run on the host before anything is enqueued; a failed check
+ *     returns its code, enqueues nothing and sets ft_last_error().
+ *   - Failures found on the device (a bounded wait that ran out) are ORed
+ *     into the context's device status word, read with ft_sync_status().
+ *     No call aborts the process and no call traps on the device.
+ *   - Keypoint octaves must lie in [0, nlevels); coordinates must be finite.
+ *     Inputs outside that are not detected; results for them are unspecified
+ *     but every memory access stays in bounds.
+ *   - A context (ft_ctx) owns its preallocated device arena, pinned staging
+ *     buffers, CUDA graphs and tuning table.  Its calls reuse the same
+ *     scratch, so one context serves one stream at a time; calls on another
+ *     stream are ordered after the previous call by an event.
+ */
+#ifndef FASTTRACK_H
+#define FASTTRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FT_DESC_BYTES 32        /* 256-bit ORB descriptor, rows of [n][32] uint8 */
+#define FT_MAX_LEVELS 16        /* pyramid levels */
+#define FT_GRID_COLS 64         /* keypoint grid of the search step */
+#define FT_GRID_ROWS 48
+#define FT_SAD_W 5              /* SAD half window: 11x11 patches */
+#define FT_SAD_L 5              /* SAD shifts k in [-5, 5] */
+#define FT_NO_SHIFT (-128)      /* sad_shift when the SAD windows left the image */
+#define FT_MAX_KEYPOINTS (1 << 20)   /* per image; indices travel in 20 bits */
+#define FT_MAX_MAP_POINTS (1 << 30)
+
+typedef enum {
+    FT_OK = 0,
+    FT_EINVAL = 1,     /* bad argument (NULL, size, range) */
+    FT_EALIGN = 2,     /* descriptor or map record not 16-byte aligned */
+    FT_ENOMEM = 3,     /* the context's arena cannot hold this call */
+    FT_EBUSY = 4,      /* admission refused (server) */
+    FT_ECUDA = 5,      /* a CUDA runtime call failed */
+    FT_ETIMEOUT = 6    /* a bounded device wait ran out (device status) */
+} ft_status;
+
+typedef enum { FT_CAMERA_PINHOLE = 0, FT_CAMERA_FISHEYE = 1 } ft_camera_model;
+
+/* Constants the paper does not print; each default is a reading of the
+ * algorithm family (fill with ft_params_default). */
+typedef struct {
+    int   nlevels;          /* S pyramid levels (8) */
+    float scale_factor;     /* s level scale (1.2); scale[l] = scale[l-1]*s in FP32 */
+    int   th_stereo;        /* stereo: accept best Hamming distance d < 75 */
+    float median_factor;    /* stereo: drop SAD >= factor * median (1.5f*1.4f) */
+    float fisheye_ratio;    /* fisheye: accept d1 < 0.7 * d2 */
+    int   th_search;        /* search: accept d1 <= 100 */
+    float nn_ratio;         /* search: reject d1 > 0.8 * d2 ... */
+    int   ratio_any_octave; /* ... always (1) or only if both share an octave (0) */
+    float search_th;        /* search radius factor th (1.0) */
+    float view_cos_min;     /* reject viewing cosine < 0.5 */
+    float view_cos_narrow;  /* narrow radius if viewing cosine > 0.998 */
+    float radius_narrow;    /* 2.5 px at level 0 */
+    float radius_wide;      /* 4.0 px at level 0 */
+    float dist_lo;          /* in view if dist >= 0.8 * dmin ... */
+    float dist_hi;          /* ... and dist <= 1.2 * dmax */
+} ft_params;
+
+/* Keypoints of one image (level-0 pixel coordinates).  desc is [n][32]
+ * uint8 and must be 16-byte aligned.  n in [0, FT_MAX_KEYPOINTS). */
+typedef struct {
+    int n;
+    const float *x, *y;
+    const int8_t *oct;
+    const uint8_t *desc;
+} ft_keypoints;
+
+/* Image pyramid: level l is width[l] x height[l] uint8 with row pitch[l]
+ * bytes (pitch >= width). */
+typedef struct {
+    int nlevels;
+    const uint8_t *data[FT_MAX_LEVELS];
+    int width[FT_MAX_LEVELS], height[FT_MAX_LEVELS], pitch[FT_MAX_LEVELS];
+} ft_pyramid;
+
+/* Rectified pinhole stereo camera.  bf = b * fx.  [min_x, max_x] x
+ * [min_y, max_y] bounds the image for the frustum test and the grid. */
+typedef struct {
+    float fx, fy, cx, cy, b, bf;
+    int width, height;
+    float min_x, max_x, min_y, max_y;
+} ft_pinhole;
+
+/* Kannala-Brandt fisheye camera (equidistant with k1..k4). */
+typedef struct {
+    float fx, fy, cx, cy, k[4];
+    int width, height;
+    float min_x, max_x, min_y, max_y;
+} ft_kb8;
+
+/* Fisheye stereo rig: right <- left transform (row-major R_rl, t_rl) and the
+ * overlap x-ranges of the two images. */
+typedef struct {
+    ft_kb8 left, right;
+    float R_rl[9], t_rl[3];
+    float b;
+    float lap_l0, lap_l1, lap_r0, lap_r1;
+} ft_fisheye_rig;
+
+/* Camera pose: world -> camera rotation (row-major) and translation, and the
+ * camera centre in world coordinates. */
+typedef struct {
+    float R[9], t[3], O[3];
+} ft_pose;
+
+/* Local map points, structure of arrays (the paper splits the map-point
+ * record into fine-grained parts, section IV-E).  pos is [n][4] floats
+ * (x, y, z, dmin), nrm is [n][4] (mean viewing direction nx, ny, nz, dmax),
+ * desc [n][32]; pos, nrm and desc 16-byte aligned.  skip[m] != 0 leaves a
+ * point out of the search (may be NULL). */
+typedef struct {
+    int n;
+    const float *pos;
+    const float *nrm;
+    const uint8_t *desc;
+    const uint8_t *skip;
+} ft_map_view;
+
+/* One stereo frame (pinhole: both pyramids are needed for the refinement). */
+typedef struct {
+    ft_keypoints left, right;
+    ft_pyramid pyr_left, pyr_right;
+} ft_stereo_frame;
+
+/* Pinhole stereo output, one entry per left keypoint:
+ *   best_r     right index of the best Hamming match if d < th_stereo, else -1
+ *   dist       smallest Hamming distance over the candidates (-1: none)
+ *   sad_shift  best SAD shift in [-5, 5] (FT_NO_SHIFT: windows left the image
+ *              or no match)
+ *   sad_best   SAD at the best shift for matches that passed the parabola and
+ *              disparity checks (before median rejection), else -1
+ *   u_right    right x coordinate (level 0) of the final match, else -1
+ *   depth      bf / disparity of the final match, else -1 */
+typedef struct {
+    int32_t *best_r, *dist, *sad_shift, *sad_best;
+    float *u_right, *depth;
+} ft_stereo_out;
+
+/* Fisheye stereo output per left keypoint: r_idx (accepted right index or
+ * -1), d1 / d2 (smallest and second smallest Hamming distance over the
+ * overlap candidates; d2 = 256 with a single candidate; both -1 outside the
+ * overlap or with no candidate). */
+typedef struct {
+    int32_t *r_idx, *d1, *d2;
+} ft_fisheye_out;
+
+/* Search output for one camera:
+ *   level  [M] predicted level, -1 if the point is not in view (or skipped)
+ *   proj   [M][4] (u, v, u_right, viewing cosine), zeros when not in view
+ *          (u_right is -1 for fisheye cameras); may be NULL
+ *   mp_kp  [M] matched keypoint index after conflict resolution, else -1
+ *   mp_d1, mp_d2 [M] best and second-best distance (-1 / 256 as above)
+ *   kp_mp  [N] map point that owns keypoint k, else -1 */
+typedef struct {
+    int8_t *level;
+    float *proj;
+    int32_t *mp_kp, *mp_d1, *mp_d2, *kp_mp;
+} ft_search_cam_out;
+
+typedef struct {
+    ft_search_cam_out left;
+    ft_search_cam_out right;   /* fisheye frames only */
+} ft_search_out;
+
+/* A frame as seen by the search step.  Pinhole: left keypoints only, with
+ * u_right from stereo matching (NULL: no stereo consistency check).
+ * Fisheye: left and right keypoints, each camera with its own grid; O_right
+ * is the right camera centre in world coordinates. */
+typedef struct {
+    int camera;                 /* ft_camera_model */
+    ft_pinhole pinhole;
+    ft_fisheye_rig fisheye;
+    ft_keypoints left, right;
+    const float *u_right;
+    const uint8_t *taken_left;  /* keypoints already matched (may be NULL) */
+    const uint8_t *taken_right;
+    float O_right[3];
+} ft_frame_view;
+
+/* One frame of a batch: stereo matching then search of local points. */
+typedef struct {
+    int camera;                 /* ft_camera_model */
+    ft_pinhole pinhole;
+    ft_fisheye_rig fisheye;
+    ft_keypoints left, right;
+    ft_pyramid pyr_left, pyr_right;     /* pinhole only */
+    const uint8_t *taken_left, *taken_right;
+    ft_pose pose;
+    float O_right[3];                   /* fisheye only */
+    ft_map_view map;
+    ft_stereo_out stereo;               /* pinhole */
+    ft_fisheye_out fisheye_out;         /* fisheye */
+    ft_search_out search;
+} ft_frame_job;
+
+/* A ragged batch.  frames points to HOST memory (n entries).  If
+ * stage_in_bytes > 0 the library first copies stage_in_bytes from the
+ * pinned host buffer stage_in_host to the device buffer stage_in_dev on the
+ * stream (the frame pointers then refer into stage_in_dev); likewise it
+ * copies stage_out_bytes from stage_out_dev to the pinned host buffer
+ * stage_out_host after the work.  This is how a caller runs the whole path
+ * from host memory through one call. */
+typedef struct {
+    int n;
+    const ft_frame_job *frames;
+    const void *stage_in_host;
+    void *stage_in_dev;
+    size_t stage_in_bytes;
+    const void *stage_out_dev;
+    void *stage_out_host;
+    size_t stage_out_bytes;
+} ft_batch;
+
+typedef struct {
+    int device;             /* CUDA device ordinal */
+    size_t arena_bytes;     /* preallocated scratch (0: 64 MiB) */
+    int max_frames;         /* largest batch (0: 256) */
+    int use_graphs;         /* replay ft_track_batch through CUDA graphs */
+} ft_ctx_desc;
+
+typedef struct ft_ctx ft_ctx;
+
+/* Launch shape of the fused kernel (chosen per batch-shape bucket by the
+ * autotuner, or set by hand). */
+typedef struct {
+    int strip_rows;         /* image rows per pinhole stereo work item */
+    int search_tile;        /* map points per search work item (multiple of 256) */
+    int fisheye_tile;       /* left keypoints per fisheye work item (256 or 512) */
+    int resolve_tile;       /* entries per conflict-resolution item */
+    int ctas_per_sm;        /* persistent CTAs per SM (0: occupancy limit) */
+} ft_tuning;
+
+/* Fill p with the default readings. */
+void ft_params_default(ft_params *p);
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char *ft_last_error(void);
+
+/* Create a context on desc->device: allocates the device arena once (the
+ * paper preallocates all device memory at start-up, section IV-A), pinned
+ * staging buffers and events.  Returns FT_ECUDA / FT_ENOMEM on failure. */
+ft_status ft_create(ft_ctx **out, const ft_ctx_desc *desc);
+
+/* Wait for the context's work, then free everything it owns. */
+void ft_destroy(ft_ctx *ctx);
+
+/* Synchronize the context's last stream, return the device status word
+ * (0 or FT_ETIMEOUT) in *status and clear it. */
+ft_status ft_sync_status(ft_ctx *ctx, int32_t *status);
+
+/* Pinhole stereo matching of one frame (sections II-B, IV-C): row-band
+ * Hamming search, SAD refinement over +-5 px at the keypoint's level,
+ * parabola sub-pixel disparity, depth, median-based rejection.
+ * params NULL = defaults.  Outputs: ft_stereo_out, each [left.n]. */
+ft_status ft_stereo_match_pinhole(ft_ctx *ctx, void *stream, const ft_params *params,
+                                  const ft_pinhole *cam, const ft_stereo_frame *frame,
+                                  ft_stereo_out *out);
+
+/* Fisheye stereo matching of one frame (sections II-B, IV-C): brute force
+ * over the right keypoints inside [lap_r0, lap_r1] for every left keypoint
+ * inside [lap_l0, lap_l1], best/second best and ratio test.  Outputs: each
+ * [left->n]. */
+ft_status ft_stereo_match_fisheye(ft_ctx *ctx, void *stream, const ft_params *params,
+                                  const ft_fisheye_rig *rig, const ft_keypoints *left,
+                                  const ft_keypoints *right, ft_fisheye_out *out);
+
+/* Search of local map points by projection for one frame (sections II-D,
+ * IV-E): frustum test, FP32 projection, predicted level, 64x48 grid-window
+ * candidates, best/second-best Hamming with ratio test, and conflict
+ * resolution (a keypoint keeps the smallest (distance, map index)). */
+ft_status ft_search_local_points(ft_ctx *ctx, void *stream, const ft_params *params,
+                                 const ft_frame_view *frame, const ft_pose *Tcw,
+                                 const ft_map_view *map, ft_search_out *out);
+
+/* Stereo matching followed by the search, for a ragged batch of frames, in
+ * one persistent fused launch (CUDA-graph replayed per batch-shape bucket if
+ * the context was created with use_graphs).  Each frame's results equal
+ * those of the per-frame calls. */
+ft_status ft_track_batch(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch);
+
+/* Time candidate launch shapes on this batch (iters runs each) and keep the
+ * fastest for the batch's bucket; *best receives it (may be NULL). */
+ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch,
+                      int iters, ft_tuning *best);
+
+/* Set / get the launch shape used for a batch's bucket. */
+ft_status ft_set_tuning(ft_ctx *ctx, const ft_batch *batch, const ft_tuning *t);
+ft_status ft_get_tuning(ft_ctx *ctx, const ft_batch *batch, ft_tuning *t);
+
+/* Persist / load the tuning table (text file, one bucket per line). */
+ft_status ft_save_tuning(ft_ctx *ctx, const char *path);
+ft_status ft_load_tuning(ft_ctx *ctx, const char *path);
+
+/* Test hook for the bounded device waits: flags bit 0 makes the stereo step
+ * withhold its "stereo done" signal, so the search step's wait runs out after
+ * timeout_ns (0: the default of 2 s) and the call reports FT_ETIMEOUT through
+ * ft_sync_status.  Use flags = 0 for normal operation. */
+ft_status ft_set_debug(ft_ctx *ctx, unsigned flags, uint64_t timeout_ns);
+
+/* Kernel launches issued by this context so far (all entry points). */
+uint64_t ft_launch_count(ft_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

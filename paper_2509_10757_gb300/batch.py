@@ -1,0 +1,364 @@
+"""Argument marshalling for libfasttrack.so: lay frames out in device memory
+and build the C structs that point into it.
+
+A PackedBatch puts every input of a list of frames into ONE contiguous blob
+(pinned host copy + device copy) and every output into a second blob, each
+array 256-byte aligned.  The C structs (ft_frame_job, ft_stereo_frame, ...)
+hold device pointers into those blobs.  Nothing here computes any step of
+the method: the work runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+ALIGN = 256
+
+
+def _align(n: int) -> int:
+    return (n + ALIGN - 1) // ALIGN * ALIGN
+
+
+class _Layout:
+    def __init__(self):
+        self.items = []           # (key, offset, dtype, shape)
+        self.index = {}
+        self.size = 0
+
+    def add(self, key, dtype, shape):
+        nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
+        off = self.size
+        self.items.append((key, off, np.dtype(dtype), tuple(shape)))
+        self.index[key] = len(self.items) - 1
+        self.size = _align(off + max(nbytes, 1))
+        return off
+
+
+def _input_arrays(f, fr):
+    """(key, array) pairs of frame `f`'s inputs."""
+    out = [((f, "lx"), fr.left.x), ((f, "ly"), fr.left.y), ((f, "loct"), fr.left.oct),
+           ((f, "ldesc"), fr.left.desc), ((f, "rx"), fr.right.x), ((f, "ry"), fr.right.y),
+           ((f, "roct"), fr.right.oct), ((f, "rdesc"), fr.right.desc),
+           ((f, "taken_l"), fr.taken_l)]
+    if fr.camera == "pinhole":
+        for l, img in enumerate(fr.pyr_left):
+            out.append(((f, f"pyrL{l}"), img))
+        for l, img in enumerate(fr.pyr_right):
+            out.append(((f, f"pyrR{l}"), img))
+    else:
+        out.append(((f, "taken_r"), fr.taken_r))
+    out += [((f, "pos"), fr.map.pos), ((f, "nrm"), fr.map.nrm), ((f, "mdesc"), fr.map.desc),
+            ((f, "skip"), fr.map.skip)]
+    return out
+
+
+def _output_specs(f, fr):
+    nl, nr, m = fr.left.n, fr.right.n, fr.map.n
+    spec = []
+    if fr.camera == "pinhole":
+        spec += [((f, k), np.int32, (nl,)) for k in ("best_r", "dist", "sad_shift", "sad_best")]
+        spec += [((f, "u_right"), np.float32, (nl,)), ((f, "depth"), np.float32, (nl,))]
+        sides = (("l", nl),)
+    else:
+        spec += [((f, k), np.int32, (nl,)) for k in ("r_idx", "d1", "d2")]
+        sides = (("l", nl), ("r", nr))
+    for s, nk in sides:
+        spec += [((f, f"level_{s}"), np.int8, (m,)), ((f, f"proj_{s}"), np.float32, (m, 4))]
+        spec += [((f, f"{k}_{s}"), np.int32, (m,)) for k in ("mp_kp", "mp_d1", "mp_d2")]
+        spec += [((f, f"kp_mp_{s}"), np.int32, (nk,))]
+    return spec
+
+
+def _f32(a):
+    return [float(v) for v in np.asarray(a, np.float32).reshape(-1)]
+
+
+def pinhole_struct(cam) -> L.ft_pinhole:
+    s = L.ft_pinhole()
+    for name, _ in L.ft_pinhole._fields_:
+        setattr(s, name, getattr(cam, name))
+    return s
+
+
+def kb8_struct(cam) -> L.ft_kb8:
+    s = L.ft_kb8()
+    for name in ("fx", "fy", "cx", "cy", "width", "height", "min_x", "max_x", "min_y", "max_y"):
+        setattr(s, name, getattr(cam, name))
+    s.k[:] = _f32(cam.k)
+    return s
+
+
+def rig_struct(rig) -> L.ft_fisheye_rig:
+    s = L.ft_fisheye_rig()
+    s.left = kb8_struct(rig.left)
+    s.right = kb8_struct(rig.right)
+    s.R_rl[:] = _f32(rig.R_rl)
+    s.t_rl[:] = _f32(rig.t_rl)
+    for name in ("b", "lap_l0", "lap_l1", "lap_r0", "lap_r1"):
+        setattr(s, name, getattr(rig, name))
+    return s
+
+
+def pose_struct(pose) -> L.ft_pose:
+    s = L.ft_pose()
+    s.R[:] = _f32(pose.R)
+    s.t[:] = _f32(pose.t)
+    s.O[:] = _f32(pose.O)
+    return s
+
+
+class PackedBatch:
+    """Inputs and outputs of a list of generated frames, packed for the GPU."""
+
+    def __init__(self, frames, device: str | torch.device = "cuda", pin: bool = True):
+        self.frames = list(frames)
+        self.device = torch.device(device)
+        self.lin = _Layout()
+        self.lout = _Layout()
+        arrays = []
+        for f, fr in enumerate(self.frames):
+            for key, a in _input_arrays(f, fr):
+                a = np.ascontiguousarray(a)
+                self.lin.add(key, a.dtype, a.shape)
+                arrays.append(a)
+            for key, dt, shape in _output_specs(f, fr):
+                self.lout.add(key, dt, shape)
+        self.host_in = torch.empty(self.lin.size, dtype=torch.uint8, pin_memory=pin)
+        self.host_out = torch.empty(self.lout.size, dtype=torch.uint8, pin_memory=pin)
+        hin = self.host_in.numpy()
+        for (key, off, dt, shape), a in zip(self.lin.items, arrays):
+            hin[off:off + a.nbytes] = a.reshape(-1).view(np.uint8)
+        self.dev_in = torch.empty(self.lin.size, dtype=torch.uint8, device=self.device)
+        self.dev_out = torch.empty(self.lout.size, dtype=torch.uint8, device=self.device)
+        self.in_base = self.dev_in.data_ptr()
+        self.out_base = self.dev_out.data_ptr()
+        self.jobs = (L.ft_frame_job * max(1, len(self.frames)))()
+        for f in range(len(self.frames)):
+            self.jobs[f] = self.job(f)
+
+    # ---------------------------------------------------------------- pointers
+    def pin_(self, f, key):
+        return self.in_base + self.lin.items[self.lin.index[(f, key)]][1]
+
+    def pout(self, f, key):
+        return self.out_base + self.lout.items[self.lout.index[(f, key)]][1]
+
+    def has_out(self, f, key):
+        return (f, key) in self.lout.index
+
+    # ---------------------------------------------------------------- structs
+    def keypoints(self, f, side: str) -> L.ft_keypoints:
+        fr = self.frames[f]
+        k = fr.left if side == "l" else fr.right
+        s = L.ft_keypoints()
+        s.n = k.n
+        s.x, s.y = self.pin_(f, side + "x"), self.pin_(f, side + "y")
+        s.oct, s.desc = self.pin_(f, side + "oct"), self.pin_(f, side + "desc")
+        return s
+
+    def pyramid(self, f, side: str) -> L.ft_pyramid:
+        fr = self.frames[f]
+        levels = fr.pyr_left if side == "L" else fr.pyr_right
+        s = L.ft_pyramid()
+        s.nlevels = len(levels)
+        for l, img in enumerate(levels):
+            s.data[l] = self.pin_(f, f"pyr{side}{l}")
+            s.height[l], s.width[l] = img.shape
+            s.pitch[l] = img.shape[1]
+        return s
+
+    def map_view(self, f) -> L.ft_map_view:
+        s = L.ft_map_view()
+        s.n = self.frames[f].map.n
+        s.pos, s.nrm = self.pin_(f, "pos"), self.pin_(f, "nrm")
+        s.desc, s.skip = self.pin_(f, "mdesc"), self.pin_(f, "skip")
+        return s
+
+    def stereo_out(self, f) -> L.ft_stereo_out:
+        s = L.ft_stereo_out()
+        for k in ("best_r", "dist", "sad_shift", "sad_best", "u_right", "depth"):
+            setattr(s, k, self.pout(f, k))
+        return s
+
+    def fisheye_out(self, f) -> L.ft_fisheye_out:
+        s = L.ft_fisheye_out()
+        for k in ("r_idx", "d1", "d2"):
+            setattr(s, k, self.pout(f, k))
+        return s
+
+    def search_out(self, f) -> L.ft_search_out:
+        s = L.ft_search_out()
+        for side, dst in (("l", s.left), ("r", s.right)):
+            if self.has_out(f, f"level_{side}"):
+                for k in ("level", "proj", "mp_kp", "mp_d1", "mp_d2", "kp_mp"):
+                    setattr(dst, k, self.pout(f, f"{k}_{side}"))
+        return s
+
+    def frame_view(self, f, u_right: bool = True) -> L.ft_frame_view:
+        fr = self.frames[f]
+        s = L.ft_frame_view()
+        s.left = self.keypoints(f, "l")
+        s.right = self.keypoints(f, "r")
+        s.taken_left = self.pin_(f, "taken_l")
+        if fr.camera == "pinhole":
+            s.camera = L.FT_CAMERA_PINHOLE
+            s.pinhole = pinhole_struct(fr.cam)
+            s.u_right = self.pout(f, "u_right") if u_right else None
+        else:
+            s.camera = L.FT_CAMERA_FISHEYE
+            s.fisheye = rig_struct(fr.rig)
+            s.taken_right = self.pin_(f, "taken_r")
+            s.O_right[:] = _f32(fr.O_right)
+        return s
+
+    def stereo_frame(self, f) -> L.ft_stereo_frame:
+        s = L.ft_stereo_frame()
+        s.left, s.right = self.keypoints(f, "l"), self.keypoints(f, "r")
+        s.pyr_left, s.pyr_right = self.pyramid(f, "L"), self.pyramid(f, "R")
+        return s
+
+    def job(self, f) -> L.ft_frame_job:
+        fr = self.frames[f]
+        j = L.ft_frame_job()
+        j.left, j.right = self.keypoints(f, "l"), self.keypoints(f, "r")
+        j.taken_left = self.pin_(f, "taken_l")
+        j.pose = pose_struct(fr.pose)
+        j.map = self.map_view(f)
+        j.search = self.search_out(f)
+        if fr.camera == "pinhole":
+            j.camera = L.FT_CAMERA_PINHOLE
+            j.pinhole = pinhole_struct(fr.cam)
+            j.pyr_left, j.pyr_right = self.pyramid(f, "L"), self.pyramid(f, "R")
+            j.stereo = self.stereo_out(f)
+        else:
+            j.camera = L.FT_CAMERA_FISHEYE
+            j.fisheye = rig_struct(fr.rig)
+            j.taken_right = self.pin_(f, "taken_r")
+            j.O_right[:] = _f32(fr.O_right)
+            j.fisheye_out = self.fisheye_out(f)
+        return j
+
+    def batch(self, stage: bool = False) -> L.ft_batch:
+        b = L.ft_batch()
+        b.n = len(self.frames)
+        b.frames = C.cast(self.jobs, C.POINTER(L.ft_frame_job))
+        if stage:
+            b.stage_in_host = self.host_in.data_ptr()
+            b.stage_in_dev = self.in_base
+            b.stage_in_bytes = self.lin.size
+            b.stage_out_dev = self.out_base
+            b.stage_out_host = self.host_out.data_ptr()
+            b.stage_out_bytes = self.lout.size
+        return b
+
+    # ---------------------------------------------------------------- data movement
+    def upload(self):
+        self.dev_in.copy_(self.host_in)
+
+    def download(self):
+        torch.cuda.synchronize(self.device)
+        self.host_out.copy_(self.dev_out)
+
+    def clear_outputs(self, value: int = 0x5a):
+        self.dev_out.fill_(value)
+
+    @property
+    def in_bytes(self) -> int:
+        return self.lin.size
+
+    @property
+    def out_bytes(self) -> int:
+        return self.lout.size
+
+    def outputs(self, f) -> dict:
+        """numpy views of frame f's outputs in the pinned host copy."""
+        h = self.host_out.numpy()
+        out = {}
+        for key, off, dt, shape in self.lout.items:
+            if key[0] != f:
+                continue
+            n = int(np.prod(shape)) * dt.itemsize
+            out[key[1]] = h[off:off + n].view(dt).reshape(shape)
+        return out
+
+
+class Context:
+    """Owns an ft_ctx (device arena, staging, graphs, tuning table)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 256 << 20, max_frames: int = 256,
+                 use_graphs: bool = False):
+        self.lib = L.load()
+        d = L.ft_ctx_desc(device=device, arena_bytes=arena_bytes, max_frames=max_frames,
+                          use_graphs=int(use_graphs))
+        self.ptr = C.c_void_p()
+        L.check(self.lib.ft_create(C.byref(self.ptr), C.byref(d)), "ft_create")
+
+    def close(self):
+        if self.ptr:
+            self.lib.ft_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self) -> int:
+        st = C.c_int32(-1)
+        L.check(self.lib.ft_sync_status(self.ptr, C.byref(st)), "ft_sync_status")
+        return st.value
+
+    def launches(self) -> int:
+        return int(self.lib.ft_launch_count(self.ptr))
+
+
+def stream_handle(stream: torch.cuda.Stream | None = None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def run_stereo(ctx: Context, pb: PackedBatch, f: int, params: L.ft_params | None = None, stream=None):
+    """Per-frame stereo entry point (pinhole or fisheye) on frame f."""
+    fr = pb.frames[f]
+    p = C.byref(params) if params is not None else None
+    if fr.camera == "pinhole":
+        st = pb.stereo_frame(f)
+        out = pb.stereo_out(f)
+        cam = pinhole_struct(fr.cam)
+        r = ctx.lib.ft_stereo_match_pinhole(ctx.ptr, stream_handle(stream), p, C.byref(cam),
+                                            C.byref(st), C.byref(out))
+        L.check(r, "ft_stereo_match_pinhole")
+    else:
+        rig = rig_struct(fr.rig)
+        kl, kr = pb.keypoints(f, "l"), pb.keypoints(f, "r")
+        out = pb.fisheye_out(f)
+        r = ctx.lib.ft_stereo_match_fisheye(ctx.ptr, stream_handle(stream), p, C.byref(rig),
+                                            C.byref(kl), C.byref(kr), C.byref(out))
+        L.check(r, "ft_stereo_match_fisheye")
+
+
+def run_search(ctx: Context, pb: PackedBatch, f: int, params: L.ft_params | None = None,
+               stream=None, u_right: bool = True):
+    """Per-frame search entry point on frame f (pinhole uses the stereo u_right)."""
+    fv = pb.frame_view(f, u_right=u_right)
+    pose = pose_struct(pb.frames[f].pose)
+    mv = pb.map_view(f)
+    out = pb.search_out(f)
+    p = C.byref(params) if params is not None else None
+    r = ctx.lib.ft_search_local_points(ctx.ptr, stream_handle(stream), p, C.byref(fv),
+                                       C.byref(pose), C.byref(mv), C.byref(out))
+    L.check(r, "ft_search_local_points")
+
+
+def run_batch(ctx: Context, pb: PackedBatch, params: L.ft_params | None = None, stream=None,
+              stage: bool = False):
+    """Fused stereo + search over all frames of pb (one launch)."""
+    b = pb.batch(stage=stage)
+    p = C.byref(params) if params is not None else None
+    L.check(ctx.lib.ft_track_batch(ctx.ptr, stream_handle(stream), p, C.byref(b)),
+            "ft_track_batch")

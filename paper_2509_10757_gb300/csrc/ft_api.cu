@@ -1,0 +1,936 @@
+// ft_api.cu -- host side of libfasttrack.so: the C ABI of fasttrack.h.
+//
+// Context = one device arena allocated once at creation (the paper
+// preallocates all GPU memory at start-up and reuses it, section IV-A),
+// a ring of pinned staging slots for the per-call batch table, events, a
+// CUDA-graph cache and the tuning table.  Every entry point turns its
+// arguments into a batch table (see ft_internal.h), copies it into the
+// arena with one cudaMemcpyAsync and launches the fused persistent kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ft_internal.h"
+
+using namespace ft;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ft_status fail(ft_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define FT_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(FT_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+constexpr int kSlots = 4;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+struct TableLayout {
+    size_t hdr, queue, counters, prefix, frames, total;
+};
+
+TableLayout table_layout(int n)
+{
+    TableLayout L{};
+    size_t off = 0;
+    L.hdr = off;
+    off = align_up(off + sizeof(BatchHeader));
+    L.queue = off;
+    off = align_up(off + 64);
+    L.counters = off;
+    off = align_up(off + sizeof(unsigned) * kCounters * (size_t)std::max(n, 1));
+    L.prefix = off;
+    off = align_up(off + sizeof(int) * K_KINDS * (size_t)(n + 1));
+    L.frames = off;
+    off = align_up(off + sizeof(FrameDev) * (size_t)std::max(n, 1));
+    L.total = off;
+    return L;
+}
+
+struct Bucket {
+    int frames_p2, has_pinhole, has_fisheye, nl_p2, m_p2;
+    bool operator<(const Bucket &o) const
+    {
+        return std::tie(frames_p2, has_pinhole, has_fisheye, nl_p2, m_p2) <
+               std::tie(o.frames_p2, o.has_pinhole, o.has_fisheye, o.nl_p2, o.m_p2);
+    }
+};
+
+// One frame as the table builder sees it (built from the public structs).
+struct Job {
+    int camera = FT_CAMERA_PINHOLE;
+    bool do_stereo = false, do_search = false, wait_stereo = false;
+    ft_pinhole pin{};
+    ft_fisheye_rig rig{};
+    ft_keypoints left{}, right{};
+    ft_pyramid pyr_l{}, pyr_r{};
+    const uint8_t *taken_l = nullptr, *taken_r = nullptr;
+    ft_pose pose{};
+    float O_right[3] = {0, 0, 0};
+    ft_map_view map{};
+    ft_stereo_out st{};
+    ft_fisheye_out fo{};
+    ft_search_out so{};
+    const float *u_right_in = nullptr;
+};
+
+}  // namespace
+
+struct ft_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int occ = 1;                      // max resident CTAs per SM of the fused kernel
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    int max_frames = 0;
+    size_t table_cap = 0;             // bytes of the table region
+    size_t scratch_off = 0;           // scratch region offset in the arena
+    unsigned *status = nullptr;       // device status word
+    char *staging[kSlots] = {};
+    cudaEvent_t slot_done[kSlots] = {};
+    int slot = 0;
+    cudaEvent_t done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool have_last = false;
+    bool use_graphs = false;
+    cudaStream_t capture_stream = nullptr;
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM, slot)
+    std::map<Bucket, ft_tuning> tuning;
+    uint64_t launches = 0;
+    unsigned debug_flags = 0;
+    unsigned long long timeout_ns = 2000000000ull;
+};
+
+namespace {
+
+ft_tuning default_tuning()
+{
+    ft_tuning t{};
+    t.strip_rows = 32;
+    t.search_tile = 512;
+    t.fisheye_tile = 256;
+    t.resolve_tile = 2048;
+    t.ctas_per_sm = 0;
+    return t;
+}
+
+ft_status check_params(const ft_params &p)
+{
+    if (p.nlevels < 1 || p.nlevels > FT_MAX_LEVELS) return fail(FT_EINVAL, "nlevels %d out of [1, 16]", p.nlevels);
+    if (!(p.scale_factor >= 1.0f) || !std::isfinite(p.scale_factor))
+        return fail(FT_EINVAL, "scale_factor must be >= 1");
+    if (!(p.median_factor >= 0.0f)) return fail(FT_EINVAL, "median_factor must be >= 0");
+    if (!(p.search_th > 0.0f)) return fail(FT_EINVAL, "search_th must be > 0");
+    float sc = 1.0f;
+    for (int l = 1; l < p.nlevels; ++l) sc = sc * p.scale_factor;
+    const double halo = std::ceil(2.0 * (double)sc) + 3.0;
+    if (2.0 * halo + 1.0 > (double)kRowCap)
+        return fail(FT_EINVAL, "scale_factor^(nlevels-1) = %g: row bands wider than the %d-row window", sc, kRowCap);
+    return FT_OK;
+}
+
+ft_status check_kps(const ft_keypoints &k, const char *what)
+{
+    if (k.n < 0 || k.n >= FT_MAX_KEYPOINTS) return fail(FT_EINVAL, "%s: n=%d out of range", what, k.n);
+    if (k.n == 0) return FT_OK;
+    if (!k.x || !k.y || !k.oct || !k.desc) return fail(FT_EINVAL, "%s: NULL array", what);
+    if (!aligned16(k.desc)) return fail(FT_EALIGN, "%s: desc not 16-byte aligned", what);
+    return FT_OK;
+}
+
+ft_status check_pyramid(const ft_pyramid &p, int nlevels, const char *what)
+{
+    if (p.nlevels < nlevels) return fail(FT_EINVAL, "%s: %d levels, need %d", what, p.nlevels, nlevels);
+    for (int l = 0; l < nlevels; ++l) {
+        if (!p.data[l]) return fail(FT_EINVAL, "%s: level %d is NULL", what, l);
+        if (p.width[l] <= 0 || p.height[l] <= 0 || p.pitch[l] < p.width[l])
+            return fail(FT_EINVAL, "%s: level %d has bad size %dx%d pitch %d", what, l, p.width[l],
+                        p.height[l], p.pitch[l]);
+    }
+    return FT_OK;
+}
+
+ft_status check_bounds(float a, float b, const char *what)
+{
+    if (!(b > a) || !std::isfinite(a) || !std::isfinite(b)) return fail(FT_EINVAL, "%s: empty range", what);
+    return FT_OK;
+}
+
+ft_status check_job(const Job &j, const ft_params &p)
+{
+    ft_status s;
+    if ((s = check_kps(j.left, "left keypoints")) != FT_OK) return s;
+    if (j.camera == FT_CAMERA_FISHEYE || j.do_stereo)
+        if ((s = check_kps(j.right, "right keypoints")) != FT_OK) return s;
+    if (j.camera == FT_CAMERA_PINHOLE) {
+        if (j.pin.width <= 0 || j.pin.height <= 0) return fail(FT_EINVAL, "pinhole: bad image size");
+        if (j.do_search) {
+            if ((s = check_bounds(j.pin.min_x, j.pin.max_x, "pinhole x bounds")) != FT_OK) return s;
+            if ((s = check_bounds(j.pin.min_y, j.pin.max_y, "pinhole y bounds")) != FT_OK) return s;
+        }
+        if (j.do_stereo) {
+            if (!(j.pin.b > 0.0f)) return fail(FT_EINVAL, "pinhole: baseline must be > 0");
+            if ((s = check_pyramid(j.pyr_l, p.nlevels, "left pyramid")) != FT_OK) return s;
+            if ((s = check_pyramid(j.pyr_r, p.nlevels, "right pyramid")) != FT_OK) return s;
+            const ft_stereo_out &o = j.st;
+            if (j.left.n > 0 && (!o.best_r || !o.dist || !o.sad_shift || !o.sad_best || !o.u_right || !o.depth))
+                return fail(FT_EINVAL, "stereo output: NULL array");
+        }
+    } else if (j.camera == FT_CAMERA_FISHEYE) {
+        if (j.do_stereo && j.left.n > 0 && (!j.fo.r_idx || !j.fo.d1 || !j.fo.d2))
+            return fail(FT_EINVAL, "fisheye output: NULL array");
+        if (j.do_search) {
+            const ft_kb8 *c[2] = {&j.rig.left, &j.rig.right};
+            for (auto *cam : c) {
+                if ((s = check_bounds(cam->min_x, cam->max_x, "fisheye x bounds")) != FT_OK) return s;
+                if ((s = check_bounds(cam->min_y, cam->max_y, "fisheye y bounds")) != FT_OK) return s;
+            }
+        }
+    } else {
+        return fail(FT_EINVAL, "unknown camera model %d", j.camera);
+    }
+    if (j.do_search) {
+        const ft_map_view &m = j.map;
+        if (m.n < 0 || m.n >= FT_MAX_MAP_POINTS) return fail(FT_EINVAL, "map: n=%d out of range", m.n);
+        if (m.n > 0) {
+            if (!m.pos || !m.nrm || !m.desc) return fail(FT_EINVAL, "map: NULL array");
+            if (!aligned16(m.pos) || !aligned16(m.nrm) || !aligned16(m.desc))
+                return fail(FT_EALIGN, "map: pos/nrm/desc not 16-byte aligned");
+        }
+        const int ncam = j.camera == FT_CAMERA_FISHEYE ? 2 : 1;
+        for (int c = 0; c < ncam; ++c) {
+            const ft_search_cam_out &o = c ? j.so.right : j.so.left;
+            const int nk = c ? j.right.n : j.left.n;
+            if (m.n > 0 && (!o.level || !o.mp_kp || !o.mp_d1 || !o.mp_d2))
+                return fail(FT_EINVAL, "search output: NULL array");
+            if (nk > 0 && !o.kp_mp) return fail(FT_EINVAL, "search output: NULL kp_mp");
+            if (o.proj && !aligned16(o.proj)) return fail(FT_EALIGN, "search output: proj not 16-byte aligned");
+        }
+    }
+    return FT_OK;
+}
+
+DevParams make_dev_params(const ft_params &p)
+{
+    DevParams d{};
+    d.nlevels = p.nlevels;
+    d.th_stereo = p.th_stereo;
+    d.th_search = p.th_search;
+    d.ratio_any_octave = p.ratio_any_octave;
+    float sc = 1.0f;
+    float rmax = 0.0f;
+    for (int l = 0; l < FT_MAX_LEVELS; ++l) {
+        if (l > 0 && l < p.nlevels) sc = sc * p.scale_factor;
+        d.sc[l] = sc;
+        d.isc[l] = 1.0f / sc;
+        d.band_r[l] = 2.0f * sc;
+        if (l < p.nlevels) rmax = std::max(rmax, d.band_r[l]);
+    }
+    d.median_factor = p.median_factor;
+    d.fisheye_ratio = p.fisheye_ratio;
+    d.nn_ratio = p.nn_ratio;
+    d.search_th = p.search_th;
+    d.view_cos_min = p.view_cos_min;
+    d.view_cos_narrow = p.view_cos_narrow;
+    d.radius_narrow = p.radius_narrow;
+    d.radius_wide = p.radius_wide;
+    d.dist_lo = p.dist_lo;
+    d.dist_hi = p.dist_hi;
+    // a right keypoint's band reaches rows within ceil(r) + 2 of floor(y); +1 margin
+    d.halo = (int)std::ceil(rmax) + 3;
+    return d;
+}
+
+Bucket bucket_of(const std::vector<Job> &jobs)
+{
+    Bucket b{};
+    b.frames_p2 = next_pow2((int)jobs.size());
+    int nl = 1, m = 1;
+    for (const Job &j : jobs) {
+        if (j.camera == FT_CAMERA_FISHEYE) b.has_fisheye = 1;
+        else b.has_pinhole = 1;
+        nl = std::max(nl, j.left.n);
+        m = std::max(m, j.map.n);
+    }
+    b.nl_p2 = next_pow2(nl);
+    b.m_p2 = next_pow2(m);
+    return b;
+}
+
+void fill_cam_kb8(CamDev &C, const ft_kb8 &k)
+{
+    C.model = FT_CAMERA_FISHEYE;
+    C.fx = k.fx;
+    C.fy = k.fy;
+    C.cx = k.cx;
+    C.cy = k.cy;
+    for (int i = 0; i < 4; ++i) C.k[i] = k.k[i];
+    C.minx = k.min_x;
+    C.maxx = k.max_x;
+    C.miny = k.min_y;
+    C.maxy = k.max_y;
+}
+
+void fill_cam_out(CamDev &C, const ft_search_cam_out &o)
+{
+    C.level = o.level;
+    C.proj = reinterpret_cast<float4 *>(o.proj);
+    C.mp_kp = o.mp_kp;
+    C.mp_d1 = o.mp_d1;
+    C.mp_d2 = o.mp_d2;
+    C.kp_mp = o.kp_mp;
+}
+
+void fill_cam_kps(CamDev &C, const ft_keypoints &k, const uint8_t *taken)
+{
+    C.nk = k.n;
+    C.kx = k.x;
+    C.ky = k.y;
+    C.koct = k.oct;
+    C.kdesc = reinterpret_cast<const uint4 *>(k.desc);
+    C.taken = taken;
+}
+
+// Build the table for `jobs` into host buffer `h` (laid out for the device
+// base `dev`), carving per-frame scratch from the arena.  Returns bytes used.
+ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Job> &jobs,
+                      const ft_tuning &tune, char *h, char *dev, size_t *bytes_out, int *items_out)
+{
+    const int n = (int)jobs.size();
+    const TableLayout L = table_layout(n);
+    if (L.total > ctx->table_cap) return fail(FT_ENOMEM, "batch table of %d frames exceeds the context", n);
+    std::memset(h, 0, L.total);
+    BatchHeader &B = *reinterpret_cast<BatchHeader *>(h + L.hdr);
+    B.p = make_dev_params(params);
+    B.nframes = n;
+    B.debug_flags = ctx->debug_flags;
+    B.prefix = reinterpret_cast<const int *>(dev + L.prefix);
+    B.frames = reinterpret_cast<const FrameDev *>(dev + L.frames);
+    B.queue = reinterpret_cast<unsigned *>(dev + L.queue);
+    B.status = ctx->status;
+    B.timeout_ns = ctx->timeout_ns;
+    unsigned *ctr_h = reinterpret_cast<unsigned *>(h + L.counters);
+    unsigned *ctr_d = reinterpret_cast<unsigned *>(dev + L.counters);
+    int *prefix = reinterpret_cast<int *>(h + L.prefix);
+    FrameDev *frames = reinterpret_cast<FrameDev *>(h + L.frames);
+
+    size_t scratch = ctx->scratch_off;
+    auto carve = [&](size_t bytes) -> char * {
+        char *p = ctx->arena + scratch;
+        scratch = align_up(scratch + std::max<size_t>(bytes, 1));
+        return p;
+    };
+    const int halo = B.p.halo;
+    int counts[K_KINDS] = {0, 0, 0, 0};
+    for (int f = 0; f < n; ++f) {
+        const Job &j = jobs[f];
+        FrameDev &F = frames[f];
+        F.camera = j.camera;
+        F.do_stereo = j.do_stereo;
+        F.do_search = j.do_search;
+        F.wait_stereo = j.wait_stereo;
+        F.nl = j.left.n;
+        F.nr = j.right.n;
+        F.nm = j.do_search ? j.map.n : 0;
+        F.lx = j.left.x;
+        F.ly = j.left.y;
+        F.loct = j.left.oct;
+        F.ldesc = reinterpret_cast<const uint4 *>(j.left.desc);
+        F.rx = j.right.x;
+        F.ry = j.right.y;
+        F.roct = j.right.oct;
+        F.rdesc = reinterpret_cast<const uint4 *>(j.right.desc);
+        F.ctr = ctr_d + (size_t)kCounters * f;
+        unsigned *ctr = ctr_h + (size_t)kCounters * f;
+        int n_stereo = 0;
+        if (j.camera == FT_CAMERA_PINHOLE) {
+            F.H = j.pin.height;
+            F.b = j.pin.b;
+            F.bf = j.pin.bf;
+            if (j.do_stereo) {
+                for (int l = 0; l < params.nlevels; ++l) {
+                    F.pyrL[l] = j.pyr_l.data[l];
+                    F.lw[l] = j.pyr_l.width[l];
+                    F.lh[l] = j.pyr_l.height[l];
+                    F.lp[l] = j.pyr_l.pitch[l];
+                    F.pyrR[l] = j.pyr_r.data[l];
+                    F.rw[l] = j.pyr_r.width[l];
+                    F.rh[l] = j.pyr_r.height[l];
+                    F.rp[l] = j.pyr_r.pitch[l];
+                }
+                F.best_r = j.st.best_r;
+                F.dist = j.st.dist;
+                F.sad_shift = j.st.sad_shift;
+                F.sad_best = j.st.sad_best;
+                F.u_right = j.st.u_right;
+                F.depth = j.st.depth;
+                // strip height: the window (strip + 2 halo rows) must fit the
+                // shared row table, and its expected right keypoints the stage
+                int sr = std::max(1, tune.strip_rows);
+                sr = std::min(sr, kRowCap - 2 * halo);
+                if (F.nr > 0) {
+                    const double per_row = (double)F.nr / (double)std::max(1, F.H);
+                    const int cap_rows = (int)(0.75 * kStageCap / per_row) - 2 * halo;
+                    sr = std::max(1, std::min(sr, cap_rows));
+                }
+                F.strip_rows = sr;
+                n_stereo = (F.H + sr - 1) / sr;
+            }
+        } else {
+            F.lap_l0 = j.rig.lap_l0;
+            F.lap_l1 = j.rig.lap_l1;
+            F.lap_r0 = j.rig.lap_r0;
+            F.lap_r1 = j.rig.lap_r1;
+            for (int i = 0; i < 9; ++i) F.R_rl[i] = j.rig.R_rl[i];
+            for (int i = 0; i < 3; ++i) F.t_rl[i] = j.rig.t_rl[i];
+            if (j.do_stereo) {
+                F.r_idx = j.fo.r_idx;
+                F.fd1 = j.fo.d1;
+                F.fd2 = j.fo.d2;
+                F.fisheye_tile = tune.fisheye_tile >= 512 ? 512 : 256;
+                n_stereo = (F.nl + F.fisheye_tile - 1) / F.fisheye_tile;
+            }
+        }
+        F.n_stereo_items = n_stereo;
+        if (n_stereo == 0) ctr[C_STEREO_READY] = 1;
+
+        int n_index = 0, n_search[2] = {0, 0}, n_resolve[2] = {0, 0};
+        if (j.do_search) {
+            F.ncam = j.camera == FT_CAMERA_FISHEYE ? 2 : 1;
+            F.u_right_in = j.camera == FT_CAMERA_PINHOLE ? j.u_right_in : nullptr;
+            F.pos = reinterpret_cast<const float4 *>(j.map.pos);
+            F.nrm = reinterpret_cast<const float4 *>(j.map.nrm);
+            F.mdesc = reinterpret_cast<const uint4 *>(j.map.desc);
+            F.skip = j.map.skip;
+            F.search_tile = std::max(kThreads, tune.search_tile / kThreads * kThreads);
+            F.resolve_tile = std::max(kThreads, tune.resolve_tile / kThreads * kThreads);
+            for (int c = 0; c < F.ncam; ++c) {
+                CamDev &C = F.cam[c];
+                if (j.camera == FT_CAMERA_PINHOLE) {
+                    C.model = FT_CAMERA_PINHOLE;
+                    C.fx = j.pin.fx;
+                    C.fy = j.pin.fy;
+                    C.cx = j.pin.cx;
+                    C.cy = j.pin.cy;
+                    C.bf = j.pin.bf;
+                    C.minx = j.pin.min_x;
+                    C.maxx = j.pin.max_x;
+                    C.miny = j.pin.min_y;
+                    C.maxy = j.pin.max_y;
+                } else {
+                    fill_cam_kb8(C, c ? j.rig.right : j.rig.left);
+                }
+                for (int i = 0; i < 9; ++i) C.R[i] = j.pose.R[i];
+                for (int i = 0; i < 3; ++i) {
+                    C.t[i] = j.pose.t[i];
+                    C.O[i] = c ? j.O_right[i] : j.pose.O[i];
+                }
+                fill_cam_kps(C, c ? j.right : j.left, c ? j.taken_r : j.taken_l);
+                fill_cam_out(C, c ? j.so.right : j.so.left);
+                C.cell_ptr = reinterpret_cast<int *>(carve(sizeof(int) * (kCells + 1)));
+                C.gkp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)C.nk));
+                C.gdesc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)C.nk));
+                C.owner = reinterpret_cast<unsigned long long *>(carve(sizeof(unsigned long long) * (size_t)C.nk));
+                n_search[c] = (F.nm + F.search_tile - 1) / F.search_tile;
+                n_resolve[c] = (std::max(F.nm, C.nk) + F.resolve_tile - 1) / F.resolve_tile;
+            }
+            n_index = F.ncam;
+        }
+        if (scratch > ctx->arena_bytes)
+            return fail(FT_ENOMEM, "arena of %zu bytes too small for this batch (needs %zu)", ctx->arena_bytes, scratch);
+        F.n_index_items = n_index;
+        F.n_search_items[0] = n_search[0];
+        F.n_search_items[1] = n_search[1];
+        F.n_resolve_items[0] = n_resolve[0];
+        F.n_resolve_items[1] = n_resolve[1];
+        const int per_kind[K_KINDS] = {n_index, n_stereo, n_search[0] + n_search[1],
+                                       n_resolve[0] + n_resolve[1]};
+        for (int k = 0; k < K_KINDS; ++k) {
+            prefix[k * (n + 1) + f] = counts[k];
+            counts[k] += per_kind[k];
+        }
+    }
+    int total = 0;
+    for (int k = 0; k < K_KINDS; ++k) {
+        prefix[k * (n + 1) + n] = counts[k];
+        B.kind_begin[k] = total;
+        total += counts[k];
+    }
+    B.kind_begin[K_KINDS] = total;
+    B.total_items = total;
+    *bytes_out = L.total;
+    *items_out = total;
+    return FT_OK;
+}
+
+ft_status order_stream(ft_ctx *ctx, cudaStream_t s)
+{
+    if (ctx->have_last && ctx->last_stream != s) FT_CUDA(cudaStreamWaitEvent(s, ctx->done, 0));
+    return FT_OK;
+}
+
+ft_status finish_call(ft_ctx *ctx, cudaStream_t s)
+{
+    FT_CUDA(cudaEventRecord(ctx->done, s));
+    ctx->last_stream = s;
+    ctx->have_last = true;
+    return FT_OK;
+}
+
+ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int slot, int grid,
+                    size_t copy_bytes, cudaGraphExec_t *out)
+{
+    const auto key = std::make_tuple(frames_p2, cps, slot);
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+        *out = it->second;
+        return FT_OK;
+    }
+    // captured on the context's own stream; the graph then runs on any stream
+    cudaStream_t cs = ctx->capture_stream;
+    cudaGraph_t g = nullptr;
+    FT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e1 = cudaMemcpyAsync(table_dev, ctx->staging[slot], copy_bytes, cudaMemcpyHostToDevice, cs);
+    const cudaError_t e2 = launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), grid, cs);
+    const cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(FT_ECUDA, "graph capture failed: %s / %s / %s", cudaGetErrorString(e1),
+                    cudaGetErrorString(e2), cudaGetErrorString(e3));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e4 = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e4 != cudaSuccess) return fail(FT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e4));
+    ctx->graphs[key] = exec;
+    *out = exec;
+    return FT_OK;
+}
+
+ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, const std::vector<Job> &jobs,
+                 const ft_tuning *force_tuning, bool allow_graph)
+{
+    ft_status s = check_params(params);
+    if (s != FT_OK) return s;
+    if ((int)jobs.size() > ctx->max_frames)
+        return fail(FT_EINVAL, "%zu frames exceed the context's max_frames %d", jobs.size(), ctx->max_frames);
+    for (size_t f = 0; f < jobs.size(); ++f) {
+        if ((s = check_job(jobs[f], params)) != FT_OK) {
+            g_last_error = "frame " + std::to_string(f) + ": " + g_last_error;
+            return s;
+        }
+    }
+    FT_CUDA(cudaSetDevice(ctx->device));
+    const Bucket bk = bucket_of(jobs);
+    ft_tuning tune = default_tuning();
+    if (force_tuning) tune = *force_tuning;
+    else {
+        auto it = ctx->tuning.find(bk);
+        if (it != ctx->tuning.end()) tune = it->second;
+    }
+    const int slot = ctx->slot;
+    ctx->slot = (ctx->slot + 1) % kSlots;
+    FT_CUDA(cudaEventSynchronize(ctx->slot_done[slot]));      // staging slot free again
+    char *table_dev = ctx->arena + align_up(sizeof(unsigned) * 64);
+    size_t bytes = 0;
+    int items = 0;
+    if ((s = build_table(ctx, params, jobs, tune, ctx->staging[slot], table_dev, &bytes, &items)) != FT_OK)
+        return s;
+    if ((s = order_stream(ctx, stream)) != FT_OK) return s;
+    const int cps = tune.ctas_per_sm > 0 ? std::min(tune.ctas_per_sm, ctx->occ) : ctx->occ;
+    const int grid_max = ctx->sm_count * cps;
+    if (items > 0) {
+        if (allow_graph && ctx->use_graphs) {
+            const int fp2 = bk.frames_p2;
+            const size_t copy = std::max(bytes, table_layout(fp2).total);
+            cudaGraphExec_t exec = nullptr;
+            if ((s = get_graph(ctx, table_dev, fp2, cps, slot, grid_max, std::min(copy, ctx->table_cap),
+                               &exec)) != FT_OK)
+                return s;
+            FT_CUDA(cudaGraphLaunch(exec, stream));
+        } else {
+            FT_CUDA(cudaMemcpyAsync(table_dev, ctx->staging[slot], bytes, cudaMemcpyHostToDevice, stream));
+            FT_CUDA(launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), std::min(items, grid_max), stream));
+        }
+        ctx->launches += 1;
+    }
+    FT_CUDA(cudaEventRecord(ctx->slot_done[slot], stream));
+    return finish_call(ctx, stream);
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+void ft_params_default(ft_params *p)
+{
+    if (!p) return;
+    p->nlevels = 8;
+    p->scale_factor = 1.2f;
+    p->th_stereo = 75;
+    p->median_factor = 1.5f * 1.4f;
+    p->fisheye_ratio = 0.7f;
+    p->th_search = 100;
+    p->nn_ratio = 0.8f;
+    p->ratio_any_octave = 0;
+    p->search_th = 1.0f;
+    p->view_cos_min = 0.5f;
+    p->view_cos_narrow = 0.998f;
+    p->radius_narrow = 2.5f;
+    p->radius_wide = 4.0f;
+    p->dist_lo = 0.8f;
+    p->dist_hi = 1.2f;
+}
+
+const char *ft_last_error(void) { return g_last_error.c_str(); }
+
+ft_status ft_create(ft_ctx **out, const ft_ctx_desc *desc)
+{
+    if (!out) return fail(FT_EINVAL, "ft_create: out is NULL");
+    *out = nullptr;
+    ft_ctx_desc d{};
+    if (desc) d = *desc;
+    if (d.arena_bytes == 0) d.arena_bytes = (size_t)64 << 20;
+    if (d.max_frames <= 0) d.max_frames = 256;
+    if (d.max_frames > 65536) return fail(FT_EINVAL, "max_frames %d too large", d.max_frames);
+    int ndev = 0;
+    FT_CUDA(cudaGetDeviceCount(&ndev));
+    if (d.device < 0 || d.device >= ndev) return fail(FT_EINVAL, "device %d not present", d.device);
+    FT_CUDA(cudaSetDevice(d.device));
+    ft_ctx *c = new ft_ctx();
+    c->device = d.device;
+    c->max_frames = d.max_frames;
+    c->use_graphs = d.use_graphs != 0;
+    cudaDeviceProp prop{};
+    cudaError_t e = cudaGetDeviceProperties(&prop, d.device);
+    if (e == cudaSuccess) e = fused_occupancy(&c->occ);
+    c->sm_count = prop.multiProcessorCount;
+    if (c->occ < 1) c->occ = 1;
+    c->table_cap = table_layout(d.max_frames).total;
+    const size_t head = align_up(sizeof(unsigned) * 64);
+    c->scratch_off = align_up(head + c->table_cap);
+    c->arena_bytes = std::max(d.arena_bytes, c->scratch_off + ((size_t)1 << 20));
+    if (e == cudaSuccess) e = cudaMalloc(&c->arena, c->arena_bytes);
+    if (e == cudaSuccess) {
+        c->status = reinterpret_cast<unsigned *>(c->arena);
+        e = cudaMemset(c->arena, 0, head);
+    }
+    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
+        e = cudaMallocHost(&c->staging[i], c->table_cap);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->slot_done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        ft_destroy(c);
+        return fail(e == cudaErrorMemoryAllocation ? FT_ENOMEM : FT_ECUDA, "ft_create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return FT_OK;
+}
+
+void ft_destroy(ft_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (int i = 0; i < kSlots; ++i) {
+        if (c->staging[i]) cudaFreeHost(c->staging[i]);
+        if (c->slot_done[i]) cudaEventDestroy(c->slot_done[i]);
+    }
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->arena) cudaFree(c->arena);
+    delete c;
+}
+
+ft_status ft_sync_status(ft_ctx *c, int32_t *status)
+{
+    if (!c || !status) return fail(FT_EINVAL, "ft_sync_status: NULL argument");
+    FT_CUDA(cudaSetDevice(c->device));
+    if (c->have_last) FT_CUDA(cudaStreamSynchronize(c->last_stream));
+    unsigned v = 0;
+    FT_CUDA(cudaMemcpy(&v, c->status, sizeof(v), cudaMemcpyDeviceToHost));
+    FT_CUDA(cudaMemset(c->status, 0, sizeof(unsigned)));
+    *status = (v & kStatusTimeout) ? FT_ETIMEOUT : FT_OK;
+    return FT_OK;
+}
+
+uint64_t ft_launch_count(ft_ctx *c) { return c ? c->launches : 0; }
+
+ft_status ft_set_debug(ft_ctx *c, unsigned flags, uint64_t timeout_ns)
+{
+    if (!c) return fail(FT_EINVAL, "ft_set_debug: NULL context");
+    c->debug_flags = flags;
+    c->timeout_ns = timeout_ns ? timeout_ns : 2000000000ull;
+    return FT_OK;
+}
+
+ft_status ft_stereo_match_pinhole(ft_ctx *ctx, void *stream, const ft_params *params,
+                                  const ft_pinhole *cam, const ft_stereo_frame *frame, ft_stereo_out *out)
+{
+    if (!ctx || !cam || !frame || !out) return fail(FT_EINVAL, "ft_stereo_match_pinhole: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    Job j;
+    j.camera = FT_CAMERA_PINHOLE;
+    j.do_stereo = true;
+    j.pin = *cam;
+    j.left = frame->left;
+    j.right = frame->right;
+    j.pyr_l = frame->pyr_left;
+    j.pyr_r = frame->pyr_right;
+    j.st = *out;
+    return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
+}
+
+ft_status ft_stereo_match_fisheye(ft_ctx *ctx, void *stream, const ft_params *params,
+                                  const ft_fisheye_rig *rig, const ft_keypoints *left,
+                                  const ft_keypoints *right, ft_fisheye_out *out)
+{
+    if (!ctx || !rig || !left || !right || !out) return fail(FT_EINVAL, "ft_stereo_match_fisheye: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    Job j;
+    j.camera = FT_CAMERA_FISHEYE;
+    j.do_stereo = true;
+    j.rig = *rig;
+    j.left = *left;
+    j.right = *right;
+    j.fo = *out;
+    return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
+}
+
+ft_status ft_search_local_points(ft_ctx *ctx, void *stream, const ft_params *params,
+                                 const ft_frame_view *frame, const ft_pose *Tcw, const ft_map_view *map,
+                                 ft_search_out *out)
+{
+    if (!ctx || !frame || !Tcw || !map || !out) return fail(FT_EINVAL, "ft_search_local_points: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    Job j;
+    j.camera = frame->camera;
+    j.do_search = true;
+    j.pin = frame->pinhole;
+    j.rig = frame->fisheye;
+    j.left = frame->left;
+    j.right = frame->right;
+    j.u_right_in = frame->u_right;
+    j.taken_l = frame->taken_left;
+    j.taken_r = frame->taken_right;
+    j.pose = *Tcw;
+    for (int i = 0; i < 3; ++i) j.O_right[i] = frame->O_right[i];
+    j.map = *map;
+    j.so = *out;
+    return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
+}
+
+static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
+{
+    if (!batch || batch->n < 0 || (batch->n > 0 && !batch->frames))
+        return fail(FT_EINVAL, "batch: bad frame list");
+    jobs.resize(batch->n);
+    for (int f = 0; f < batch->n; ++f) {
+        const ft_frame_job &s = batch->frames[f];
+        Job &j = jobs[f];
+        j.camera = s.camera;
+        j.do_stereo = true;
+        j.do_search = true;
+        j.wait_stereo = s.camera == FT_CAMERA_PINHOLE;
+        j.pin = s.pinhole;
+        j.rig = s.fisheye;
+        j.left = s.left;
+        j.right = s.right;
+        j.pyr_l = s.pyr_left;
+        j.pyr_r = s.pyr_right;
+        j.taken_l = s.taken_left;
+        j.taken_r = s.taken_right;
+        j.pose = s.pose;
+        for (int i = 0; i < 3; ++i) j.O_right[i] = s.O_right[i];
+        j.map = s.map;
+        j.st = s.stereo;
+        j.fo = s.fisheye_out;
+        j.so = s.search;
+        j.u_right_in = s.camera == FT_CAMERA_PINHOLE ? s.stereo.u_right : nullptr;
+    }
+    return FT_OK;
+}
+
+ft_status ft_track_batch(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch)
+{
+    if (!ctx || !batch) return fail(FT_EINVAL, "ft_track_batch: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    std::vector<Job> jobs;
+    ft_status s = jobs_of_batch(batch, jobs);
+    if (s != FT_OK) return s;
+    if (batch->stage_in_bytes && (!batch->stage_in_host || !batch->stage_in_dev))
+        return fail(FT_EINVAL, "batch: stage-in buffers missing");
+    if (batch->stage_out_bytes && (!batch->stage_out_host || !batch->stage_out_dev))
+        return fail(FT_EINVAL, "batch: stage-out buffers missing");
+    cudaStream_t st = (cudaStream_t)stream;
+    FT_CUDA(cudaSetDevice(ctx->device));
+    if (batch->stage_in_bytes) {
+        if ((s = order_stream(ctx, st)) != FT_OK) return s;
+        FT_CUDA(cudaMemcpyAsync(batch->stage_in_dev, batch->stage_in_host, batch->stage_in_bytes,
+                                cudaMemcpyHostToDevice, st));
+    }
+    if ((s = submit(ctx, st, p, jobs, nullptr, true)) != FT_OK) return s;
+    if (batch->stage_out_bytes)
+        FT_CUDA(cudaMemcpyAsync(batch->stage_out_host, batch->stage_out_dev, batch->stage_out_bytes,
+                                cudaMemcpyDeviceToHost, st));
+    return FT_OK;
+}
+
+ft_status ft_set_tuning(ft_ctx *ctx, const ft_batch *batch, const ft_tuning *t)
+{
+    if (!ctx || !batch || !t) return fail(FT_EINVAL, "ft_set_tuning: NULL argument");
+    std::vector<Job> jobs;
+    ft_status s = jobs_of_batch(batch, jobs);
+    if (s != FT_OK) return s;
+    ctx->tuning[bucket_of(jobs)] = *t;
+    return FT_OK;
+}
+
+ft_status ft_get_tuning(ft_ctx *ctx, const ft_batch *batch, ft_tuning *t)
+{
+    if (!ctx || !batch || !t) return fail(FT_EINVAL, "ft_get_tuning: NULL argument");
+    std::vector<Job> jobs;
+    ft_status s = jobs_of_batch(batch, jobs);
+    if (s != FT_OK) return s;
+    auto it = ctx->tuning.find(bucket_of(jobs));
+    *t = it != ctx->tuning.end() ? it->second : default_tuning();
+    return FT_OK;
+}
+
+ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch, int iters,
+                      ft_tuning *best)
+{
+    if (!ctx || !batch) return fail(FT_EINVAL, "ft_autotune: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    std::vector<Job> jobs;
+    ft_status s = jobs_of_batch(batch, jobs);
+    if (s != FT_OK) return s;
+    if (iters < 1) iters = 3;
+    cudaStream_t st = (cudaStream_t)stream;
+    FT_CUDA(cudaSetDevice(ctx->device));
+    cudaEvent_t e0, e1;
+    FT_CUDA(cudaEventCreate(&e0));
+    FT_CUDA(cudaEventCreate(&e1));
+    const int strips[] = {16, 32, 64};
+    const int tiles[] = {256, 512, 1024};
+    const int fish[] = {256, 512};
+    int occs[] = {ctx->occ, std::max(1, ctx->occ / 2)};
+    ft_tuning best_t = default_tuning();
+    float best_ms = 1e30f;
+    for (int a : strips)
+        for (int b : tiles)
+            for (int c : fish)
+                for (int o : occs) {
+                    ft_tuning t = default_tuning();
+                    t.strip_rows = a;
+                    t.search_tile = b;
+                    t.fisheye_tile = c;
+                    t.ctas_per_sm = o;
+                    if ((s = submit(ctx, st, p, jobs, &t, false)) != FT_OK) goto out;
+                    cudaEventRecord(e0, st);
+                    for (int i = 0; i < iters; ++i)
+                        if ((s = submit(ctx, st, p, jobs, &t, false)) != FT_OK) goto out;
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        s = fail(FT_ECUDA, "autotune: event sync failed");
+                        goto out;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_t = t;
+                    }
+                }
+    ctx->tuning[bucket_of(jobs)] = best_t;
+    if (best) *best = best_t;
+out:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
+ft_status ft_save_tuning(ft_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(FT_EINVAL, "ft_save_tuning: NULL argument");
+    FILE *f = std::fopen(path, "w");
+    if (!f) return fail(FT_EINVAL, "cannot write %s", path);
+    std::fprintf(f, "# frames_p2 has_pinhole has_fisheye nl_p2 m_p2 strip_rows search_tile fisheye_tile resolve_tile ctas_per_sm\n");
+    for (auto &kv : ctx->tuning) {
+        const Bucket &b = kv.first;
+        const ft_tuning &t = kv.second;
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", b.frames_p2, b.has_pinhole, b.has_fisheye, b.nl_p2,
+                     b.m_p2, t.strip_rows, t.search_tile, t.fisheye_tile, t.resolve_tile, t.ctas_per_sm);
+    }
+    std::fclose(f);
+    return FT_OK;
+}
+
+ft_status ft_load_tuning(ft_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(FT_EINVAL, "ft_load_tuning: NULL argument");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return fail(FT_EINVAL, "cannot read %s", path);
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        Bucket b{};
+        ft_tuning t{};
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &b.frames_p2, &b.has_pinhole, &b.has_fisheye,
+                        &b.nl_p2, &b.m_p2, &t.strip_rows, &t.search_tile, &t.fisheye_tile, &t.resolve_tile,
+                        &t.ctas_per_sm) == 10)
+            ctx->tuning[b] = t;
+    }
+    std::fclose(f);
+    return FT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// ft_internal.h -- structures shared by the library's host and device code.
+//
+// One persistent kernel runs every entry point.  The host writes a "batch
+// table" (header, per-frame descriptors, per-kind work prefixes, zeroed
+// counters) into pinned memory and copies it into the context's arena with
+// one cudaMemcpyAsync; the kernel's CTAs then pull work items from a queue
+// (an atomic head counter) in a fixed order: grid builds, stereo items,
+// search items, resolve items.  An item waits only on items that sit before
+// it in the queue, so the queue drains without deadlock whatever the number
+// of resident CTAs.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "fasttrack.h"
+
+#include <cuda_runtime.h>
+
+namespace ft {
+
+constexpr int kThreads = 256;                       // threads per CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kCells = FT_GRID_COLS * FT_GRID_ROWS; // 3072 grid cells
+constexpr int kStageCap = 768;                      // right keypoints staged per stereo item
+constexpr int kRowCap = 448;                        // rows of a stereo item's window
+constexpr int kFishChunk = 512;                     // right descriptors staged per chunk
+constexpr int kCounters = 8;                        // per-frame counters (u32)
+
+enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
+
+// per-frame counter slots
+enum Ctr { C_INDEX_DONE = 0, C_STEREO_DONE = 1, C_STEREO_READY = 2, C_SEARCH_DONE0 = 3,
+           C_SEARCH_DONE1 = 4 };
+
+// device status bits (ORed into the context's status word)
+constexpr unsigned kStatusTimeout = 1u;
+
+// debug flags of the batch header
+constexpr unsigned kDebugWithholdStereoReady = 1u;   // never publish stereo-ready
+
+struct DevParams {
+    int nlevels, th_stereo, th_search, ratio_any_octave;
+    float sc[FT_MAX_LEVELS], isc[FT_MAX_LEVELS], band_r[FT_MAX_LEVELS];
+    float median_factor, fisheye_ratio, nn_ratio, search_th;
+    float view_cos_min, view_cos_narrow, radius_narrow, radius_wide, dist_lo, dist_hi;
+    int halo;            // rows a right keypoint's band can reach beyond floor(y)
+    int pad_;
+};
+
+// One camera of the search step (pinhole: the left camera only).
+struct CamDev {
+    int model;           // ft_camera_model
+    int nk;
+    float fx, fy, cx, cy, bf;
+    float k[4];
+    float minx, maxx, miny, maxy;
+    float iw, ih;        // grid cells per pixel (computed on the device)
+    float R[9], t[3], O[3];
+    const float *kx, *ky;
+    const int8_t *koct;
+    const uint4 *kdesc;
+    const uint8_t *taken;
+    int8_t *level;
+    float4 *proj;
+    int *mp_kp, *mp_d1, *mp_d2, *kp_mp;
+    int *cell_ptr;                 // [kCells + 1]
+    float4 *gkp;                   // [nk] keypoints in cell order: x, y, index, oct | taken << 8
+    uint4 *gdesc;                  // [2 * nk]
+    unsigned long long *owner;     // [nk] (distance << 32) | map index
+};
+
+struct FrameDev {
+    int camera, do_stereo, do_search, wait_stereo;
+    int nl, nr, nm, ncam;
+    // stereo inputs
+    const float *lx, *ly, *rx, *ry;
+    const int8_t *loct, *roct;
+    const uint4 *ldesc, *rdesc;
+    const uint8_t *pyrL[FT_MAX_LEVELS], *pyrR[FT_MAX_LEVELS];
+    int lw[FT_MAX_LEVELS], lh[FT_MAX_LEVELS], lp[FT_MAX_LEVELS];
+    int rw[FT_MAX_LEVELS], rh[FT_MAX_LEVELS], rp[FT_MAX_LEVELS];
+    int H;
+    float b, bf;
+    float lap_l0, lap_l1, lap_r0, lap_r1;
+    // stereo outputs (pinhole)
+    int *best_r, *dist, *sad_shift, *sad_best;
+    float *u_right, *depth;
+    // stereo outputs (fisheye)
+    int *r_idx, *fd1, *fd2;
+    // search
+    const float *u_right_in;       // stereo consistency input (NULL: none)
+    float R_rl[9], t_rl[3];        // fisheye rig (right camera pose is composed on the device)
+    CamDev cam[2];
+    const float4 *pos, *nrm;
+    const uint4 *mdesc;
+    const uint8_t *skip;
+    // work decomposition
+    int strip_rows, n_stereo_items, fisheye_tile;
+    int search_tile, resolve_tile;
+    int n_index_items, n_search_items[2], n_resolve_items[2];
+    unsigned *ctr;                 // [kCounters]
+};
+
+struct BatchHeader {
+    DevParams p;
+    int nframes, total_items;
+    int kind_begin[K_KINDS + 1];
+    unsigned debug_flags;
+    const int *prefix;             // [K_KINDS][nframes + 1]
+    const FrameDev *frames;
+    unsigned *queue;               // [0]: next item
+    unsigned *status;              // context status word (persistent, not in the table)
+    unsigned long long timeout_ns; // bound of every device-side wait
+};
+
+}  // namespace ft
+
+// Launch helpers implemented in ft_kernels.cu (host-callable).
+namespace ft {
+cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stream);
+int fused_smem_bytes();
+cudaError_t fused_occupancy(int *ctas_per_sm);
+const void *fused_kernel_ptr();
+}  // namespace ft

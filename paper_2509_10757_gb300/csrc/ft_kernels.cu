@@ -1,0 +1,920 @@
+// ft_kernels.cu -- the fused, persistent tracking kernel for sm_103a.
+//
+// Work items (pulled in queue order by every CTA of one launch):
+//   K_INDEX    per frame and camera: 64x48 keypoint grid as a counting sort
+//              into cell order (paper section IV-E; grid reading 64x48).
+//   K_STEREO   pinhole: one horizontal strip of left keypoints.  The CTA
+//              stages the right keypoints whose rows can reach the strip in
+//              shared memory, sorted by row, then one warp per left keypoint
+//              runs the band Hamming search (warp min reduction), the 11x11
+//              SAD over +-5 shifts from shared-memory patches, the parabola,
+//              disparity and depth (section IV-C, kernels 1 and 2 fused).  The
+//              frame's last strip runs the median rejection.
+//              fisheye: one tile of left keypoints, one thread each, against
+//              the right overlap descriptors staged in shared memory chunks;
+//              best/second best kept as packed (distance, index) keys.
+//   K_SEARCH   one tile of map points, one thread each: frustum test, FP32
+//              projection, predicted level, grid-window gather, top-2 Hamming,
+//              ratio test; accepted claims go to an atomicMin per keypoint.
+//   K_RESOLVE  one tile: final map-point -> keypoint and keypoint -> map
+//              point tables from the per-keypoint winners.
+// Floating point runs through __fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn /
+// __fsqrt_rn so that no multiply-add is contracted and every operation is
+// IEEE-rounded in the order the method defines it.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ft_internal.h"
+
+namespace ft {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kNoKey = 0xffffffffu;
+constexpr int kW = FT_SAD_W;
+constexpr int kL = FT_SAD_L;
+constexpr int kPatchL = (2 * kW + 1) * (2 * kW + 1);            // 121
+constexpr int kStripW = 2 * (kW + kL) + 1;                      // 21
+constexpr int kPatchR = (2 * kW + 1) * kStripW;                 // 231
+constexpr int kShifts = 2 * kL + 1;                             // 11
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ int f2i(float x) { return __float2int_rz(x); }   // C (int) cast
+
+__device__ __forceinline__ int ham8(uint4 a0, uint4 a1, uint4 b0, uint4 b1)
+{
+    return __popc(a0.x ^ b0.x) + __popc(a0.y ^ b0.y) + __popc(a0.z ^ b0.z) +
+           __popc(a0.w ^ b0.w) + __popc(a1.x ^ b1.x) + __popc(a1.y ^ b1.y) +
+           __popc(a1.z ^ b1.z) + __popc(a1.w ^ b1.w);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Top-2 of packed (distance << 20 | index) keys: the smallest and the
+// smallest of the rest.
+__device__ __forceinline__ void top2_push(unsigned key, unsigned &best, unsigned &second)
+{
+    second = min(second, max(best, key));
+    best = min(best, key);
+}
+
+// atan2 for y >= 0, x >= 0, from the mathematics: atan2(y, x) = atan(y/x)
+// when y <= x, else pi/2 - atan(x/y); atan(t) = pi/4 + atan((t-1)/(t+1)) for
+// t > tan(pi/8); below that the Taylor series of atan with terms up to a^17
+// (coefficients (-1)^k / (2k+1) divided out in FP32), evaluated by Horner in
+// a^2.
+__device__ float atan_series(float a)
+{
+    const float a2 = fmul(a, a);
+    float p = fdiv(1.0f, 17.0f);
+    p = fadd(-fdiv(1.0f, 15.0f), fmul(a2, p));
+    p = fadd(fdiv(1.0f, 13.0f), fmul(a2, p));
+    p = fadd(-fdiv(1.0f, 11.0f), fmul(a2, p));
+    p = fadd(fdiv(1.0f, 9.0f), fmul(a2, p));
+    p = fadd(-fdiv(1.0f, 7.0f), fmul(a2, p));
+    p = fadd(fdiv(1.0f, 5.0f), fmul(a2, p));
+    p = fadd(-fdiv(1.0f, 3.0f), fmul(a2, p));
+    p = fadd(1.0f, fmul(a2, p));
+    return fmul(a, p);
+}
+
+__device__ float atan_unit(float t)
+{
+    if (t > 0.41421356237309504880f)
+        return fadd(0.78539816339744830962f, atan_series(fdiv(fsub(t, 1.0f), fadd(t, 1.0f))));
+    return atan_series(t);
+}
+
+__device__ float atan2_pos(float y, float x)
+{
+    if (y == 0.0f) return 0.0f;
+    if (y <= x) return atan_unit(fdiv(y, x));
+    return fsub(1.57079632679489661923f, atan_unit(fdiv(x, y)));
+}
+
+// Exclusive scan of n ints (in place allowed), block-wide; returns the total.
+__device__ int block_scan(const int *in, int *out, int n, int *warp_sums)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int per = (n + kThreads - 1) / kThreads;
+    const int b = tid * per;
+    int local = 0;
+    for (int i = 0; i < per; ++i)
+        if (b + i < n) local += in[b + i];
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_sums[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < kWarps ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < kWarps) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int run = v - local + (w > 0 ? warp_sums[w - 1] : 0);
+    for (int i = 0; i < per; ++i) {
+        if (b + i < n) {
+            const int x = in[b + i];
+            out[b + i] = run;
+            run += x;
+        }
+    }
+    const int total = warp_sums[kWarps - 1];
+    __syncthreads();
+    return total;
+}
+
+// ---------------------------------------------------------------- shared memory
+struct SmemStereo {
+    uint4 sdesc[2 * kStageCap];
+    float sx[kStageCap], sy[kStageCap];
+    int sj[kStageCap];
+    int rowptr[kRowCap + 2];
+    int rowfill[kRowCap + 2];
+    int sad[kWarps][12];
+    int warp_sums[kWarps];
+    int8_t soct[kStageCap];
+    uint8_t patchL[kWarps][128];
+    uint8_t patchR[kWarps][kPatchR + 1];
+};
+
+struct SmemGrid {
+    int cnt[kCells];
+    int warp_sums[kWarps];
+};
+
+struct SmemFish {
+    uint4 desc[2 * kFishChunk];
+    int idx[kFishChunk];
+    int count;
+};
+
+struct SmemMedian {
+    int hist[256];
+    int count, bin, before;
+};
+
+struct SmemSearch {
+    float pose[12];
+};
+
+union Smem {
+    SmemStereo s;
+    SmemGrid g;
+    SmemFish f;
+    SmemMedian m;
+    SmemSearch q;
+};
+
+// ---------------------------------------------------------------- waits and signals
+// Block-wide wait until *ctr >= target, bounded by the header's timeout.  On
+// timeout (or when another CTA already reported one) it records the timeout in
+// the status word and returns false.
+__device__ bool wait_geq(const BatchHeader &B, const unsigned *ctr, unsigned target, int *s_flag)
+{
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_acquire(ctr) < target) {
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire(ctr) < target) {
+                if ((++spins & 31u) == 0) {
+                    if (global_ns() - t0 > B.timeout_ns || (ld_acquire(B.status) & kStatusTimeout)) {
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(256);
+            }
+            if (!ok) atomicOr(B.status, kStatusTimeout);
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    const bool ok = *s_flag != 0;
+    __syncthreads();
+    return ok;
+}
+
+// Publish this CTA's writes and add one to *ctr; returns true in every thread
+// of the CTA that brought the counter to `total`.
+__device__ bool signal_count(unsigned *ctr, unsigned total, int *s_flag)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(ctr, 1u);
+        const int last = (prev + 1u == total);
+        if (last) __threadfence();
+        *s_flag = last;
+    }
+    __syncthreads();
+    const bool last = *s_flag != 0;
+    __syncthreads();
+    return last;
+}
+
+// ---------------------------------------------------------------- K_INDEX
+__device__ __forceinline__ int grid_cell(const CamDev &C, float iw, float ih, float x, float y)
+{
+    const int cx = f2i(roundf(fmul(fsub(x, C.minx), iw)));
+    const int cy = f2i(roundf(fmul(fsub(y, C.miny), ih)));
+    if (cx < 0 || cx >= FT_GRID_COLS || cy < 0 || cy >= FT_GRID_ROWS) return -1;
+    return cy * FT_GRID_COLS + cx;
+}
+
+__device__ void index_item(const BatchHeader &B, const FrameDev &F, int cam, SmemGrid &G,
+                           int *s_flag)
+{
+    const CamDev &C = F.cam[cam];
+    const int tid = threadIdx.x;
+    const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
+    const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
+    for (int c = tid; c < kCells; c += kThreads) G.cnt[c] = 0;
+    __syncthreads();
+    for (int k = tid; k < C.nk; k += kThreads) {
+        const int c = grid_cell(C, iw, ih, __ldg(C.kx + k), __ldg(C.ky + k));
+        if (c >= 0) atomicAdd(&G.cnt[c], 1);
+    }
+    __syncthreads();
+    const int total = block_scan(G.cnt, G.cnt, kCells, G.warp_sums);
+    for (int c = tid; c < kCells; c += kThreads) C.cell_ptr[c] = G.cnt[c];
+    if (tid == 0) C.cell_ptr[kCells] = total;
+    __syncthreads();
+    for (int k = tid; k < C.nk; k += kThreads) {
+        const float x = __ldg(C.kx + k), y = __ldg(C.ky + k);
+        const int c = grid_cell(C, iw, ih, x, y);
+        if (c >= 0) {
+            const int pos = atomicAdd(&G.cnt[c], 1);
+            const int oct = (int)__ldg(C.koct + k) & 0xff;
+            const int tk = C.taken ? (__ldg(C.taken + k) != 0) : 0;
+            C.gkp[pos] = make_float4(x, y, __int_as_float(k), __int_as_float(oct | (tk << 8)));
+            C.gdesc[2 * pos] = __ldg(C.kdesc + 2 * k);
+            C.gdesc[2 * pos + 1] = __ldg(C.kdesc + 2 * k + 1);
+        }
+        C.owner[k] = ~0ull;
+    }
+    signal_count(&F.ctr[C_INDEX_DONE], (unsigned)F.n_index_items, s_flag);
+}
+
+// ---------------------------------------------------------------- K_STEREO, pinhole
+__device__ __forceinline__ int floor_row(float y) { return f2i(floorf(y)); }
+
+// Row that owns a left keypoint (rows outside the image go to the edge strips).
+__device__ __forceinline__ int own_row(float y, int H)
+{
+    if (y < 0.0f) return 0;
+    return min(f2i(y), H - 1);
+}
+
+// Does right keypoint (y, oct) list image row `row` (band floor(y - r) ..
+// ceil(y + r), r = 2 * scale[oct], clamped to the image)?
+__device__ __forceinline__ bool band_has(const DevParams &P, float y, int oct, int row, int H)
+{
+    const float r = P.band_r[clampi(oct, 0, P.nlevels - 1)];
+    const int lo = max(f2i(floorf(fsub(y, r))), 0);
+    const int hi = min(f2i(ceilf(fadd(y, r))), H - 1);
+    return lo <= row && row <= hi;
+}
+
+__device__ void stereo_one(const BatchHeader &B, const FrameDev &F, SmemStereo &S, int i,
+                           bool staged, int w_lo, int lane, int warp)
+{
+    const DevParams &P = B.p;
+    const float xi = __ldg(F.lx + i), yi = __ldg(F.ly + i);
+    const int oi = __ldg(F.loct + i);
+    const float maxD = fdiv(F.bf, F.b);
+    int best = -1, dist = -1, shift = FT_NO_SHIFT, sadb = -1;
+    float ur = -1.0f, dep = -1.0f;
+
+    // a2: best (distance, index) over the band candidates
+    unsigned key = kNoKey;
+    if (!(yi < 0.0f)) {
+        const int row = f2i(yi);
+        if (row < F.H) {
+            const float minU = fsub(xi, maxD);
+            const float maxU = fsub(xi, 0.0f);
+            if (!(maxU < 0.0f)) {
+                const uint4 a0 = __ldg(F.ldesc + 2 * i), a1 = __ldg(F.ldesc + 2 * i + 1);
+                if (staged) {
+                    const int e0 = S.rowptr[row - P.halo - w_lo];
+                    const int e1 = S.rowptr[row + P.halo - w_lo + 1];
+                    for (int e = e0 + lane; e < e1; e += 32) {
+                        const int oj = S.soct[e];
+                        if (oj < oi - 1 || oj > oi + 1) continue;
+                        if (!band_has(P, S.sy[e], oj, row, F.H)) continue;
+                        const float xj = S.sx[e];
+                        if (xj < minU || xj > maxU) continue;
+                        const int d = ham8(a0, a1, S.sdesc[2 * e], S.sdesc[2 * e + 1]);
+                        key = min(key, ((unsigned)d << 20) | (unsigned)S.sj[e]);
+                    }
+                } else {
+                    for (int j = lane; j < F.nr; j += 32) {
+                        const int oj = __ldg(F.roct + j);
+                        if (oj < oi - 1 || oj > oi + 1) continue;
+                        if (!band_has(P, __ldg(F.ry + j), oj, row, F.H)) continue;
+                        const float xj = __ldg(F.rx + j);
+                        if (xj < minU || xj > maxU) continue;
+                        const int d = ham8(a0, a1, __ldg(F.rdesc + 2 * j), __ldg(F.rdesc + 2 * j + 1));
+                        key = min(key, ((unsigned)d << 20) | (unsigned)j);
+                    }
+                }
+            }
+        }
+    }
+    key = __reduce_min_sync(kFull, key);
+    if (key != kNoKey) {
+        dist = (int)(key >> 20);
+        if (dist < P.th_stereo) best = (int)(key & 0xfffffu);
+    }
+
+    // a3: SAD over the shifts, a4: parabola, disparity, depth
+    if (best >= 0) {
+        const int l = clampi(oi, 0, P.nlevels - 1);
+        const float xj = __ldg(F.rx + best);
+        const int ul = f2i(roundf(fmul(xi, P.isc[l])));
+        const int vl = f2i(roundf(fmul(yi, P.isc[l])));
+        const int ur0 = f2i(roundf(fmul(xj, P.isc[l])));
+        const bool inside = vl - kW >= 0 && vl + kW <= F.lh[l] - 1 && vl + kW <= F.rh[l] - 1 &&
+                            ul - kW >= 0 && ul + kW <= F.lw[l] - 1 &&
+                            ur0 - kL - kW >= 0 && ur0 + kL + kW <= F.rw[l] - 1;
+        if (inside) {
+            const uint8_t *IL = F.pyrL[l] + (size_t)(vl - kW) * F.lp[l] + (ul - kW);
+            const uint8_t *IR = F.pyrR[l] + (size_t)(vl - kW) * F.rp[l] + (ur0 - kL - kW);
+            uint8_t *pl = S.patchL[warp];
+            uint8_t *pr = S.patchR[warp];
+            for (int t = lane; t < kPatchL + kPatchR; t += 32) {
+                if (t < kPatchL) {
+                    const int dy = t / (2 * kW + 1), dx = t - dy * (2 * kW + 1);
+                    pl[t] = __ldg(IL + (size_t)dy * F.lp[l] + dx);
+                } else {
+                    const int u = t - kPatchL;
+                    const int dy = u / kStripW, dx = u - dy * kStripW;
+                    pr[u] = __ldg(IR + (size_t)dy * F.rp[l] + dx);
+                }
+            }
+            if (lane < kShifts) S.sad[warp][lane] = 0;
+            __syncwarp();
+            const int cL = pl[kW * (2 * kW + 1) + kW];
+            for (int q = lane; q < kShifts * (2 * kW + 1); q += 32) {
+                const int k = q / (2 * kW + 1), dy = q - k * (2 * kW + 1);
+                const int cR = pr[kW * kStripW + k + kW];
+                const uint8_t *rl = pl + dy * (2 * kW + 1);
+                const uint8_t *rr = pr + dy * kStripW + k;
+                int s = 0;
+#pragma unroll
+                for (int dx = 0; dx < 2 * kW + 1; ++dx) s += abs((rl[dx] - cL) - (rr[dx] - cR));
+                atomicAdd(&S.sad[warp][k], s);
+            }
+            __syncwarp();
+            unsigned kk = lane < kShifts ? (((unsigned)S.sad[warp][lane] << 4) | (unsigned)lane) : kNoKey;
+            kk = __reduce_min_sync(kFull, kk);
+            const int kb = (int)(kk & 15u);
+            shift = kb - kL;
+            if (kb != 0 && kb != 2 * kL) {
+                const float d1 = (float)S.sad[warp][kb - 1];
+                const float d2 = (float)S.sad[warp][kb];
+                const float d3 = (float)S.sad[warp][kb + 1];
+                const float delta = fdiv(fsub(d1, d3), fmul(2.0f, fsub(fadd(d1, d3), fmul(2.0f, d2))));
+                if (!(delta < -1.0f || delta > 1.0f)) {
+                    float bestuR = fmul(P.sc[l], fadd(fadd((float)ur0, (float)shift), delta));
+                    float disparity = fsub(xi, bestuR);
+                    if (disparity >= 0.0f && disparity < maxD) {
+                        if (disparity <= 0.0f) {
+                            disparity = 0.01f;
+                            bestuR = fsub(xi, 0.01f);
+                        }
+                        dep = fdiv(F.bf, disparity);
+                        ur = bestuR;
+                        sadb = S.sad[warp][kb];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        F.best_r[i] = best;
+        F.dist[i] = dist;
+        F.sad_shift[i] = shift;
+        F.sad_best[i] = sadb;
+        F.u_right[i] = ur;
+        F.depth[i] = dep;
+    }
+}
+
+// warp 0: bin of the k-th smallest value (0-based) of a 256-bin histogram
+__device__ void select_bin(const int *hist, int k, int *bin, int *before)
+{
+    const int lane = threadIdx.x & 31;
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += hist[lane * 8 + j];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - s;
+    const unsigned m = __ballot_sync(kFull, excl <= k && k < incl);
+    if (lane == __ffs(m) - 1) {
+        int c = excl;
+        for (int j = 0; j < 8; ++j) {
+            const int h = hist[lane * 8 + j];
+            if (k < c + h) {
+                *bin = lane * 8 + j;
+                *before = c;
+                break;
+            }
+            c += h;
+        }
+    }
+}
+
+// a5: median of the frame's accepted SAD minima (radix select on 2 x 8 bits),
+// then drop matches with SAD >= factor * median.
+__device__ void median_reject(const FrameDev &F, const DevParams &P, SmemMedian &M)
+{
+    const int tid = threadIdx.x;
+    for (int b = tid; b < 256; b += kThreads) M.hist[b] = 0;
+    if (tid == 0) M.count = 0;
+    __syncthreads();
+    int local = 0;
+    for (int i = tid; i < F.nl; i += kThreads) {
+        const int v = __ldcg(F.sad_best + i);
+        if (v >= 0) {
+            atomicAdd(&M.hist[(v >> 8) & 255], 1);
+            ++local;
+        }
+    }
+    local = __reduce_add_sync(kFull, local);
+    if ((tid & 31) == 0 && local) atomicAdd(&M.count, local);
+    __syncthreads();
+    const int n = M.count;
+    if (n == 0) return;
+    const int k = n / 2;
+    if (tid < 32) select_bin(M.hist, k, &M.bin, &M.before);
+    __syncthreads();
+    const int hi = M.bin;
+    const int k2 = k - M.before;
+    __syncthreads();
+    for (int b = tid; b < 256; b += kThreads) M.hist[b] = 0;
+    __syncthreads();
+    for (int i = tid; i < F.nl; i += kThreads) {
+        const int v = __ldcg(F.sad_best + i);
+        if (v >= 0 && ((v >> 8) & 255) == hi) atomicAdd(&M.hist[v & 255], 1);
+    }
+    __syncthreads();
+    if (tid < 32) select_bin(M.hist, k2, &M.bin, &M.before);
+    __syncthreads();
+    const int median = (hi << 8) | M.bin;
+    const float th = fmul(P.median_factor, (float)median);
+    for (int i = tid; i < F.nl; i += kThreads) {
+        const int v = __ldcg(F.sad_best + i);
+        if (v >= 0 && (float)v >= th) {
+            F.u_right[i] = -1.0f;
+            F.depth[i] = -1.0f;
+        }
+    }
+}
+
+__device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int strip, Smem &U,
+                                    int *s_flag)
+{
+    SmemStereo &S = U.s;
+    const DevParams &P = B.p;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int H = F.H;
+    const int r_lo = strip * F.strip_rows;
+    const int r_hi = min(H, r_lo + F.strip_rows);
+    const int w_lo = r_lo - P.halo;
+    const int nrows = (r_hi - r_lo) + 2 * P.halo;   // <= kRowCap (host guarantees)
+
+    // stage the right keypoints whose floor(y) row falls in the window, by row
+    for (int r = tid; r <= nrows; r += kThreads) S.rowptr[r] = 0;
+    __syncthreads();
+    for (int j = tid; j < F.nr; j += kThreads) {
+        const int rel = floor_row(__ldg(F.ry + j)) - w_lo;
+        if (rel >= 0 && rel < nrows) atomicAdd(&S.rowptr[rel], 1);
+    }
+    __syncthreads();
+    const int total = block_scan(S.rowptr, S.rowptr, nrows + 1, S.warp_sums);
+    const bool staged = total <= kStageCap;
+    if (staged) {
+        for (int r = tid; r <= nrows; r += kThreads) S.rowfill[r] = S.rowptr[r];
+        __syncthreads();
+        for (int j = tid; j < F.nr; j += kThreads) {
+            const float y = __ldg(F.ry + j);
+            const int rel = floor_row(y) - w_lo;
+            if (rel >= 0 && rel < nrows) {
+                const int pos = atomicAdd(&S.rowfill[rel], 1);
+                S.sx[pos] = __ldg(F.rx + j);
+                S.sy[pos] = y;
+                S.soct[pos] = __ldg(F.roct + j);
+                S.sj[pos] = j;
+                S.sdesc[2 * pos] = __ldg(F.rdesc + 2 * j);
+                S.sdesc[2 * pos + 1] = __ldg(F.rdesc + 2 * j + 1);
+            }
+        }
+    }
+    __syncthreads();
+
+    // one warp per left keypoint of this strip
+    for (int base = warp * 32; base < F.nl; base += kThreads) {
+        const int i = base + lane;
+        bool mine = false;
+        if (i < F.nl) {
+            const int orow = own_row(__ldg(F.ly + i), H);
+            mine = orow >= r_lo && orow < r_hi;
+        }
+        unsigned mask = __ballot_sync(kFull, mine);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            stereo_one(B, F, S, base + src, staged, w_lo, lane, warp);
+        }
+    }
+
+    if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
+        median_reject(F, P, U.m);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && !(B.debug_flags & kDebugWithholdStereoReady))
+            atomicExch(&F.ctr[C_STEREO_READY], 1u);
+    }
+}
+
+// ---------------------------------------------------------------- K_STEREO, fisheye
+__device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U,
+                                    int *s_flag)
+{
+    SmemFish &S = U.f;
+    const DevParams &P = B.p;
+    const int tid = threadIdx.x;
+    constexpr int Q = 2;            // left keypoints per thread (fisheye_tile <= 512)
+    int idx[Q];
+    bool act[Q];
+    uint4 a0[Q], a1[Q];
+    unsigned best[Q], second[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        idx[q] = tile * F.fisheye_tile + q * kThreads + tid;
+        act[q] = false;
+        best[q] = second[q] = kNoKey;
+        if (q * kThreads < F.fisheye_tile && idx[q] < F.nl) {
+            const float x = __ldg(F.lx + idx[q]);
+            act[q] = x >= F.lap_l0 && x <= F.lap_l1;
+            if (act[q]) {
+                a0[q] = __ldg(F.ldesc + 2 * idx[q]);
+                a1[q] = __ldg(F.ldesc + 2 * idx[q] + 1);
+            }
+        }
+    }
+    const bool any = __syncthreads_or(act[0] || act[1]);
+    if (any) {
+        for (int c0 = 0; c0 < F.nr; c0 += kFishChunk) {
+            if (tid == 0) S.count = 0;
+            __syncthreads();
+            const int c1 = min(F.nr, c0 + kFishChunk);
+            for (int j = c0 + tid; j < c1; j += kThreads) {
+                const float x = __ldg(F.rx + j);
+                if (x >= F.lap_r0 && x <= F.lap_r1) {
+                    const int pos = atomicAdd(&S.count, 1);
+                    S.idx[pos] = j;
+                    S.desc[2 * pos] = __ldg(F.rdesc + 2 * j);
+                    S.desc[2 * pos + 1] = __ldg(F.rdesc + 2 * j + 1);
+                }
+            }
+            __syncthreads();
+            const int cnt = S.count;
+            if (act[0] || act[1]) {
+                for (int e = 0; e < cnt; ++e) {
+                    const uint4 b0 = S.desc[2 * e], b1 = S.desc[2 * e + 1];
+                    const unsigned j = (unsigned)S.idx[e];
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        if (act[q]) top2_push(((unsigned)ham8(a0[q], a1[q], b0, b1) << 20) | j, best[q], second[q]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (q * kThreads < F.fisheye_tile && idx[q] < F.nl) {
+            int r = -1, d1 = -1, d2 = -1;
+            if (act[q] && best[q] != kNoKey) {
+                d1 = (int)(best[q] >> 20);
+                d2 = second[q] != kNoKey ? (int)(second[q] >> 20) : 256;
+                if ((float)d1 < fmul(P.fisheye_ratio, (float)d2)) r = (int)(best[q] & 0xfffffu);
+            }
+            F.r_idx[idx[q]] = r;
+            F.fd1[idx[q]] = d1;
+            F.fd2[idx[q]] = d2;
+        }
+    }
+    if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
+        if (tid == 0 && !(B.debug_flags & kDebugWithholdStereoReady))
+            atomicExch(&F.ctr[C_STEREO_READY], 1u);
+    }
+}
+
+// ---------------------------------------------------------------- K_SEARCH
+__device__ __forceinline__ void transform(const float *pose, float4 p, float &x, float &y, float &z)
+{
+    x = fadd(fadd(fadd(fmul(pose[0], p.x), fmul(pose[1], p.y)), fmul(pose[2], p.z)), pose[9]);
+    y = fadd(fadd(fadd(fmul(pose[3], p.x), fmul(pose[4], p.y)), fmul(pose[5], p.z)), pose[10]);
+    z = fadd(fadd(fadd(fmul(pose[6], p.x), fmul(pose[7], p.y)), fmul(pose[8], p.z)), pose[11]);
+}
+
+// distance window, viewing cosine, predicted level
+__device__ __forceinline__ bool distance_scale(const DevParams &P, const float *O, float4 pos,
+                                               float4 nrm, float &vc, int &level)
+{
+    const float px = fsub(pos.x, O[0]), py = fsub(pos.y, O[1]), pz = fsub(pos.z, O[2]);
+    const float dist = fsqrt(fadd(fadd(fmul(px, px), fmul(py, py)), fmul(pz, pz)));
+    const float maxDistance = fmul(P.dist_hi, nrm.w);
+    const float minDistance = fmul(P.dist_lo, pos.w);
+    if (dist < minDistance || dist > maxDistance) return false;
+    vc = fdiv(fadd(fadd(fmul(px, nrm.x), fmul(py, nrm.y)), fmul(pz, nrm.z)), dist);
+    if (vc < P.view_cos_min) return false;
+    const float ratio = fdiv(nrm.w, dist);
+    level = P.nlevels - 1;
+    for (int l = 0; l < P.nlevels; ++l) {
+        if (P.sc[l] >= ratio) {
+            level = l;
+            break;
+        }
+    }
+    return true;
+}
+
+__device__ bool project(const DevParams &P, const CamDev &C, const float *pose, float4 pos,
+                        float4 nrm, float &u, float &v, float &ur, float &vc, int &level)
+{
+    float x, y, z;
+    transform(pose, pos, x, y, z);
+    if (!(z > 0.0f)) return false;
+    if (C.model == FT_CAMERA_PINHOLE) {
+        const float invz = fdiv(1.0f, z);
+        u = fadd(fmul(fmul(C.fx, x), invz), C.cx);
+        v = fadd(fmul(fmul(C.fy, y), invz), C.cy);
+        if (u < C.minx || u > C.maxx) return false;
+        if (v < C.miny || v > C.maxy) return false;
+        ur = fsub(u, fmul(C.bf, invz));
+    } else {
+        const float rho = fsqrt(fadd(fmul(x, x), fmul(y, y)));
+        if (rho == 0.0f) {
+            u = C.cx;
+            v = C.cy;
+        } else {
+            const float theta = atan2_pos(rho, z);
+            const float t2 = fmul(theta, theta);
+            float poly = C.k[3];
+            poly = fadd(C.k[2], fmul(t2, poly));
+            poly = fadd(C.k[1], fmul(t2, poly));
+            poly = fadd(C.k[0], fmul(t2, poly));
+            poly = fadd(1.0f, fmul(t2, poly));
+            const float thetad = fmul(theta, poly);
+            u = fadd(fdiv(fmul(fmul(C.fx, thetad), x), rho), C.cx);
+            v = fadd(fdiv(fmul(fmul(C.fy, thetad), y), rho), C.cy);
+        }
+        if (u < C.minx || u > C.maxx) return false;
+        if (v < C.miny || v > C.maxy) return false;
+        ur = -1.0f;
+    }
+    return distance_scale(P, C.O, pos, nrm, vc, level);
+}
+
+__device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C,
+                             const float *pose, int m)
+{
+    int lvl = -1, d1 = -1, d2 = -1, kp = -1;
+    float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool skipped = F.skip != nullptr && __ldg(F.skip + m) != 0;
+    if (!skipped) {
+        const float4 pos = __ldg(F.pos + m), nrm = __ldg(F.nrm + m);
+        float u, v, ur, vc;
+        int level;
+        if (project(P, C, pose, pos, nrm, u, v, ur, vc, level)) {
+            lvl = level;
+            pj = make_float4(u, v, ur, vc);
+            float r = (vc > P.view_cos_narrow) ? P.radius_narrow : P.radius_wide;
+            r = fmul(r, P.search_th);
+            r = fmul(r, P.sc[level]);
+            const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
+            const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
+            const float du = fsub(u, C.minx), dv = fsub(v, C.miny);
+            const int x0 = max(f2i(floorf(fmul(fsub(du, r), iw))), 0);
+            const int x1 = min(f2i(ceilf(fmul(fadd(du, r), iw))), FT_GRID_COLS - 1);
+            const int y0 = max(f2i(floorf(fmul(fsub(dv, r), ih))), 0);
+            const int y1 = min(f2i(ceilf(fmul(fadd(dv, r), ih))), FT_GRID_ROWS - 1);
+            if (!(x0 >= FT_GRID_COLS || x1 < 0 || y0 >= FT_GRID_ROWS || y1 < 0)) {
+                const uint4 q0 = __ldg(F.mdesc + 2 * m), q1 = __ldg(F.mdesc + 2 * m + 1);
+                const bool check_ur = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr;
+                unsigned best = kNoKey, second = kNoKey;
+                for (int cy = y0; cy <= y1; ++cy) {
+                    const int e0 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x0);
+                    const int e1 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x1 + 1);
+                    for (int e = e0; e < e1; ++e) {
+                        const float4 g = __ldcg(C.gkp + e);
+                        const int flags = __float_as_int(g.w);
+                        const int oct = (int)(int8_t)(flags & 0xff);
+                        if (oct < level - 1 || oct > level) continue;
+                        const float distx = fsub(g.x, u), disty = fsub(g.y, v);
+                        if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
+                        if (flags >> 8) continue;
+                        const int k = __float_as_int(g.z);
+                        if (check_ur) {
+                            const float urk = __ldcg(F.u_right_in + k);
+                            if (urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
+                        }
+                        const int d = ham8(q0, q1, __ldcg(C.gdesc + 2 * e), __ldcg(C.gdesc + 2 * e + 1));
+                        top2_push(((unsigned)d << 20) | (unsigned)k, best, second);
+                    }
+                }
+                if (best != kNoKey) {
+                    d1 = (int)(best >> 20);
+                    d2 = second != kNoKey ? (int)(second >> 20) : 256;
+                    if (d1 <= P.th_search) {
+                        const int k1 = (int)(best & 0xfffffu);
+                        const int oct1 = __ldg(C.koct + k1);
+                        const int oct2 = second != kNoKey ? (int)__ldg(C.koct + (second & 0xfffffu)) : -1;
+                        const bool ratio = P.ratio_any_octave || oct1 == oct2;
+                        if (!(ratio && (float)d1 > fmul(P.nn_ratio, (float)d2))) {
+                            atomicMin(C.owner + k1, ((unsigned long long)d1 << 32) | (unsigned)m);
+                            kp = k1;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    C.level[m] = (int8_t)lvl;
+    if (C.proj) C.proj[m] = pj;
+    C.mp_d1[m] = d1;
+    C.mp_d2[m] = d2;
+    C.mp_kp[m] = kp;
+}
+
+__device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U, int *s_flag)
+{
+    const int cam = tile < F.n_search_items[0] ? 0 : 1;
+    const int t = cam ? tile - F.n_search_items[0] : tile;
+    bool ok = true;
+    if (F.wait_stereo) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
+    if (ok) ok = wait_geq(B, &F.ctr[C_INDEX_DONE], (unsigned)F.n_index_items, s_flag);
+    if (ok) {
+        const CamDev &C = F.cam[cam];
+        float *pose = U.q.pose;
+        const int tid = threadIdx.x;
+        if (tid < 12) {
+            const CamDev &L = F.cam[0];
+            float v;
+            if (cam == 0 || F.camera == FT_CAMERA_PINHOLE) {
+                v = tid < 9 ? L.R[tid] : L.t[tid - 9];
+            } else if (tid < 9) {      // right camera: R_rw = R_rl * R_lw
+                const int i = tid / 3, j = tid % 3;
+                v = fadd(fadd(fmul(F.R_rl[3 * i], L.R[j]), fmul(F.R_rl[3 * i + 1], L.R[3 + j])),
+                         fmul(F.R_rl[3 * i + 2], L.R[6 + j]));
+            } else {                   // t_rw = R_rl * t_lw + t_rl
+                const int i = tid - 9;
+                v = fadd(fadd(fadd(fmul(F.R_rl[3 * i], L.t[0]), fmul(F.R_rl[3 * i + 1], L.t[1])),
+                              fmul(F.R_rl[3 * i + 2], L.t[2])),
+                         F.t_rl[i]);
+            }
+            pose[tid] = v;
+        }
+        __syncthreads();
+        const int m0 = t * F.search_tile;
+        const int m1 = min(F.nm, m0 + F.search_tile);
+        for (int m = m0 + tid; m < m1; m += kThreads) search_point(B.p, F, C, pose, m);
+    } else {
+        // the wait ran out (reported in the status word): leave defined outputs
+        const CamDev &C = F.cam[cam];
+        const int m0 = t * F.search_tile;
+        const int m1 = min(F.nm, m0 + F.search_tile);
+        for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) {
+            C.level[m] = -1;
+            if (C.proj) C.proj[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+            C.mp_d1[m] = -1;
+            C.mp_d2[m] = -1;
+            C.mp_kp[m] = -1;
+        }
+    }
+    signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag);
+}
+
+// ---------------------------------------------------------------- K_RESOLVE
+__device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, int *s_flag)
+{
+    const int cam = tile < F.n_resolve_items[0] ? 0 : 1;
+    const int t = cam ? tile - F.n_resolve_items[0] : tile;
+    if (!wait_geq(B, &F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag)) return;
+    const CamDev &C = F.cam[cam];
+    const int i0 = t * F.resolve_tile, i1 = i0 + F.resolve_tile;
+    for (int m = i0 + threadIdx.x; m < min(i1, F.nm); m += kThreads) {
+        const int k = __ldcg(C.mp_kp + m);
+        if (k >= C.nk) {
+            C.mp_kp[m] = -1;                 // never written by a search item
+        } else if (k >= 0) {
+            const unsigned long long own = __ldcg(C.owner + k);
+            if ((unsigned)(own & 0xffffffffull) != (unsigned)m) C.mp_kp[m] = -1;
+        }
+    }
+    for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) {
+        const unsigned long long own = __ldcg(C.owner + k);
+        C.kp_mp[k] = own == ~0ull ? -1 : (int)(own & 0xffffffffull);
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+__global__ void __launch_bounds__(kThreads, 4) ft_fused_kernel(const BatchHeader *__restrict__ hdr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &U = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ int s_item;
+    __shared__ int s_flag;
+    const BatchHeader &B = *hdr;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(B.queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= B.total_items) break;
+        int kind = 0;
+        while (kind < K_KINDS - 1 && item >= B.kind_begin[kind + 1]) ++kind;
+        const int local = item - B.kind_begin[kind];
+        const int *pre = B.prefix + kind * (B.nframes + 1);
+        int lo = 0, hi = B.nframes - 1;          // last frame f with pre[f] <= local
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= local) lo = mid;
+            else hi = mid - 1;
+        }
+        const FrameDev &F = B.frames[lo];
+        const int tile = local - pre[lo];
+        switch (kind) {
+        case K_INDEX: index_item(B, F, tile, U.g, &s_flag); break;
+        case K_STEREO:
+            if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);
+            else stereo_fisheye_item(B, F, tile, U, &s_flag);
+            break;
+        case K_SEARCH: search_item(B, F, tile, U, &s_flag); break;
+        default: resolve_item(B, F, tile, &s_flag); break;
+        }
+    }
+}
+
+}  // namespace
+
+int fused_smem_bytes() { return (int)sizeof(Smem); }
+
+const void *fused_kernel_ptr() { return (const void *)ft_fused_kernel; }
+
+cudaError_t fused_occupancy(int *ctas_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(ft_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, ft_fused_kernel, kThreads,
+                                                         sizeof(Smem));
+}
+
+cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stream)
+{
+    ft_fused_kernel<<<grid, kThreads, sizeof(Smem), stream>>>(dev_hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace ft

@@ -1,0 +1,83 @@
+"""CPU checks of the C ABI boundary: the library builds for sm_103a, loads
+without a GPU, exports every entry point that include/fasttrack.h declares,
+its ctypes mirror has the C struct sizes, and its default parameters are the
+readings the oracle uses.  No compute call runs here."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fasttrack.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_10757_gb300 import build
+    build.build()
+    from paper_2509_10757_gb300 import _lib as L
+    L.load()
+    return L
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ft_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("ft_create", "ft_destroy", "ft_last_error", "ft_stereo_match_pinhole",
+              "ft_stereo_match_fisheye", "ft_search_local_points", "ft_track_batch"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = lib.load()
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+    bound = {name for name, _, _ in lib.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_ctypes_struct_sizes_match_c(lib):
+    structs = ["ft_params", "ft_keypoints", "ft_pyramid", "ft_pinhole", "ft_kb8", "ft_fisheye_rig",
+               "ft_pose", "ft_map_view", "ft_stereo_frame", "ft_stereo_out", "ft_fisheye_out",
+               "ft_search_cam_out", "ft_search_out", "ft_frame_view", "ft_frame_job", "ft_batch",
+               "ft_ctx_desc", "ft_tuning"]
+    prog = "#include <stdio.h>\n#include \"fasttrack.h\"\nint main(void){\n"
+    prog += "".join(f'printf("%zu\\n", sizeof({s}));\n' for s in structs) + "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "sz.c")
+        exe = os.path.join(d, "sz")
+        open(src, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), src, "-o", exe], check=True)
+        sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    for s, n in zip(structs, sizes):
+        assert C.sizeof(getattr(lib, s)) == n, s
+
+
+def test_default_params_are_the_oracle_readings(lib):
+    from paper_2509_10757_gb300.scenes import DEFAULT_PARAMS
+    p = lib.default_params()
+    for name, v in DEFAULT_PARAMS.items():
+        if name in ("sad_w", "sad_L"):
+            continue
+        got = getattr(p, name)
+        assert np.float32(got) == np.float32(v), name
+
+
+def test_create_fails_cleanly_without_a_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = C.c_void_p()
+    st = lib.load().ft_create(C.byref(ctx), None)
+    assert st in (lib.FT_ECUDA, lib.FT_EINVAL)
+    assert not ctx.value
+    assert lib.last_error()

@@ -1,0 +1,344 @@
+"""GPU parity: libfasttrack.so (through its C ABI) against the CPU oracle,
+element by element, on seeded synthetic frames.  Sizes span several work
+items with ragged tails (15 stereo strips of 32 rows at 480 rows, search
+tiles of 512 map points with a partial last tile, fisheye tiles of 256 left
+keypoints with a partial last tile)."""
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2509_10757_gb300 import scenes
+from tests.gpu_common import (assert_fisheye_equal, assert_search_equal, assert_stereo_equal)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2509_10757_gb300 import build
+    build.build()
+    from paper_2509_10757_gb300 import _lib as L
+    return L
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    from paper_2509_10757_gb300.batch import Context
+    c = Context(arena_bytes=1 << 30, max_frames=256)
+    yield c
+    c.close()
+
+
+def _params(lib, overrides=None):
+    return lib.default_params(overrides)
+
+
+def _oracle_params(overrides=None):
+    p = dict(scenes.DEFAULT_PARAMS)
+    p.update(overrides or {})
+    return p
+
+
+def check_frame(pb, f, params=None, what=""):
+    fr = pb.frames[f]
+    out = pb.outputs(f)
+    st, se = orc.track_frame(_oracle_params(params), fr)
+    where = f"{what} frame {f} ({fr.camera}): "
+    if fr.camera == "pinhole":
+        assert_stereo_equal(out, st, where)
+        assert_search_equal(out, se, "l", None, where)
+    else:
+        assert_fisheye_equal(out, st, where)
+        assert_search_equal(out, se, "l", "l", where)
+        assert_search_equal(out, se, "r", "r", where)
+    return out, st, se
+
+
+def run_per_frame(ctx, frames, params=None, lib=None):
+    from paper_2509_10757_gb300.batch import PackedBatch, run_search, run_stereo
+    pb = PackedBatch(frames)
+    pb.upload()
+    pb.clear_outputs()
+    p = lib.default_params(params) if lib is not None else None
+    for f in range(len(frames)):
+        run_stereo(ctx, pb, f, p)
+        run_search(ctx, pb, f, p)
+    pb.download()
+    assert ctx.sync_status() == 0
+    return pb
+
+
+def run_fused(ctx, frames, params=None, lib=None, stage=False):
+    from paper_2509_10757_gb300.batch import PackedBatch, run_batch
+    pb = PackedBatch(frames)
+    if not stage:
+        pb.upload()
+    pb.clear_outputs()
+    p = lib.default_params(params) if lib is not None else None
+    run_batch(ctx, pb, p, stage=stage)
+    if stage:
+        torch.cuda.synchronize()
+    else:
+        pb.download()
+    assert ctx.sync_status() == 0
+    return pb
+
+
+# ---------------------------------------------------------------- single frames
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pinhole_frame_per_call(ctx, lib, seed):
+    pb = run_per_frame(ctx, [scenes.single_pinhole(seed)], lib=lib)
+    out, st, _ = check_frame(pb, 0, what="per-call")
+    assert (st["u_right"] >= 0).sum() > 300 and (out["mp_kp_l"] >= 0).sum() > 100
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fisheye_frame_per_call(ctx, lib, seed):
+    pb = run_per_frame(ctx, [scenes.fisheye_frame(seed)], lib=lib)
+    out, st, _ = check_frame(pb, 0, what="per-call")
+    assert (st["r_idx"] >= 0).sum() > 300
+
+
+def test_search_without_stereo_check(ctx, lib):
+    from paper_2509_10757_gb300.batch import PackedBatch, run_search
+    fr = scenes.single_pinhole(5)
+    pb = PackedBatch([fr])
+    pb.upload()
+    pb.clear_outputs()
+    run_search(ctx, pb, 0, u_right=False)
+    pb.download()
+    se = orc.search_frame(_oracle_params(), fr, None)
+    assert_search_equal(pb.outputs(0), se, "l")
+
+
+# ---------------------------------------------------------------- fused batch
+def test_batch_mixed_shapes_matches_oracle(ctx, lib):
+    frames = [scenes.served_stream_frame(0, s) for s in range(8)]
+    assert {f.camera for f in frames} == {"pinhole", "fisheye"}
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="batch")
+
+
+def test_batch_equals_per_call(ctx, lib):
+    frames = [scenes.single_pinhole(3), scenes.fisheye_frame(3), scenes.single_pinhole(4)]
+    a = run_per_frame(ctx, frames)
+    b = run_fused(ctx, frames)
+    assert np.array_equal(a.host_out.numpy(), b.host_out.numpy())
+
+
+def test_batch_64_frames_full_size(ctx, lib):
+    frames = scenes.pinhole_batch(seed=0, n_frames=64)
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="64-frame batch")
+
+
+def test_fisheye_batch_full_size(ctx, lib):
+    frames = scenes.fisheye_batch(seed=0, n_frames=8)
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="fisheye batch")
+
+
+def test_stress_frames(ctx, lib):
+    frames = scenes.stress_batch(seed=0, n_frames=2, n_map=100_000)
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="1080p stress")
+
+
+@pytest.mark.parametrize("overrides", [{"search_th": 2.0}, {"ratio_any_octave": 1},
+                                       {"th_stereo": 40, "th_search": 60}])
+def test_parameter_variants(ctx, lib, overrides):
+    frames = [scenes.single_pinhole(6), scenes.fisheye_frame(6)]
+    pb = run_fused(ctx, frames, overrides, lib)
+    for f in range(len(frames)):
+        check_frame(pb, f, overrides, what=str(overrides))
+
+
+# ---------------------------------------------------------------- edge cases
+def _shrink(fr, nl=None, nr=None, m=None):
+    fr = dataclasses.replace(fr)
+    def cut(k, n):
+        return scenes.Keypoints(k.x[:n].copy(), k.y[:n].copy(), k.oct[:n].copy(), k.desc[:n].copy())
+    if nl is not None:
+        fr.left = cut(fr.left, nl)
+        fr.taken_l = fr.taken_l[:nl].copy()
+    if nr is not None:
+        fr.right = cut(fr.right, nr)
+        if fr.taken_r is not None:
+            fr.taken_r = fr.taken_r[:nr].copy()
+    if m is not None:
+        fr.map = scenes.LocalMap(fr.map.pos[:m].copy(), fr.map.nrm[:m].copy(),
+                                 fr.map.desc[:m].copy(), fr.map.skip[:m].copy())
+    return fr
+
+
+def test_empty_and_single_inputs(ctx, lib):
+    p, q = scenes.single_pinhole(7), scenes.fisheye_frame(7)
+    frames = [_shrink(p, nl=0), _shrink(p, nr=0), _shrink(p, m=0), _shrink(p, nl=1, nr=1, m=1),
+              _shrink(q, nl=0), _shrink(q, nr=0), _shrink(q, m=0), _shrink(q, nl=1, nr=1, m=1)]
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="edge")
+    pb2 = run_per_frame(ctx, frames)
+    assert np.array_equal(pb.host_out.numpy(), pb2.host_out.numpy())
+
+
+def test_all_equal_descriptors_break_ties_by_index(ctx, lib):
+    p, q = scenes.single_pinhole(8), scenes.fisheye_frame(8)
+    for fr in (p, q):
+        d = fr.left.desc[0].copy()
+        fr.left.desc[:] = d
+        fr.right.desc[:] = d
+        fr.map.desc[:] = d
+    pb = run_fused(ctx, [p, q])
+    check_frame(pb, 0, what="ties")
+    check_frame(pb, 1, what="ties")
+
+
+def test_keypoints_on_image_borders(ctx, lib):
+    fr = scenes.single_pinhole(9)
+    W, H = fr.cam.width, fr.cam.height
+    n = fr.left.n
+    xs = np.array([0, W - 1, 0, W - 1, 5, W - 6, 0.5, W - 0.5], np.float32)
+    ys = np.array([0, 0, H - 1, H - 1, 5, H - 6, H - 0.5, 0.49], np.float32)
+    k = len(xs)
+    fr.left.x[:k], fr.left.y[:k] = xs, ys
+    fr.right.x[:k], fr.right.y[:k] = xs - 3, ys
+    fr.right.desc[:k] = fr.left.desc[:k]
+    fr.right.oct[:k] = fr.left.oct[:k]
+    assert n > k
+    pb = run_fused(ctx, [fr])
+    check_frame(pb, 0, what="borders")
+
+
+def test_dense_rows_fall_back_to_scan(ctx, lib):
+    # thousands of right keypoints on a few rows overflow the shared-memory stage
+    fr = scenes.single_pinhole(10)
+    rng = np.random.default_rng(10)
+    m = fr.right.n
+    fr.right.y[:] = np.float32(200.0) + rng.integers(0, 4, m).astype(np.float32)
+    fr.left.y[: fr.left.n // 2] = np.float32(201.0)
+    pb = run_fused(ctx, [fr])
+    check_frame(pb, 0, what="dense rows")
+
+
+# ---------------------------------------------------------------- launch shapes, graphs, host staging
+@pytest.mark.parametrize("tune", [(1, 256, 512, 256), (7, 1024, 256, 512), (200, 512, 512, 4096)])
+def test_tuning_variants_same_results(ctx, lib, tune):
+    from paper_2509_10757_gb300.batch import PackedBatch
+    frames = [scenes.single_pinhole(11), scenes.fisheye_frame(11)]
+    pb = PackedBatch(frames)
+    t = lib.ft_tuning(strip_rows=tune[0], search_tile=tune[1], fisheye_tile=tune[2],
+                      resolve_tile=tune[3], ctas_per_sm=1)
+    b = pb.batch()
+    lib.check(lib.ft_set_tuning(ctx.ptr, C.byref(b), C.byref(t)), "ft_set_tuning")
+    try:
+        out = run_fused(ctx, frames)
+    finally:
+        d = lib.ft_tuning(strip_rows=32, search_tile=512, fisheye_tile=256, resolve_tile=2048,
+                          ctas_per_sm=0)
+        lib.ft_set_tuning(ctx.ptr, C.byref(b), C.byref(d))
+    for f in range(len(frames)):
+        check_frame(out, f, what=f"tuning {tune}")
+
+
+def test_graph_replay_and_host_staging(lib):
+    from paper_2509_10757_gb300.batch import Context
+    frames = [scenes.single_pinhole(12), scenes.fisheye_frame(12), scenes.single_pinhole(13)]
+    g = Context(arena_bytes=256 << 20, max_frames=16, use_graphs=True)
+    try:
+        a = run_fused(g, frames)
+        b = run_fused(g, frames)                 # replay of the cached graph
+        c = run_fused(g, frames, stage=True)     # host -> device -> host in the call
+    finally:
+        g.close()
+    for f in range(len(frames)):
+        check_frame(a, f, what="graph")
+    assert np.array_equal(a.host_out.numpy(), b.host_out.numpy())
+    assert np.array_equal(a.host_out.numpy(), c.host_out.numpy())
+
+
+def test_autotune_and_table_roundtrip(ctx, lib, tmp_path):
+    from paper_2509_10757_gb300.batch import PackedBatch, stream_handle
+    frames = scenes.pinhole_batch(seed=1, n_frames=4)
+    pb = PackedBatch(frames)
+    pb.upload()
+    best = lib.ft_tuning()
+    b = pb.batch()
+    lib.check(lib.ft_autotune(ctx.ptr, stream_handle(), None, C.byref(b), 1, C.byref(best)), "autotune")
+    assert best.strip_rows in (16, 32, 64) and best.search_tile in (256, 512, 1024)
+    path = str(tmp_path / "tuning.txt").encode()
+    lib.check(lib.ft_save_tuning(ctx.ptr, path), "save")
+    lib.check(lib.ft_load_tuning(ctx.ptr, path), "load")
+    got = lib.ft_tuning()
+    lib.check(lib.ft_get_tuning(ctx.ptr, C.byref(b), C.byref(got)), "get")
+    assert (got.strip_rows, got.search_tile, got.fisheye_tile) == (best.strip_rows, best.search_tile,
+                                                                   best.fisheye_tile)
+    out = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(out, f, what="tuned")
+
+
+# ---------------------------------------------------------------- failures reported, never trapped
+def test_bounded_wait_reports_timeout_and_context_recovers(lib):
+    from paper_2509_10757_gb300.batch import Context
+    frames = [scenes.single_pinhole(14)]
+    c = Context(arena_bytes=128 << 20, max_frames=4)
+    try:
+        lib.check(lib.ft_set_debug(c.ptr, 1, 20_000_000), "debug")   # withhold stereo-ready, 20 ms bound
+        from paper_2509_10757_gb300.batch import PackedBatch, run_batch
+        pb = PackedBatch(frames)
+        pb.upload()
+        run_batch(c, pb)
+        assert c.sync_status() == lib.FT_ETIMEOUT
+        lib.check(lib.ft_set_debug(c.ptr, 0, 0), "debug")
+        out = run_fused(c, frames)
+        check_frame(out, 0, what="after timeout")
+    finally:
+        c.close()
+
+
+def test_host_checks_reject_bad_arguments(ctx, lib):
+    from paper_2509_10757_gb300.batch import PackedBatch, stream_handle
+    fr = scenes.single_pinhole(15)
+    pb = PackedBatch([fr])
+    st, out = pb.stereo_frame(0), pb.stereo_out(0)
+    from paper_2509_10757_gb300.batch import pinhole_struct
+    cam = pinhole_struct(fr.cam)
+    call = lambda: lib.ft_stereo_match_pinhole(ctx.ptr, stream_handle(), None, C.byref(cam),
+                                               C.byref(st), C.byref(out))
+    st.left.desc += 1
+    assert call() == lib.FT_EALIGN
+    st.left.desc -= 1
+    st.left.n = -3
+    assert call() == lib.FT_EINVAL
+    st.left.n = fr.left.n
+    out.depth = None
+    assert call() == lib.FT_EINVAL
+    out.depth = pb.pout(0, "depth")
+    st.pyr_left.data[3] = None
+    assert call() == lib.FT_EINVAL
+    assert "level 3" in lib.last_error()
+    st.pyr_left.data[3] = pb.pin_(0, "pyrL3")
+    assert call() == lib.FT_OK
+    assert ctx.sync_status() == 0
+    # 8 frames of 4000 keypoints need about 1.9 MB of grid scratch; the
+    # smallest arena leaves 1 MB
+    big = scenes.pinhole_batch(seed=2, n_frames=8, nl_range=(4000, 4000), m_range=(100, 100))
+    from paper_2509_10757_gb300.batch import Context
+    small = Context(arena_bytes=1, max_frames=8)
+    try:
+        pbb = PackedBatch(big)
+        b = pbb.batch()
+        assert lib.ft_track_batch(small.ptr, stream_handle(), None, C.byref(b)) == lib.FT_ENOMEM
+    finally:
+        small.close()
