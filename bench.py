@@ -195,15 +195,15 @@ def time_oracle(frames, budget_s: float) -> dict:
     p = dict(DEFAULT_PARAMS)
     units, done = 0, 0
     t0 = time.perf_counter()
-    for fr in frames:
+    while time.perf_counter() - t0 < budget_s:
+        fr = frames[done % len(frames)]
         orc.track_frame(p, fr)
         units += fr.left.n + fr.map.n
         done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} of {len(frames)} frames of the batched workload, single thread, {dt:.1f} s"}
+            "sample": f"{done} frames (cycling the {len(frames)} frames of the batched workload), "
+                      f"single thread, {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -240,6 +240,96 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+KIND_NAMES = ("grid", "stereo", "search", "resolve")
+
+
+def trace_summary(recs) -> dict:
+    """Per-kind statistics of one traced launch (times in microseconds)."""
+    if not recs:
+        return {}
+    t0 = min(r.t_start for r in recs)
+    t1 = max(r.t_end for r in recs)
+    out = {"span_us": (t1 - t0) / 1e3, "items": len(recs),
+           "sms": len({r.sm for r in recs})}
+    for k, name in enumerate(KIND_NAMES):
+        rs = [r for r in recs if r.kind == k]
+        if not rs:
+            continue
+        dur = np.array([(r.t_end - r.t_start) / 1e3 for r in rs])
+        wait = np.array([r.wait_ns / 1e3 for r in rs])
+        out[name] = {"count": len(rs), "mean_us": float(dur.mean()), "p90_us": float(np.percentile(dur, 90)),
+                     "mean_wait_us": float(wait.mean()), "busy_cta_us": float((dur - wait).sum()),
+                     "first_start_us": (min(r.t_start for r in rs) - t0) / 1e3,
+                     "last_end_us": (max(r.t_end for r in rs) - t0) / 1e3}
+        # phase marks: mean time from the previous mark (or the start) to each mark
+        phases = []
+        for q in range(4):
+            d = [(r.mark[q] - (r.mark[q - 1] if q and r.mark[q - 1] else r.t_start)) / 1e3
+                 for r in rs if r.mark[q]]
+            phases.append(float(np.mean(d)) if d else None)
+        out[name]["phase_us"] = phases
+    return out
+
+
+def run_trace(args, local_rank):
+    """One traced launch of the batched workload: where the time goes."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300 import build as B
+    from paper_2509_10757_gb300 import scenes
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch
+
+    torch.cuda.set_device(local_rank)
+    B.build()
+    frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
+    pb = PackedBatch(frames)
+    pb.upload()
+    ctx = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES)
+    L.check(ctx.lib.ft_set_trace(ctx.ptr, 1 << 16), "ft_set_trace")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        run_batch(ctx, pb)
+    flush.fill_(1)
+    run_batch(ctx, pb)
+    recs = (L.ft_trace_record * (1 << 16))()
+    n = C.c_int(0)
+    L.check(ctx.lib.ft_read_trace(ctx.ptr, recs, 1 << 16, C.byref(n)), "ft_read_trace")
+    rs = list(recs[:n.value])
+    summ = trace_summary(rs)
+    if args.trace_out:
+        with open(args.trace_out, "w") as f:
+            json.dump([[r.item, r.kind, r.frame, r.sm, r.t_start, r.t_end, r.wait_ns, list(r.mark)]
+                       for r in rs], f)
+    ctx.close()
+    print(json.dumps({"trace": summ, "workload": WORKLOAD}), flush=True)
+
+
+def run_profile(args, local_rank):
+    """Small fixed run for ncu: warm-up launches, then `steps` launches of the
+    fused kernel on the batched workload (default tuning, no graphs)."""
+    import torch
+
+    from paper_2509_10757_gb300 import build as B
+    from paper_2509_10757_gb300 import scenes
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch
+
+    torch.cuda.set_device(local_rank)
+    B.build()
+    frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
+    pb = PackedBatch(frames)
+    pb.upload()
+    ctx = Context(device=local_rank, arena_bytes=64 << 20, max_frames=FRAMES)
+    for _ in range(args.warmup + args.steps):
+        run_batch(ctx, pb)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    ctx.close()
+    print(json.dumps({"profile_run": "ok", "launches": args.warmup + args.steps}), flush=True)
+
+
 def run_gpu(args, rank, world, local_rank):
     import ctypes as C
 
@@ -341,7 +431,7 @@ def run_gpu(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle(frames, budget_s=15.0)
+        cpu = time_oracle(frames, budget_s=12.0)
     ctx_tuning = {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
                   "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm}
     ctx.close()
@@ -383,11 +473,17 @@ def run_gpu(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile"])
+    ap.add_argument("--trace-out", default=None)
     args = ap.parse_args()
+    if args.mode == "trace":
+        return run_trace(args, dist_env()[2])
+    if args.mode == "profile":
+        return run_profile(args, dist_env()[2])
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch

@@ -326,6 +326,27 @@ ft_status ft_load_tuning(ft_ctx *ctx, const char *path);
  * ft_sync_status.  Use flags = 0 for normal operation. */
 ft_status ft_set_debug(ft_ctx *ctx, unsigned flags, uint64_t timeout_ns);
 
+/* Device-side trace of the fused kernel's work items (the tracing
+ * subsystem): one record per item of the last call.  kind: 0 grid build,
+ * 1 stereo, 2 search, 3 conflict resolution.  Times are the GPU global
+ * timer in ns; wait_ns is the part of [t_start, t_end] spent in bounded
+ * waits on other items. */
+typedef struct {
+    int32_t item, kind, frame, sm;
+    uint64_t t_start, t_end, wait_ns;
+    uint64_t mark[4];   /* phase ends inside the item (0: not reached); pinhole
+                           stereo: staging done, Hamming phase done, SAD
+                           rounds done, median done (last strip only) */
+} ft_trace_record;
+
+/* Enable tracing with room for `capacity` records per call (allocated once
+ * here; 0 disables and frees it). */
+ft_status ft_set_trace(ft_ctx *ctx, int capacity);
+
+/* Synchronize, then copy up to max records of the last call to out;
+ * *n receives the number of records the call produced (may exceed max). */
+ft_status ft_read_trace(ft_ctx *ctx, ft_trace_record *out, int max, int *n);
+
 /* Kernel launches issued by this context so far (all entry points). */
 uint64_t ft_launch_count(ft_ctx *ctx);
 

@@ -124,6 +124,12 @@ class ft_tuning(C.Structure):
                 ("resolve_tile", i32), ("ctas_per_sm", i32)]
 
 
+class ft_trace_record(C.Structure):
+    _fields_ = [("item", i32), ("kind", i32), ("frame", i32), ("sm", i32),
+                ("t_start", C.c_uint64), ("t_end", C.c_uint64), ("wait_ns", C.c_uint64),
+                ("mark", C.c_uint64 * 4)]
+
+
 # (name, restype, argtypes): every entry point the header declares
 SIGNATURES = [
     ("ft_params_default", None, [C.POINTER(ft_params)]),
@@ -147,6 +153,8 @@ SIGNATURES = [
     ("ft_save_tuning", i32, [vp, C.c_char_p]),
     ("ft_load_tuning", i32, [vp, C.c_char_p]),
     ("ft_set_debug", i32, [vp, C.c_uint, C.c_uint64]),
+    ("ft_set_trace", i32, [vp, i32]),
+    ("ft_read_trace", i32, [vp, C.POINTER(ft_trace_record), i32, C.POINTER(i32)]),
     ("ft_launch_count", C.c_uint64, [vp]),
 ]
 

@@ -132,6 +132,8 @@ struct ft_ctx {
     uint64_t launches = 0;
     unsigned debug_flags = 0;
     unsigned long long timeout_ns = 2000000000ull;
+    ft_trace_record *trace = nullptr;  // device buffer (tracing on)
+    int trace_cap = 0;
 };
 
 namespace {
@@ -156,9 +158,7 @@ ft_status check_params(const ft_params &p)
     if (!(p.search_th > 0.0f)) return fail(FT_EINVAL, "search_th must be > 0");
     float sc = 1.0f;
     for (int l = 1; l < p.nlevels; ++l) sc = sc * p.scale_factor;
-    const double halo = std::ceil(2.0 * (double)sc) + 3.0;
-    if (2.0 * halo + 1.0 > (double)kRowCap)
-        return fail(FT_EINVAL, "scale_factor^(nlevels-1) = %g: row bands wider than the %d-row window", sc, kRowCap);
+    if (!(2.0f * sc < 1.0e6f)) return fail(FT_EINVAL, "scale_factor^(nlevels-1) = %g is too large", sc);
     return FT_OK;
 }
 
@@ -203,6 +203,8 @@ ft_status check_job(const Job &j, const ft_params &p)
         }
         if (j.do_stereo) {
             if (!(j.pin.b > 0.0f)) return fail(FT_EINVAL, "pinhole: baseline must be > 0");
+            if (j.pin.height > kMaxRows)
+                return fail(FT_EINVAL, "pinhole: %d rows exceed the %d-row stereo limit", j.pin.height, kMaxRows);
             if ((s = check_pyramid(j.pyr_l, p.nlevels, "left pyramid")) != FT_OK) return s;
             if ((s = check_pyramid(j.pyr_r, p.nlevels, "right pyramid")) != FT_OK) return s;
             const ft_stereo_out &o = j.st;
@@ -271,6 +273,11 @@ DevParams make_dev_params(const ft_params &p)
     d.dist_hi = p.dist_hi;
     // a right keypoint's band reaches rows within ceil(r) + 2 of floor(y); +1 margin
     d.halo = (int)std::ceil(rmax) + 3;
+    // a left keypoint of octave o only meets right octaves up to o + 1
+    for (int o = 0; o < FT_MAX_LEVELS; ++o) {
+        const int top = std::min(o + 1, std::max(p.nlevels - 1, 0));
+        d.halo_oct[o] = (int)std::ceil(d.band_r[top]) + 3;
+    }
     return d;
 }
 
@@ -342,6 +349,8 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
     B.queue = reinterpret_cast<unsigned *>(dev + L.queue);
     B.status = ctx->status;
     B.timeout_ns = ctx->timeout_ns;
+    B.trace = ctx->trace;
+    B.trace_cap = ctx->trace_cap;
     unsigned *ctr_h = reinterpret_cast<unsigned *>(h + L.counters);
     unsigned *ctr_d = reinterpret_cast<unsigned *>(dev + L.counters);
     int *prefix = reinterpret_cast<int *>(h + L.prefix);
@@ -397,10 +406,10 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 F.sad_best = j.st.sad_best;
                 F.u_right = j.st.u_right;
                 F.depth = j.st.depth;
-                // strip height: the window (strip + 2 halo rows) must fit the
-                // shared row table, and its expected right keypoints the stage
+                // strip height: the expected right keypoints of the strip's
+                // window (strip + 2 halo rows) must fit the shared-memory stage
                 int sr = std::max(1, tune.strip_rows);
-                sr = std::min(sr, kRowCap - 2 * halo);
+                sr = std::min(sr, std::max(1, F.H));
                 if (F.nr > 0) {
                     const double per_row = (double)F.nr / (double)std::max(1, F.H);
                     const int cap_rows = (int)(0.75 * kStageCap / per_row) - 2 * halo;
@@ -408,6 +417,12 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 }
                 F.strip_rows = sr;
                 n_stereo = (F.H + sr - 1) / sr;
+                F.rowsort = 1;
+                F.row_ptr_l = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
+                F.row_ptr_r = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
+                F.ls_idx = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)F.nl));
+                F.rs_kp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)F.nr));
+                F.rs_desc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)F.nr));
             }
         } else {
             F.lap_l0 = j.rig.lap_l0;
@@ -467,8 +482,9 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 n_search[c] = (F.nm + F.search_tile - 1) / F.search_tile;
                 n_resolve[c] = (std::max(F.nm, C.nk) + F.resolve_tile - 1) / F.resolve_tile;
             }
-            n_index = F.ncam;
+            F.n_grid_items = F.ncam;
         }
+        n_index = F.rowsort + F.n_grid_items;
         if (scratch > ctx->arena_bytes)
             return fail(FT_ENOMEM, "arena of %zu bytes too small for this batch (needs %zu)", ctx->arena_bytes, scratch);
         F.n_index_items = n_index;
@@ -677,6 +693,7 @@ void ft_destroy(ft_ctx *c)
     if (c->done) cudaEventDestroy(c->done);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->arena) cudaFree(c->arena);
+    if (c->trace) cudaFree(c->trace);
     delete c;
 }
 
@@ -693,6 +710,38 @@ ft_status ft_sync_status(ft_ctx *c, int32_t *status)
 }
 
 uint64_t ft_launch_count(ft_ctx *c) { return c ? c->launches : 0; }
+
+ft_status ft_set_trace(ft_ctx *c, int capacity)
+{
+    if (!c || capacity < 0) return fail(FT_EINVAL, "ft_set_trace: bad argument");
+    FT_CUDA(cudaSetDevice(c->device));
+    if (c->have_last) FT_CUDA(cudaStreamSynchronize(c->last_stream));
+    if (c->trace) {
+        FT_CUDA(cudaFree(c->trace));
+        c->trace = nullptr;
+        c->trace_cap = 0;
+    }
+    if (capacity > 0) {
+        FT_CUDA(cudaMalloc(&c->trace, sizeof(ft_trace_record) * (size_t)capacity));
+        c->trace_cap = capacity;
+    }
+    return FT_OK;
+}
+
+ft_status ft_read_trace(ft_ctx *c, ft_trace_record *out, int max, int *n)
+{
+    if (!c || !n || (max > 0 && !out)) return fail(FT_EINVAL, "ft_read_trace: bad argument");
+    FT_CUDA(cudaSetDevice(c->device));
+    if (c->have_last) FT_CUDA(cudaStreamSynchronize(c->last_stream));
+    unsigned cnt = 0;
+    const char *queue = c->arena + align_up(sizeof(unsigned) * 64) + table_layout(1).queue;
+    FT_CUDA(cudaMemcpy(&cnt, queue + sizeof(unsigned), sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *n = (int)cnt;
+    const int k = std::min<int>(std::min<unsigned>(cnt, (unsigned)c->trace_cap), max);
+    if (k > 0 && c->trace)
+        FT_CUDA(cudaMemcpy(out, c->trace, sizeof(ft_trace_record) * (size_t)k, cudaMemcpyDeviceToHost));
+    return FT_OK;
+}
 
 ft_status ft_set_debug(ft_ctx *c, unsigned flags, uint64_t timeout_ns)
 {

@@ -23,15 +23,16 @@ constexpr int kThreads = 256;                       // threads per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kCells = FT_GRID_COLS * FT_GRID_ROWS; // 3072 grid cells
 constexpr int kStageCap = 768;                      // right keypoints staged per stereo item
-constexpr int kRowCap = 448;                        // rows of a stereo item's window
+constexpr int kMaxRows = 4096;                      // image rows the row sort handles
+constexpr int kRefineChunk = 64;                    // matches refined per SAD round
 constexpr int kFishChunk = 512;                     // right descriptors staged per chunk
 constexpr int kCounters = 8;                        // per-frame counters (u32)
 
 enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
 
 // per-frame counter slots
-enum Ctr { C_INDEX_DONE = 0, C_STEREO_DONE = 1, C_STEREO_READY = 2, C_SEARCH_DONE0 = 3,
-           C_SEARCH_DONE1 = 4 };
+enum Ctr { C_GRID_DONE = 0, C_STEREO_DONE = 1, C_STEREO_READY = 2, C_SEARCH_DONE0 = 3,
+           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5 };
 
 // device status bits (ORed into the context's status word)
 constexpr unsigned kStatusTimeout = 1u;
@@ -44,8 +45,8 @@ struct DevParams {
     float sc[FT_MAX_LEVELS], isc[FT_MAX_LEVELS], band_r[FT_MAX_LEVELS];
     float median_factor, fisheye_ratio, nn_ratio, search_th;
     float view_cos_min, view_cos_narrow, radius_narrow, radius_wide, dist_lo, dist_hi;
-    int halo;            // rows a right keypoint's band can reach beyond floor(y)
-    int pad_;
+    int halo;            // rows a right keypoint's band can reach beyond floor(y), any octave
+    int halo_oct[FT_MAX_LEVELS];   // same for the octave window of a left keypoint of octave o
 };
 
 // One camera of the search step (pinhole: the left camera only).
@@ -83,6 +84,11 @@ struct FrameDev {
     int H;
     float b, bf;
     float lap_l0, lap_l1, lap_r0, lap_r1;
+    // row sort of the pinhole stereo step (scratch): keypoints bucketed by row
+    int *row_ptr_l, *row_ptr_r;    // [H + 1]
+    int *ls_idx;                   // [nl] left indices in row order
+    float4 *rs_kp;                 // [nr] right x, y, index, octave in row order
+    uint4 *rs_desc;                // [2 * nr]
     // stereo outputs (pinhole)
     int *best_r, *dist, *sad_shift, *sad_best;
     float *u_right, *depth;
@@ -98,7 +104,8 @@ struct FrameDev {
     // work decomposition
     int strip_rows, n_stereo_items, fisheye_tile;
     int search_tile, resolve_tile;
-    int n_index_items, n_search_items[2], n_resolve_items[2];
+    int rowsort;                   // 1: index item 0 is the row sort
+    int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]
 };
 
@@ -109,9 +116,12 @@ struct BatchHeader {
     unsigned debug_flags;
     const int *prefix;             // [K_KINDS][nframes + 1]
     const FrameDev *frames;
-    unsigned *queue;               // [0]: next item
+    unsigned *queue;               // [0]: next item, [1]: trace records written
     unsigned *status;              // context status word (persistent, not in the table)
     unsigned long long timeout_ns; // bound of every device-side wait
+    ft_trace_record *trace;        // NULL: tracing off
+    int trace_cap;
+    int pad_;
 };
 
 }  // namespace ft

@@ -1,14 +1,20 @@
 // ft_kernels.cu -- the fused, persistent tracking kernel for sm_103a.
 //
 // Work items (pulled in queue order by every CTA of one launch):
-//   K_INDEX    per frame and camera: 64x48 keypoint grid as a counting sort
-//              into cell order (paper section IV-E; grid reading 64x48).
-//   K_STEREO   pinhole: one horizontal strip of left keypoints.  The CTA
-//              stages the right keypoints whose rows can reach the strip in
-//              shared memory, sorted by row, then one warp per left keypoint
-//              runs the band Hamming search (warp min reduction), the 11x11
-//              SAD over +-5 shifts from shared-memory patches, the parabola,
-//              disparity and depth (section IV-C, kernels 1 and 2 fused).  The
+//   K_INDEX    per frame: the row sort of the pinhole stereo step (left and
+//              right keypoints bucketed by image row, a counting sort), and
+//              per camera the 64x48 keypoint grid of the search step (paper
+//              section IV-E; grid reading 64x48), also a counting sort.
+//   K_STEREO   pinhole: one horizontal strip of image rows.  The CTA stages
+//              the row-sorted right keypoints that can reach the strip in
+//              shared memory, then runs three CTA-wide phases so that every
+//              memory latency is paid once per phase, not once per keypoint:
+//              (1) one thread per left keypoint: band Hamming search over the
+//              staged candidates (kernel 1 of section IV-C); (2) the 11x11
+//              left patches and 11x21 right strips of all matches gathered
+//              into shared memory; (3) one thread per (match, shift): SAD of
+//              centre-subtracted patches, then per match the best shift,
+//              parabola, disparity and depth (kernel 2 of section IV-C).  The
 //              frame's last strip runs the median rejection.
 //              fisheye: one tile of left keypoints, one thread each, against
 //              the right overlap descriptors staged in shared memory chunks;
@@ -34,10 +40,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kNoKey = 0xffffffffu;
 constexpr int kW = FT_SAD_W;
 constexpr int kL = FT_SAD_L;
-constexpr int kPatchL = (2 * kW + 1) * (2 * kW + 1);            // 121
 constexpr int kStripW = 2 * (kW + kL) + 1;                      // 21
-constexpr int kPatchR = (2 * kW + 1) * kStripW;                 // 231
 constexpr int kShifts = 2 * kL + 1;                             // 11
+constexpr int kBatch = 4;                                       // loads issued ahead per thread
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
@@ -153,17 +158,31 @@ __device__ int block_scan(const int *in, int *out, int n, int *warp_sums)
 }
 
 // ---------------------------------------------------------------- shared memory
+// one match waiting for its SAD refinement
+struct RefineJob {
+    int i, j, d, l, ul, vl, ur0;
+    float xi;
+};
+
+constexpr int kGroup = 8;                       // lanes per left keypoint in the Hamming phase
+constexpr int kGroups = kThreads / kGroup;      // left keypoints in flight per CTA
+constexpr int kWinRows = 512;                   // window rows whose pointers are staged
+constexpr int kSadChunk = 128;                  // matches whose SADs are summed per round
+
 struct SmemStereo {
+    float4 rkp[kStageCap];             // staged right keypoints: x, y, index, octave
     uint4 sdesc[2 * kStageCap];
-    float sx[kStageCap], sy[kStageCap];
-    int sj[kStageCap];
-    int rowptr[kRowCap + 2];
-    int rowfill[kRowCap + 2];
-    int sad[kWarps][12];
+    float4 lkp[kThreads];              // left keypoints of the pass: x, y, index, octave
+    uint4 ldesc[2 * kThreads];
+    RefineJob ref[kThreads];
+    int sad[kSadChunk][12];
+    int wrow[kWinRows + 1];            // row pointers of the staged window (relative)
+    int nref;
+};
+
+struct SmemRows {
+    int cnt[kMaxRows + 1];
     int warp_sums[kWarps];
-    int8_t soct[kStageCap];
-    uint8_t patchL[kWarps][128];
-    uint8_t patchR[kWarps][kPatchR + 1];
 };
 
 struct SmemGrid {
@@ -188,6 +207,7 @@ struct SmemSearch {
 
 union Smem {
     SmemStereo s;
+    SmemRows r;
     SmemGrid g;
     SmemFish f;
     SmemMedian m;
@@ -195,6 +215,15 @@ union Smem {
 };
 
 // ---------------------------------------------------------------- waits and signals
+// time this CTA spent in waits during the current item, and phase marks (tracing)
+__shared__ unsigned long long s_wait_ns;
+__shared__ unsigned long long s_mark[4];
+
+__device__ __forceinline__ void mark(const BatchHeader &B, int k)
+{
+    if (B.trace != nullptr && threadIdx.x == 0) s_mark[k] = global_ns();
+}
+
 // Block-wide wait until *ctr >= target, bounded by the header's timeout.  On
 // timeout (or when another CTA already reported one) it records the timeout in
 // the status word and returns false.
@@ -215,6 +244,7 @@ __device__ bool wait_geq(const BatchHeader &B, const unsigned *ctr, unsigned tar
                 __nanosleep(256);
             }
             if (!ok) atomicOr(B.status, kStatusTimeout);
+            s_wait_ns += global_ns() - t0;
         }
         *s_flag = ok;
     }
@@ -251,8 +281,8 @@ __device__ __forceinline__ int grid_cell(const CamDev &C, float iw, float ih, fl
     return cy * FT_GRID_COLS + cx;
 }
 
-__device__ void index_item(const BatchHeader &B, const FrameDev &F, int cam, SmemGrid &G,
-                           int *s_flag)
+__device__ void grid_item(const BatchHeader &B, const FrameDev &F, int cam, SmemGrid &G,
+                          int *s_flag)
 {
     const CamDev &C = F.cam[cam];
     const int tid = threadIdx.x;
@@ -260,9 +290,19 @@ __device__ void index_item(const BatchHeader &B, const FrameDev &F, int cam, Sme
     const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
     for (int c = tid; c < kCells; c += kThreads) G.cnt[c] = 0;
     __syncthreads();
-    for (int k = tid; k < C.nk; k += kThreads) {
-        const int c = grid_cell(C, iw, ih, __ldg(C.kx + k), __ldg(C.ky + k));
-        if (c >= 0) atomicAdd(&G.cnt[c], 1);
+    for (int base = 0; base < C.nk; base += kBatch * kThreads) {
+        float x[kBatch], y[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = base + u * kThreads + tid;
+            x[u] = k < C.nk ? __ldg(C.kx + k) : 0.0f;
+            y[u] = k < C.nk ? __ldg(C.ky + k) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int c = grid_cell(C, iw, ih, x[u], y[u]);
+            if (base + u * kThreads + tid < C.nk && c >= 0) atomicAdd(&G.cnt[c], 1);
+        }
     }
     __syncthreads();
     const int total = block_scan(G.cnt, G.cnt, kCells, G.warp_sums);
@@ -282,19 +322,77 @@ __device__ void index_item(const BatchHeader &B, const FrameDev &F, int cam, Sme
         }
         C.owner[k] = ~0ull;
     }
-    signal_count(&F.ctr[C_INDEX_DONE], (unsigned)F.n_index_items, s_flag);
+    signal_count(&F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
 }
 
-// ---------------------------------------------------------------- K_STEREO, pinhole
+// ---------------------------------------------------------------- K_INDEX: row sort
 __device__ __forceinline__ int floor_row(float y) { return f2i(floorf(y)); }
 
-// Row that owns a left keypoint (rows outside the image go to the edge strips).
+// Row that owns a keypoint in the row sort (rows outside the image go to the
+// edge rows).
 __device__ __forceinline__ int own_row(float y, int H)
 {
     if (y < 0.0f) return 0;
     return min(f2i(y), H - 1);
 }
 
+// Right keypoints are bucketed by floor(y) clamped to the image, left
+// keypoints by the row they search (int)y clamped to the image.
+__device__ void rowsort_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
+{
+    const int tid = threadIdx.x, H = F.H;
+    for (int r = tid; r <= H; r += kThreads) S.cnt[r] = 0;
+    __syncthreads();
+    for (int base = 0; base < F.nr; base += kBatch * kThreads) {
+        float y[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int j = base + u * kThreads + tid;
+            y[u] = j < F.nr ? __ldg(F.ry + j) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (base + u * kThreads + tid < F.nr) atomicAdd(&S.cnt[clampi(floor_row(y[u]), 0, H - 1)], 1);
+    }
+    __syncthreads();
+    int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
+    for (int r = tid; r < H; r += kThreads) F.row_ptr_r[r] = S.cnt[r];
+    if (tid == 0) F.row_ptr_r[H] = total;
+    __syncthreads();
+    for (int j = tid; j < F.nr; j += kThreads) {
+        const float x = __ldg(F.rx + j), y = __ldg(F.ry + j);
+        const int pos = atomicAdd(&S.cnt[clampi(floor_row(y), 0, H - 1)], 1);
+        F.rs_kp[pos] = make_float4(x, y, __int_as_float(j), __int_as_float((int)__ldg(F.roct + j)));
+        F.rs_desc[2 * pos] = __ldg(F.rdesc + 2 * j);
+        F.rs_desc[2 * pos + 1] = __ldg(F.rdesc + 2 * j + 1);
+    }
+    __syncthreads();
+    for (int r = tid; r <= H; r += kThreads) S.cnt[r] = 0;
+    __syncthreads();
+    for (int base = 0; base < F.nl; base += kBatch * kThreads) {
+        float y[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = base + u * kThreads + tid;
+            y[u] = i < F.nl ? __ldg(F.ly + i) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (base + u * kThreads + tid < F.nl) atomicAdd(&S.cnt[own_row(y[u], H)], 1);
+    }
+    __syncthreads();
+    total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
+    for (int r = tid; r < H; r += kThreads) F.row_ptr_l[r] = S.cnt[r];
+    if (tid == 0) F.row_ptr_l[H] = total;
+    __syncthreads();
+    for (int i = tid; i < F.nl; i += kThreads) {
+        const int pos = atomicAdd(&S.cnt[own_row(__ldg(F.ly + i), H)], 1);
+        F.ls_idx[pos] = i;
+    }
+    signal_count(&F.ctr[C_ROWS_DONE], 1u, s_flag);
+}
+
+// ---------------------------------------------------------------- K_STEREO, pinhole
 // Does right keypoint (y, oct) list image row `row` (band floor(y - r) ..
 // ceil(y + r), r = 2 * scale[oct], clamped to the image)?
 __device__ __forceinline__ bool band_has(const DevParams &P, float y, int oct, int row, int H)
@@ -305,130 +403,178 @@ __device__ __forceinline__ bool band_has(const DevParams &P, float y, int oct, i
     return lo <= row && row <= hi;
 }
 
-__device__ void stereo_one(const BatchHeader &B, const FrameDev &F, SmemStereo &S, int i,
-                           bool staged, int w_lo, int lane, int warp)
+__device__ __forceinline__ void write_stereo(const FrameDev &F, int i, int best, int dist, int shift,
+                                             int sadb, float ur, float dep)
 {
-    const DevParams &P = B.p;
-    const float xi = __ldg(F.lx + i), yi = __ldg(F.ly + i);
-    const int oi = __ldg(F.loct + i);
-    const float maxD = fdiv(F.bf, F.b);
-    int best = -1, dist = -1, shift = FT_NO_SHIFT, sadb = -1;
-    float ur = -1.0f, dep = -1.0f;
+    F.best_r[i] = best;
+    F.dist[i] = dist;
+    F.sad_shift[i] = shift;
+    F.sad_best[i] = sadb;
+    F.u_right[i] = ur;
+    F.depth[i] = dep;
+}
 
-    // a2: best (distance, index) over the band candidates
-    unsigned key = kNoKey;
-    if (!(yi < 0.0f)) {
-        const int row = f2i(yi);
-        if (row < F.H) {
+// Phase 1: the 8 lanes of a group scan the band candidates of one left
+// keypoint (consecutive candidates per lane, conflict-free shared loads) and
+// reduce to the smallest (distance, right index); lane 0 of the group queues
+// the match for refinement or writes the final "no match" outputs.
+__device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo &S, int npass,
+                              bool staged, int w_a, int e_base)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = lane & (kGroup - 1), gw = lane / kGroup;
+    const float maxD = fdiv(F.bf, F.b);
+    for (int tb = warp * (32 / kGroup); tb < npass; tb += kGroups) {
+        const int t = tb + gw;
+        const bool have = t < npass;
+        unsigned key = kNoKey;
+        float xb = 0.0f;
+        float xi = 0.0f, yi = 0.0f;
+        int oi = 0, i = 0;
+        if (have) {
+            const float4 L = S.lkp[t];
+            xi = L.x;
+            yi = L.y;
+            i = __float_as_int(L.z);
+            oi = __float_as_int(L.w);
+            const int row = f2i(yi);
             const float minU = fsub(xi, maxD);
             const float maxU = fsub(xi, 0.0f);
-            if (!(maxU < 0.0f)) {
-                const uint4 a0 = __ldg(F.ldesc + 2 * i), a1 = __ldg(F.ldesc + 2 * i + 1);
+            if (!(yi < 0.0f) && row < F.H && !(maxU < 0.0f)) {
+                const int h = (oi >= 0 && oi < P.nlevels) ? P.halo_oct[oi] : P.halo;
+                const int ra = max(row - h, 0), rb = min(row + h, F.H - 1) + 1;
+                int e0, e1;
                 if (staged) {
-                    const int e0 = S.rowptr[row - P.halo - w_lo];
-                    const int e1 = S.rowptr[row + P.halo - w_lo + 1];
-                    for (int e = e0 + lane; e < e1; e += 32) {
-                        const int oj = S.soct[e];
-                        if (oj < oi - 1 || oj > oi + 1) continue;
-                        if (!band_has(P, S.sy[e], oj, row, F.H)) continue;
-                        const float xj = S.sx[e];
-                        if (xj < minU || xj > maxU) continue;
-                        const int d = ham8(a0, a1, S.sdesc[2 * e], S.sdesc[2 * e + 1]);
-                        key = min(key, ((unsigned)d << 20) | (unsigned)S.sj[e]);
-                    }
+                    e0 = S.wrow[ra - w_a];
+                    e1 = S.wrow[rb - w_a];
                 } else {
-                    for (int j = lane; j < F.nr; j += 32) {
-                        const int oj = __ldg(F.roct + j);
-                        if (oj < oi - 1 || oj > oi + 1) continue;
-                        if (!band_has(P, __ldg(F.ry + j), oj, row, F.H)) continue;
-                        const float xj = __ldg(F.rx + j);
-                        if (xj < minU || xj > maxU) continue;
-                        const int d = ham8(a0, a1, __ldg(F.rdesc + 2 * j), __ldg(F.rdesc + 2 * j + 1));
-                        key = min(key, ((unsigned)d << 20) | (unsigned)j);
+                    e0 = __ldcg(F.row_ptr_r + ra) - e_base;
+                    e1 = __ldcg(F.row_ptr_r + rb) - e_base;
+                }
+                const uint4 a0 = S.ldesc[2 * t], a1 = S.ldesc[2 * t + 1];
+                for (int e = e0 + sub; e < e1; e += kGroup) {
+                    const float4 g = staged ? S.rkp[e] : __ldcg(F.rs_kp + e_base + e);
+                    const int oj = __float_as_int(g.w);
+                    if (oj < oi - 1 || oj > oi + 1) continue;
+                    if (!band_has(P, g.y, oj, row, F.H)) continue;
+                    if (g.x < minU || g.x > maxU) continue;
+                    uint4 b0, b1;
+                    if (staged) {
+                        b0 = S.sdesc[2 * e];
+                        b1 = S.sdesc[2 * e + 1];
+                    } else {
+                        b0 = __ldcg(F.rs_desc + 2 * (e_base + e));
+                        b1 = __ldcg(F.rs_desc + 2 * (e_base + e) + 1);
+                    }
+                    const unsigned k = ((unsigned)ham8(a0, a1, b0, b1) << 20) | (unsigned)__float_as_int(g.z);
+                    if (k < key) {
+                        key = k;
+                        xb = g.x;
                     }
                 }
             }
         }
-    }
-    key = __reduce_min_sync(kFull, key);
-    if (key != kNoKey) {
-        dist = (int)(key >> 20);
-        if (dist < P.th_stereo) best = (int)(key & 0xfffffu);
-    }
-
-    // a3: SAD over the shifts, a4: parabola, disparity, depth
-    if (best >= 0) {
-        const int l = clampi(oi, 0, P.nlevels - 1);
-        const float xj = __ldg(F.rx + best);
-        const int ul = f2i(roundf(fmul(xi, P.isc[l])));
-        const int vl = f2i(roundf(fmul(yi, P.isc[l])));
-        const int ur0 = f2i(roundf(fmul(xj, P.isc[l])));
-        const bool inside = vl - kW >= 0 && vl + kW <= F.lh[l] - 1 && vl + kW <= F.rh[l] - 1 &&
-                            ul - kW >= 0 && ul + kW <= F.lw[l] - 1 &&
-                            ur0 - kL - kW >= 0 && ur0 + kL + kW <= F.rw[l] - 1;
-        if (inside) {
-            const uint8_t *IL = F.pyrL[l] + (size_t)(vl - kW) * F.lp[l] + (ul - kW);
-            const uint8_t *IR = F.pyrR[l] + (size_t)(vl - kW) * F.rp[l] + (ur0 - kL - kW);
-            uint8_t *pl = S.patchL[warp];
-            uint8_t *pr = S.patchR[warp];
-            for (int t = lane; t < kPatchL + kPatchR; t += 32) {
-                if (t < kPatchL) {
-                    const int dy = t / (2 * kW + 1), dx = t - dy * (2 * kW + 1);
-                    pl[t] = __ldg(IL + (size_t)dy * F.lp[l] + dx);
-                } else {
-                    const int u = t - kPatchL;
-                    const int dy = u / kStripW, dx = u - dy * kStripW;
-                    pr[u] = __ldg(IR + (size_t)dy * F.rp[l] + dx);
-                }
-            }
-            if (lane < kShifts) S.sad[warp][lane] = 0;
-            __syncwarp();
-            const int cL = pl[kW * (2 * kW + 1) + kW];
-            for (int q = lane; q < kShifts * (2 * kW + 1); q += 32) {
-                const int k = q / (2 * kW + 1), dy = q - k * (2 * kW + 1);
-                const int cR = pr[kW * kStripW + k + kW];
-                const uint8_t *rl = pl + dy * (2 * kW + 1);
-                const uint8_t *rr = pr + dy * kStripW + k;
-                int s = 0;
 #pragma unroll
-                for (int dx = 0; dx < 2 * kW + 1; ++dx) s += abs((rl[dx] - cL) - (rr[dx] - cR));
-                atomicAdd(&S.sad[warp][k], s);
+        for (int o = kGroup / 2; o > 0; o >>= 1) {
+            const unsigned k2 = __shfl_xor_sync(kFull, key, o);
+            const float x2 = __shfl_xor_sync(kFull, xb, o);
+            if (k2 < key) {
+                key = k2;
+                xb = x2;
             }
-            __syncwarp();
-            unsigned kk = lane < kShifts ? (((unsigned)S.sad[warp][lane] << 4) | (unsigned)lane) : kNoKey;
-            kk = __reduce_min_sync(kFull, kk);
-            const int kb = (int)(kk & 15u);
-            shift = kb - kL;
-            if (kb != 0 && kb != 2 * kL) {
-                const float d1 = (float)S.sad[warp][kb - 1];
-                const float d2 = (float)S.sad[warp][kb];
-                const float d3 = (float)S.sad[warp][kb + 1];
-                const float delta = fdiv(fsub(d1, d3), fmul(2.0f, fsub(fadd(d1, d3), fmul(2.0f, d2))));
-                if (!(delta < -1.0f || delta > 1.0f)) {
-                    float bestuR = fmul(P.sc[l], fadd(fadd((float)ur0, (float)shift), delta));
-                    float disparity = fsub(xi, bestuR);
-                    if (disparity >= 0.0f && disparity < maxD) {
-                        if (disparity <= 0.0f) {
-                            disparity = 0.01f;
-                            bestuR = fsub(xi, 0.01f);
-                        }
-                        dep = fdiv(F.bf, disparity);
-                        ur = bestuR;
-                        sadb = S.sad[warp][kb];
-                    }
+        }
+        if (have && sub == 0) {
+            int best = -1, dist = -1;
+            if (key != kNoKey) {
+                dist = (int)(key >> 20);
+                if (dist < P.th_stereo) best = (int)(key & 0xfffffu);
+            }
+            bool queued = false;
+            if (best >= 0) {
+                const int l = clampi(oi, 0, P.nlevels - 1);
+                const int ul = f2i(roundf(fmul(xi, P.isc[l])));
+                const int vl = f2i(roundf(fmul(yi, P.isc[l])));
+                const int ur0 = f2i(roundf(fmul(xb, P.isc[l])));
+                const bool inside = vl - kW >= 0 && vl + kW <= F.lh[l] - 1 && vl + kW <= F.rh[l] - 1 &&
+                                    ul - kW >= 0 && ul + kW <= F.lw[l] - 1 &&
+                                    ur0 - kL - kW >= 0 && ur0 + kL + kW <= F.rw[l] - 1;
+                if (inside) {
+                    const int slot = atomicAdd(&S.nref, 1);
+                    S.ref[slot] = RefineJob{i, best, dist, l, ul, vl, ur0, xi};
+                    queued = true;
                 }
             }
-            __syncwarp();
+            if (!queued) write_stereo(F, i, best, dist, FT_NO_SHIFT, -1, -1.0f, -1.0f);
         }
     }
-    if (lane == 0) {
-        F.best_r[i] = best;
-        F.dist[i] = dist;
-        F.sad_shift[i] = shift;
-        F.sad_best[i] = sadb;
-        F.u_right[i] = ur;
-        F.depth[i] = dep;
+}
+
+// Phases 2-3 for refine jobs [r0, r0 + nc): one thread per (job, patch row)
+// loads that row of the left patch and of the right strip plus the centre
+// values (all loads in flight together), adds the row's part of the 11 SADs
+// of centre-subtracted patches; then per job the first strict minimum over
+// the shifts, the parabola, disparity and depth.
+__device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &S, int r0, int nc)
+{
+    const int tid = threadIdx.x;
+    for (int q = tid; q < nc * kShifts; q += kThreads) S.sad[q / kShifts][q % kShifts] = 0;
+    __syncthreads();
+    for (int q = tid; q < nc * (2 * kW + 1); q += kThreads) {
+        const int dy = q / nc, m = q - dy * nc;
+        const RefineJob &J = S.ref[r0 + m];
+        const uint8_t *IL = F.pyrL[J.l];
+        const uint8_t *IR = F.pyrR[J.l];
+        const int lp = F.lp[J.l], rp = F.rp[J.l];
+        const uint8_t *gl = IL + (size_t)(J.vl - kW + dy) * lp + (J.ul - kW);
+        const uint8_t *gr = IR + (size_t)(J.vl - kW + dy) * rp + (J.ur0 - kL - kW);
+        const uint8_t *gc = IR + (size_t)J.vl * rp + (J.ur0 - kL);
+        int lv[2 * kW + 1], rv[kStripW], cr[kShifts];
+#pragma unroll
+        for (int c = 0; c < 2 * kW + 1; ++c) lv[c] = __ldg(gl + c);
+#pragma unroll
+        for (int c = 0; c < kStripW; ++c) rv[c] = __ldg(gr + c);
+#pragma unroll
+        for (int c = 0; c < kShifts; ++c) cr[c] = __ldg(gc + c);
+        const int cl = __ldg(IL + (size_t)J.vl * lp + J.ul);
+#pragma unroll
+        for (int k = 0; k < kShifts; ++k) {
+            int s = 0;
+#pragma unroll
+            for (int dx = 0; dx < 2 * kW + 1; ++dx) s += abs((lv[dx] - cl) - (rv[k + dx] - cr[k]));
+            atomicAdd(&S.sad[m][k], s);
+        }
     }
+    __syncthreads();
+    for (int m = tid; m < nc; m += kThreads) {
+        const RefineJob &J = S.ref[r0 + m];
+        const int *sad = S.sad[m];
+        int kb = 0;
+        for (int k = 1; k < kShifts; ++k)
+            if (sad[k] < sad[kb]) kb = k;
+        const int shift = kb - kL;
+        int sadb = -1;
+        float ur = -1.0f, dep = -1.0f;
+        if (kb != 0 && kb != 2 * kL) {
+            const float d1 = (float)sad[kb - 1], d2 = (float)sad[kb], d3 = (float)sad[kb + 1];
+            const float delta = fdiv(fsub(d1, d3), fmul(2.0f, fsub(fadd(d1, d3), fmul(2.0f, d2))));
+            if (!(delta < -1.0f || delta > 1.0f)) {
+                float bestuR = fmul(P.sc[J.l], fadd(fadd((float)J.ur0, (float)shift), delta));
+                float disparity = fsub(J.xi, bestuR);
+                const float maxD = fdiv(F.bf, F.b);
+                if (disparity >= 0.0f && disparity < maxD) {
+                    if (disparity <= 0.0f) {
+                        disparity = 0.01f;
+                        bestuR = fsub(J.xi, 0.01f);
+                    }
+                    dep = fdiv(F.bf, disparity);
+                    ur = bestuR;
+                    sadb = sad[kb];
+                }
+            }
+        }
+        write_stereo(F, J.i, J.j, J.d, shift, sadb, ur, dep);
+    }
+    __syncthreads();
 }
 
 // warp 0: bin of the k-th smallest value (0-based) of a 256-bin histogram
@@ -512,62 +658,54 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
 {
     SmemStereo &S = U.s;
     const DevParams &P = B.p;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int H = F.H;
-    const int r_lo = strip * F.strip_rows;
-    const int r_hi = min(H, r_lo + F.strip_rows);
-    const int w_lo = r_lo - P.halo;
-    const int nrows = (r_hi - r_lo) + 2 * P.halo;   // <= kRowCap (host guarantees)
-
-    // stage the right keypoints whose floor(y) row falls in the window, by row
-    for (int r = tid; r <= nrows; r += kThreads) S.rowptr[r] = 0;
-    __syncthreads();
-    for (int j = tid; j < F.nr; j += kThreads) {
-        const int rel = floor_row(__ldg(F.ry + j)) - w_lo;
-        if (rel >= 0 && rel < nrows) atomicAdd(&S.rowptr[rel], 1);
-    }
-    __syncthreads();
-    const int total = block_scan(S.rowptr, S.rowptr, nrows + 1, S.warp_sums);
-    const bool staged = total <= kStageCap;
-    if (staged) {
-        for (int r = tid; r <= nrows; r += kThreads) S.rowfill[r] = S.rowptr[r];
-        __syncthreads();
-        for (int j = tid; j < F.nr; j += kThreads) {
-            const float y = __ldg(F.ry + j);
-            const int rel = floor_row(y) - w_lo;
-            if (rel >= 0 && rel < nrows) {
-                const int pos = atomicAdd(&S.rowfill[rel], 1);
-                S.sx[pos] = __ldg(F.rx + j);
-                S.sy[pos] = y;
-                S.soct[pos] = __ldg(F.roct + j);
-                S.sj[pos] = j;
-                S.sdesc[2 * pos] = __ldg(F.rdesc + 2 * j);
-                S.sdesc[2 * pos + 1] = __ldg(F.rdesc + 2 * j + 1);
+    const int tid = threadIdx.x;
+    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 1u, s_flag)) {
+        const int H = F.H;
+        const int r_lo = strip * F.strip_rows;
+        const int r_hi = min(H, r_lo + F.strip_rows);
+        // stage the row-sorted right keypoints of rows [w_a, w_b] and their row pointers
+        const int w_a = max(r_lo - P.halo, 0);
+        const int w_b = min(r_hi - 1 + P.halo, H - 1);
+        const int e_base = __ldcg(F.row_ptr_r + w_a);
+        const int e_end = __ldcg(F.row_ptr_r + w_b + 1);
+        const bool staged = e_end - e_base <= kStageCap && w_b - w_a + 1 <= kWinRows;
+        if (staged) {
+            for (int e = tid; e < e_end - e_base; e += kThreads) {
+                S.rkp[e] = __ldcg(F.rs_kp + e_base + e);
+                S.sdesc[2 * e] = __ldcg(F.rs_desc + 2 * (e_base + e));
+                S.sdesc[2 * e + 1] = __ldcg(F.rs_desc + 2 * (e_base + e) + 1);
             }
+            for (int r = tid; r <= w_b - w_a + 1; r += kThreads) S.wrow[r] = __ldcg(F.row_ptr_r + w_a + r) - e_base;
+        }
+        if (tid == 0) S.nref = 0;
+        const int l_lo = __ldcg(F.row_ptr_l + r_lo), l_hi = __ldcg(F.row_ptr_l + r_hi);
+        mark(B, 0);
+        for (int pass = l_lo; pass < l_hi; pass += kThreads) {
+            // the pass's left keypoints, one thread each, into shared memory
+            const int npass = min(kThreads, l_hi - pass);
+            if (tid < npass) {
+                const int i = __ldcg(F.ls_idx + pass + tid);
+                S.lkp[tid] = make_float4(__ldg(F.lx + i), __ldg(F.ly + i), __int_as_float(i),
+                                         __int_as_float((int)__ldg(F.loct + i)));
+                S.ldesc[2 * tid] = __ldg(F.ldesc + 2 * i);
+                S.ldesc[2 * tid + 1] = __ldg(F.ldesc + 2 * i + 1);
+            }
+            __syncthreads();
+            hamming_phase(P, F, S, npass, staged, w_a, e_base);
+            __syncthreads();
+            mark(B, 1);
+            const int nref = S.nref;
+            for (int r0 = 0; r0 < nref; r0 += kSadChunk) refine_round(P, F, S, r0, min(kSadChunk, nref - r0));
+            if (tid == 0) S.nref = 0;
+            __syncthreads();
+            mark(B, 2);
         }
     }
-    __syncthreads();
-
-    // one warp per left keypoint of this strip
-    for (int base = warp * 32; base < F.nl; base += kThreads) {
-        const int i = base + lane;
-        bool mine = false;
-        if (i < F.nl) {
-            const int orow = own_row(__ldg(F.ly + i), H);
-            mine = orow >= r_lo && orow < r_hi;
-        }
-        unsigned mask = __ballot_sync(kFull, mine);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            stereo_one(B, F, S, base + src, staged, w_lo, lane, warp);
-        }
-    }
-
     if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
         median_reject(F, P, U.m);
         __threadfence();
         __syncthreads();
+        mark(B, 3);
         if (tid == 0 && !(B.debug_flags & kDebugWithholdStereoReady))
             atomicExch(&F.ctr[C_STEREO_READY], 1u);
     }
@@ -743,11 +881,14 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                 const uint4 q0 = __ldg(F.mdesc + 2 * m), q1 = __ldg(F.mdesc + 2 * m + 1);
                 const bool check_ur = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr;
                 unsigned best = kNoKey, second = kNoKey;
+                int oct1 = -1, oct2 = -1;
                 for (int cy = y0; cy <= y1; ++cy) {
                     const int e0 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x0);
                     const int e1 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x1 + 1);
                     for (int e = e0; e < e1; ++e) {
+                        // the keypoint record and its descriptor are fetched together
                         const float4 g = __ldcg(C.gkp + e);
+                        const uint4 b0 = __ldcg(C.gdesc + 2 * e), b1 = __ldcg(C.gdesc + 2 * e + 1);
                         const int flags = __float_as_int(g.w);
                         const int oct = (int)(int8_t)(flags & 0xff);
                         if (oct < level - 1 || oct > level) continue;
@@ -759,8 +900,16 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                             const float urk = __ldcg(F.u_right_in + k);
                             if (urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
                         }
-                        const int d = ham8(q0, q1, __ldcg(C.gdesc + 2 * e), __ldcg(C.gdesc + 2 * e + 1));
-                        top2_push(((unsigned)d << 20) | (unsigned)k, best, second);
+                        const unsigned key = ((unsigned)ham8(q0, q1, b0, b1) << 20) | (unsigned)k;
+                        if (key < best) {
+                            second = best;
+                            oct2 = oct1;
+                            best = key;
+                            oct1 = oct;
+                        } else if (key < second) {
+                            second = key;
+                            oct2 = oct;
+                        }
                     }
                 }
                 if (best != kNoKey) {
@@ -768,8 +917,6 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                     d2 = second != kNoKey ? (int)(second >> 20) : 256;
                     if (d1 <= P.th_search) {
                         const int k1 = (int)(best & 0xfffffu);
-                        const int oct1 = __ldg(C.koct + k1);
-                        const int oct2 = second != kNoKey ? (int)__ldg(C.koct + (second & 0xfffffu)) : -1;
                         const bool ratio = P.ratio_any_octave || oct1 == oct2;
                         if (!(ratio && (float)d1 > fmul(P.nn_ratio, (float)d2))) {
                             atomicMin(C.owner + k1, ((unsigned long long)d1 << 32) | (unsigned)m);
@@ -793,7 +940,7 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
     const int t = cam ? tile - F.n_search_items[0] : tile;
     bool ok = true;
     if (F.wait_stereo) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
-    if (ok) ok = wait_geq(B, &F.ctr[C_INDEX_DONE], (unsigned)F.n_index_items, s_flag);
+    if (ok) ok = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
     if (ok) {
         const CamDev &C = F.cam[cam];
         float *pose = U.q.pose;
@@ -816,9 +963,11 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
             pose[tid] = v;
         }
         __syncthreads();
+        mark(B, 0);
         const int m0 = t * F.search_tile;
         const int m1 = min(F.nm, m0 + F.search_tile);
         for (int m = m0 + tid; m < m1; m += kThreads) search_point(B.p, F, C, pose, m);
+        mark(B, 1);
     } else {
         // the wait ran out (reported in the status word): leave defined outputs
         const CamDev &C = F.cam[cam];
@@ -840,9 +989,17 @@ __device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, 
 {
     const int cam = tile < F.n_resolve_items[0] ? 0 : 1;
     const int t = cam ? tile - F.n_resolve_items[0] : tile;
-    if (!wait_geq(B, &F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag)) return;
+    // the grid build initialises the owners (a frame without map points has no
+    // search item to order the two)
     const CamDev &C = F.cam[cam];
     const int i0 = t * F.resolve_tile, i1 = i0 + F.resolve_tile;
+    if (!wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag) ||
+        !wait_geq(B, &F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag)) {
+        // the wait ran out (reported in the status word): leave defined outputs
+        for (int m = i0 + threadIdx.x; m < min(i1, F.nm); m += kThreads) C.mp_kp[m] = -1;
+        for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) C.kp_mp[k] = -1;
+        return;
+    }
     for (int m = i0 + threadIdx.x; m < min(i1, F.nm); m += kThreads) {
         const int k = __ldcg(C.mp_kp + m);
         if (k >= C.nk) {
@@ -859,7 +1016,7 @@ __device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, 
 }
 
 // ---------------------------------------------------------------- the kernel
-__global__ void __launch_bounds__(kThreads, 4) ft_fused_kernel(const BatchHeader *__restrict__ hdr)
+__global__ void __launch_bounds__(kThreads, 3) ft_fused_kernel(const BatchHeader *__restrict__ hdr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &U = *reinterpret_cast<Smem *>(smem_raw);
@@ -884,14 +1041,40 @@ __global__ void __launch_bounds__(kThreads, 4) ft_fused_kernel(const BatchHeader
         }
         const FrameDev &F = B.frames[lo];
         const int tile = local - pre[lo];
+        unsigned long long t_start = 0;
+        if (B.trace != nullptr && threadIdx.x == 0) {
+            t_start = global_ns();
+            s_wait_ns = 0;
+            s_mark[0] = s_mark[1] = s_mark[2] = s_mark[3] = 0;
+        }
         switch (kind) {
-        case K_INDEX: index_item(B, F, tile, U.g, &s_flag); break;
+        case K_INDEX:
+            if (F.rowsort && tile == 0) rowsort_item(B, F, U.r, &s_flag);
+            else grid_item(B, F, tile - F.rowsort, U.g, &s_flag);
+            break;
         case K_STEREO:
             if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);
             else stereo_fisheye_item(B, F, tile, U, &s_flag);
             break;
         case K_SEARCH: search_item(B, F, tile, U, &s_flag); break;
         default: resolve_item(B, F, tile, &s_flag); break;
+        }
+        if (B.trace != nullptr && threadIdx.x == 0) {
+            const unsigned slot = atomicAdd(B.queue + 1, 1u);
+            if (slot < (unsigned)B.trace_cap) {
+                unsigned sm;
+                asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+                ft_trace_record r;
+                r.item = item;
+                r.kind = kind;
+                r.frame = lo;
+                r.sm = (int)sm;
+                r.t_start = t_start;
+                r.t_end = global_ns();
+                r.wait_ns = s_wait_ns;
+                for (int q = 0; q < 4; ++q) r.mark[q] = s_mark[q];
+                B.trace[slot] = r;
+            }
         }
     }
 }
