@@ -347,6 +347,38 @@ ft_status ft_set_trace(ft_ctx *ctx, int capacity);
  * *n receives the number of records the call produced (may exceed max). */
 ft_status ft_read_trace(ft_ctx *ctx, ft_trace_record *out, int max, int *n);
 
+/* Pinhole stereo matching of one frame, like ft_stereo_match_pinhole, for
+ * callers that must not allocate memory.  The paper has no counterpart: it is
+ * an addition of this library.
+ *
+ * Who needs it: code that may not allocate device memory once it runs -- a
+ * tracking loop with a hard per-frame deadline (cudaMalloc can block and
+ * synchronize the device), a deployment that reserves all device memory at
+ * start-up, or a host framework whose memory manager forbids allocations
+ * behind its back.  Such callers cannot create an ft_ctx (ft_create
+ * allocates its arena), so this call needs no context: its scratch (work
+ * table, counters, row sort) lives in a fixed 1 MiB device array that is part
+ * of the library, held on every device that loads the library until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The caller passes inputs and outputs as for
+ * ft_stereo_match_pinhole, on the current device.
+ *
+ * Limits: at most 16384 left and 16384 right keypoints and 4096 image rows
+ * per call; larger frames are rejected with FT_EINVAL and a message in
+ * ft_last_error().
+ *
+ * The first call on a device looks up the array's device address and the
+ * kernel's launch shape for that device (with the device current); make that
+ * first call before starting any stream capture.  All calls share the one
+ * array and each call overwrites what the previous one left there, so calls
+ * whose GPU work overlaps (two streams at once) race and give wrong results:
+ * keep them on one stream or order them.  If device_status is not NULL it
+ * receives (on the stream) 0, or a nonzero value when a bounded device wait
+ * ran out. */
+ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
+                                          const ft_pinhole *cam, const ft_stereo_frame *frame,
+                                          ft_stereo_out *out, int32_t *device_status);
+
 /* Kernel launches issued by this context so far (all entry points). */
 uint64_t ft_launch_count(ft_ctx *ctx);
 

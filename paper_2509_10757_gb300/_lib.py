@@ -156,6 +156,9 @@ SIGNATURES = [
     ("ft_set_trace", i32, [vp, i32]),
     ("ft_read_trace", i32, [vp, C.POINTER(ft_trace_record), i32, C.POINTER(i32)]),
     ("ft_launch_count", C.c_uint64, [vp]),
+    ("ft_stereo_match_pinhole_noalloc", i32, [vp, C.POINTER(ft_params), C.POINTER(ft_pinhole),
+                                              C.POINTER(ft_stereo_frame), C.POINTER(ft_stereo_out),
+                                              vp]),
 ]
 
 _lib = None

@@ -609,6 +609,8 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
 
 }  // namespace
 
+void ft::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 // ======================================================================== C ABI
 extern "C" {
 

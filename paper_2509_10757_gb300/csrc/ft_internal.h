@@ -132,4 +132,6 @@ cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stre
 int fused_smem_bytes();
 cudaError_t fused_occupancy(int *ctas_per_sm);
 const void *fused_kernel_ptr();
+// set the text ft_last_error() returns on this thread (ft_api.cu)
+void set_last_error(const char *msg);
 }  // namespace ft
