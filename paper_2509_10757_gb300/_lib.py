@@ -10,7 +10,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfasttrack.so")
+# FT_LIB names another build of the library (for instance a variant compiled
+# with different launch bounds); default: the in-tree build
+LIB_PATH = os.environ.get("FT_LIB") or os.path.join(HERE, "libfasttrack.so")
 
 FT_DESC_BYTES = 32
 FT_MAX_LEVELS = 16

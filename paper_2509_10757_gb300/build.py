@@ -44,7 +44,25 @@ def _stale(target: str, deps: list) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          defines: tuple = (), out: str | None = None) -> str:
+    """Compile (if stale) and return the library path.  `defines` adds -D
+    flags and `out` names another output (a variant build: its objects go to
+    a build folder of their own)."""
+    global BUILD, LIB
+    if defines or out:
+        tag = "_".join(d.replace("=", "") for d in defines) or "variant"
+        saved = (BUILD, LIB)
+        BUILD = os.path.join(HERE, "_build", tag)
+        LIB = out or os.path.join(BUILD, "libfasttrack.so")
+        try:
+            return _build(force, verbose, ptxas_info, ["-D" + d for d in defines])
+        finally:
+            BUILD, LIB = saved
+    return _build(force, verbose, ptxas_info, [])
+
+
+def _build(force: bool, verbose: bool, ptxas_info: bool, dflags: list) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
     headers.append(os.path.join(INCLUDE, "fasttrack.h"))
@@ -56,7 +74,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
-            cmd = [exe] + _flags() + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", path, "-o", obj]
+            cmd = [exe] + _flags() + dflags + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", path, "-o", obj]
             jobs.append(cmd)
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:

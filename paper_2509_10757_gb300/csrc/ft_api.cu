@@ -277,6 +277,7 @@ DevParams make_dev_params(const ft_params &p)
     for (int o = 0; o < FT_MAX_LEVELS; ++o) {
         const int top = std::min(o + 1, std::max(p.nlevels - 1, 0));
         d.halo_oct[o] = (int)std::ceil(d.band_r[top]) + 3;
+        d.halo_c[o] = (int)std::ceil(d.band_r[std::min(o, std::max(p.nlevels - 1, 0))]) + 3;
     }
     return d;
 }
@@ -410,6 +411,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 // window (strip + 2 halo rows) must fit the shared-memory stage
                 int sr = std::max(1, tune.strip_rows);
                 sr = std::min(sr, std::max(1, F.H));
+                sr = std::min(sr, std::max(1, kWinRows - 2 * halo));
                 if (F.nr > 0) {
                     const double per_row = (double)F.nr / (double)std::max(1, F.H);
                     const int cap_rows = (int)(0.75 * kStageCap / per_row) - 2 * halo;
@@ -417,7 +419,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 }
                 F.strip_rows = sr;
                 n_stereo = (F.H + sr - 1) / sr;
-                F.rowsort = 1;
+                F.rowsort = 2;
                 F.row_ptr_l = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
                 F.row_ptr_r = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
                 F.ls_idx = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)F.nl));

@@ -22,8 +22,10 @@ namespace ft {
 constexpr int kThreads = 256;                       // threads per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kCells = FT_GRID_COLS * FT_GRID_ROWS; // 3072 grid cells
-constexpr int kStageCap = 768;                      // right keypoints staged per stereo item
+constexpr int kStageCap = 512;                      // right keypoints staged per stereo item
 constexpr int kMaxRows = 4096;                      // image rows the row sort handles
+constexpr int kWinRows = 192;                       // rows of a stereo item's staged window
+constexpr int kOctBuckets = 8;                      // octaves a staged window separates
 constexpr int kRefineChunk = 64;                    // matches refined per SAD round
 constexpr int kFishChunk = 512;                     // right descriptors staged per chunk
 constexpr int kCounters = 8;                        // per-frame counters (u32)
@@ -47,6 +49,7 @@ struct DevParams {
     float view_cos_min, view_cos_narrow, radius_narrow, radius_wide, dist_lo, dist_hi;
     int halo;            // rows a right keypoint's band can reach beyond floor(y), any octave
     int halo_oct[FT_MAX_LEVELS];   // same for the octave window of a left keypoint of octave o
+    int halo_c[FT_MAX_LEVELS];     // same for a right keypoint of octave o
 };
 
 // One camera of the search step (pinhole: the left camera only).
@@ -87,7 +90,7 @@ struct FrameDev {
     // row sort of the pinhole stereo step (scratch): keypoints bucketed by row
     int *row_ptr_l, *row_ptr_r;    // [H + 1]
     int *ls_idx;                   // [nl] left indices in row order
-    float4 *rs_kp;                 // [nr] right x, y, index, octave in row order
+    float4 *rs_kp;                 // [nr] right x, band rows lo | hi << 16, row, index | octave << 20
     uint4 *rs_desc;                // [2 * nr]
     // stereo outputs (pinhole)
     int *best_r, *dist, *sad_shift, *sad_best;
@@ -104,7 +107,7 @@ struct FrameDev {
     // work decomposition
     int strip_rows, n_stereo_items, fisheye_tile;
     int search_tile, resolve_tile;
-    int rowsort;                   // 1: index item 0 is the row sort
+    int rowsort;                   // 2: index items 0 and 1 are the left and right row sorts
     int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]
 };

@@ -44,6 +44,11 @@ constexpr int kStripW = 2 * (kW + kL) + 1;                      // 21
 constexpr int kShifts = 2 * kL + 1;                             // 11
 constexpr int kBatch = 4;                                       // loads issued ahead per thread
 
+// resident CTAs per SM the register budget is sized for
+#ifndef FT_MIN_CTAS_PER_SM
+#define FT_MIN_CTAS_PER_SM 3
+#endif
+
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
@@ -164,19 +169,19 @@ struct RefineJob {
     float xi;
 };
 
-constexpr int kGroup = 8;                       // lanes per left keypoint in the Hamming phase
+constexpr int kGroup = 4;                       // lanes per left keypoint in the Hamming phase
 constexpr int kGroups = kThreads / kGroup;      // left keypoints in flight per CTA
-constexpr int kWinRows = 512;                   // window rows whose pointers are staged
 constexpr int kSadChunk = 128;                  // matches whose SADs are summed per round
 
 struct SmemStereo {
-    float4 rkp[kStageCap];             // staged right keypoints: x, y, index, octave
+    float4 rkp[kStageCap];             // staged right keypoints sorted by (octave, row)
     uint4 sdesc[2 * kStageCap];
     float4 lkp[kThreads];              // left keypoints of the pass: x, y, index, octave
     uint4 ldesc[2 * kThreads];
     RefineJob ref[kThreads];
     int sad[kSadChunk][12];
-    int wrow[kWinRows + 1];            // row pointers of the staged window (relative)
+    int bptr[kOctBuckets * kWinRows + 1];   // start of each (octave, window row) bucket
+    int warp_sums[kWarps];
     int nref;
 };
 
@@ -337,8 +342,9 @@ __device__ __forceinline__ int own_row(float y, int H)
 }
 
 // Right keypoints are bucketed by floor(y) clamped to the image, left
-// keypoints by the row they search (int)y clamped to the image.
-__device__ void rowsort_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
+// keypoints by the row they search, (int)y clamped to the image.  The two
+// sorts are separate work items so they run side by side.
+__device__ void rowsort_right_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
 {
     const int tid = threadIdx.x, H = F.H;
     for (int r = tid; r <= H; r += kThreads) S.cnt[r] = 0;
@@ -355,18 +361,47 @@ __device__ void rowsort_item(const BatchHeader &B, const FrameDev &F, SmemRows &
             if (base + u * kThreads + tid < F.nr) atomicAdd(&S.cnt[clampi(floor_row(y[u]), 0, H - 1)], 1);
     }
     __syncthreads();
-    int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
+    const int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
     for (int r = tid; r < H; r += kThreads) F.row_ptr_r[r] = S.cnt[r];
     if (tid == 0) F.row_ptr_r[H] = total;
     __syncthreads();
-    for (int j = tid; j < F.nr; j += kThreads) {
-        const float x = __ldg(F.rx + j), y = __ldg(F.ry + j);
-        const int pos = atomicAdd(&S.cnt[clampi(floor_row(y), 0, H - 1)], 1);
-        F.rs_kp[pos] = make_float4(x, y, __int_as_float(j), __int_as_float((int)__ldg(F.roct + j)));
-        F.rs_desc[2 * pos] = __ldg(F.rdesc + 2 * j);
-        F.rs_desc[2 * pos + 1] = __ldg(F.rdesc + 2 * j + 1);
+    for (int base = 0; base < F.nr; base += 2 * kThreads) {
+        float x[2], y[2];
+        int oct[2];
+        uint4 d0[2], d1[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int j = min(base + u * kThreads + tid, F.nr - 1);
+            x[u] = __ldg(F.rx + j);
+            y[u] = __ldg(F.ry + j);
+            oct[u] = __ldg(F.roct + j);
+            d0[u] = __ldg(F.rdesc + 2 * j);
+            d1[u] = __ldg(F.rdesc + 2 * j + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int j = base + u * kThreads + tid;
+            if (j >= F.nr) continue;
+            const int row = clampi(floor_row(y[u]), 0, H - 1);
+            const int pos = atomicAdd(&S.cnt[row], 1);
+            // the rows this keypoint lists: floor(y - r) .. ceil(y + r), r = 2 scale[oct],
+            // clamped to the image (computed once here, tested per candidate later;
+            // an empty band stays empty: lo in [0, H], hi in [-1, H - 1])
+            const float r = B.p.band_r[clampi(oct[u], 0, B.p.nlevels - 1)];
+            const int lo = min(max(f2i(floorf(fsub(y[u], r))), 0), H);
+            const int hi = max(min(f2i(ceilf(fadd(y[u], r))), H - 1), -1);
+            F.rs_kp[pos] = make_float4(x[u], __int_as_float(lo | (hi << 16)), __int_as_float(row),
+                                       __int_as_float(j | ((oct[u] & 0xff) << 20)));
+            F.rs_desc[2 * pos] = d0[u];
+            F.rs_desc[2 * pos + 1] = d1[u];
+        }
     }
-    __syncthreads();
+    signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
+}
+
+__device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
+{
+    const int tid = threadIdx.x, H = F.H;
     for (int r = tid; r <= H; r += kThreads) S.cnt[r] = 0;
     __syncthreads();
     for (int base = 0; base < F.nl; base += kBatch * kThreads) {
@@ -381,27 +416,36 @@ __device__ void rowsort_item(const BatchHeader &B, const FrameDev &F, SmemRows &
             if (base + u * kThreads + tid < F.nl) atomicAdd(&S.cnt[own_row(y[u], H)], 1);
     }
     __syncthreads();
-    total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
+    const int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
     for (int r = tid; r < H; r += kThreads) F.row_ptr_l[r] = S.cnt[r];
     if (tid == 0) F.row_ptr_l[H] = total;
     __syncthreads();
-    for (int i = tid; i < F.nl; i += kThreads) {
-        const int pos = atomicAdd(&S.cnt[own_row(__ldg(F.ly + i), H)], 1);
-        F.ls_idx[pos] = i;
+    for (int base = 0; base < F.nl; base += kBatch * kThreads) {
+        float y[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = base + u * kThreads + tid;
+            y[u] = i < F.nl ? __ldg(F.ly + i) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = base + u * kThreads + tid;
+            if (i < F.nl) F.ls_idx[atomicAdd(&S.cnt[own_row(y[u], H)], 1)] = i;
+        }
     }
-    signal_count(&F.ctr[C_ROWS_DONE], 1u, s_flag);
+    signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
 }
 
 // ---------------------------------------------------------------- K_STEREO, pinhole
-// Does right keypoint (y, oct) list image row `row` (band floor(y - r) ..
-// ceil(y + r), r = 2 * scale[oct], clamped to the image)?
-__device__ __forceinline__ bool band_has(const DevParams &P, float y, int oct, int row, int H)
+// A row-sorted right keypoint record: x, band rows lo | hi << 16, bucket row,
+// index | octave << 20.
+__device__ __forceinline__ bool band_has(float packed, int row)
 {
-    const float r = P.band_r[clampi(oct, 0, P.nlevels - 1)];
-    const int lo = max(f2i(floorf(fsub(y, r))), 0);
-    const int hi = min(f2i(ceilf(fadd(y, r))), H - 1);
-    return lo <= row && row <= hi;
+    const int b = __float_as_int(packed);
+    return (b & 0xffff) <= row && row <= (b >> 16);
 }
+__device__ __forceinline__ int rec_index(float w) { return __float_as_int(w) & 0xfffff; }
+__device__ __forceinline__ int rec_octave(float w) { return (int)(int8_t)((__float_as_int(w) >> 20) & 0xff); }
 
 __device__ __forceinline__ void write_stereo(const FrameDev &F, int i, int best, int dist, int shift,
                                              int sadb, float ur, float dep)
@@ -419,7 +463,7 @@ __device__ __forceinline__ void write_stereo(const FrameDev &F, int i, int best,
 // reduce to the smallest (distance, right index); lane 0 of the group queues
 // the match for refinement or writes the final "no match" outputs.
 __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo &S, int npass,
-                              bool staged, int w_a, int e_base)
+                              bool staged, int w_a, int nrows, int e_base)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane & (kGroup - 1), gw = lane / kGroup;
@@ -441,35 +485,46 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
             const float minU = fsub(xi, maxD);
             const float maxU = fsub(xi, 0.0f);
             if (!(yi < 0.0f) && row < F.H && !(maxU < 0.0f)) {
-                const int h = (oi >= 0 && oi < P.nlevels) ? P.halo_oct[oi] : P.halo;
-                const int ra = max(row - h, 0), rb = min(row + h, F.H - 1) + 1;
-                int e0, e1;
-                if (staged) {
-                    e0 = S.wrow[ra - w_a];
-                    e1 = S.wrow[rb - w_a];
-                } else {
-                    e0 = __ldcg(F.row_ptr_r + ra) - e_base;
-                    e1 = __ldcg(F.row_ptr_r + rb) - e_base;
-                }
                 const uint4 a0 = S.ldesc[2 * t], a1 = S.ldesc[2 * t + 1];
-                for (int e = e0 + sub; e < e1; e += kGroup) {
-                    const float4 g = staged ? S.rkp[e] : __ldcg(F.rs_kp + e_base + e);
-                    const int oj = __float_as_int(g.w);
-                    if (oj < oi - 1 || oj > oi + 1) continue;
-                    if (!band_has(P, g.y, oj, row, F.H)) continue;
-                    if (g.x < minU || g.x > maxU) continue;
-                    uint4 b0, b1;
-                    if (staged) {
-                        b0 = S.sdesc[2 * e];
-                        b1 = S.sdesc[2 * e + 1];
-                    } else {
-                        b0 = __ldcg(F.rs_desc + 2 * (e_base + e));
-                        b1 = __ldcg(F.rs_desc + 2 * (e_base + e) + 1);
+                if (staged) {
+                    // candidate octaves oi-1 .. oi+1, each over the rows its band can reach
+                    const int olo = max(oi - 1, 0), ohi = min(oi + 1, kOctBuckets - 1);
+                    for (int o = olo; o <= ohi; ++o) {
+                        const int h = P.halo_c[o];
+                        const int ra = max(row - h, w_a) - w_a;
+                        const int rb = min(row + h, w_a + nrows - 1) - w_a;
+                        const int e1 = S.bptr[o * nrows + rb + 1];
+                        for (int e = S.bptr[o * nrows + ra] + sub; e < e1; e += kGroup) {
+                            const float4 g = S.rkp[e];
+                            const int oj = rec_octave(g.w);
+                            if (oj < oi - 1 || oj > oi + 1) continue;
+                            if (!band_has(g.y, row)) continue;
+                            if (g.x < minU || g.x > maxU) continue;
+                            const unsigned k = ((unsigned)ham8(a0, a1, S.sdesc[2 * e], S.sdesc[2 * e + 1]) << 20) |
+                                               (unsigned)rec_index(g.w);
+                            if (k < key) {
+                                key = k;
+                                xb = g.x;
+                            }
+                        }
                     }
-                    const unsigned k = ((unsigned)ham8(a0, a1, b0, b1) << 20) | (unsigned)__float_as_int(g.z);
-                    if (k < key) {
-                        key = k;
-                        xb = g.x;
+                } else {
+                    const int h = (oi >= 0 && oi < P.nlevels) ? P.halo_oct[oi] : P.halo;
+                    const int e0 = __ldcg(F.row_ptr_r + max(row - h, 0));
+                    const int e1 = __ldcg(F.row_ptr_r + min(row + h, F.H - 1) + 1);
+                    for (int e = e0 + sub; e < e1; e += kGroup) {
+                        const float4 g = __ldcg(F.rs_kp + e);
+                        const int oj = rec_octave(g.w);
+                        if (oj < oi - 1 || oj > oi + 1) continue;
+                        if (!band_has(g.y, row)) continue;
+                        if (g.x < minU || g.x > maxU) continue;
+                        const unsigned k = ((unsigned)ham8(a0, a1, __ldcg(F.rs_desc + 2 * e),
+                                                           __ldcg(F.rs_desc + 2 * e + 1)) << 20) |
+                                           (unsigned)rec_index(g.w);
+                        if (k < key) {
+                            key = k;
+                            xb = g.x;
+                        }
                     }
                 }
             }
@@ -659,23 +714,48 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     SmemStereo &S = U.s;
     const DevParams &P = B.p;
     const int tid = threadIdx.x;
-    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 1u, s_flag)) {
+    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag)) {
         const int H = F.H;
         const int r_lo = strip * F.strip_rows;
         const int r_hi = min(H, r_lo + F.strip_rows);
-        // stage the row-sorted right keypoints of rows [w_a, w_b] and their row pointers
+        // stage the row-sorted right keypoints of rows [w_a, w_b], re-bucketed
+        // by (octave, row) so that a left keypoint visits only its octaves
         const int w_a = max(r_lo - P.halo, 0);
         const int w_b = min(r_hi - 1 + P.halo, H - 1);
+        const int nrows = w_b - w_a + 1;
         const int e_base = __ldcg(F.row_ptr_r + w_a);
         const int e_end = __ldcg(F.row_ptr_r + w_b + 1);
-        const bool staged = e_end - e_base <= kStageCap && w_b - w_a + 1 <= kWinRows;
+        const int n_st = e_end - e_base;
+        const bool staged = n_st <= kStageCap && nrows <= kWinRows && P.nlevels <= kOctBuckets;
         if (staged) {
-            for (int e = tid; e < e_end - e_base; e += kThreads) {
-                S.rkp[e] = __ldcg(F.rs_kp + e_base + e);
-                S.sdesc[2 * e] = __ldcg(F.rs_desc + 2 * (e_base + e));
-                S.sdesc[2 * e + 1] = __ldcg(F.rs_desc + 2 * (e_base + e) + 1);
+            constexpr int Q = kStageCap / kThreads;
+            const int nb = kOctBuckets * nrows;
+            for (int b = tid; b <= nb; b += kThreads) S.bptr[b] = 0;
+            __syncthreads();
+            float4 g[Q];
+            int bucket[Q], rank[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int e = q * kThreads + tid;
+                if (e < n_st) {
+                    g[q] = __ldcg(F.rs_kp + e_base + e);
+                    bucket[q] = clampi(rec_octave(g[q].w), 0, kOctBuckets - 1) * nrows +
+                                (__float_as_int(g[q].z) - w_a);
+                    rank[q] = atomicAdd(&S.bptr[bucket[q]], 1);
+                }
             }
-            for (int r = tid; r <= w_b - w_a + 1; r += kThreads) S.wrow[r] = __ldcg(F.row_ptr_r + w_a + r) - e_base;
+            __syncthreads();
+            block_scan(S.bptr, S.bptr, nb + 1, S.warp_sums);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int e = q * kThreads + tid;
+                if (e < n_st) {
+                    const int pos = S.bptr[bucket[q]] + rank[q];
+                    S.rkp[pos] = g[q];
+                    S.sdesc[2 * pos] = __ldcg(F.rs_desc + 2 * (e_base + e));
+                    S.sdesc[2 * pos + 1] = __ldcg(F.rs_desc + 2 * (e_base + e) + 1);
+                }
+            }
         }
         if (tid == 0) S.nref = 0;
         const int l_lo = __ldcg(F.row_ptr_l + r_lo), l_hi = __ldcg(F.row_ptr_l + r_hi);
@@ -691,7 +771,7 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
                 S.ldesc[2 * tid + 1] = __ldg(F.ldesc + 2 * i + 1);
             }
             __syncthreads();
-            hamming_phase(P, F, S, npass, staged, w_a, e_base);
+            hamming_phase(P, F, S, npass, staged, w_a, nrows, e_base);
             __syncthreads();
             mark(B, 1);
             const int nref = S.nref;
@@ -855,7 +935,7 @@ __device__ bool project(const DevParams &P, const CamDev &C, const float *pose, 
 }
 
 __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C,
-                             const float *pose, int m)
+                             const float *pose, float iw, float ih, int m)
 {
     int lvl = -1, d1 = -1, d2 = -1, kp = -1;
     float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -870,8 +950,6 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
             float r = (vc > P.view_cos_narrow) ? P.radius_narrow : P.radius_wide;
             r = fmul(r, P.search_th);
             r = fmul(r, P.sc[level]);
-            const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
-            const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
             const float du = fsub(u, C.minx), dv = fsub(v, C.miny);
             const int x0 = max(f2i(floorf(fmul(fsub(du, r), iw))), 0);
             const int x1 = min(f2i(ceilf(fmul(fadd(du, r), iw))), FT_GRID_COLS - 1);
@@ -966,7 +1044,9 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         mark(B, 0);
         const int m0 = t * F.search_tile;
         const int m1 = min(F.nm, m0 + F.search_tile);
-        for (int m = m0 + tid; m < m1; m += kThreads) search_point(B.p, F, C, pose, m);
+        const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
+        const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
+        for (int m = m0 + tid; m < m1; m += kThreads) search_point(B.p, F, C, pose, iw, ih, m);
         mark(B, 1);
     } else {
         // the wait ran out (reported in the status word): leave defined outputs
@@ -1016,7 +1096,7 @@ __device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, 
 }
 
 // ---------------------------------------------------------------- the kernel
-__global__ void __launch_bounds__(kThreads, 3) ft_fused_kernel(const BatchHeader *__restrict__ hdr)
+__global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(const BatchHeader *__restrict__ hdr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &U = *reinterpret_cast<Smem *>(smem_raw);
@@ -1049,8 +1129,12 @@ __global__ void __launch_bounds__(kThreads, 3) ft_fused_kernel(const BatchHeader
         }
         switch (kind) {
         case K_INDEX:
-            if (F.rowsort && tile == 0) rowsort_item(B, F, U.r, &s_flag);
-            else grid_item(B, F, tile - F.rowsort, U.g, &s_flag);
+            if (tile < F.rowsort) {
+                if (tile == 0) rowsort_left_item(B, F, U.r, &s_flag);
+                else rowsort_right_item(B, F, U.r, &s_flag);
+            } else {
+                grid_item(B, F, tile - F.rowsort, U.g, &s_flag);
+            }
             break;
         case K_STEREO:
             if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);

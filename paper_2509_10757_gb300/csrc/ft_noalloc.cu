@@ -196,7 +196,10 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     P.dist_lo = p.dist_lo;
     P.dist_hi = p.dist_hi;
     P.halo = (int)std::ceil(rmax) + 3;
-    for (int o = 0; o < FT_MAX_LEVELS; ++o) P.halo_oct[o] = (int)std::ceil(P.band_r[std::min(o + 1, p.nlevels - 1)]) + 3;
+    for (int o = 0; o < FT_MAX_LEVELS; ++o) {
+        P.halo_oct[o] = (int)std::ceil(P.band_r[std::min(o + 1, p.nlevels - 1)]) + 3;
+        P.halo_c[o] = (int)std::ceil(P.band_r[std::min(o, p.nlevels - 1)]) + 3;
+    }
     B.nframes = 1;
     B.prefix = reinterpret_cast<const int *>(d + o_prefix);
     B.frames = reinterpret_cast<const FrameDev *>(d + o_frame);
@@ -251,11 +254,11 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     }
     F.strip_rows = sr;
     F.n_stereo_items = (H + sr - 1) / sr;
-    F.rowsort = 1;
-    F.n_index_items = 1;
+    F.rowsort = 2;
+    F.n_index_items = 2;
     F.ctr = reinterpret_cast<unsigned *>(d + o_ctr);
     int *prefix = reinterpret_cast<int *>(host + o_prefix);
-    const int per_kind[K_KINDS] = {1, F.n_stereo_items, 0, 0};
+    const int per_kind[K_KINDS] = {2, F.n_stereo_items, 0, 0};
     int total = 0;
     for (int k = 0; k < K_KINDS; ++k) {
         prefix[2 * k] = 0;
