@@ -330,6 +330,113 @@ def run_profile(args, local_rank):
     print(json.dumps({"profile_run": "ok", "launches": args.warmup + args.steps}), flush=True)
 
 
+def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batch: int, seed: int = 0):
+    """Drive the served loop with Poisson arrivals (rate_hz per stream) for
+    `seconds`; returns throughput, latency percentiles and dropped frames."""
+    import ctypes as C
+
+    from paper_2509_10757_gb300.batch import HostFrame, stream_desc_of
+    d = L.ft_server_desc()
+    L.ft_server_desc_default(C.byref(d))
+    need = 0
+    descs = [stream_desc_of(fr) for fr in frames]
+    d.hbm_budget = 8 << 30
+    d.n_slots, d.max_batch = n_slots, max_batch
+    d.slot_arena_bytes = 512 << 20
+    srv = C.c_void_p()
+    L.check(L.ft_server_create(C.byref(srv), C.byref(d), None), "ft_server_create")
+    hosts, sids = [], []
+    try:
+        for fr, desc in zip(frames, descs):
+            h = HostFrame(fr)
+            sid = C.c_int()
+            L.check(L.ft_server_open_stream(srv, C.byref(desc), C.byref(sid)), "open_stream")
+            if fr.camera == "pinhole":
+                pl, pr = h.pyramids()
+                L.check(L.ft_server_set_pyramids(srv, sid.value, C.byref(pl), C.byref(pr)), "pyramids")
+            L.check(L.ft_server_set_map(srv, sid.value, C.byref(h.map_view())), "map")
+            hosts.append(h)
+            sids.append(sid.value)
+        reqs = [h.request(sid, 0) for h, sid in zip(hosts, sids)]
+        units = [fr.left.n + fr.map.n for fr in frames]
+        rng = np.random.default_rng(seed)
+        arrivals = []
+        for k in range(len(frames)):
+            t = rng.exponential(1.0 / rate_hz)
+            while t < seconds:
+                arrivals.append((t, k))
+                t += rng.exponential(1.0 / rate_hz)
+        arrivals.sort()
+        done = []
+        stop = threading.Event()
+
+        def poller():
+            buf = (L.ft_completion * 512)()
+            while not stop.is_set() or len(done) < submitted[0] - dropped[0]:
+                k = L.ft_server_poll(srv, buf, 512, 2000)
+                for i in range(k):
+                    c = buf[i]
+                    done.append((c.stream_id, c.t_submit_us, c.t_done_us))
+                if stop.is_set() and k == 0 and time.time() > deadline[0]:
+                    break
+
+        submitted, dropped, deadline = [0], [0], [0.0]
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (t, k) in enumerate(arrivals):
+            while True:
+                dt = t - (time.perf_counter() - t0)
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.0005))
+            r = reqs[k]
+            r.tag = i
+            st = L.ft_server_submit(srv, C.byref(r))
+            submitted[0] += 1
+            if st == L.FT_EBUSY:
+                dropped[0] += 1
+        t_end = time.perf_counter()
+        deadline[0] = time.time() + 30.0
+        stop.set()
+        th.join(timeout=40.0)
+        wall = max(t_end - t0, 1e-9)
+        stats = L.ft_server_stats()
+        L.ft_server_get_stats(srv, C.byref(stats))
+    finally:
+        L.ft_server_destroy(srv)
+    lat = np.array([(b - a) / 1e3 for _, a, b in done]) if done else np.zeros(1)
+    t_last = max((b for _, _, b in done), default=0.0)
+    t_first = min((a for _, a, _ in done), default=0.0)
+    span = max((t_last - t_first) / 1e6, wall)
+    served_units = sum(units[sids.index(sid)] for sid, _, _ in done)
+    return {"value": served_units / span, "unit": UNIT, "offered_hz": rate_hz * len(frames),
+            "completed": len(done), "dropped": dropped[0], "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_batch": stats.frames_launched / max(1, stats.batches),
+            "slots": n_slots, "max_batch": max_batch, "seconds": seconds}
+
+
+def run_served(args, local_rank, seconds: float = 4.0, streams: int = 256):
+    """Served mixed streams: 256 camera streams of uneven shapes, Poisson 30 Hz
+    each, resident state, HBM-budget admission; the batched server against
+    the plain form (one frame per launch, one slot)."""
+    import torch
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300 import build as B
+    from paper_2509_10757_gb300 import scenes
+    torch.cuda.set_device(local_rank)
+    B.build()
+    L.load()
+    frames = [scenes.served_stream_frame(0, s) for s in range(streams)]
+    out = {"workload": "served mixed streams: 256 camera streams (640x480, 752x480, 1280x720 pinhole, "
+                       "512x512 fisheye), 500-4000 keypoints, 1k-20k map points, Poisson arrivals"}
+    out["served_30hz"] = serve_load(frames, L, 30.0, seconds, n_slots=3, max_batch=64)
+    out["plain_30hz"] = serve_load(frames, L, 30.0, seconds, n_slots=1, max_batch=1)
+    out["served_120hz"] = serve_load(frames, L, 120.0, seconds, n_slots=3, max_batch=64)
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import ctypes as C
 
@@ -477,13 +584,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served"])
     ap.add_argument("--trace-out", default=None)
     args = ap.parse_args()
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])
     if args.mode == "profile":
         return run_profile(args, dist_env()[2])
+    if args.mode == "served":
+        print(json.dumps(run_served(args, dist_env()[2])), flush=True)
+        return
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch

@@ -347,6 +347,103 @@ ft_status ft_set_trace(ft_ctx *ctx, int capacity);
  * *n receives the number of records the call produced (may exceed max). */
 ft_status ft_read_trace(ft_ctx *ctx, ft_trace_record *out, int max, int *n);
 
+/* ----------------------------------------------------------------------
+ * Served request loop: continuous batching of tracking requests from many
+ * independent camera streams on one GPU (an addition of this library; the
+ * paper tracks one camera).
+ *
+ * Camera streams are admitted against an HBM budget: the server allocates a
+ * device pool of hbm_budget bytes once and gives every admitted stream a
+ * block for its resident state (both pyramids, the local map, the per-frame
+ * keypoint block and the result block); a stream that does not fit is
+ * refused with FT_EBUSY until others close.  Requests (one frame: keypoints,
+ * descriptors, taken flags and pose, all in host memory) are copied into
+ * the stream's pinned staging at submit.  A scheduler thread fills free
+ * slots -- n_slots contexts, each with its own arena and CUDA stream -- with
+ * batches of up to max_batch pending requests in arrival order, at most one
+ * per stream and none of a stream whose previous request is still running;
+ * one launch of ft_track_batch serves a batch.  Requests arriving while
+ * batches run go to the next free slot, so work overlaps on the device.
+ * Results are copied back to pinned host memory and returned by
+ * ft_server_poll with submit / start / completion times (host clock, us).
+ * With dry_run the server touches no GPU: batches "complete" after
+ * dry_run_latency_us, for testing the scheduling and admission logic.
+ * ---------------------------------------------------------------------- */
+typedef struct ft_server ft_server;
+
+typedef struct {
+    int device;
+    size_t hbm_budget;          /* device pool for resident stream state */
+    int n_slots;                /* batches in flight at once (>= 1) */
+    int max_batch;              /* frames per batch (>= 1) */
+    size_t slot_arena_bytes;    /* scratch arena of each slot's context */
+    int dry_run;                /* 1: no GPU, fake completions */
+    double dry_run_latency_us;  /* fake batch duration */
+} ft_server_desc;
+
+/* A camera stream: its model, pyramid level sizes (pinhole; level pitch =
+ * width) and capacities. */
+typedef struct {
+    int camera;
+    ft_pinhole pinhole;
+    ft_fisheye_rig fisheye;
+    int nlevels;
+    int level_width[FT_MAX_LEVELS], level_height[FT_MAX_LEVELS];
+    int max_left, max_right, max_map;
+} ft_stream_desc;
+
+/* One frame of a stream (all pointers in host memory; taken may be NULL). */
+typedef struct {
+    int stream_id;
+    uint64_t tag;
+    ft_keypoints left, right;
+    const uint8_t *taken_left, *taken_right;
+    ft_pose pose;
+    float O_right[3];
+} ft_request;
+
+/* Host copies of one request's results (valid until the stream's second
+ * next request completes). */
+typedef struct {
+    int n_left, n_right, n_map;
+    ft_stereo_out stereo;       /* pinhole */
+    ft_fisheye_out fisheye;     /* fisheye */
+    ft_search_out search;
+} ft_results;
+
+typedef struct {
+    uint64_t tag;
+    int stream_id;
+    int32_t status;
+    double t_submit_us, t_start_us, t_done_us;
+    ft_results results;
+} ft_completion;
+
+typedef struct {
+    uint64_t submitted, completed, batches, frames_launched, streams_open, pending;
+    size_t pool_used, pool_capacity;
+    int32_t last_error;         /* status of the last failed launch (0: none) */
+} ft_server_stats;
+
+void ft_server_desc_default(ft_server_desc *d);
+/* params NULL = defaults (the parameters every batch uses). */
+ft_status ft_server_create(ft_server **out, const ft_server_desc *desc, const ft_params *params);
+/* Stops the scheduler, waits for work in flight, frees everything. */
+void ft_server_destroy(ft_server *s);
+/* Admit a stream (FT_EBUSY: the HBM budget cannot hold it now). */
+ft_status ft_server_open_stream(ft_server *s, const ft_stream_desc *d, int *stream_id);
+/* Release a stream's block (FT_EBUSY while it has requests queued or running). */
+ft_status ft_server_close_stream(ft_server *s, int stream_id);
+/* Upload a stream's resident pyramids / local map from host memory (synchronous). */
+ft_status ft_server_set_pyramids(ft_server *s, int stream_id, const ft_pyramid *left, const ft_pyramid *right);
+ft_status ft_server_set_map(ft_server *s, int stream_id, const ft_map_view *map);
+/* Queue one frame (FT_EBUSY: the stream already has two frames waiting). */
+ft_status ft_server_submit(ft_server *s, const ft_request *req);
+/* Move up to max completions to out, waiting up to timeout_us for the first;
+ * returns how many. */
+int ft_server_poll(ft_server *s, ft_completion *out, int max, int timeout_us);
+ft_status ft_server_get_stats(ft_server *s, ft_server_stats *stats);
+
 /* Pinhole stereo matching of one frame, like ft_stereo_match_pinhole, for
  * callers that must not allocate memory.  The paper has no counterpart: it is
  * an addition of this library.

@@ -132,6 +132,42 @@ class ft_trace_record(C.Structure):
                 ("mark", C.c_uint64 * 4)]
 
 
+class ft_server_desc(C.Structure):
+    _fields_ = [("device", i32), ("hbm_budget", C.c_size_t), ("n_slots", i32), ("max_batch", i32),
+                ("slot_arena_bytes", C.c_size_t), ("dry_run", i32), ("dry_run_latency_us", C.c_double)]
+
+
+class ft_stream_desc(C.Structure):
+    _fields_ = [("camera", i32), ("pinhole", ft_pinhole), ("fisheye", ft_fisheye_rig),
+                ("nlevels", i32), ("level_width", i32 * FT_MAX_LEVELS),
+                ("level_height", i32 * FT_MAX_LEVELS), ("max_left", i32), ("max_right", i32),
+                ("max_map", i32)]
+
+
+class ft_request(C.Structure):
+    _fields_ = [("stream_id", i32), ("tag", C.c_uint64), ("left", ft_keypoints),
+                ("right", ft_keypoints), ("taken_left", vp), ("taken_right", vp),
+                ("pose", ft_pose), ("O_right", f32 * 3)]
+
+
+class ft_results(C.Structure):
+    _fields_ = [("n_left", i32), ("n_right", i32), ("n_map", i32), ("stereo", ft_stereo_out),
+                ("fisheye", ft_fisheye_out), ("search", ft_search_out)]
+
+
+class ft_completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("stream_id", i32), ("status", C.c_int32),
+                ("t_submit_us", C.c_double), ("t_start_us", C.c_double), ("t_done_us", C.c_double),
+                ("results", ft_results)]
+
+
+class ft_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
+                ("frames_launched", C.c_uint64), ("streams_open", C.c_uint64),
+                ("pending", C.c_uint64), ("pool_used", C.c_size_t), ("pool_capacity", C.c_size_t),
+                ("last_error", C.c_int32)]
+
+
 # (name, restype, argtypes): every entry point the header declares
 SIGNATURES = [
     ("ft_params_default", None, [C.POINTER(ft_params)]),
@@ -158,6 +194,16 @@ SIGNATURES = [
     ("ft_set_trace", i32, [vp, i32]),
     ("ft_read_trace", i32, [vp, C.POINTER(ft_trace_record), i32, C.POINTER(i32)]),
     ("ft_launch_count", C.c_uint64, [vp]),
+    ("ft_server_desc_default", None, [C.POINTER(ft_server_desc)]),
+    ("ft_server_create", i32, [C.POINTER(vp), C.POINTER(ft_server_desc), C.POINTER(ft_params)]),
+    ("ft_server_destroy", None, [vp]),
+    ("ft_server_open_stream", i32, [vp, C.POINTER(ft_stream_desc), C.POINTER(i32)]),
+    ("ft_server_close_stream", i32, [vp, i32]),
+    ("ft_server_set_pyramids", i32, [vp, i32, C.POINTER(ft_pyramid), C.POINTER(ft_pyramid)]),
+    ("ft_server_set_map", i32, [vp, i32, C.POINTER(ft_map_view)]),
+    ("ft_server_submit", i32, [vp, C.POINTER(ft_request)]),
+    ("ft_server_poll", i32, [vp, C.POINTER(ft_completion), i32, i32]),
+    ("ft_server_get_stats", i32, [vp, C.POINTER(ft_server_stats)]),
     ("ft_stereo_match_pinhole_noalloc", i32, [vp, C.POINTER(ft_params), C.POINTER(ft_pinhole),
                                               C.POINTER(ft_stereo_frame), C.POINTER(ft_stereo_out),
                                               vp]),

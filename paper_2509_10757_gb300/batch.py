@@ -362,3 +362,104 @@ def run_batch(ctx: Context, pb: PackedBatch, params: L.ft_params | None = None, 
     p = C.byref(params) if params is not None else None
     L.check(ctx.lib.ft_track_batch(ctx.ptr, stream_handle(stream), p, C.byref(b)),
             "ft_track_batch")
+
+
+# ---------------------------------------------------------------- served loop marshalling
+def stream_desc_of(frame, slack: float = 1.0) -> L.ft_stream_desc:
+    """Stream description for frames shaped like `frame` (capacities scaled by slack)."""
+    d = L.ft_stream_desc()
+    if frame.camera == "pinhole":
+        d.camera = L.FT_CAMERA_PINHOLE
+        d.pinhole = pinhole_struct(frame.cam)
+        d.nlevels = len(frame.pyr_left)
+        for l, img in enumerate(frame.pyr_left):
+            d.level_height[l], d.level_width[l] = img.shape
+    else:
+        d.camera = L.FT_CAMERA_FISHEYE
+        d.fisheye = rig_struct(frame.rig)
+        d.nlevels = 8
+    d.max_left = int(frame.left.n * slack)
+    d.max_right = int(frame.right.n * slack)
+    d.max_map = int(frame.map.n * slack)
+    return d
+
+
+class HostFrame:
+    """Host arrays of one frame kept alive for ft_request / ft_server_set_* calls."""
+
+    def __init__(self, frame):
+        self.frame = frame
+        c = np.ascontiguousarray
+        self.lx, self.ly = c(frame.left.x, np.float32), c(frame.left.y, np.float32)
+        self.lo, self.ld = c(frame.left.oct, np.int8), c(frame.left.desc, np.uint8)
+        self.rx, self.ry = c(frame.right.x, np.float32), c(frame.right.y, np.float32)
+        self.ro, self.rd = c(frame.right.oct, np.int8), c(frame.right.desc, np.uint8)
+        self.tl = c(frame.taken_l, np.uint8)
+        self.tr = c(frame.taken_r, np.uint8) if frame.taken_r is not None else None
+        self.pos, self.nrm = c(frame.map.pos, np.float32), c(frame.map.nrm, np.float32)
+        self.md, self.sk = c(frame.map.desc, np.uint8), c(frame.map.skip, np.uint8)
+        self.pyr = None
+        if frame.camera == "pinhole":
+            self.pyr = [[c(x, np.uint8) for x in frame.pyr_left], [c(x, np.uint8) for x in frame.pyr_right]]
+
+    def request(self, sid: int, tag: int) -> L.ft_request:
+        r = L.ft_request()
+        r.stream_id, r.tag = sid, tag
+        r.left = L.ft_keypoints(self.frame.left.n, self.lx.ctypes.data, self.ly.ctypes.data,
+                                self.lo.ctypes.data, self.ld.ctypes.data)
+        r.right = L.ft_keypoints(self.frame.right.n, self.rx.ctypes.data, self.ry.ctypes.data,
+                                 self.ro.ctypes.data, self.rd.ctypes.data)
+        r.taken_left = self.tl.ctypes.data
+        r.taken_right = None if self.tr is None else self.tr.ctypes.data
+        r.pose = pose_struct(self.frame.pose)
+        if self.frame.O_right is not None:
+            r.O_right[:] = _f32(self.frame.O_right)
+        return r
+
+    def map_view(self) -> L.ft_map_view:
+        return L.ft_map_view(self.frame.map.n, self.pos.ctypes.data, self.nrm.ctypes.data,
+                             self.md.ctypes.data, self.sk.ctypes.data)
+
+    def pyramids(self):
+        out = []
+        for levels in self.pyr:
+            p = L.ft_pyramid()
+            p.nlevels = len(levels)
+            for l, img in enumerate(levels):
+                p.data[l] = img.ctypes.data
+                p.height[l], p.width[l] = img.shape
+                p.pitch[l] = img.shape[1]
+            out.append(p)
+        return out
+
+
+def results_arrays(c: L.ft_completion, camera: str) -> dict:
+    """numpy copies of a completion's host results."""
+    r = c.results
+    nl, nr, m = r.n_left, r.n_right, r.n_map
+
+    def arr(ptr, n, ct, dt, shape=None):
+        if n == 0 or not ptr:
+            return np.zeros(shape or (n,), dt)
+        a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(n,)).copy()
+        return a.reshape(shape) if shape else a
+
+    out = {}
+    if camera == "pinhole":
+        s = r.stereo
+        for k in ("best_r", "dist", "sad_shift", "sad_best"):
+            out[k] = arr(getattr(s, k), nl, C.c_int32, np.int32)
+        out["u_right"] = arr(s.u_right, nl, C.c_float, np.float32)
+        out["depth"] = arr(s.depth, nl, C.c_float, np.float32)
+        sides = (("l", r.search.left, nl),)
+    else:
+        for k in ("r_idx", "d1", "d2"):
+            out[k] = arr(getattr(r.fisheye, k), nl, C.c_int32, np.int32)
+        sides = (("l", r.search.left, nl), ("r", r.search.right, nr))
+    for sfx, o, nk in sides:
+        out["level_" + sfx] = arr(o.level, m, C.c_int8, np.int8)
+        out["proj_" + sfx] = arr(o.proj, 4 * m, C.c_float, np.float32, (m, 4))
+        for k in ("mp_kp", "mp_d1", "mp_d2"):
+            out[f"{k}_{sfx}"] = arr(getattr(o, k), m, C.c_int32, np.int32)
+        out["kp_mp_" + sfx] = arr(o.kp_mp, nk, C.c_int32, np.int32)
+    return out
