@@ -539,6 +539,9 @@ def run_gpu(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(frames, budget_s=12.0)
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = run_served(args, local_rank, seconds=3.0)
     ctx_tuning = {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
                   "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm}
     ctx.close()
@@ -574,16 +577,19 @@ def run_gpu(args, rank, world, local_rank):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if served is not None:
+        line["served"] = served
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served"])
     ap.add_argument("--trace-out", default=None)
     args = ap.parse_args()
