@@ -46,9 +46,9 @@ def _input_arrays(f, fr):
            ((f, "taken_l"), fr.taken_l)]
     if fr.camera == "pinhole":
         for l, img in enumerate(fr.pyr_left):
-            out.append(((f, f"pyrL{l}"), img))
+            out.append(((f, f"pyrL{l}"), pad_rows(img)))
         for l, img in enumerate(fr.pyr_right):
-            out.append(((f, f"pyrR{l}"), img))
+            out.append(((f, f"pyrR{l}"), pad_rows(img)))
     else:
         out.append(((f, "taken_r"), fr.taken_r))
     out += [((f, "pos"), fr.map.pos), ((f, "nrm"), fr.map.nrm), ((f, "mdesc"), fr.map.desc),
@@ -71,6 +71,16 @@ def _output_specs(f, fr):
         spec += [((f, f"{k}_{s}"), np.int32, (m,)) for k in ("mp_kp", "mp_d1", "mp_d2")]
         spec += [((f, f"kp_mp_{s}"), np.int32, (nk,))]
     return spec
+
+
+def pad_rows(img: np.ndarray, align: int = 16) -> np.ndarray:
+    """Copy of a level image with its row pitch rounded up to `align` bytes
+    (the library reads pyramid rows as 32-bit words)."""
+    h, w = img.shape
+    pitch = (w + align - 1) // align * align
+    out = np.zeros((h, pitch), np.uint8)
+    out[:, :w] = img
+    return out
 
 
 def _f32(a):
@@ -168,7 +178,7 @@ class PackedBatch:
         for l, img in enumerate(levels):
             s.data[l] = self.pin_(f, f"pyr{side}{l}")
             s.height[l], s.width[l] = img.shape
-            s.pitch[l] = img.shape[1]
+            s.pitch[l] = pad_rows(img[:1]).shape[1]
         return s
 
     def map_view(self, f) -> L.ft_map_view:

@@ -179,6 +179,9 @@ ft_status check_pyramid(const ft_pyramid &p, int nlevels, const char *what)
         if (p.width[l] <= 0 || p.height[l] <= 0 || p.pitch[l] < p.width[l])
             return fail(FT_EINVAL, "%s: level %d has bad size %dx%d pitch %d", what, l, p.width[l],
                         p.height[l], p.pitch[l]);
+        if ((reinterpret_cast<uintptr_t>(p.data[l]) & 3u) || (p.pitch[l] & 3))
+            return fail(FT_EALIGN, "%s: level %d needs a 4-byte aligned pointer and pitch (pitch %d)", what, l,
+                        p.pitch[l]);
     }
     return FT_OK;
 }
@@ -483,6 +486,14 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 C.owner = reinterpret_cast<unsigned long long *>(carve(sizeof(unsigned long long) * (size_t)C.nk));
                 n_search[c] = (F.nm + F.search_tile - 1) / F.search_tile;
                 n_resolve[c] = (std::max(F.nm, C.nk) + F.resolve_tile - 1) / F.resolve_tile;
+            }
+            // small frames: the last search item resolves (no resolve items wait)
+            bool fold = true;
+            for (int c = 0; c < F.ncam; ++c)
+                fold = fold && n_search[c] > 0 && std::max(F.nm, F.cam[c].nk) <= kFoldResolveMax;
+            if (fold) {
+                F.fold_resolve = 1;
+                n_resolve[0] = n_resolve[1] = 0;
             }
             F.n_grid_items = F.ncam;
         }

@@ -28,6 +28,7 @@ constexpr int kWinRows = 192;                       // rows of a stereo item's s
 constexpr int kOctBuckets = 8;                      // octaves a staged window separates
 constexpr int kRefineChunk = 64;                    // matches refined per SAD round
 constexpr int kFishChunk = 512;                     // right descriptors staged per chunk
+constexpr int kFoldResolveMax = 8192;               // frames up to this size resolve in their last search item
 constexpr int kCounters = 8;                        // per-frame counters (u32)
 
 enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
@@ -108,6 +109,7 @@ struct FrameDev {
     int strip_rows, n_stereo_items, fisheye_tile;
     int search_tile, resolve_tile;
     int rowsort;                   // 2: index items 0 and 1 are the left and right row sorts
+    int fold_resolve;              // 1: the last search item of a camera writes the final tables
     int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]
 };

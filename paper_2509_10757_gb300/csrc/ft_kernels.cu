@@ -171,13 +171,28 @@ struct RefineJob {
 
 constexpr int kGroup = 4;                       // lanes per left keypoint in the Hamming phase
 constexpr int kGroups = kThreads / kGroup;      // left keypoints in flight per CTA
-constexpr int kSadChunk = 128;                  // matches whose SADs are summed per round
+constexpr int kSadChunk = 64;                   // matches refined per round
+constexpr int kRowL = 12;                       // padded bytes of a left patch row (11 used)
+constexpr int kRowR = 24;                       // padded bytes of a right strip row (21 used)
+
+// patches of one refinement round, rows padded to whole words
+struct PatchBuf {
+    uint8_t l[kSadChunk][(2 * kW + 1) * kRowL];
+    uint8_t r[kSadChunk][(2 * kW + 1) * kRowR];
+};
+// left keypoints of a pass (Hamming phase)
+struct LeftBuf {
+    float4 lkp[kThreads];              // x, y, index, octave
+    uint4 ldesc[2 * kThreads];
+};
 
 struct SmemStereo {
     float4 rkp[kStageCap];             // staged right keypoints sorted by (octave, row)
     uint4 sdesc[2 * kStageCap];
-    float4 lkp[kThreads];              // left keypoints of the pass: x, y, index, octave
-    uint4 ldesc[2 * kThreads];
+    union {                            // the pass's left keypoints are dead once the
+        LeftBuf left;                  // Hamming phase is over; the patches reuse them
+        PatchBuf patch;
+    } u;
     RefineJob ref[kThreads];
     int sad[kSadChunk][12];
     int bptr[kOctBuckets * kWinRows + 1];   // start of each (octave, window row) bucket
@@ -201,9 +216,12 @@ struct SmemFish {
     int count;
 };
 
+constexpr int kMedianSmem = 8192;               // left keypoints whose SADs the median keeps on chip
+
 struct SmemMedian {
     int hist[256];
     int count, bin, before;
+    int vals[kMedianSmem];
 };
 
 struct SmemSearch {
@@ -476,7 +494,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
         float xi = 0.0f, yi = 0.0f;
         int oi = 0, i = 0;
         if (have) {
-            const float4 L = S.lkp[t];
+            const float4 L = S.u.left.lkp[t];
             xi = L.x;
             yi = L.y;
             i = __float_as_int(L.z);
@@ -485,7 +503,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
             const float minU = fsub(xi, maxD);
             const float maxU = fsub(xi, 0.0f);
             if (!(yi < 0.0f) && row < F.H && !(maxU < 0.0f)) {
-                const uint4 a0 = S.ldesc[2 * t], a1 = S.ldesc[2 * t + 1];
+                const uint4 a0 = S.u.left.ldesc[2 * t], a1 = S.u.left.ldesc[2 * t + 1];
                 if (staged) {
                     // candidate octaves oi-1 .. oi+1, each over the rows its band can reach
                     const int olo = max(oi - 1, 0), ohi = min(oi + 1, kOctBuckets - 1);
@@ -564,38 +582,64 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
     }
 }
 
-// Phases 2-3 for refine jobs [r0, r0 + nc): one thread per (job, patch row)
-// loads that row of the left patch and of the right strip plus the centre
-// values (all loads in flight together), adds the row's part of the 11 SADs
-// of centre-subtracted patches; then per job the first strict minimum over
-// the shifts, the parabola, disparity and depth.
+// Phases 2-3 for refine jobs [r0, r0 + nc), nc <= kSadChunk:
+// (2) one warp per match copies its 11 left patch rows and 11 right strip
+//     rows into shared memory, lanes on consecutive bytes (coalesced);
+// (3) one thread per (match, patch row) reads its rows as words and adds the
+//     row's part of the 11 SADs of centre-subtracted patches; then per match
+//     the first strict minimum over the shifts, the parabola, disparity and
+//     depth.
 __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &S, int r0, int nc)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kRows = 2 * kW + 1;
     for (int q = tid; q < nc * kShifts; q += kThreads) S.sad[q / kShifts][q % kShifts] = 0;
+    // one thread per (match, row, side): the 32-bit words holding the row's
+    // bytes (level rows are 4-byte aligned: pointer and pitch checked on the
+    // host) are all requested first, then re-aligned with funnel shifts into
+    // the padded shared-memory row
+    for (int q = tid; q < nc * 2 * kRows; q += kThreads) {
+        const int mm = q / (2 * kRows), rem = q - mm * (2 * kRows);
+        const int row = rem >> 1;
+        const bool right = (rem & 1) != 0;
+        const RefineJob &J = S.ref[r0 + mm];
+        const uint8_t *base = right ? F.pyrR[J.l] + (size_t)(J.vl - kW + row) * F.rp[J.l] + (J.ur0 - kL - kW)
+                                    : F.pyrL[J.l] + (size_t)(J.vl - kW + row) * F.lp[J.l] + (J.ul - kW);
+        const int len = right ? kStripW : 2 * kW + 1;
+        const int off = (int)(reinterpret_cast<uintptr_t>(base) & 3u);
+        const unsigned *wp = reinterpret_cast<const unsigned *>(base - off);
+        const int nw = ((off + len - 1) >> 2) + 1;                 // words holding the row (<= 6)
+        unsigned w[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) w[k] = k < nw ? __ldg(wp + k) : 0u;
+        unsigned *dst = right ? reinterpret_cast<unsigned *>(S.u.patch.r[mm] + row * kRowR)
+                              : reinterpret_cast<unsigned *>(S.u.patch.l[mm] + row * kRowL);
+        const int nout = (len + 3) >> 2;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < nout) dst[k] = __funnelshift_r(w[k], w[k + 1], 8 * off);
+    }
     __syncthreads();
-    for (int q = tid; q < nc * (2 * kW + 1); q += kThreads) {
+    for (int q = tid; q < nc * kRows; q += kThreads) {
         const int dy = q / nc, m = q - dy * nc;
-        const RefineJob &J = S.ref[r0 + m];
-        const uint8_t *IL = F.pyrL[J.l];
-        const uint8_t *IR = F.pyrR[J.l];
-        const int lp = F.lp[J.l], rp = F.rp[J.l];
-        const uint8_t *gl = IL + (size_t)(J.vl - kW + dy) * lp + (J.ul - kW);
-        const uint8_t *gr = IR + (size_t)(J.vl - kW + dy) * rp + (J.ur0 - kL - kW);
-        const uint8_t *gc = IR + (size_t)J.vl * rp + (J.ur0 - kL);
-        int lv[2 * kW + 1], rv[kStripW], cr[kShifts];
+        const unsigned *wl = reinterpret_cast<const unsigned *>(S.u.patch.l[m] + dy * kRowL);
+        const unsigned *wr = reinterpret_cast<const unsigned *>(S.u.patch.r[m] + dy * kRowR);
+        const unsigned *wc = reinterpret_cast<const unsigned *>(S.u.patch.r[m] + kW * kRowR);
+        // left row minus the left centre, right row, and the centres of the
+        // 11 right patches (bytes 5..15 of the right centre row)
+        const int cl = S.u.patch.l[m][kW * kRowL + kW];
+        int lc[2 * kW + 1], rv[kStripW], cr[kShifts];
 #pragma unroll
-        for (int c = 0; c < 2 * kW + 1; ++c) lv[c] = __ldg(gl + c);
+        for (int b = 0; b < 2 * kW + 1; ++b) lc[b] = (int)((wl[b >> 2] >> (8 * (b & 3))) & 0xff) - cl;
 #pragma unroll
-        for (int c = 0; c < kStripW; ++c) rv[c] = __ldg(gr + c);
+        for (int b = 0; b < kStripW; ++b) rv[b] = (wr[b >> 2] >> (8 * (b & 3))) & 0xff;
 #pragma unroll
-        for (int c = 0; c < kShifts; ++c) cr[c] = __ldg(gc + c);
-        const int cl = __ldg(IL + (size_t)J.vl * lp + J.ul);
+        for (int k = 0; k < kShifts; ++k) cr[k] = (wc[(k + kW) >> 2] >> (8 * ((k + kW) & 3))) & 0xff;
 #pragma unroll
         for (int k = 0; k < kShifts; ++k) {
             int s = 0;
 #pragma unroll
-            for (int dx = 0; dx < 2 * kW + 1; ++dx) s += abs((lv[dx] - cl) - (rv[k + dx] - cr[k]));
+            for (int dx = 0; dx < 2 * kW + 1; ++dx) s += abs(lc[dx] - (rv[k + dx] - cr[k]));
             atomicAdd(&S.sad[m][k], s);
         }
     }
@@ -662,18 +706,28 @@ __device__ void select_bin(const int *hist, int k, int *bin, int *before)
 }
 
 // a5: median of the frame's accepted SAD minima (radix select on 2 x 8 bits),
-// then drop matches with SAD >= factor * median.
+// then drop matches with SAD >= factor * median.  Frames of up to
+// kMedianSmem left keypoints load the values once into shared memory;
+// larger frames read them three times.
+__device__ __forceinline__ int median_value(const FrameDev &F, const SmemMedian &M, bool on_chip, int i)
+{
+    return on_chip ? M.vals[i] : __ldcg(F.sad_best + i);
+}
+
 __device__ void median_reject(const FrameDev &F, const DevParams &P, SmemMedian &M)
 {
     const int tid = threadIdx.x;
+    const bool on_chip = F.nl <= kMedianSmem;
+    if (on_chip)
+        for (int i = tid; i < F.nl; i += kThreads) M.vals[i] = __ldcg(F.sad_best + i);
     for (int b = tid; b < 256; b += kThreads) M.hist[b] = 0;
     if (tid == 0) M.count = 0;
     __syncthreads();
     int local = 0;
     for (int i = tid; i < F.nl; i += kThreads) {
-        const int v = __ldcg(F.sad_best + i);
-        if (v >= 0) {
-            atomicAdd(&M.hist[(v >> 8) & 255], 1);
+        const int x = median_value(F, M, on_chip, i);
+        if (x >= 0) {
+            atomicAdd(&M.hist[(x >> 8) & 255], 1);
             ++local;
         }
     }
@@ -691,8 +745,8 @@ __device__ void median_reject(const FrameDev &F, const DevParams &P, SmemMedian 
     for (int b = tid; b < 256; b += kThreads) M.hist[b] = 0;
     __syncthreads();
     for (int i = tid; i < F.nl; i += kThreads) {
-        const int v = __ldcg(F.sad_best + i);
-        if (v >= 0 && ((v >> 8) & 255) == hi) atomicAdd(&M.hist[v & 255], 1);
+        const int x = median_value(F, M, on_chip, i);
+        if (x >= 0 && ((x >> 8) & 255) == hi) atomicAdd(&M.hist[x & 255], 1);
     }
     __syncthreads();
     if (tid < 32) select_bin(M.hist, k2, &M.bin, &M.before);
@@ -700,8 +754,8 @@ __device__ void median_reject(const FrameDev &F, const DevParams &P, SmemMedian 
     const int median = (hi << 8) | M.bin;
     const float th = fmul(P.median_factor, (float)median);
     for (int i = tid; i < F.nl; i += kThreads) {
-        const int v = __ldcg(F.sad_best + i);
-        if (v >= 0 && (float)v >= th) {
+        const int x = median_value(F, M, on_chip, i);
+        if (x >= 0 && (float)x >= th) {
             F.u_right[i] = -1.0f;
             F.depth[i] = -1.0f;
         }
@@ -765,10 +819,10 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
             const int npass = min(kThreads, l_hi - pass);
             if (tid < npass) {
                 const int i = __ldcg(F.ls_idx + pass + tid);
-                S.lkp[tid] = make_float4(__ldg(F.lx + i), __ldg(F.ly + i), __int_as_float(i),
-                                         __int_as_float((int)__ldg(F.loct + i)));
-                S.ldesc[2 * tid] = __ldg(F.ldesc + 2 * i);
-                S.ldesc[2 * tid + 1] = __ldg(F.ldesc + 2 * i + 1);
+                S.u.left.lkp[tid] = make_float4(__ldg(F.lx + i), __ldg(F.ly + i), __int_as_float(i),
+                                                __int_as_float((int)__ldg(F.loct + i)));
+                S.u.left.ldesc[2 * tid] = __ldg(F.ldesc + 2 * i);
+                S.u.left.ldesc[2 * tid + 1] = __ldg(F.ldesc + 2 * i + 1);
             }
             __syncthreads();
             hamming_phase(P, F, S, npass, staged, w_a, nrows, e_base);
@@ -868,6 +922,8 @@ __device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int
 }
 
 // ---------------------------------------------------------------- K_SEARCH
+__device__ void resolve_range(const CamDev &C, int nm, int i0, int i1);
+
 __device__ __forceinline__ void transform(const float *pose, float4 p, float &x, float &y, float &z)
 {
     x = fadd(fadd(fadd(fmul(pose[0], p.x), fmul(pose[1], p.y)), fmul(pose[2], p.z)), pose[9]);
@@ -1061,10 +1117,34 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
             C.mp_kp[m] = -1;
         }
     }
-    signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag);
+    if (signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag) &&
+        F.fold_resolve) {
+        // the last search item of this camera also writes the final tables
+        // (small frames: no separate resolve items wait for the search)
+        resolve_range(F.cam[cam], F.nm, 0, max(F.nm, F.cam[cam].nk));
+    }
 }
 
 // ---------------------------------------------------------------- K_RESOLVE
+// Final tables for entries [i0, i1): a map point keeps its keypoint only if
+// it owns it; a keypoint gets its owner (or -1).
+__device__ void resolve_range(const CamDev &C, int nm, int i0, int i1)
+{
+    for (int m = i0 + threadIdx.x; m < min(i1, nm); m += kThreads) {
+        const int k = __ldcg(C.mp_kp + m);
+        if (k >= C.nk) {
+            C.mp_kp[m] = -1;                 // never written by a search item
+        } else if (k >= 0) {
+            const unsigned long long own = __ldcg(C.owner + k);
+            if ((unsigned)(own & 0xffffffffull) != (unsigned)m) C.mp_kp[m] = -1;
+        }
+    }
+    for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) {
+        const unsigned long long own = __ldcg(C.owner + k);
+        C.kp_mp[k] = own == ~0ull ? -1 : (int)(own & 0xffffffffull);
+    }
+}
+
 __device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, int *s_flag)
 {
     const int cam = tile < F.n_resolve_items[0] ? 0 : 1;
@@ -1080,29 +1160,31 @@ __device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, 
         for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) C.kp_mp[k] = -1;
         return;
     }
-    for (int m = i0 + threadIdx.x; m < min(i1, F.nm); m += kThreads) {
-        const int k = __ldcg(C.mp_kp + m);
-        if (k >= C.nk) {
-            C.mp_kp[m] = -1;                 // never written by a search item
-        } else if (k >= 0) {
-            const unsigned long long own = __ldcg(C.owner + k);
-            if ((unsigned)(own & 0xffffffffull) != (unsigned)m) C.mp_kp[m] = -1;
-        }
-    }
-    for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) {
-        const unsigned long long own = __ldcg(C.owner + k);
-        C.kp_mp[k] = own == ~0ull ? -1 : (int)(own & 0xffffffffull);
-    }
+    resolve_range(C, F.nm, i0, i1);
 }
 
 // ---------------------------------------------------------------- the kernel
+__device__ __forceinline__ void copy_words(void *dst, const void *src, size_t bytes)
+{
+    const unsigned *a = reinterpret_cast<const unsigned *>(src);
+    unsigned *b = reinterpret_cast<unsigned *>(dst);
+    for (size_t i = threadIdx.x; i < bytes / 4; i += kThreads) b[i] = __ldg(a + i);
+}
+
 __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(const BatchHeader *__restrict__ hdr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &U = *reinterpret_cast<Smem *>(smem_raw);
     __shared__ int s_item;
     __shared__ int s_flag;
-    const BatchHeader &B = *hdr;
+    // the launch header and the current frame's descriptor live in shared
+    // memory: their many indexed fields (level sizes, pitches, scales) are
+    // then shared-memory loads instead of dependent global loads
+    __shared__ __align__(16) BatchHeader sB;
+    __shared__ __align__(16) FrameDev sF;
+    copy_words(&sB, hdr, sizeof(BatchHeader));
+    __syncthreads();
+    const BatchHeader &B = sB;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(B.queue, 1u);
         __syncthreads();
@@ -1119,7 +1201,9 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
             if (pre[mid] <= local) lo = mid;
             else hi = mid - 1;
         }
-        const FrameDev &F = B.frames[lo];
+        copy_words(&sF, B.frames + lo, sizeof(FrameDev));
+        __syncthreads();
+        const FrameDev &F = sF;
         const int tile = local - pre[lo];
         unsigned long long t_start = 0;
         if (B.trace != nullptr && threadIdx.x == 0) {

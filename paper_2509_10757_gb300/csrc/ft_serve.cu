@@ -237,6 +237,9 @@ void CUDART_CB host_done(void *p)
     a->server->cv.notify_one();
 }
 
+// resident pyramid rows are padded to 16 bytes (the kernel reads 4-byte words)
+size_t level_pitch(const ft_stream_desc &d, int l) { return al16((size_t)d.level_width[l]); }
+
 size_t stream_block_bytes(const ft_stream_desc &d, ft_params const &p, StreamState *S)
 {
     size_t o = 0;
@@ -246,8 +249,8 @@ size_t stream_block_bytes(const ft_stream_desc &d, ft_params const &p, StreamSta
     };
     size_t dummy;
     if (d.camera == FT_CAMERA_PINHOLE) {
-        for (int l = 0; l < p.nlevels; ++l) put(S ? S->o_pyrL[l] : dummy, (size_t)d.level_width[l] * d.level_height[l]);
-        for (int l = 0; l < p.nlevels; ++l) put(S ? S->o_pyrR[l] : dummy, (size_t)d.level_width[l] * d.level_height[l]);
+        for (int l = 0; l < p.nlevels; ++l) put(S ? S->o_pyrL[l] : dummy, level_pitch(d, l) * d.level_height[l]);
+        for (int l = 0; l < p.nlevels; ++l) put(S ? S->o_pyrR[l] : dummy, level_pitch(d, l) * d.level_height[l]);
     }
     put(S ? S->o_pos : dummy, 16 * (size_t)d.max_map);
     put(S ? S->o_nrm : dummy, 16 * (size_t)d.max_map);
@@ -314,7 +317,7 @@ ft_frame_job job_of(const StreamState &S, const Request &r)
             j.pyr_right.data[l] = reinterpret_cast<uint8_t *>(S.dev + S.o_pyrR[l]);
             j.pyr_left.width[l] = j.pyr_right.width[l] = d.level_width[l];
             j.pyr_left.height[l] = j.pyr_right.height[l] = d.level_height[l];
-            j.pyr_left.pitch[l] = j.pyr_right.pitch[l] = d.level_width[l];
+            j.pyr_left.pitch[l] = j.pyr_right.pitch[l] = (int)level_pitch(d, l);
         }
     }
     j.pose = r.pose;
@@ -616,8 +619,8 @@ ft_status ft_server_set_pyramids(ft_server *s, int sid, const ft_pyramid *left, 
         for (int k = 0; k < 2; ++k) {
             if (!src[k]->data[l] || src[k]->width[l] != w || src[k]->height[l] != h || src[k]->pitch[l] < w)
                 return fail(FT_EINVAL, "pyramid level %d does not match the stream", l);
-            if (cudaMemcpy2D(S.dev + dst[k], (size_t)w, src[k]->data[l], (size_t)src[k]->pitch[l], (size_t)w,
-                             (size_t)h, cudaMemcpyHostToDevice) != cudaSuccess)
+            if (cudaMemcpy2D(S.dev + dst[k], level_pitch(S.desc, l), src[k]->data[l], (size_t)src[k]->pitch[l],
+                             (size_t)w, (size_t)h, cudaMemcpyHostToDevice) != cudaSuccess)
                 return fail(FT_ECUDA, "pyramid upload failed");
         }
     }

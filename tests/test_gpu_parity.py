@@ -329,6 +329,10 @@ def test_host_checks_reject_bad_arguments(ctx, lib):
     assert call() == lib.FT_EINVAL
     assert "level 3" in lib.last_error()
     st.pyr_left.data[3] = pb.pin_(0, "pyrL3")
+    pitch = st.pyr_left.pitch[2]
+    st.pyr_left.pitch[2] = pitch + 1                 # rows must be 4-byte aligned
+    assert call() == lib.FT_EALIGN
+    st.pyr_left.pitch[2] = pitch
     assert call() == lib.FT_OK
     assert ctx.sync_status() == 0
     # 8 frames of 4000 keypoints need about 1.9 MB of grid scratch; the
