@@ -172,13 +172,14 @@ struct RefineJob {
 constexpr int kGroup = 4;                       // lanes per left keypoint in the Hamming phase
 constexpr int kGroups = kThreads / kGroup;      // left keypoints in flight per CTA
 constexpr int kSadChunk = 64;                   // matches refined per round
-constexpr int kRowL = 12;                       // padded bytes of a left patch row (11 used)
-constexpr int kRowR = 24;                       // padded bytes of a right strip row (21 used)
+constexpr int kWordsL = 4;                      // 32-bit words holding a left patch row (11 bytes)
+constexpr int kWordsR = 6;                      // words holding a right strip row (21 bytes)
 
-// patches of one refinement round, rows padded to whole words
+// patches of one refinement round as the raw 32-bit words of their rows
+// (copied asynchronously; the bytes start at offset (column & 3))
 struct PatchBuf {
-    uint8_t l[kSadChunk][(2 * kW + 1) * kRowL];
-    uint8_t r[kSadChunk][(2 * kW + 1) * kRowR];
+    unsigned l[kSadChunk][2 * kW + 1][kWordsL];
+    unsigned r[kSadChunk][2 * kW + 1][kWordsR];
 };
 // left keypoints of a pass (Hamming phase)
 struct LeftBuf {
@@ -224,8 +225,14 @@ struct SmemMedian {
     int vals[kMedianSmem];
 };
 
+constexpr int kSearchStage = 1536;              // keypoints of one camera the search keeps on chip
+
+// a camera's keypoints in cell order, staged for the search of one tile:
+// x, y, index | octave << 20 | taken << 28, right coordinate (or -1)
 struct SmemSearch {
     float pose[12];
+    float4 rec[kSearchStage];
+    uint4 desc[2 * kSearchStage];
 };
 
 union Smem {
@@ -236,6 +243,9 @@ union Smem {
     SmemMedian m;
     SmemSearch q;
 };
+// three CTAs per SM: dynamic + static shared memory + the 1 KB the SM
+// reserves per CTA must stay within the SM's 228 KB
+static_assert(3 * (sizeof(Smem) + 2 * 1024 + 1024) <= 228 * 1024, "shared memory above three CTAs per SM");
 
 // ---------------------------------------------------------------- waits and signals
 // time this CTA spent in waits during the current item, and phase marks (tracing)
@@ -591,43 +601,58 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
 //     depth.
 __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &S, int r0, int nc)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     constexpr int kRows = 2 * kW + 1;
     for (int q = tid; q < nc * kShifts; q += kThreads) S.sad[q / kShifts][q % kShifts] = 0;
-    // one thread per (match, row, side): the 32-bit words holding the row's
-    // bytes (level rows are 4-byte aligned: pointer and pitch checked on the
-    // host) are all requested first, then re-aligned with funnel shifts into
-    // the padded shared-memory row
-    for (int q = tid; q < nc * 2 * kRows; q += kThreads) {
-        const int mm = q / (2 * kRows), rem = q - mm * (2 * kRows);
-        const int row = rem >> 1;
-        const bool right = (rem & 1) != 0;
+    // asynchronous copies of the 32-bit words holding every patch row; a
+    // match has ten word slots (four of a left row, six of a right row) and
+    // one thread per slot walks the 11 rows, so that consecutive lanes copy
+    // consecutive words and one warp copy touches few cache lines.  Level
+    // pointers and pitches are 4-byte aligned (checked on the host): a row's
+    // words start at its column rounded down to a multiple of 4 and never
+    // leave the level image.  One memory latency for the whole round.
+    constexpr int kSlots = kWordsL + kWordsR;
+    for (int q = tid; q < nc * kSlots; q += kThreads) {
+        const int mm = q / kSlots, w = q - mm * kSlots;
+        const bool right = w >= kWordsL;
+        const int k = right ? w - kWordsL : w;
         const RefineJob &J = S.ref[r0 + mm];
-        const uint8_t *base = right ? F.pyrR[J.l] + (size_t)(J.vl - kW + row) * F.rp[J.l] + (J.ur0 - kL - kW)
-                                    : F.pyrL[J.l] + (size_t)(J.vl - kW + row) * F.lp[J.l] + (J.ul - kW);
+        const int col = right ? J.ur0 - kL - kW : J.ul - kW;
         const int len = right ? kStripW : 2 * kW + 1;
-        const int off = (int)(reinterpret_cast<uintptr_t>(base) & 3u);
-        const unsigned *wp = reinterpret_cast<const unsigned *>(base - off);
-        const int nw = ((off + len - 1) >> 2) + 1;                 // words holding the row (<= 6)
-        unsigned w[7];
+        if (k > (((col & 3) + len - 1) >> 2)) continue;     // the word holds none of the row's bytes
+        const int pitch = right ? F.rp[J.l] : F.lp[J.l];
+        const uint8_t *row0 = (right ? F.pyrR[J.l] : F.pyrL[J.l]) + (size_t)(J.vl - kW) * pitch;
+        const unsigned *src = reinterpret_cast<const unsigned *>(row0) + (col >> 2) + k;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(right ? &S.u.patch.r[mm][0][k]
+                                                                       : &S.u.patch.l[mm][0][k]);
+        const unsigned dstep = 4u * (right ? kWordsR : kWordsL);
+        const int sstep = pitch >> 2;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) w[k] = k < nw ? __ldg(wp + k) : 0u;
-        unsigned *dst = right ? reinterpret_cast<unsigned *>(S.u.patch.r[mm] + row * kRowR)
-                              : reinterpret_cast<unsigned *>(S.u.patch.l[mm] + row * kRowL);
-        const int nout = (len + 3) >> 2;
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if (k < nout) dst[k] = __funnelshift_r(w[k], w[k + 1], 8 * off);
+        for (int row = 0; row < kRows; ++row)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + row * dstep),
+                         "l"(src + (size_t)row * sstep)
+                         : "memory");
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     for (int q = tid; q < nc * kRows; q += kThreads) {
         const int dy = q / nc, m = q - dy * nc;
-        const unsigned *wl = reinterpret_cast<const unsigned *>(S.u.patch.l[m] + dy * kRowL);
-        const unsigned *wr = reinterpret_cast<const unsigned *>(S.u.patch.r[m] + dy * kRowR);
-        const unsigned *wc = reinterpret_cast<const unsigned *>(S.u.patch.r[m] + kW * kRowR);
+        const RefineJob &J = S.ref[r0 + m];
+        const int offl = 8 * ((J.ul - kW) & 3), offr = 8 * ((J.ur0 - kL - kW) & 3);
+        const unsigned *ql = S.u.patch.l[m][dy];
+        const unsigned *qr = S.u.patch.r[m][dy];
+        const unsigned *qc = S.u.patch.r[m][kW];
+        // realigned words: byte b of the row is byte b & 3 of word b >> 2
+        unsigned wl[3], wr[6], wc[4];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) wl[k] = __funnelshift_r(ql[k], ql[k + 1], offl);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) wr[k] = __funnelshift_r(qr[k], k + 1 < kWordsR ? qr[k + 1] : 0u, offr);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) wc[k] = __funnelshift_r(qc[k], k + 1 < kWordsR ? qc[k + 1] : 0u, offr);
         // left row minus the left centre, right row, and the centres of the
         // 11 right patches (bytes 5..15 of the right centre row)
-        const int cl = S.u.patch.l[m][kW * kRowL + kW];
+        const int cl = (int)((__funnelshift_r(S.u.patch.l[m][kW][1], S.u.patch.l[m][kW][2], offl) >> 8) & 0xff);
         int lc[2 * kW + 1], rv[kStripW], cr[kShifts];
 #pragma unroll
         for (int b = 0; b < 2 * kW + 1; ++b) lc[b] = (int)((wl[b >> 2] >> (8 * (b & 3))) & 0xff) - cl;
@@ -639,7 +664,7 @@ __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &
         for (int k = 0; k < kShifts; ++k) {
             int s = 0;
 #pragma unroll
-            for (int dx = 0; dx < 2 * kW + 1; ++dx) s += abs(lc[dx] - (rv[k + dx] - cr[k]));
+            for (int dx = 0; dx < 2 * kW + 1; ++dx) s = __sad(lc[dx] + cr[k], rv[k + dx], s);
             atomicAdd(&S.sad[m][k], s);
         }
     }
@@ -990,9 +1015,13 @@ __device__ bool project(const DevParams &P, const CamDev &C, const float *pose, 
     return distance_scale(P, C.O, pos, nrm, vc, level);
 }
 
-__device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C,
-                             const float *pose, float iw, float ih, int m)
+// One map point against the keypoints of its search window.  kStaged: the
+// camera's cell-ordered records and descriptors sit in shared memory.
+template <bool kStaged>
+__device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C, const SmemSearch &Q,
+                             float iw, float ih, int m)
 {
+    const float *pose = Q.pose;
     int lvl = -1, d1 = -1, d2 = -1, kp = -1;
     float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool skipped = F.skip != nullptr && __ldg(F.skip + m) != 0;
@@ -1020,19 +1049,43 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                     const int e0 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x0);
                     const int e1 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x1 + 1);
                     for (int e = e0; e < e1; ++e) {
-                        // the keypoint record and its descriptor are fetched together
-                        const float4 g = __ldcg(C.gkp + e);
-                        const uint4 b0 = __ldcg(C.gdesc + 2 * e), b1 = __ldcg(C.gdesc + 2 * e + 1);
-                        const int flags = __float_as_int(g.w);
-                        const int oct = (int)(int8_t)(flags & 0xff);
+                        int oct, k;
+                        bool taken;
+                        float gx, gy, urk;
+                        uint4 b0, b1;
+                        if (kStaged) {
+                            const float4 g = Q.rec[e];
+                            const unsigned z = __float_as_uint(g.z);
+                            gx = g.x;
+                            gy = g.y;
+                            k = (int)(z & 0xfffffu);
+                            oct = (int)(int8_t)((z >> 20) & 0xffu);
+                            taken = (z >> 28) != 0;
+                            urk = g.w;
+                        } else {
+                            // the keypoint record and its descriptor are fetched together
+                            const float4 g = __ldcg(C.gkp + e);
+                            b0 = __ldcg(C.gdesc + 2 * e);
+                            b1 = __ldcg(C.gdesc + 2 * e + 1);
+                            const int flags = __float_as_int(g.w);
+                            gx = g.x;
+                            gy = g.y;
+                            k = __float_as_int(g.z);
+                            oct = (int)(int8_t)(flags & 0xff);
+                            taken = (flags >> 8) != 0;
+                            urk = 0.0f;
+                        }
                         if (oct < level - 1 || oct > level) continue;
-                        const float distx = fsub(g.x, u), disty = fsub(g.y, v);
+                        const float distx = fsub(gx, u), disty = fsub(gy, v);
                         if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
-                        if (flags >> 8) continue;
-                        const int k = __float_as_int(g.z);
+                        if (taken) continue;
                         if (check_ur) {
-                            const float urk = __ldcg(F.u_right_in + k);
+                            if (!kStaged) urk = __ldcg(F.u_right_in + k);
                             if (urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
+                        }
+                        if (kStaged) {
+                            b0 = Q.desc[2 * e];
+                            b1 = Q.desc[2 * e + 1];
                         }
                         const unsigned key = ((unsigned)ham8(q0, q1, b0, b1) << 20) | (unsigned)k;
                         if (key < best) {
@@ -1077,7 +1130,8 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
     if (ok) ok = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
     if (ok) {
         const CamDev &C = F.cam[cam];
-        float *pose = U.q.pose;
+        SmemSearch &Q = U.q;
+        float *pose = Q.pose;
         const int tid = threadIdx.x;
         if (tid < 12) {
             const CamDev &L = F.cam[0];
@@ -1096,13 +1150,46 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
             }
             pose[tid] = v;
         }
+        // stage the camera's cell-ordered keypoints when they fit: the raw
+        // records and descriptors by asynchronous copies, then each record's
+        // flags repacked beside its index and its right coordinate gathered
+        // (pinhole frames with stereo results).  Only the records the grid
+        // step placed exist: keypoints outside the grid have none.
+        const int nk = __ldcg(C.cell_ptr + kCells);
+        const bool staged = nk <= kSearchStage;
+        if (staged) {
+            const unsigned srec = (unsigned)__cvta_generic_to_shared(Q.rec);
+            const unsigned sdesc = (unsigned)__cvta_generic_to_shared(Q.desc);
+            for (int e = tid; e < nk; e += kThreads)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(srec + 16u * e), "l"(C.gkp + e)
+                             : "memory");
+            for (int e = tid; e < 2 * nk; e += kThreads)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdesc + 16u * e), "l"(C.gdesc + e)
+                             : "memory");
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            const bool ur_in = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr;
+#pragma unroll 4
+            for (int e = tid; e < nk; e += kThreads) {
+                float4 g = Q.rec[e];
+                const int flags = __float_as_int(g.w), k = __float_as_int(g.z);
+                g.z = __uint_as_float((unsigned)k | ((unsigned)(flags & 0xff) << 20) |
+                                      ((unsigned)((flags >> 8) & 1) << 28));
+                g.w = ur_in ? __ldcg(F.u_right_in + k) : -1.0f;
+                Q.rec[e] = g;
+            }
+        }
         __syncthreads();
         mark(B, 0);
         const int m0 = t * F.search_tile;
         const int m1 = min(F.nm, m0 + F.search_tile);
         const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
         const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
-        for (int m = m0 + tid; m < m1; m += kThreads) search_point(B.p, F, C, pose, iw, ih, m);
+        if (staged) {
+            for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, iw, ih, m);
+        } else {
+            for (int m = m0 + tid; m < m1; m += kThreads) search_point<false>(B.p, F, C, Q, iw, ih, m);
+        }
         mark(B, 1);
     } else {
         // the wait ran out (reported in the status word): leave defined outputs

@@ -154,6 +154,21 @@ def test_stress_frames(ctx, lib):
         check_frame(pb, f, what="1080p stress")
 
 
+def test_search_keypoints_on_chip_boundary(ctx, lib):
+    # the search keeps up to 1536 keypoints of a camera in shared memory and
+    # reads larger frames from device memory: both sides of the boundary,
+    # fused (right coordinates from the stereo step) and per call
+    frames = [scenes.pinhole_frame(40 + n, 752, 480, n, 0.2, 0.05, 3000) for n in (1535, 1536, 1537)]
+    frames.append(scenes.fisheye_frame(43, 1536, n_map=3000))
+    frames.append(scenes.fisheye_frame(44, 1537, n_map=3000))
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="on-chip boundary, fused")
+    pb = run_per_frame(ctx, frames)
+    for f in range(len(frames)):
+        check_frame(pb, f, what="on-chip boundary, per call")
+
+
 @pytest.mark.parametrize("overrides", [{"search_th": 2.0}, {"ratio_any_octave": 1},
                                        {"th_stereo": 40, "th_search": 60}])
 def test_parameter_variants(ctx, lib, overrides):
