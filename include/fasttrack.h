@@ -456,7 +456,7 @@ ft_status ft_server_get_stats(ft_server *s, ft_server_stats *stats);
  * start-up, or a host framework whose memory manager forbids allocations
  * behind its back.  Such callers cannot create an ft_ctx (ft_create
  * allocates its arena), so this call needs no context: its scratch (work
- * table, counters, row sort) lives in a fixed 1 MiB device array that is part
+ * table, counters, row sort) lives in a fixed 2 MiB device array that is part
  * of the library, held on every device that loads the library until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating
  * routine.  The caller passes inputs and outputs as for

@@ -425,7 +425,8 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 F.rowsort = 2;
                 F.row_ptr_l = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
                 F.row_ptr_r = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
-                F.ls_idx = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)F.nl));
+                F.ls_kp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)F.nl));
+                F.ls_desc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)F.nl));
                 F.rs_kp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)F.nr));
                 F.rs_desc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)F.nr));
             }

@@ -90,7 +90,8 @@ struct FrameDev {
     float lap_l0, lap_l1, lap_r0, lap_r1;
     // row sort of the pinhole stereo step (scratch): keypoints bucketed by row
     int *row_ptr_l, *row_ptr_r;    // [H + 1]
-    int *ls_idx;                   // [nl] left indices in row order
+    float4 *ls_kp;                 // [nl] left x, y, index, octave in row order
+    uint4 *ls_desc;                // [2 * nl]
     float4 *rs_kp;                 // [nr] right x, band rows lo | hi << 16, row, index | octave << 20
     uint4 *rs_desc;                // [2 * nr]
     // stereo outputs (pinhole)

@@ -245,7 +245,8 @@ union Smem {
 };
 // three CTAs per SM: dynamic + static shared memory + the 1 KB the SM
 // reserves per CTA must stay within the SM's 228 KB
-static_assert(3 * (sizeof(Smem) + 2 * 1024 + 1024) <= 228 * 1024, "shared memory above three CTAs per SM");
+static_assert(3 * (sizeof(Smem) + sizeof(BatchHeader) + sizeof(FrameDev) + 256 + 1024) <= 228 * 1024,
+              "shared memory above three CTAs per SM");
 
 // ---------------------------------------------------------------- waits and signals
 // time this CTA spent in waits during the current item, and phase marks (tracing)
@@ -458,7 +459,15 @@ __device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemR
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int i = base + u * kThreads + tid;
-            if (i < F.nl) F.ls_idx[atomicAdd(&S.cnt[own_row(y[u], H)], 1)] = i;
+            if (i < F.nl) {
+                // a row-ordered copy of the keypoint and its descriptor, so
+                // that the stereo strips read their left keypoints contiguously
+                const int pos = atomicAdd(&S.cnt[own_row(y[u], H)], 1);
+                F.ls_kp[pos] = make_float4(__ldg(F.lx + i), y[u], __int_as_float(i),
+                                           __int_as_float((int)__ldg(F.loct + i)));
+                F.ls_desc[2 * pos] = __ldg(F.ldesc + 2 * i);
+                F.ls_desc[2 * pos + 1] = __ldg(F.ldesc + 2 * i + 1);
+            }
         }
     }
     signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
@@ -566,7 +575,8 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                 xb = x2;
             }
         }
-        if (have && sub == 0) {
+        // every lane of the group holds the reduced key
+        if (have) {
             int best = -1, dist = -1;
             if (key != kNoKey) {
                 dist = (int)(key >> 20);
@@ -582,12 +592,26 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                                     ul - kW >= 0 && ul + kW <= F.lw[l] - 1 &&
                                     ur0 - kL - kW >= 0 && ur0 + kL + kW <= F.rw[l] - 1;
                 if (inside) {
-                    const int slot = atomicAdd(&S.nref, 1);
-                    S.ref[slot] = RefineJob{i, best, dist, l, ul, vl, ur0, xi};
+                    // the lanes ask L2 for the patch rows now, so that the
+                    // refinement's copies find them there
+                    for (int rr = sub; rr < 2 * kW + 1; rr += kGroup) {
+                        const uint8_t *pl = F.pyrL[l] + (size_t)(vl - kW + rr) * F.lp[l] + (ul - kW);
+                        const uint8_t *pr = F.pyrR[l] + (size_t)(vl - kW + rr) * F.rp[l] + (ur0 - kL - kW);
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(pl));
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(pr));
+                        if (((reinterpret_cast<uintptr_t>(pr) & 127u) + kStripW - 1) >= 128u)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(pr + kStripW - 1));
+                        if (((reinterpret_cast<uintptr_t>(pl) & 127u) + 2 * kW) >= 128u)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + 2 * kW));
+                    }
+                    if (sub == 0) {
+                        const int slot = atomicAdd(&S.nref, 1);
+                        S.ref[slot] = RefineJob{i, best, dist, l, ul, vl, ur0, xi};
+                    }
                     queued = true;
                 }
             }
-            if (!queued) write_stereo(F, i, best, dist, FT_NO_SHIFT, -1, -1.0f, -1.0f);
+            if (!queued && sub == 0) write_stereo(F, i, best, dist, FT_NO_SHIFT, -1, -1.0f, -1.0f);
         }
     }
 }
@@ -843,11 +867,9 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
             // the pass's left keypoints, one thread each, into shared memory
             const int npass = min(kThreads, l_hi - pass);
             if (tid < npass) {
-                const int i = __ldcg(F.ls_idx + pass + tid);
-                S.u.left.lkp[tid] = make_float4(__ldg(F.lx + i), __ldg(F.ly + i), __int_as_float(i),
-                                                __int_as_float((int)__ldg(F.loct + i)));
-                S.u.left.ldesc[2 * tid] = __ldg(F.ldesc + 2 * i);
-                S.u.left.ldesc[2 * tid + 1] = __ldg(F.ldesc + 2 * i + 1);
+                S.u.left.lkp[tid] = __ldcg(F.ls_kp + pass + tid);
+                S.u.left.ldesc[2 * tid] = __ldcg(F.ls_desc + 2 * (pass + tid));
+                S.u.left.ldesc[2 * tid + 1] = __ldcg(F.ls_desc + 2 * (pass + tid) + 1);
             }
             __syncthreads();
             hamming_phase(P, F, S, npass, staged, w_a, nrows, e_base);

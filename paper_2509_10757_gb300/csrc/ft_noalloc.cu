@@ -37,7 +37,7 @@ namespace {
 // Maximum sizes accepted by the allocation-free path.
 constexpr int kNoAllocMaxKeypoints = 16384;     // per image (left and right each)
 constexpr int kNoAllocMaxRows = kMaxRows;       // level-0 image height
-constexpr size_t kNoAllocScratchBytes = (size_t)1 << 20;
+constexpr size_t kNoAllocScratchBytes = (size_t)2 << 20;
 constexpr int kMaxDevices = 64;
 
 // The scratch memory: 1 MiB per device, resident from library load to exit.
@@ -156,8 +156,10 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     off = up256(off + sizeof(int) * (size_t)(H + 1));
     const size_t o_rpr = off;
     off = up256(off + sizeof(int) * (size_t)(H + 1));
-    const size_t o_lsi = off;
-    off = up256(off + sizeof(int) * (size_t)L.n);
+    const size_t o_lkp = off;
+    off = up256(off + sizeof(float4) * (size_t)L.n);
+    const size_t o_lds = off;
+    off = up256(off + sizeof(uint4) * 2 * (size_t)L.n);
     const size_t o_rkp = off;
     off = up256(off + sizeof(float4) * (size_t)R.n);
     const size_t o_rds = off;
@@ -244,7 +246,8 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     F.depth = out->depth;
     F.row_ptr_l = reinterpret_cast<int *>(d + o_rpl);
     F.row_ptr_r = reinterpret_cast<int *>(d + o_rpr);
-    F.ls_idx = reinterpret_cast<int *>(d + o_lsi);
+    F.ls_kp = reinterpret_cast<float4 *>(d + o_lkp);
+    F.ls_desc = reinterpret_cast<uint4 *>(d + o_lds);
     F.rs_kp = reinterpret_cast<float4 *>(d + o_rkp);
     F.rs_desc = reinterpret_cast<uint4 *>(d + o_rds);
     // strips of 32 rows, fewer if the expected right keypoints of a window
