@@ -484,6 +484,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 C.cell_ptr = reinterpret_cast<int *>(carve(sizeof(int) * (kCells + 1)));
                 C.gkp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)C.nk));
                 C.gdesc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)C.nk));
+                C.gpos = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)C.nk));
                 C.owner = reinterpret_cast<unsigned long long *>(carve(sizeof(unsigned long long) * (size_t)C.nk));
                 n_search[c] = (F.nm + F.search_tile - 1) / F.search_tile;
                 n_resolve[c] = (std::max(F.nm, C.nk) + F.resolve_tile - 1) / F.resolve_tile;

@@ -70,8 +70,10 @@ struct CamDev {
     float4 *proj;
     int *mp_kp, *mp_d1, *mp_d2, *kp_mp;
     int *cell_ptr;                 // [kCells + 1]
-    float4 *gkp;                   // [nk] keypoints in cell order: x, y, index, oct | taken << 8
+    float4 *gkp;                   // [nk] keypoints in cell order: x, y,
+                                   // index | octave << 20 | taken << 28, right coordinate (or -1)
     uint4 *gdesc;                  // [2 * nk]
+    int *gpos;                     // [nk] cell-order position of keypoint k (-1: outside the grid)
     unsigned long long *owner;     // [nk] (distance << 32) | map index
 };
 

@@ -195,6 +195,7 @@ struct SmemStereo {
         PatchBuf patch;
     } u;
     RefineJob ref[kThreads];
+    int gp[kSadChunk];                 // grid record of each match of the round (-1: none)
     int sad[kSadChunk][12];
     int bptr[kOctBuckets * kWinRows + 1];   // start of each (octave, window row) bucket
     int warp_sums[kWarps];
@@ -343,17 +344,24 @@ __device__ void grid_item(const BatchHeader &B, const FrameDev &F, int cam, Smem
     for (int c = tid; c < kCells; c += kThreads) C.cell_ptr[c] = G.cnt[c];
     if (tid == 0) C.cell_ptr[kCells] = total;
     __syncthreads();
+    // the record's right coordinate: a stereo step in this launch fills it
+    // in later (pinhole frames that wait for their stereo); otherwise it is
+    // the caller's u_right input, or -1 (no consistency check)
+    const bool ur_in = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr && !F.wait_stereo;
     for (int k = tid; k < C.nk; k += kThreads) {
         const float x = __ldg(C.kx + k), y = __ldg(C.ky + k);
         const int c = grid_cell(C, iw, ih, x, y);
+        int pos = -1;
         if (c >= 0) {
-            const int pos = atomicAdd(&G.cnt[c], 1);
-            const int oct = (int)__ldg(C.koct + k) & 0xff;
-            const int tk = C.taken ? (__ldg(C.taken + k) != 0) : 0;
-            C.gkp[pos] = make_float4(x, y, __int_as_float(k), __int_as_float(oct | (tk << 8)));
+            pos = atomicAdd(&G.cnt[c], 1);
+            const unsigned oct = (unsigned)__ldg(C.koct + k) & 0xffu;
+            const unsigned tk = C.taken ? (__ldg(C.taken + k) != 0) : 0u;
+            const float ur = ur_in ? __ldg(F.u_right_in + k) : -1.0f;
+            C.gkp[pos] = make_float4(x, y, __uint_as_float((unsigned)k | (oct << 20) | (tk << 28)), ur);
             C.gdesc[2 * pos] = __ldg(C.kdesc + 2 * k);
             C.gdesc[2 * pos + 1] = __ldg(C.kdesc + 2 * k + 1);
         }
+        C.gpos[k] = pos;
         C.owner[k] = ~0ull;
     }
     signal_count(&F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
@@ -623,7 +631,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
 //     row's part of the 11 SADs of centre-subtracted patches; then per match
 //     the first strict minimum over the shifts, the parabola, disparity and
 //     depth.
-__device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &S, int r0, int nc)
+__device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &S, int r0, int nc, bool rec)
 {
     const int tid = threadIdx.x;
     constexpr int kRows = 2 * kW + 1;
@@ -656,6 +664,12 @@ __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + row * dstep),
                          "l"(src + (size_t)row * sstep)
                          : "memory");
+    }
+    // the grid record of each match (the search reads the right coordinate there)
+    if (rec && tid < nc) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&S.gp[tid]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(F.cam[0].gpos + S.ref[r0 + tid].i)
+                     : "memory");
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -721,6 +735,7 @@ __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &
             }
         }
         write_stereo(F, J.i, J.j, J.d, shift, sadb, ur, dep);
+        if (rec && sadb >= 0 && S.gp[m] >= 0) reinterpret_cast<float *>(F.cam[0].gkp + S.gp[m])[3] = ur;
     }
     __syncthreads();
 }
@@ -763,9 +778,14 @@ __device__ __forceinline__ int median_value(const FrameDev &F, const SmemMedian 
     return on_chip ? M.vals[i] : __ldcg(F.sad_best + i);
 }
 
-__device__ void median_reject(const FrameDev &F, const DevParams &P, SmemMedian &M)
+__device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedian &M, int *s_flag)
 {
+    const DevParams &P = B.p;
     const int tid = threadIdx.x;
+    // a search in this launch reads the final right coordinates from the
+    // grid records: a rejected match takes its coordinate back there too
+    const bool rec = F.wait_stereo && F.u_right_in != nullptr &&
+                     wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
     const bool on_chip = F.nl <= kMedianSmem;
     if (on_chip)
         for (int i = tid; i < F.nl; i += kThreads) M.vals[i] = __ldcg(F.sad_best + i);
@@ -802,11 +822,17 @@ __device__ void median_reject(const FrameDev &F, const DevParams &P, SmemMedian 
     __syncthreads();
     const int median = (hi << 8) | M.bin;
     const float th = fmul(P.median_factor, (float)median);
+    const CamDev &C = F.cam[0];
     for (int i = tid; i < F.nl; i += kThreads) {
         const int x = median_value(F, M, on_chip, i);
-        if (x >= 0 && (float)x >= th) {
+        if (x < 0) continue;
+        if ((float)x >= th) {
             F.u_right[i] = -1.0f;
             F.depth[i] = -1.0f;
+            if (rec) {
+                const int pos = __ldcg(C.gpos + i);
+                if (pos >= 0) reinterpret_cast<float *>(C.gkp + pos)[3] = -1.0f;
+            }
         }
     }
 }
@@ -817,7 +843,11 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     SmemStereo &S = U.s;
     const DevParams &P = B.p;
     const int tid = threadIdx.x;
-    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag)) {
+    // a search in this launch reads each refined match's right coordinate
+    // from the grid record, written here once the grid step is done
+    const bool rec = F.wait_stereo && F.u_right_in != nullptr;
+    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag) &&
+        (!rec || wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag))) {
         const int H = F.H;
         const int r_lo = strip * F.strip_rows;
         const int r_hi = min(H, r_lo + F.strip_rows);
@@ -876,14 +906,14 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
             __syncthreads();
             mark(B, 1);
             const int nref = S.nref;
-            for (int r0 = 0; r0 < nref; r0 += kSadChunk) refine_round(P, F, S, r0, min(kSadChunk, nref - r0));
+            for (int r0 = 0; r0 < nref; r0 += kSadChunk) refine_round(P, F, S, r0, min(kSadChunk, nref - r0), rec);
             if (tid == 0) S.nref = 0;
             __syncthreads();
             mark(B, 2);
         }
     }
     if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
-        median_reject(F, P, U.m);
+        median_reject(B, F, U.m, s_flag);
         __threadfence();
         __syncthreads();
         mark(B, 3);
@@ -1064,7 +1094,7 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
             const int y1 = min(f2i(ceilf(fmul(fadd(dv, r), ih))), FT_GRID_ROWS - 1);
             if (!(x0 >= FT_GRID_COLS || x1 < 0 || y0 >= FT_GRID_ROWS || y1 < 0)) {
                 const uint4 q0 = __ldg(F.mdesc + 2 * m), q1 = __ldg(F.mdesc + 2 * m + 1);
-                const bool check_ur = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr;
+                const bool check_ur = C.model == FT_CAMERA_PINHOLE;
                 unsigned best = kNoKey, second = kNoKey;
                 int oct1 = -1, oct2 = -1;
                 for (int cy = y0; cy <= y1; ++cy) {
@@ -1075,36 +1105,27 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                         bool taken;
                         float gx, gy, urk;
                         uint4 b0, b1;
+                        float4 g;
                         if (kStaged) {
-                            const float4 g = Q.rec[e];
-                            const unsigned z = __float_as_uint(g.z);
-                            gx = g.x;
-                            gy = g.y;
-                            k = (int)(z & 0xfffffu);
-                            oct = (int)(int8_t)((z >> 20) & 0xffu);
-                            taken = (z >> 28) != 0;
-                            urk = g.w;
+                            g = Q.rec[e];
                         } else {
                             // the keypoint record and its descriptor are fetched together
-                            const float4 g = __ldcg(C.gkp + e);
+                            g = __ldcg(C.gkp + e);
                             b0 = __ldcg(C.gdesc + 2 * e);
                             b1 = __ldcg(C.gdesc + 2 * e + 1);
-                            const int flags = __float_as_int(g.w);
-                            gx = g.x;
-                            gy = g.y;
-                            k = __float_as_int(g.z);
-                            oct = (int)(int8_t)(flags & 0xff);
-                            taken = (flags >> 8) != 0;
-                            urk = 0.0f;
                         }
+                        const unsigned z = __float_as_uint(g.z);
+                        gx = g.x;
+                        gy = g.y;
+                        k = (int)(z & 0xfffffu);
+                        oct = (int)(int8_t)((z >> 20) & 0xffu);
+                        taken = (z >> 28) != 0;
+                        urk = g.w;
                         if (oct < level - 1 || oct > level) continue;
                         const float distx = fsub(gx, u), disty = fsub(gy, v);
                         if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
                         if (taken) continue;
-                        if (check_ur) {
-                            if (!kStaged) urk = __ldcg(F.u_right_in + k);
-                            if (urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
-                        }
+                        if (check_ur && urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
                         if (kStaged) {
                             b0 = Q.desc[2 * e];
                             b1 = Q.desc[2 * e + 1];
@@ -1172,12 +1193,10 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
             }
             pose[tid] = v;
         }
-        // stage the camera's cell-ordered keypoints when they fit: the raw
-        // records and descriptors by asynchronous copies, then each record's
-        // flags repacked beside its index and its right coordinate gathered
-        // (pinhole frames with stereo results).  Only the records the grid
-        // step placed exist: keypoints outside the grid have none.
-        const int nk = __ldcg(C.cell_ptr + kCells);
+        // stage the camera's cell-ordered keypoint records and descriptors
+        // by asynchronous copies when they fit (the tail past the placed
+        // records is copied but never read)
+        const int nk = C.nk;
         const bool staged = nk <= kSearchStage;
         if (staged) {
             const unsigned srec = (unsigned)__cvta_generic_to_shared(Q.rec);
@@ -1189,17 +1208,6 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdesc + 16u * e), "l"(C.gdesc + e)
                              : "memory");
             asm volatile("cp.async.wait_all;" ::: "memory");
-            __syncthreads();
-            const bool ur_in = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr;
-#pragma unroll 4
-            for (int e = tid; e < nk; e += kThreads) {
-                float4 g = Q.rec[e];
-                const int flags = __float_as_int(g.w), k = __float_as_int(g.z);
-                g.z = __uint_as_float((unsigned)k | ((unsigned)(flags & 0xff) << 20) |
-                                      ((unsigned)((flags >> 8) & 1) << 28));
-                g.w = ur_in ? __ldcg(F.u_right_in + k) : -1.0f;
-                Q.rec[e] = g;
-            }
         }
         __syncthreads();
         mark(B, 0);
