@@ -437,6 +437,149 @@ def run_served(args, local_rank, seconds: float = 4.0, streams: int = 256):
     return out
 
 
+# ---------------------------------------------------------------- other workloads
+POPC_PER_SM_CLK = 16             # population-count issue rate per SM per clock
+POPC_PER_PAIR = 8                # 256-bit descriptors: eight 32-bit popcounts per pair
+
+
+def fisheye_pairs(frames) -> int:
+    """Descriptor pairs the fisheye overlap brute force compares (left overlap x right overlap)."""
+    n = 0
+    for fr in frames:
+        rig = fr.rig
+        nl = int(np.count_nonzero((fr.left.x >= rig.lap_l0) & (fr.left.x <= rig.lap_l1)))
+        nr = int(np.count_nonzero((fr.right.x >= rig.lap_r0) & (fr.right.x <= rig.lap_r1)))
+        n += nl * nr
+    return n
+
+
+def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_bytes: int) -> dict:
+    """One fused launch per step over `frames` (graph replay, autotuned tiles,
+    L2 flushed between steps): launch time, throughput and the HBM roofline."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch, stream_handle
+
+    pb = PackedBatch(frames, device=dev)
+    pb.upload()
+    ctx = Context(device=local_rank, arena_bytes=arena_bytes, max_frames=max(len(frames), 1), use_graphs=True)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    best = L.ft_tuning()
+    with torch.cuda.stream(stream):
+        b = pb.batch()
+        L.check(ctx.lib.ft_autotune(ctx.ptr, stream_handle(stream), None, C.byref(b), 2, C.byref(best)),
+                "ft_autotune")
+    for _ in range(warmup):
+        run_batch(ctx, pb, stream=stream)
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)
+            starts[i].record(stream)
+            run_batch(ctx, pb, stream=stream)
+            stops[i].record(stream)
+    torch.cuda.synchronize(dev)
+    assert ctx.sync_status() == 0
+    ms = [a.elapsed_time(z) for a, z in zip(starts, stops)]
+    pb.download()
+    alg = algorithmic_bytes(pb)
+    kp, mp = units_of(frames)
+    mean_s = statistics.mean(ms) / 1e3
+    peaks = measured_peaks()
+    out = {"frames": len(frames), "ms_per_launch": mean_s * 1e3,
+           "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+           "value": (kp + mp) / mean_s, "unit": UNIT,
+           "hbm": {"achieved_gbs": alg / mean_s / 1e9, "frac": alg / mean_s / 1e9 / peaks["hbm_gbs"],
+                   "algorithmic_bytes": alg},
+           "tuning": {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
+                      "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm}}
+    ctx.close()
+    return out
+
+
+def run_configs(args, local_rank):
+    """The other workloads, one JSON line each: single pinhole frames (per-frame
+    latency over 1000 frames, plain calls and a one-frame fused launch), the
+    fisheye batch (32 frames of 512x512) and the 1080p stress batch sweep."""
+    import torch
+
+    from paper_2509_10757_gb300 import build as B
+    from paper_2509_10757_gb300 import scenes
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch, run_search, run_stereo
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B.build()
+    lines = []
+
+    # single 752x480 frames: synchronous per-frame latency
+    frames = [scenes.pinhole_frame(500 + s) for s in range(16)]
+    nframes = 1000 if args.steps >= 1000 else max(args.steps, 50)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(device=local_rank, arena_bytes=256 << 20, max_frames=4, use_graphs=True)
+    pbs = [PackedBatch([fr], device=dev) for fr in frames]
+    for pb in pbs:
+        pb.upload()
+    lat = {}
+    for form in ("plain", "fused"):
+        ms = []
+        for i in range(nframes + 10):
+            pb = pbs[i % len(pbs)]
+            with torch.cuda.stream(stream):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if form == "plain":
+                    run_stereo(ctx, pb, 0, stream=stream)
+                    run_search(ctx, pb, 0, stream=stream)
+                else:
+                    run_batch(ctx, pb, stream=stream)
+                e1.record(stream)
+            e1.synchronize()
+            if i >= 10:
+                ms.append(e0.elapsed_time(e1))
+        units = sum(frames[i % len(frames)].left.n + frames[i % len(frames)].map.n for i in range(nframes))
+        lat[form] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                     "value": units / (sum(ms) / 1e3), "unit": UNIT}
+    assert ctx.sync_status() == 0
+    ctx.close()
+    lines.append({"workload": "single pinhole frame 752x480, 1200 left keypoints, 3000 map points, "
+                              f"synchronous per frame, {nframes} frames",
+                  "plain": lat["plain"], "fused_one_frame": lat["fused"]})
+
+    # fisheye batch: 32 frames of 512x512, 1500 keypoints, 6000 map points
+    frames = scenes.fisheye_batch(seed=0, n_frames=32)
+    r = time_batch(frames, steps=max(50, min(args.steps, 500)), warmup=max(3, args.warmup), dev=dev,
+                   local_rank=local_rank, arena_bytes=512 << 20)
+    pairs = fisheye_pairs(frames)
+    clk = 2070e6
+    popc_peak = 152 * POPC_PER_SM_CLK * clk
+    r["popcount"] = {"pairs_per_launch": pairs, "achieved_popc_per_s": pairs * POPC_PER_PAIR / (r["ms_per_launch"] / 1e3),
+                     "peak_popc_per_s": popc_peak,
+                     "frac": pairs * POPC_PER_PAIR / (r["ms_per_launch"] / 1e3) / popc_peak,
+                     "peak_source": "152 SMs x 16 popcounts/clk x 2070 MHz"}
+    lines.append({"workload": "fisheye batch: 32 frames 512x512 KB8, 1500 keypoints (60% overlap), "
+                              "6000 map points", **r})
+
+    # 1080p stress: batch sweep (16 distinct frames, repeated to fill a batch)
+    base = scenes.stress_batch(seed=0, n_frames=16)
+    sweep = []
+    for n in (1, 2, 4, 8, 16, 32, 64, 128):
+        frames = [base[i % len(base)] for i in range(n)]
+        steps = max(20, min(args.steps, 2000 // n))
+        sweep.append(time_batch(frames, steps=steps, warmup=max(3, args.warmup), dev=dev,
+                                local_rank=local_rank, arena_bytes=(64 << 20) + n * (24 << 20)))
+    lines.append({"workload": "stress 1920x1080, 8000 keypoints, 100k map points per frame; batch sweep",
+                  "sweep": sweep})
+    for ln in lines:
+        print(json.dumps(ln), flush=True)
+
+
 def run_gpu(args, rank, world, local_rank):
     import ctypes as C
 
@@ -590,13 +733,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served", "configs"])
     ap.add_argument("--trace-out", default=None)
     args = ap.parse_args()
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])
     if args.mode == "profile":
         return run_profile(args, dist_env()[2])
+    if args.mode == "configs":
+        return run_configs(args, dist_env()[2])
     if args.mode == "served":
         print(json.dumps(run_served(args, dist_env()[2])), flush=True)
         return
