@@ -284,19 +284,24 @@ def run_trace(args, local_rank):
 
     torch.cuda.set_device(local_rank)
     B.build()
-    frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
+    if args.workload == "stress":
+        frames = scenes.stress_batch(seed=0, n_frames=32)
+    elif args.workload == "fisheye":
+        frames = scenes.fisheye_batch(seed=0, n_frames=32)
+    else:
+        frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
     pb = PackedBatch(frames)
     pb.upload()
-    ctx = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES)
-    L.check(ctx.lib.ft_set_trace(ctx.ptr, 1 << 16), "ft_set_trace")
+    ctx = Context(device=local_rank, arena_bytes=2 << 30, max_frames=len(frames))
+    L.check(ctx.lib.ft_set_trace(ctx.ptr, 1 << 20), "ft_set_trace")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(max(3, args.warmup)):
         run_batch(ctx, pb)
     flush.fill_(1)
     run_batch(ctx, pb)
-    recs = (L.ft_trace_record * (1 << 16))()
+    recs = (L.ft_trace_record * (1 << 20))()
     n = C.c_int(0)
-    L.check(ctx.lib.ft_read_trace(ctx.ptr, recs, 1 << 16, C.byref(n)), "ft_read_trace")
+    L.check(ctx.lib.ft_read_trace(ctx.ptr, recs, 1 << 20, C.byref(n)), "ft_read_trace")
     rs = list(recs[:n.value])
     summ = trace_summary(rs)
     if args.trace_out:
@@ -304,7 +309,7 @@ def run_trace(args, local_rank):
             json.dump([[r.item, r.kind, r.frame, r.sm, r.t_start, r.t_end, r.wait_ns, list(r.mark)]
                        for r in rs], f)
     ctx.close()
-    print(json.dumps({"trace": summ, "workload": WORKLOAD}), flush=True)
+    print(json.dumps({"trace": summ, "workload": args.workload}), flush=True)
 
 
 def run_profile(args, local_rank):
@@ -735,6 +740,8 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served", "configs"])
     ap.add_argument("--trace-out", default=None)
+    ap.add_argument("--workload", default="batched", choices=["batched", "stress", "fisheye"],
+                    help="workload of --mode trace")
     args = ap.parse_args()
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])

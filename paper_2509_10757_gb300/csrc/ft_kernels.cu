@@ -259,17 +259,32 @@ __device__ __forceinline__ void mark(const BatchHeader &B, int k)
     if (B.trace != nullptr && threadIdx.x == 0) s_mark[k] = global_ns();
 }
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+
 // Block-wide wait until *ctr >= target, bounded by the header's timeout.  On
 // timeout (or when another CTA already reported one) it records the timeout in
 // the status word and returns false.
-__device__ bool wait_geq(const BatchHeader &B, const unsigned *ctr, unsigned target, int *s_flag)
+// A second counter (ctr2 non-null) is polled in the same round trip.
+__device__ bool wait_geq(const BatchHeader &B, const unsigned *ctr, unsigned target, int *s_flag,
+                         const unsigned *ctr2 = nullptr, unsigned target2 = 0)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (ld_acquire(ctr) < target) {
+        auto ready = [&]() {
+            const unsigned a = ld_acquire(ctr);
+            const unsigned b = ctr2 ? ld_acquire(ctr2) : target2;
+            return a >= target && b >= target2;
+        };
+        if (!ready()) {
             const unsigned long long t0 = global_ns();
             unsigned spins = 0;
-            while (ld_acquire(ctr) < target) {
+            while (!ready()) {
                 if ((++spins & 31u) == 0) {
                     if (global_ns() - t0 > B.timeout_ns || (ld_acquire(B.status) & kStatusTimeout)) {
                         ok = 0;
@@ -340,10 +355,12 @@ __device__ void grid_item(const BatchHeader &B, const FrameDev &F, int cam, Smem
         }
     }
     __syncthreads();
+    mark(B, 0);
     const int total = block_scan(G.cnt, G.cnt, kCells, G.warp_sums);
     for (int c = tid; c < kCells; c += kThreads) C.cell_ptr[c] = G.cnt[c];
     if (tid == 0) C.cell_ptr[kCells] = total;
     __syncthreads();
+    mark(B, 1);
     // the record's right coordinate: a stereo step in this launch fills it
     // in later (pinhole frames that wait for their stereo); otherwise it is
     // the caller's u_right input, or -1 (no consistency check)
@@ -364,7 +381,9 @@ __device__ void grid_item(const BatchHeader &B, const FrameDev &F, int cam, Smem
         C.gpos[k] = pos;
         C.owner[k] = ~0ull;
     }
+    mark(B, 2);
     signal_count(&F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
+    mark(B, 3);
 }
 
 // ---------------------------------------------------------------- K_INDEX: row sort
@@ -398,10 +417,12 @@ __device__ void rowsort_right_item(const BatchHeader &B, const FrameDev &F, Smem
             if (base + u * kThreads + tid < F.nr) atomicAdd(&S.cnt[clampi(floor_row(y[u]), 0, H - 1)], 1);
     }
     __syncthreads();
+    mark(B, 0);
     const int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
     for (int r = tid; r < H; r += kThreads) F.row_ptr_r[r] = S.cnt[r];
     if (tid == 0) F.row_ptr_r[H] = total;
     __syncthreads();
+    mark(B, 1);
     for (int base = 0; base < F.nr; base += 2 * kThreads) {
         float x[2], y[2];
         int oct[2];
@@ -433,7 +454,9 @@ __device__ void rowsort_right_item(const BatchHeader &B, const FrameDev &F, Smem
             F.rs_desc[2 * pos + 1] = d1[u];
         }
     }
+    mark(B, 2);
     signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
+    mark(B, 3);
 }
 
 __device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
@@ -453,10 +476,12 @@ __device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemR
             if (base + u * kThreads + tid < F.nl) atomicAdd(&S.cnt[own_row(y[u], H)], 1);
     }
     __syncthreads();
+    mark(B, 0);
     const int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
     for (int r = tid; r < H; r += kThreads) F.row_ptr_l[r] = S.cnt[r];
     if (tid == 0) F.row_ptr_l[H] = total;
     __syncthreads();
+    mark(B, 1);
     for (int base = 0; base < F.nl; base += kBatch * kThreads) {
         float y[kBatch];
 #pragma unroll
@@ -478,7 +503,9 @@ __device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemR
             }
         }
     }
+    mark(B, 2);
     signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
+    mark(B, 3);
 }
 
 // ---------------------------------------------------------------- K_STEREO, pinhole
@@ -545,7 +572,8 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                             if (oj < oi - 1 || oj > oi + 1) continue;
                             if (!band_has(g.y, row)) continue;
                             if (g.x < minU || g.x > maxU) continue;
-                            const unsigned k = ((unsigned)ham8(a0, a1, S.sdesc[2 * e], S.sdesc[2 * e + 1]) << 20) |
+                            const int at = __float_as_int(g.z);
+                            const unsigned k = ((unsigned)ham8(a0, a1, S.sdesc[2 * at], S.sdesc[2 * at + 1]) << 20) |
                                                (unsigned)rec_index(g.w);
                             if (k < key) {
                                 key = k;
@@ -846,8 +874,8 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     // a search in this launch reads each refined match's right coordinate
     // from the grid record, written here once the grid step is done
     const bool rec = F.wait_stereo && F.u_right_in != nullptr;
-    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag) &&
-        (!rec || wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag))) {
+    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag, rec ? &F.ctr[C_GRID_DONE] : nullptr,
+                 (unsigned)F.n_grid_items)) {
         const int H = F.H;
         const int r_lo = strip * F.strip_rows;
         const int r_hi = min(H, r_lo + F.strip_rows);
@@ -858,8 +886,19 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
         const int nrows = w_b - w_a + 1;
         const int e_base = __ldcg(F.row_ptr_r + w_a);
         const int e_end = __ldcg(F.row_ptr_r + w_b + 1);
+        const int l_lo = __ldcg(F.row_ptr_l + r_lo), l_hi = __ldcg(F.row_ptr_l + r_hi);
         const int n_st = e_end - e_base;
         const bool staged = n_st <= kStageCap && nrows <= kWinRows && P.nlevels <= kOctBuckets;
+        // asynchronous copies, in flight during the bucketing below: the first
+        // pass's left keypoints and (staged) the window's right descriptors in
+        // row order (a staged record keeps its row-order position)
+        if (tid < min(kThreads, l_hi - l_lo)) {
+            cp_async16(&S.u.left.lkp[tid], F.ls_kp + l_lo + tid);
+            cp_async16(&S.u.left.ldesc[2 * tid], F.ls_desc + 2 * (l_lo + tid));
+            cp_async16(&S.u.left.ldesc[2 * tid + 1], F.ls_desc + 2 * (l_lo + tid) + 1);
+        }
+        if (staged)
+            for (int e = tid; e < 2 * n_st; e += kThreads) cp_async16(&S.sdesc[e], F.rs_desc + 2 * e_base + e);
         if (staged) {
             constexpr int Q = kStageCap / kThreads;
             const int nb = kOctBuckets * nrows;
@@ -883,20 +922,19 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
             for (int q = 0; q < Q; ++q) {
                 const int e = q * kThreads + tid;
                 if (e < n_st) {
-                    const int pos = S.bptr[bucket[q]] + rank[q];
-                    S.rkp[pos] = g[q];
-                    S.sdesc[2 * pos] = __ldcg(F.rs_desc + 2 * (e_base + e));
-                    S.sdesc[2 * pos + 1] = __ldcg(F.rs_desc + 2 * (e_base + e) + 1);
+                    g[q].z = __int_as_float(e);          // row-order position: its descriptor
+                    S.rkp[S.bptr[bucket[q]] + rank[q]] = g[q];
                 }
             }
         }
         if (tid == 0) S.nref = 0;
-        const int l_lo = __ldcg(F.row_ptr_l + r_lo), l_hi = __ldcg(F.row_ptr_l + r_hi);
+        asm volatile("cp.async.wait_all;" ::: "memory");
         mark(B, 0);
         for (int pass = l_lo; pass < l_hi; pass += kThreads) {
             // the pass's left keypoints, one thread each, into shared memory
+            // (the first pass's are already there)
             const int npass = min(kThreads, l_hi - pass);
-            if (tid < npass) {
+            if (pass != l_lo && tid < npass) {
                 S.u.left.lkp[tid] = __ldcg(F.ls_kp + pass + tid);
                 S.u.left.ldesc[2 * tid] = __ldcg(F.ls_desc + 2 * (pass + tid));
                 S.u.left.ldesc[2 * tid + 1] = __ldcg(F.ls_desc + 2 * (pass + tid) + 1);
