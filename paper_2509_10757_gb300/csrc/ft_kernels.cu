@@ -43,6 +43,8 @@ constexpr int kL = FT_SAD_L;
 constexpr int kStripW = 2 * (kW + kL) + 1;                      // 21
 constexpr int kShifts = 2 * kL + 1;                             // 11
 constexpr int kBatch = 4;                                       // loads issued ahead per thread
+constexpr int kScatter = 3;                                     // keypoints per thread per scatter batch
+constexpr int kGridScatter = 2;
 
 // resident CTAs per SM the register budget is sized for
 #ifndef FT_MIN_CTAS_PER_SM
@@ -365,21 +367,37 @@ __device__ void grid_item(const BatchHeader &B, const FrameDev &F, int cam, Smem
     // in later (pinhole frames that wait for their stereo); otherwise it is
     // the caller's u_right input, or -1 (no consistency check)
     const bool ur_in = C.model == FT_CAMERA_PINHOLE && F.u_right_in != nullptr && !F.wait_stereo;
-    for (int k = tid; k < C.nk; k += kThreads) {
-        const float x = __ldg(C.kx + k), y = __ldg(C.ky + k);
-        const int c = grid_cell(C, iw, ih, x, y);
-        int pos = -1;
-        if (c >= 0) {
-            pos = atomicAdd(&G.cnt[c], 1);
-            const unsigned oct = (unsigned)__ldg(C.koct + k) & 0xffu;
-            const unsigned tk = C.taken ? (__ldg(C.taken + k) != 0) : 0u;
-            const float ur = ur_in ? __ldg(F.u_right_in + k) : -1.0f;
-            C.gkp[pos] = make_float4(x, y, __uint_as_float((unsigned)k | (oct << 20) | (tk << 28)), ur);
-            C.gdesc[2 * pos] = __ldg(C.kdesc + 2 * k);
-            C.gdesc[2 * pos + 1] = __ldg(C.kdesc + 2 * k + 1);
+    for (int base = 0; base < C.nk; base += kGridScatter * kThreads) {
+        float x[kGridScatter], y[kGridScatter], ur[kGridScatter];
+        unsigned oct[kGridScatter], tk[kGridScatter];
+        uint4 d0[kGridScatter], d1[kGridScatter];
+#pragma unroll
+        for (int u = 0; u < kGridScatter; ++u) {
+            const int k = min(base + u * kThreads + tid, C.nk - 1);
+            x[u] = __ldg(C.kx + k);
+            y[u] = __ldg(C.ky + k);
+            oct[u] = (unsigned)__ldg(C.koct + k) & 0xffu;
+            tk[u] = C.taken ? (__ldg(C.taken + k) != 0) : 0u;
+            ur[u] = ur_in ? __ldg(F.u_right_in + k) : -1.0f;
+            d0[u] = __ldg(C.kdesc + 2 * k);
+            d1[u] = __ldg(C.kdesc + 2 * k + 1);
         }
-        C.gpos[k] = pos;
-        C.owner[k] = ~0ull;
+#pragma unroll
+        for (int u = 0; u < kGridScatter; ++u) {
+            const int k = base + u * kThreads + tid;
+            if (k >= C.nk) continue;
+            const int c = grid_cell(C, iw, ih, x[u], y[u]);
+            int pos = -1;
+            if (c >= 0) {
+                pos = atomicAdd(&G.cnt[c], 1);
+                C.gkp[pos] = make_float4(x[u], y[u], __uint_as_float((unsigned)k | (oct[u] << 20) | (tk[u] << 28)),
+                                         ur[u]);
+                C.gdesc[2 * pos] = d0[u];
+                C.gdesc[2 * pos + 1] = d1[u];
+            }
+            C.gpos[k] = pos;
+            C.owner[k] = ~0ull;
+        }
     }
     mark(B, 2);
     signal_count(&F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
@@ -423,12 +441,12 @@ __device__ void rowsort_right_item(const BatchHeader &B, const FrameDev &F, Smem
     if (tid == 0) F.row_ptr_r[H] = total;
     __syncthreads();
     mark(B, 1);
-    for (int base = 0; base < F.nr; base += 2 * kThreads) {
-        float x[2], y[2];
-        int oct[2];
-        uint4 d0[2], d1[2];
+    for (int base = 0; base < F.nr; base += kScatter * kThreads) {
+        float x[kScatter], y[kScatter];
+        int oct[kScatter];
+        uint4 d0[kScatter], d1[kScatter];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kScatter; ++u) {
             const int j = min(base + u * kThreads + tid, F.nr - 1);
             x[u] = __ldg(F.rx + j);
             y[u] = __ldg(F.ry + j);
@@ -437,7 +455,7 @@ __device__ void rowsort_right_item(const BatchHeader &B, const FrameDev &F, Smem
             d1[u] = __ldg(F.rdesc + 2 * j + 1);
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kScatter; ++u) {
             const int j = base + u * kThreads + tid;
             if (j >= F.nr) continue;
             const int row = clampi(floor_row(y[u]), 0, H - 1);
@@ -482,25 +500,30 @@ __device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemR
     if (tid == 0) F.row_ptr_l[H] = total;
     __syncthreads();
     mark(B, 1);
-    for (int base = 0; base < F.nl; base += kBatch * kThreads) {
-        float y[kBatch];
+    // a row-ordered copy of the keypoints and their descriptors, so that the
+    // stereo strips read their left keypoints contiguously (all loads of a
+    // batch are issued before its shared-memory atomics)
+    for (int base = 0; base < F.nl; base += kScatter * kThreads) {
+        float x[kScatter], y[kScatter];
+        int oct[kScatter];
+        uint4 d0[kScatter], d1[kScatter];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int i = base + u * kThreads + tid;
-            y[u] = i < F.nl ? __ldg(F.ly + i) : 0.0f;
+        for (int u = 0; u < kScatter; ++u) {
+            const int i = min(base + u * kThreads + tid, F.nl - 1);
+            x[u] = __ldg(F.lx + i);
+            y[u] = __ldg(F.ly + i);
+            oct[u] = __ldg(F.loct + i);
+            d0[u] = __ldg(F.ldesc + 2 * i);
+            d1[u] = __ldg(F.ldesc + 2 * i + 1);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
+        for (int u = 0; u < kScatter; ++u) {
             const int i = base + u * kThreads + tid;
-            if (i < F.nl) {
-                // a row-ordered copy of the keypoint and its descriptor, so
-                // that the stereo strips read their left keypoints contiguously
-                const int pos = atomicAdd(&S.cnt[own_row(y[u], H)], 1);
-                F.ls_kp[pos] = make_float4(__ldg(F.lx + i), y[u], __int_as_float(i),
-                                           __int_as_float((int)__ldg(F.loct + i)));
-                F.ls_desc[2 * pos] = __ldg(F.ldesc + 2 * i);
-                F.ls_desc[2 * pos + 1] = __ldg(F.ldesc + 2 * i + 1);
-            }
+            if (i >= F.nl) continue;
+            const int pos = atomicAdd(&S.cnt[own_row(y[u], H)], 1);
+            F.ls_kp[pos] = make_float4(x[u], y[u], __int_as_float(i), __int_as_float(oct[u]));
+            F.ls_desc[2 * pos] = d0[u];
+            F.ls_desc[2 * pos + 1] = d1[u];
         }
     }
     mark(B, 2);
