@@ -922,15 +922,15 @@ ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const 
     if (iters < 1) iters = 3;
     cudaStream_t st = (cudaStream_t)stream;
     FT_CUDA(cudaSetDevice(ctx->device));
-    cudaEvent_t e0, e1;
-    FT_CUDA(cudaEventCreate(&e0));
-    FT_CUDA(cudaEventCreate(&e1));
+    // Two rounds: every candidate is timed launch by launch (after one
+    // untimed launch) and ranked by its median; the four best are then
+    // re-timed in turn, four times as often, so that clock drift and one-off
+    // delays do not pick the winner.
     const int strips[] = {16, 32, 64};
     const int tiles[] = {256, 512, 1024};
     const int fish[] = {256, 512};
-    int occs[] = {ctx->occ, std::max(1, ctx->occ / 2)};
-    ft_tuning best_t = default_tuning();
-    float best_ms = 1e30f;
+    const int occs[] = {ctx->occ, std::max(1, ctx->occ / 2)};
+    std::vector<ft_tuning> cand;
     for (int a : strips)
         for (int b : tiles)
             for (int c : fish)
@@ -940,27 +940,63 @@ ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const 
                     t.search_tile = b;
                     t.fisheye_tile = c;
                     t.ctas_per_sm = o;
-                    if ((s = submit(ctx, st, p, jobs, &t, false)) != FT_OK) goto out;
-                    cudaEventRecord(e0, st);
-                    for (int i = 0; i < iters; ++i)
-                        if ((s = submit(ctx, st, p, jobs, &t, false)) != FT_OK) goto out;
-                    cudaEventRecord(e1, st);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        s = fail(FT_ECUDA, "autotune: event sync failed");
-                        goto out;
-                    }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        best_t = t;
-                    }
+                    cand.push_back(t);
                 }
-    ctx->tuning[bucket_of(jobs)] = best_t;
-    if (best) *best = best_t;
-out:
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    const int slots = 4 * iters;
+    std::vector<cudaEvent_t> ev(2 * (size_t)slots, nullptr);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(FT_ECUDA, "autotune: cannot create events");
+        }
+    // times n launches of candidate t, one after another; the median in ms
+    auto time_one = [&](const ft_tuning &t, int n, float *med) -> ft_status {
+        ft_status r;
+        for (int i = 0; i < n; ++i) {
+            cudaEventRecord(ev[2 * i], st);
+            if ((r = submit(ctx, st, p, jobs, &t, false)) != FT_OK) return r;
+            cudaEventRecord(ev[2 * i + 1], st);
+        }
+        if (cudaEventSynchronize(ev[2 * n - 1]) != cudaSuccess) return fail(FT_ECUDA, "autotune: event sync failed");
+        std::vector<float> ms((size_t)n);
+        for (int i = 0; i < n; ++i) cudaEventElapsedTime(&ms[i], ev[2 * i], ev[2 * i + 1]);
+        std::nth_element(ms.begin(), ms.begin() + n / 2, ms.end());
+        *med = ms[n / 2];
+        return FT_OK;
+    };
+    std::vector<std::pair<float, int>> score;
+    for (size_t k = 0; k < cand.size() && s == FT_OK; ++k) {
+        float med = 0;
+        if ((s = submit(ctx, st, p, jobs, &cand[k], false)) != FT_OK) break;
+        if ((s = time_one(cand[k], iters, &med)) != FT_OK) break;
+        score.push_back({med, (int)k});
+    }
+    if (s == FT_OK) {
+        std::sort(score.begin(), score.end());
+        const int top = std::min<int>(4, (int)score.size());
+        std::vector<std::vector<float>> again((size_t)top);
+        for (int round = 0; round < 4 * iters && s == FT_OK; ++round)
+            for (int q = 0; q < top && s == FT_OK; ++q) {
+                float med = 0;
+                if ((s = time_one(cand[score[q].second], 1, &med)) == FT_OK) again[q].push_back(med);
+            }
+        if (s == FT_OK) {
+            int win = 0;
+            float win_ms = 1e30f;
+            for (int q = 0; q < top; ++q) {
+                auto &v = again[q];
+                std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+                if (v[v.size() / 2] < win_ms) {
+                    win_ms = v[v.size() / 2];
+                    win = score[q].second;
+                }
+            }
+            ctx->tuning[bucket_of(jobs)] = cand[win];
+            if (best) *best = cand[win];
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
     return s;
 }
 
