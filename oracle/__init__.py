@@ -55,6 +55,7 @@ class OrcParams(C.Structure):
         ("search_th", C.c_float), ("view_cos_min", C.c_float),
         ("view_cos_narrow", C.c_float), ("radius_narrow", C.c_float),
         ("radius_wide", C.c_float), ("dist_lo", C.c_float), ("dist_hi", C.c_float),
+        ("kb_iters", C.c_int), ("min_depth", C.c_float),
     ]
 
 
@@ -128,6 +129,16 @@ def _lib_handle():
             lib.orc_stereo_fisheye.argtypes = [P(OrcParams), P(OrcKeypoints), P(OrcKeypoints),
                                                C.c_float, C.c_float, C.c_float, C.c_float,
                                                vp, vp, vp]
+            lib.orc_sin_series.restype = C.c_float
+            lib.orc_sin_series.argtypes = [C.c_float]
+            lib.orc_cos_series.restype = C.c_float
+            lib.orc_cos_series.argtypes = [C.c_float]
+            lib.orc_unproject_kb8.restype = C.c_int
+            lib.orc_unproject_kb8.argtypes = [P(OrcKB8), C.c_int, C.c_float, C.c_float, vp]
+            lib.orc_triangulate.restype = C.c_int
+            lib.orc_triangulate.argtypes = [vp, vp, vp, vp, C.c_float, vp]
+            lib.orc_fisheye_triangulate.argtypes = [P(OrcParams), P(OrcKB8), P(OrcKB8), vp, vp,
+                                                    P(OrcKeypoints), P(OrcKeypoints), vp, vp, vp]
             lib.orc_grid_cell.restype = C.c_int
             lib.orc_grid_cell.argtypes = [C.c_float, C.c_float, C.c_float, C.c_float,
                                           C.c_float, C.c_float, P(C.c_int), P(C.c_int)]
@@ -328,17 +339,61 @@ def stereo_pinhole(params: dict, cam, left, right, pyr_left, pyr_right) -> dict:
 
 
 def stereo_fisheye(params: dict, rig, left, right) -> dict:
-    """a6 for one fisheye stereo frame."""
+    """a6 for one fisheye stereo frame, then f1: the accepted matches
+    triangulated (depth and left-camera point per left keypoint)."""
     lib = _lib_handle()
     keep = _Keep()
     L, R = kps_struct(left, keep), kps_struct(right, keep)
     n = L.n
-    out = dict(r_idx=np.zeros(n, np.int32), d1=np.zeros(n, np.int32), d2=np.zeros(n, np.int32))
+    out = dict(r_idx=np.zeros(n, np.int32), d1=np.zeros(n, np.int32), d2=np.zeros(n, np.int32),
+               fdepth=np.zeros(n, np.float32), xyz=np.zeros((n, 4), np.float32))
     p = params_struct(params)
     lib.orc_stereo_fisheye(C.byref(p), C.byref(L), C.byref(R), rig.lap_l0, rig.lap_l1,
                            rig.lap_r0, rig.lap_r1, _ptr(out["r_idx"]), _ptr(out["d1"]),
                            _ptr(out["d2"]))
+    fisheye_triangulate(params, rig, left, right, out["r_idx"], out)
     return out
+
+
+def unproject_kb8(cam, iters: int, u: float, v: float):
+    """f1: (ok, ray) of a Kannala-Brandt pixel."""
+    ray = np.zeros(3, np.float32)
+    c = kb8_struct(cam)
+    ok = _lib_handle().orc_unproject_kb8(C.byref(c), iters, u, v, _ptr(ray))
+    return bool(ok), ray
+
+
+def triangulate(ray_l, ray_r, R_rl, t_rl, min_depth: float):
+    """f1: (ok, point in left-camera coordinates) of two rays."""
+    arrs = [_c(a, np.float32) for a in (ray_l, ray_r, R_rl, t_rl)]
+    P = np.zeros(3, np.float32)
+    ok = _lib_handle().orc_triangulate(*[_ptr(a) for a in arrs], min_depth, _ptr(P))
+    return bool(ok), P
+
+
+def fisheye_triangulate(params: dict, rig, left, right, r_idx, out: dict | None = None) -> dict:
+    """f1 for one frame's accepted fisheye matches."""
+    lib = _lib_handle()
+    keep = _Keep()
+    L, R = kps_struct(left, keep), kps_struct(right, keep)
+    n = L.n
+    if out is None:
+        out = dict(fdepth=np.zeros(n, np.float32), xyz=np.zeros((n, 4), np.float32))
+    ridx = _c(r_idx, np.int32)
+    Rrl, trl = _c(rig.R_rl, np.float32), _c(rig.t_rl, np.float32)
+    p, cl, cr = params_struct(params), kb8_struct(rig.left), kb8_struct(rig.right)
+    lib.orc_fisheye_triangulate(C.byref(p), C.byref(cl), C.byref(cr), _ptr(Rrl), _ptr(trl),
+                                C.byref(L), C.byref(R), _ptr(ridx), _ptr(out["fdepth"]),
+                                _ptr(out["xyz"]))
+    return out
+
+
+def sin_series(t: float) -> float:
+    return float(_lib_handle().orc_sin_series(t))
+
+
+def cos_series(t: float) -> float:
+    return float(_lib_handle().orc_cos_series(t))
 
 
 def grid_cell(x: float, y: float, min_x: float, max_x: float, min_y: float, max_y: float):

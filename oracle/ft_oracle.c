@@ -516,6 +516,141 @@ int orc_project_kb8(const orc_params *p, const orc_kb8 *cam, const float *R, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* f1: fisheye triangulation.  The paper matches fisheye keypoints "to       */
+/* calculate depth" (section II-B) and says nothing more; the reading here:  */
+/*  - unprojection of a Kannala-Brandt pixel: m = ((u-cx)/fx, (v-cy)/fy),    */
+/*    theta_d = |m|; theta solves theta*(1+k1 t+k2 t^2+k3 t^3+k4 t^4) =      */
+/*    theta_d (t = theta^2) by kb_iters Newton steps from theta = theta_d,   */
+/*    kept if the residual is at most 2e-6 rad where the model still rises   */
+/*    (a pixel past the lens model's maximum has no ray);                     */
+/*    the ray is (m * sin(theta)/theta_d, cos(theta)) ((0, 0, 1) at the       */
+/*    principal point);                                                       */
+/*  - the two rays, in left-camera coordinates (right centre C = -R^T t,     */
+/*    right ray R^T r), are joined by their common perpendicular; the point  */
+/*    is its midpoint, kept when the rays are not parallel                   */
+/*    (|l x r|^2 > 1e-10 |l|^2 |r|^2), both ray parameters are positive and  */
+/*    its depth (left z) exceeds min_depth.                                  */
+/* sin and cos are their Taylor series (written out below, |t| <= 2 keeps   */
+/* the remainder under 2e-8), so both implementations share one definition.*/
+/* ------------------------------------------------------------------------ */
+float orc_sin_series(float t)
+{
+    /* t * (1 - t^2/3! + t^4/5! - ... + t^12/13!), Horner in t^2 */
+    const float t2 = t * t;
+    float s = 1.60590444e-10f;               /*  1/13! */
+    s = -2.50521079e-08f + t2 * s;           /* -1/11! */
+    s = 2.75573188e-06f + t2 * s;            /*  1/9!  */
+    s = -1.98412701e-04f + t2 * s;           /* -1/7!  */
+    s = 8.33333377e-03f + t2 * s;            /*  1/5!  */
+    s = -1.66666672e-01f + t2 * s;           /* -1/3!  */
+    s = 1.0f + t2 * s;
+    return t * s;
+}
+
+float orc_cos_series(float t)
+{
+    /* 1 - t^2/2! + t^4/4! - ... - t^14/14!, Horner in t^2 */
+    const float t2 = t * t;
+    float c = -1.14707454e-11f;              /* -1/14! */
+    c = 2.08767559e-09f + t2 * c;            /*  1/12! */
+    c = -2.75573200e-07f + t2 * c;           /* -1/10! */
+    c = 2.48015876e-05f + t2 * c;            /*  1/8!  */
+    c = -1.38888892e-03f + t2 * c;           /* -1/6!  */
+    c = 4.16666679e-02f + t2 * c;            /*  1/4!  */
+    c = -0.5f + t2 * c;                      /* -1/2!  */
+    return 1.0f + t2 * c;
+}
+
+int orc_unproject_kb8(const orc_kb8 *cam, int iters, float u, float v, float *ray)
+{
+    const float mx = (u - cam->cx) / cam->fx;
+    const float my = (v - cam->cy) / cam->fy;
+    const float thd = sqrtf(mx * mx + my * my);
+    if (thd == 0.0f) {
+        ray[0] = 0.0f;
+        ray[1] = 0.0f;
+        ray[2] = 1.0f;
+        return 1;
+    }
+    float th = thd, f = 0.0f, dp = 1.0f;
+    for (int it = 0; it <= iters; ++it) {
+        const float t2 = th * th;
+        float poly = cam->k[3];
+        poly = cam->k[2] + t2 * poly;
+        poly = cam->k[1] + t2 * poly;
+        poly = cam->k[0] + t2 * poly;
+        poly = 1.0f + t2 * poly;
+        f = th * poly - thd;
+        dp = 9.0f * cam->k[3];
+        dp = 7.0f * cam->k[2] + t2 * dp;
+        dp = 5.0f * cam->k[1] + t2 * dp;
+        dp = 3.0f * cam->k[0] + t2 * dp;
+        dp = 1.0f + t2 * dp;
+        if (it == iters) break;                  /* the last pass only measures the residual */
+        th = th - f / dp;
+    }
+    /* no solution (a pixel beyond the lens model's monotonic range), not
+     * converged, or outside the series' range */
+    if (!(fabsf(f) <= 2e-6f && dp > 0.0f && th >= 0.0f && th <= 2.0f)) return 0;
+    const float s = orc_sin_series(th) / thd;
+    ray[0] = mx * s;
+    ray[1] = my * s;
+    ray[2] = orc_cos_series(th);
+    return 1;
+}
+
+static float dot3(const float *a, const float *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const float *a, const float *b, float *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Lines s*l (left centre at the origin) and C + t*r: with n = l x r the
+ * closest points have s = ((C x r).n)/(n.n) and t = ((C x l).n)/(n.n); the
+ * cross products keep FP32 accurate for rays a few milliradians apart. */
+int orc_triangulate(const float *ray_l, const float *ray_r, const float *R_rl, const float *t_rl,
+                    float min_depth, float *xyz)
+{
+    float C[3], dr[3], n[3], cr[3], cl[3];
+    for (int i = 0; i < 3; ++i) {
+        C[i] = -(R_rl[i] * t_rl[0] + R_rl[3 + i] * t_rl[1] + R_rl[6 + i] * t_rl[2]);
+        dr[i] = R_rl[i] * ray_r[0] + R_rl[3 + i] * ray_r[1] + R_rl[6 + i] * ray_r[2];
+    }
+    cross3(ray_l, dr, n);
+    const float nn = dot3(n, n);
+    if (!(nn > 1e-10f * (dot3(ray_l, ray_l) * dot3(dr, dr)))) return 0;
+    cross3(C, dr, cr);
+    cross3(C, ray_l, cl);
+    const float s = dot3(cr, n) / nn;
+    const float t = dot3(cl, n) / nn;
+    if (!(s > 0.0f && t > 0.0f)) return 0;
+    for (int i = 0; i < 3; ++i) xyz[i] = 0.5f * (s * ray_l[i] + (C[i] + t * dr[i]));
+    return xyz[2] > min_depth;
+}
+
+void orc_fisheye_triangulate(const orc_params *p, const orc_kb8 *camL, const orc_kb8 *camR,
+                             const float *R_rl, const float *t_rl, const orc_keypoints *L,
+                             const orc_keypoints *R, const int32_t *r_idx, float *depth, float *xyz4)
+{
+    for (int i = 0; i < L->n; ++i) {
+        float P[3] = {0.0f, 0.0f, 0.0f}, rl[3], rr[3];
+        int ok = 0;
+        const int j = r_idx[i];
+        if (j >= 0 && orc_unproject_kb8(camL, p->kb_iters, L->x[i], L->y[i], rl) &&
+            orc_unproject_kb8(camR, p->kb_iters, R->x[j], R->y[j], rr))
+            ok = orc_triangulate(rl, rr, R_rl, t_rl, p->min_depth, P);
+        depth[i] = ok ? P[2] : -1.0f;
+        if (xyz4) {
+            for (int c = 0; c < 3; ++c) xyz4[4 * i + c] = ok ? P[c] : 0.0f;
+            xyz4[4 * i + 3] = ok ? 1.0f : 0.0f;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* a9 + a10 for one camera.  For each map point in view (level >= 0):      */
 /*   radius = (narrow if cos > view_cos_narrow else wide) * th * scale[lv];  */
 /*   cells [floor((u-min_x-r)*iw), ceil((u-min_x+r)*iw)] clamped to the     */

@@ -59,6 +59,9 @@ typedef struct {
     float radius_wide;      /* 4.0 px */
     float dist_lo;          /* distance must be >= dist_lo * dmin (0.8) */
     float dist_hi;          /* distance must be <= dist_hi * dmax (1.2) */
+    /* fisheye triangulation (next row f1) */
+    int   kb_iters;         /* Newton iterations of the Kannala-Brandt unprojection (10) */
+    float min_depth;        /* keep a triangulated point only if its depth > min_depth (1e-4 m) */
 } orc_params;
 
 typedef struct {
@@ -125,6 +128,16 @@ void orc_stereo_pinhole(const orc_params *p, const orc_pinhole *cam,
 void orc_stereo_fisheye(const orc_params *p, const orc_keypoints *L, const orc_keypoints *R,
                         float lap_l0, float lap_l1, float lap_r0, float lap_r1,
                         int32_t *r_idx, int32_t *d1, int32_t *d2);
+
+/* ---- fisheye triangulation (next row f1) ------------------------------ */
+float orc_sin_series(float t);           /* sin t by its Taylor series to t^13, |t| <= 2 */
+float orc_cos_series(float t);           /* cos t by its Taylor series to t^14, |t| <= 2 */
+int orc_unproject_kb8(const orc_kb8 *cam, int iters, float u, float v, float *ray);
+int orc_triangulate(const float *ray_l, const float *ray_r, const float *R_rl, const float *t_rl,
+                    float min_depth, float *xyz);
+void orc_fisheye_triangulate(const orc_params *p, const orc_kb8 *camL, const orc_kb8 *camR,
+                             const float *R_rl, const float *t_rl, const orc_keypoints *L,
+                             const orc_keypoints *R, const int32_t *r_idx, float *depth, float *xyz4);
 
 /* ---- search of local points (steps a7-a10) --------------------------- */
 int orc_grid_cell(float x, float y, float min_x, float max_x, float min_y, float max_y,

@@ -66,6 +66,8 @@ DEFAULT_PARAMS = dict(
     radius_wide=4.0,
     dist_lo=0.8,
     dist_hi=1.2,
+    kb_iters=10,
+    min_depth=1e-4,
 )
 
 
@@ -547,7 +549,8 @@ def fisheye_frame(seed: int, n_left: int = 1500, overlap_frac: float = 0.6, flip
     taken_r = (rng.random(right.n) < taken_frac).astype(np.uint8)
     return Frame(camera="fisheye", left=left, right=right, pose=make_pose(R_est, O_est), map=lmap,
                  taken_l=taken_l, rig=rig, O_right=O_right, taken_r=taken_r,
-                 pose_true=make_pose(R_true, O_true), truth=dict(true_r=true_r, map_kp=assoc))
+                 pose_true=make_pose(R_true, O_true),
+                 truth=dict(true_r=true_r, map_kp=assoc, P_left=Pl))
 
 
 # --------------------------------------------------------------------------

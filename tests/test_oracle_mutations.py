@@ -45,6 +45,19 @@ MUTANTS = [
     ("kb8_horner", "float poly = cam->k[3];", "float poly = cam->k[0];"),
     ("atan_reduction", "return pi_4 + atan_small", "return pi_4 - atan_small"),
     ("taken_ignored", "if (taken && taken[k]) continue;", ""),
+    # fisheye triangulation (next row f1)
+    ("tri_centre_sign", "C[i] = -(R_rl[i] * t_rl[0] + R_rl[3 + i] * t_rl[1] + R_rl[6 + i] * t_rl[2]);",
+     "C[i] = (R_rl[i] * t_rl[0] + R_rl[3 + i] * t_rl[1] + R_rl[6 + i] * t_rl[2]);"),
+    ("tri_rotation_transpose", "dr[i] = R_rl[i] * ray_r[0] + R_rl[3 + i] * ray_r[1] + R_rl[6 + i] * ray_r[2];",
+     "dr[i] = R_rl[3 * i] * ray_r[0] + R_rl[3 * i + 1] * ray_r[1] + R_rl[3 * i + 2] * ray_r[2];"),
+    ("tri_param_swap", "const float s = dot3(cr, n) / nn;", "const float s = dot3(cl, n) / nn;"),
+    ("tri_parallel_guard", "if (!(nn > 1e-10f * (dot3(ray_l, ray_l) * dot3(dr, dr)))) return 0;", ""),
+    ("tri_depth_threshold", "return xyz[2] > min_depth;", "return xyz[2] > 0.0f;"),
+    ("unproject_fy", "const float my = (v - cam->cy) / cam->fy;", "const float my = (v - cam->cy) / cam->fx;"),
+    ("newton_residual_sign", "f = th * poly - thd;", "f = th * poly + thd;"),
+    ("newton_no_check", "if (!(fabsf(f) <= 2e-6f && dp > 0.0f", "if (!(fabsf(f) <= 2e10f && dp > -1e30f"),
+    ("sine_coefficient", "s = -1.66666672e-01f + t2 * s;", "s = -1.66666672e-02f + t2 * s;"),
+    ("cosine_coefficient", "c = -0.5f + t2 * c;", "c = -0.25f + t2 * c;"),
 ]
 
 
@@ -64,7 +77,8 @@ def _run_mutant(tmp, name, old, new):
     env = dict(os.environ, FT_ORACLE_LIB=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_stereo.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_search.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_search.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_triangulation.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
