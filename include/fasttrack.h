@@ -83,6 +83,9 @@ typedef struct {
     float radius_wide;      /* 4.0 px at level 0 */
     float dist_lo;          /* in view if dist >= 0.8 * dmin ... */
     float dist_hi;          /* ... and dist <= 1.2 * dmax */
+    int   kb_iters;         /* fisheye triangulation: Newton steps of the
+                               Kannala-Brandt unprojection (10), in [1, 64] */
+    float min_depth;        /* fisheye triangulation: keep depth > 1e-4 m */
 } ft_params;
 
 /* Keypoints of one image (level-0 pixel coordinates).  desc is [n][32]
@@ -170,9 +173,22 @@ typedef struct {
 /* Fisheye stereo output per left keypoint: r_idx (accepted right index or
  * -1), d1 / d2 (smallest and second smallest Hamming distance over the
  * overlap candidates; d2 = 256 with a single candidate; both -1 outside the
- * overlap or with no candidate). */
+ * overlap or with no candidate).
+ * Triangulation of the accepted matches (the paper matches stereo keypoints
+ * to obtain depth, section II-B; the method is a reading): each pixel is
+ * unprojected through its Kannala-Brandt model (kb_iters Newton steps on
+ * theta, kept if the residual is at most 2e-6 rad where the model still
+ * rises), the right ray is taken to left-camera coordinates, and the point is
+ * the midpoint of the two rays' common perpendicular, kept if the rays are
+ * not parallel (|l x r|^2 > 1e-10 |l|^2 |r|^2), lie in front of both
+ * centres and its left depth exceeds min_depth.
+ *   depth [n] left-camera z of the point, else -1; may be NULL (no
+ *         triangulation)
+ *   xyz   [n][4] (x, y, z, 1) in left-camera coordinates, else zeros; may be
+ *         NULL; 16-byte aligned */
 typedef struct {
     int32_t *r_idx, *d1, *d2;
+    float *depth, *xyz;
 } ft_fisheye_out;
 
 /* Search output for one camera:

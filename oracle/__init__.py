@@ -351,7 +351,8 @@ def stereo_fisheye(params: dict, rig, left, right) -> dict:
     lib.orc_stereo_fisheye(C.byref(p), C.byref(L), C.byref(R), rig.lap_l0, rig.lap_l1,
                            rig.lap_r0, rig.lap_r1, _ptr(out["r_idx"]), _ptr(out["d1"]),
                            _ptr(out["d2"]))
-    fisheye_triangulate(params, rig, left, right, out["r_idx"], out)
+    if rig.left is not None and rig.right is not None:   # matching-only rigs carry no cameras
+        fisheye_triangulate(params, rig, left, right, out["r_idx"], out)
     return out
 
 

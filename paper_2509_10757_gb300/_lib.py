@@ -35,7 +35,8 @@ class ft_params(C.Structure):
                 ("median_factor", f32), ("fisheye_ratio", f32), ("th_search", i32),
                 ("nn_ratio", f32), ("ratio_any_octave", i32), ("search_th", f32),
                 ("view_cos_min", f32), ("view_cos_narrow", f32), ("radius_narrow", f32),
-                ("radius_wide", f32), ("dist_lo", f32), ("dist_hi", f32)]
+                ("radius_wide", f32), ("dist_lo", f32), ("dist_hi", f32), ("kb_iters", i32),
+                ("min_depth", f32)]
 
 
 class ft_keypoints(C.Structure):
@@ -83,7 +84,7 @@ class ft_stereo_out(C.Structure):
 
 
 class ft_fisheye_out(C.Structure):
-    _fields_ = [("r_idx", vp), ("d1", vp), ("d2", vp)]
+    _fields_ = [("r_idx", vp), ("d1", vp), ("d2", vp), ("depth", vp), ("xyz", vp)]
 
 
 class ft_search_cam_out(C.Structure):

@@ -65,6 +65,7 @@ def _output_specs(f, fr):
         sides = (("l", nl),)
     else:
         spec += [((f, k), np.int32, (nl,)) for k in ("r_idx", "d1", "d2")]
+        spec += [((f, "fdepth"), np.float32, (nl,)), ((f, "xyz"), np.float32, (nl, 4))]
         sides = (("l", nl), ("r", nr))
     for s, nk in sides:
         spec += [((f, f"level_{s}"), np.int8, (m,)), ((f, f"proj_{s}"), np.float32, (m, 4))]
@@ -198,6 +199,8 @@ class PackedBatch:
         s = L.ft_fisheye_out()
         for k in ("r_idx", "d1", "d2"):
             setattr(s, k, self.pout(f, k))
+        s.depth = self.pout(f, "fdepth")
+        s.xyz = self.pout(f, "xyz")
         return s
 
     def search_out(self, f) -> L.ft_search_out:
@@ -465,6 +468,8 @@ def results_arrays(c: L.ft_completion, camera: str) -> dict:
     else:
         for k in ("r_idx", "d1", "d2"):
             out[k] = arr(getattr(r.fisheye, k), nl, C.c_int32, np.int32)
+        out["fdepth"] = arr(r.fisheye.depth, nl, C.c_float, np.float32)
+        out["xyz"] = arr(r.fisheye.xyz, 4 * nl, C.c_float, np.float32, (nl, 4))
         sides = (("l", r.search.left, nl), ("r", r.search.right, nr))
     for sfx, o, nk in sides:
         out["level_" + sfx] = arr(o.level, m, C.c_int8, np.int8)

@@ -156,6 +156,8 @@ ft_status check_params(const ft_params &p)
         return fail(FT_EINVAL, "scale_factor must be >= 1");
     if (!(p.median_factor >= 0.0f)) return fail(FT_EINVAL, "median_factor must be >= 0");
     if (!(p.search_th > 0.0f)) return fail(FT_EINVAL, "search_th must be > 0");
+    if (p.kb_iters < 1 || p.kb_iters > 64) return fail(FT_EINVAL, "kb_iters %d out of [1, 64]", p.kb_iters);
+    if (!(p.min_depth >= 0.0f) || !std::isfinite(p.min_depth)) return fail(FT_EINVAL, "min_depth must be >= 0");
     float sc = 1.0f;
     for (int l = 1; l < p.nlevels; ++l) sc = sc * p.scale_factor;
     if (!(2.0f * sc < 1.0e6f)) return fail(FT_EINVAL, "scale_factor^(nlevels-1) = %g is too large", sc);
@@ -215,6 +217,8 @@ ft_status check_job(const Job &j, const ft_params &p)
                 return fail(FT_EINVAL, "stereo output: NULL array");
         }
     } else if (j.camera == FT_CAMERA_FISHEYE) {
+        if (j.do_stereo && j.fo.xyz && !aligned16(j.fo.xyz))
+            return fail(FT_EALIGN, "fisheye output: xyz not 16-byte aligned");
         if (j.do_stereo && j.left.n > 0 && (!j.fo.r_idx || !j.fo.d1 || !j.fo.d2))
             return fail(FT_EINVAL, "fisheye output: NULL array");
         if (j.do_search) {
@@ -273,6 +277,8 @@ DevParams make_dev_params(const ft_params &p)
     d.radius_narrow = p.radius_narrow;
     d.radius_wide = p.radius_wide;
     d.dist_lo = p.dist_lo;
+    d.kb_iters = p.kb_iters;
+    d.min_depth = p.min_depth;
     d.dist_hi = p.dist_hi;
     // a right keypoint's band reaches rows within ceil(r) + 2 of floor(y); +1 margin
     d.halo = (int)std::ceil(rmax) + 3;
@@ -437,10 +443,21 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             F.lap_r1 = j.rig.lap_r1;
             for (int i = 0; i < 9; ++i) F.R_rl[i] = j.rig.R_rl[i];
             for (int i = 0; i < 3; ++i) F.t_rl[i] = j.rig.t_rl[i];
+            const ft_kb8 *kb[2] = {&j.rig.left, &j.rig.right};
+            for (int c = 0; c < 2; ++c) {
+                float *d = c ? F.kbr : F.kbl;
+                d[0] = kb[c]->fx;
+                d[1] = kb[c]->fy;
+                d[2] = kb[c]->cx;
+                d[3] = kb[c]->cy;
+                for (int i = 0; i < 4; ++i) d[4 + i] = kb[c]->k[i];
+            }
             if (j.do_stereo) {
                 F.r_idx = j.fo.r_idx;
                 F.fd1 = j.fo.d1;
                 F.fd2 = j.fo.d2;
+                F.fdepth = j.fo.depth;
+                F.fxyz = reinterpret_cast<float4 *>(j.fo.depth ? j.fo.xyz : nullptr);
                 F.fisheye_tile = tune.fisheye_tile >= 512 ? 512 : 256;
                 n_stereo = (F.nl + F.fisheye_tile - 1) / F.fisheye_tile;
             }
@@ -647,6 +664,8 @@ void ft_params_default(ft_params *p)
     p->radius_wide = 4.0f;
     p->dist_lo = 0.8f;
     p->dist_hi = 1.2f;
+    p->kb_iters = 10;
+    p->min_depth = 1e-4f;
 }
 
 const char *ft_last_error(void) { return g_last_error.c_str(); }

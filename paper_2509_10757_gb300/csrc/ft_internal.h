@@ -48,6 +48,8 @@ struct DevParams {
     float sc[FT_MAX_LEVELS], isc[FT_MAX_LEVELS], band_r[FT_MAX_LEVELS];
     float median_factor, fisheye_ratio, nn_ratio, search_th;
     float view_cos_min, view_cos_narrow, radius_narrow, radius_wide, dist_lo, dist_hi;
+    int kb_iters;
+    float min_depth;
     int halo;            // rows a right keypoint's band can reach beyond floor(y), any octave
     int halo_oct[FT_MAX_LEVELS];   // same for the octave window of a left keypoint of octave o
     int halo_c[FT_MAX_LEVELS];     // same for a right keypoint of octave o
@@ -101,6 +103,9 @@ struct FrameDev {
     float *u_right, *depth;
     // stereo outputs (fisheye)
     int *r_idx, *fd1, *fd2;
+    float *fdepth;                 // triangulated depth per left keypoint (NULL: no triangulation)
+    float4 *fxyz;                  // triangulated point (may be NULL)
+    float kbl[8], kbr[8];          // fx, fy, cx, cy, k1..k4 of the left and right fisheye cameras
     // search
     const float *u_right_in;       // stereo consistency input (NULL: none)
     float R_rl[9], t_rl[3];        // fisheye rig (right camera pose is composed on the device)

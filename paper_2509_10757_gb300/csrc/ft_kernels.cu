@@ -983,6 +983,127 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     }
 }
 
+// ---------------------------------------------------------------- f1: fisheye triangulation
+// sin and cos by their Taylor series (to t^13 and t^14; |t| <= 2 keeps the
+// remainder under 2e-8), Horner in t^2, every operation explicitly rounded
+__device__ __forceinline__ float sin_series(float t)
+{
+    const float t2 = fmul(t, t);
+    float s = 1.60590444e-10f;               //  1/13!
+    s = fadd(-2.50521079e-08f, fmul(t2, s)); // -1/11!
+    s = fadd(2.75573188e-06f, fmul(t2, s));  //  1/9!
+    s = fadd(-1.98412701e-04f, fmul(t2, s)); // -1/7!
+    s = fadd(8.33333377e-03f, fmul(t2, s));  //  1/5!
+    s = fadd(-1.66666672e-01f, fmul(t2, s)); // -1/3!
+    s = fadd(1.0f, fmul(t2, s));
+    return fmul(t, s);
+}
+
+__device__ __forceinline__ float cos_series(float t)
+{
+    const float t2 = fmul(t, t);
+    float c = -1.14707454e-11f;              // -1/14!
+    c = fadd(2.08767559e-09f, fmul(t2, c));  //  1/12!
+    c = fadd(-2.75573200e-07f, fmul(t2, c)); // -1/10!
+    c = fadd(2.48015876e-05f, fmul(t2, c));  //  1/8!
+    c = fadd(-1.38888892e-03f, fmul(t2, c)); // -1/6!
+    c = fadd(4.16666679e-02f, fmul(t2, c));  //  1/4!
+    c = fadd(-0.5f, fmul(t2, c));            // -1/2!
+    return fadd(1.0f, fmul(t2, c));
+}
+
+// Ray of a Kannala-Brandt pixel (kb = fx, fy, cx, cy, k1..k4): theta solves
+// theta * (1 + k1 t + k2 t^2 + k3 t^3 + k4 t^4) = |m| (t = theta^2) by
+// `iters` Newton steps from theta = |m|; false if the residual stays above
+// 2e-6 rad, the model no longer rises there, or theta leaves [0, 2].
+__device__ bool unproject_kb8(const float *kb, int iters, float u, float v, float *ray)
+{
+    const float mx = fdiv(fsub(u, kb[2]), kb[0]);
+    const float my = fdiv(fsub(v, kb[3]), kb[1]);
+    const float thd = fsqrt(fadd(fmul(mx, mx), fmul(my, my)));
+    if (thd == 0.0f) {
+        ray[0] = 0.0f;
+        ray[1] = 0.0f;
+        ray[2] = 1.0f;
+        return true;
+    }
+    float th = thd, f = 0.0f, dp = 1.0f;
+    for (int it = 0; it <= iters; ++it) {
+        const float t2 = fmul(th, th);
+        float poly = kb[7];
+        poly = fadd(kb[6], fmul(t2, poly));
+        poly = fadd(kb[5], fmul(t2, poly));
+        poly = fadd(kb[4], fmul(t2, poly));
+        poly = fadd(1.0f, fmul(t2, poly));
+        f = fsub(fmul(th, poly), thd);
+        dp = fmul(9.0f, kb[7]);
+        dp = fadd(fmul(7.0f, kb[6]), fmul(t2, dp));
+        dp = fadd(fmul(5.0f, kb[5]), fmul(t2, dp));
+        dp = fadd(fmul(3.0f, kb[4]), fmul(t2, dp));
+        dp = fadd(1.0f, fmul(t2, dp));
+        if (it == iters) break;             // the last pass only measures the residual
+        th = fsub(th, fdiv(f, dp));
+    }
+    if (!(fabsf(f) <= 2e-6f && dp > 0.0f && th >= 0.0f && th <= 2.0f)) return false;
+    const float sn = fdiv(sin_series(th), thd);
+    ray[0] = fmul(mx, sn);
+    ray[1] = fmul(my, sn);
+    ray[2] = cos_series(th);
+    return true;
+}
+
+__device__ __forceinline__ float dot3f(const float *a, const float *b)
+{
+    return fadd(fadd(fmul(a[0], b[0]), fmul(a[1], b[1])), fmul(a[2], b[2]));
+}
+
+__device__ __forceinline__ void cross3f(const float *a, const float *b, float *c)
+{
+    c[0] = fsub(fmul(a[1], b[2]), fmul(a[2], b[1]));
+    c[1] = fsub(fmul(a[2], b[0]), fmul(a[0], b[2]));
+    c[2] = fsub(fmul(a[0], b[1]), fmul(a[1], b[0]));
+}
+
+// Midpoint of the common perpendicular of the left ray l (from the left
+// centre) and the right ray r (right camera coordinates; X_r = R_rl X_l +
+// t_rl), in left-camera coordinates: with C = -R^T t, d = R^T r and
+// n = l x d, s = ((C x d).n)/(n.n), t = ((C x l).n)/(n.n).  Kept if the rays
+// are not parallel, both parameters are positive and the depth exceeds
+// min_depth.
+__device__ bool triangulate(const float *l, const float *r, const float *R, const float *t, float min_depth,
+                            float *X)
+{
+    float C[3], d[3], n[3], cd[3], cl[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        C[i] = -fadd(fadd(fmul(R[i], t[0]), fmul(R[3 + i], t[1])), fmul(R[6 + i], t[2]));
+        d[i] = fadd(fadd(fmul(R[i], r[0]), fmul(R[3 + i], r[1])), fmul(R[6 + i], r[2]));
+    }
+    cross3f(l, d, n);
+    const float nn = dot3f(n, n);
+    if (!(nn > fmul(1e-10f, fmul(dot3f(l, l), dot3f(d, d))))) return false;
+    cross3f(C, d, cd);
+    cross3f(C, l, cl);
+    const float s = fdiv(dot3f(cd, n), nn);
+    const float tt = fdiv(dot3f(cl, n), nn);
+    if (!(s > 0.0f && tt > 0.0f)) return false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) X[i] = fmul(0.5f, fadd(fmul(s, l[i]), fadd(C[i], fmul(tt, d[i]))));
+    return X[2] > min_depth;
+}
+
+// f1 for left keypoint i with accepted right keypoint j (j < 0: none)
+__device__ void triangulate_match(const DevParams &P, const FrameDev &F, int i, int j)
+{
+    float X[3] = {0.0f, 0.0f, 0.0f}, rl[3], rr[3];
+    bool ok = false;
+    if (j >= 0 && unproject_kb8(F.kbl, P.kb_iters, __ldg(F.lx + i), __ldg(F.ly + i), rl) &&
+        unproject_kb8(F.kbr, P.kb_iters, __ldg(F.rx + j), __ldg(F.ry + j), rr))
+        ok = triangulate(rl, rr, F.R_rl, F.t_rl, P.min_depth, X);
+    F.fdepth[i] = ok ? X[2] : -1.0f;
+    if (F.fxyz) F.fxyz[i] = ok ? make_float4(X[0], X[1], X[2], 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------- K_STEREO, fisheye
 __device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U,
                                     int *s_flag)
@@ -1051,6 +1172,7 @@ __device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int
             F.r_idx[idx[q]] = r;
             F.fd1[idx[q]] = d1;
             F.fd2[idx[q]] = d2;
+            if (F.fdepth) triangulate_match(P, F, idx[q], r);
         }
     }
     if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {

@@ -132,7 +132,7 @@ DynLayout dyn_layout(int nl, int nr)
 
 struct OutLayout {
     size_t st[6];                  // best_r, dist, sad_shift, sad_best, u_right, depth (pinhole)
-    size_t fo[3];                  // r_idx, d1, d2 (fisheye)
+    size_t fo[5];                  // r_idx, d1, d2, depth, xyz (fisheye)
     size_t cam[2][6];              // level, proj, mp_kp, mp_d1, mp_d2, kp_mp per camera
     size_t bytes;
 };
@@ -147,7 +147,8 @@ OutLayout out_layout(int camera, int nl, int nr, int m)
     if (camera == FT_CAMERA_PINHOLE) {
         for (int k = 0; k < 6; ++k) put(L.st[k], 4 * (size_t)nl);
     } else {
-        for (int k = 0; k < 3; ++k) put(L.fo[k], 4 * (size_t)nl);
+        for (int k = 0; k < 4; ++k) put(L.fo[k], 4 * (size_t)nl);
+        put(L.fo[4], 16 * (size_t)nl);
     }
     const int ncam = camera == FT_CAMERA_FISHEYE ? 2 : 1;
     for (int c = 0; c < ncam; ++c) {
@@ -280,6 +281,8 @@ ft_results results_of(const StreamState &S, const Request &r, const char *base)
         R.fisheye.r_idx = reinterpret_cast<int32_t *>(at(O.fo[0]));
         R.fisheye.d1 = reinterpret_cast<int32_t *>(at(O.fo[1]));
         R.fisheye.d2 = reinterpret_cast<int32_t *>(at(O.fo[2]));
+        R.fisheye.depth = reinterpret_cast<float *>(at(O.fo[3]));
+        R.fisheye.xyz = reinterpret_cast<float *>(at(O.fo[4]));
     }
     const int ncam = S.desc.camera == FT_CAMERA_FISHEYE ? 2 : 1;
     for (int c = 0; c < ncam; ++c) {

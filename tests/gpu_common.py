@@ -38,6 +38,9 @@ def assert_stereo_equal(gpu: dict, ref: dict, where: str = ""):
 def assert_fisheye_equal(gpu: dict, ref: dict, where: str = ""):
     for k in FISHEYE_INT:
         assert np.array_equal(gpu[k], ref[k]), where + _diff(k, gpu[k], ref[k])
+    # triangulation: the same FP32 operations in the same order on both sides
+    for k in ("fdepth", "xyz"):
+        assert np.array_equal(gpu[k].view(np.uint32), ref[k].view(np.uint32)), where + _diff(k, gpu[k], ref[k])
 
 
 def assert_search_equal(gpu: dict, ref: dict, side: str, ref_side: str | None = None, where: str = ""):

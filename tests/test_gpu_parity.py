@@ -169,7 +169,38 @@ def test_search_keypoints_on_chip_boundary(ctx, lib):
         check_frame(pb, f, what="on-chip boundary, per call")
 
 
-@pytest.mark.parametrize("overrides", [{"search_th": 2.0}, {"ratio_any_octave": 1},
+def test_fisheye_triangulation_outputs_are_optional(ctx, lib):
+    # depth without xyz, and neither (matching only): the other outputs stay
+    # untouched and the matches are the same
+    from paper_2509_10757_gb300.batch import PackedBatch, rig_struct, stream_handle
+    fr = scenes.fisheye_frame(9)
+    st = orc.stereo_frame(_oracle_params(), fr)
+    pb = PackedBatch([fr])
+    pb.upload()
+    rig = rig_struct(fr.rig)
+    kl, kr = pb.keypoints(0, "l"), pb.keypoints(0, "r")
+    for keep_depth in (True, False):
+        pb.clear_outputs(0x5a)
+        out = pb.fisheye_out(0)
+        out.xyz = None
+        if not keep_depth:
+            out.depth = None
+        lib.check(ctx.lib.ft_stereo_match_fisheye(ctx.ptr, stream_handle(), None, C.byref(rig), C.byref(kl),
+                                                  C.byref(kr), C.byref(out)), "ft_stereo_match_fisheye")
+        pb.download()
+        assert ctx.sync_status() == 0
+        got = pb.outputs(0)
+        for k in ("r_idx", "d1", "d2"):
+            assert np.array_equal(got[k], st[k])
+        assert np.all(got["xyz"].view(np.uint8) == 0x5a)
+        if keep_depth:
+            assert np.array_equal(got["fdepth"].view(np.uint32), st["fdepth"].view(np.uint32))
+        else:
+            assert np.all(got["fdepth"].view(np.uint8) == 0x5a)
+    assert (st["fdepth"] > 0).sum() > 300
+
+
+@pytest.mark.parametrize("overrides", [{"search_th": 2.0}, {"ratio_any_octave": 1}, {"kb_iters": 3, "min_depth": 2.0},
                                        {"th_stereo": 40, "th_search": 60}])
 def test_parameter_variants(ctx, lib, overrides):
     frames = [scenes.single_pinhole(6), scenes.fisheye_frame(6)]
