@@ -83,6 +83,7 @@ typedef struct {
     float radius_wide;      /* 4.0 px at level 0 */
     float dist_lo;          /* in view if dist >= 0.8 * dmin ... */
     float dist_hi;          /* ... and dist <= 1.2 * dmax */
+    float th_last;          /* last-frame search: radius = 7 * scale[last octave] */
     int   kb_iters;         /* fisheye triangulation: Newton steps of the
                                Kannala-Brandt unprojection (10), in [1, 64] */
     float min_depth;        /* fisheye triangulation: keep depth > 1e-4 m */

@@ -55,7 +55,7 @@ class OrcParams(C.Structure):
         ("search_th", C.c_float), ("view_cos_min", C.c_float),
         ("view_cos_narrow", C.c_float), ("radius_narrow", C.c_float),
         ("radius_wide", C.c_float), ("dist_lo", C.c_float), ("dist_hi", C.c_float),
-        ("kb_iters", C.c_int), ("min_depth", C.c_float),
+        ("th_last", C.c_float), ("kb_iters", C.c_int), ("min_depth", C.c_float),
     ]
 
 
@@ -139,6 +139,18 @@ def _lib_handle():
             lib.orc_triangulate.argtypes = [vp, vp, vp, vp, C.c_float, vp]
             lib.orc_fisheye_triangulate.argtypes = [P(OrcParams), P(OrcKB8), P(OrcKB8), vp, vp,
                                                     P(OrcKeypoints), P(OrcKeypoints), vp, vp, vp]
+            lib.orc_motion.restype = C.c_int
+            lib.orc_motion.argtypes = [P(OrcPose), P(OrcPose), C.c_float]
+            lib.orc_search_last_camera.argtypes = [P(OrcParams), C.c_float, C.c_float, C.c_float,
+                                                   C.c_float, P(OrcKeypoints), vp, vp, C.c_int, vp,
+                                                   vp, vp, C.c_int, vp, vp, vp, vp]
+            lib.orc_search_last_pinhole.argtypes = [P(OrcParams), P(OrcPinhole), P(OrcPose), P(OrcPose),
+                                                    P(OrcKeypoints), vp, vp, C.c_int, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp, vp, vp]
+            lib.orc_search_last_fisheye.argtypes = [P(OrcParams), P(OrcKB8), P(OrcKB8), vp, vp,
+                                                    C.c_float, P(OrcPose), P(OrcPose), P(OrcKeypoints),
+                                                    vp, P(OrcKeypoints), vp, C.c_int, vp, vp, vp, vp,
+                                                    vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_grid_cell.restype = C.c_int
             lib.orc_grid_cell.argtypes = [C.c_float, C.c_float, C.c_float, C.c_float,
                                           C.c_float, C.c_float, P(C.c_int), P(C.c_int)]
@@ -525,3 +537,72 @@ def track_frame(params: dict, frame) -> tuple[dict, dict]:
     """Stereo then search for one frame, as the tracking thread runs them."""
     st = stereo_frame(params, frame)
     return st, search_frame(params, frame, st)
+
+
+def motion(cur_pose, last_pose, b: float) -> int:
+    """f2: +1 if the camera moved forward by more than b, -1 backward, else 0."""
+    a, c = pose_struct(cur_pose), pose_struct(last_pose)
+    return int(_lib_handle().orc_motion(C.byref(a), C.byref(c), b))
+
+
+def search_last_frame(params: dict, frame, last, u_right=None) -> dict:
+    """f2: the last frame's points searched in `frame` (pinhole: left camera
+    with the stereo u_right; fisheye: both cameras).  Keys as search_frame."""
+    lib = _lib_handle()
+    keep = _Keep()
+    M = last.n
+    pos = keep.add(_c(last.pos, np.float32).reshape(-1, 4))
+    md = keep.add(_c(last.desc, np.uint8).reshape(-1, 32))
+    lo = keep.add(_c(last.oct, np.int8))
+    sk = keep.add(_c(last.skip, np.uint8))
+    p = params_struct(params)
+    T, TL = pose_struct(frame.pose), pose_struct(last.pose)
+    keys = ("level", "proj", "mp_kp", "mp_d1", "mp_d2", "kp_mp")
+
+    def alloc(nk, sfx=""):
+        return {f"level{sfx}": np.zeros(M, np.int8), f"proj{sfx}": np.zeros((M, 4), np.float32),
+                f"mp_kp{sfx}": np.zeros(M, np.int32), f"mp_d1{sfx}": np.zeros(M, np.int32),
+                f"mp_d2{sfx}": np.zeros(M, np.int32), f"kp_mp{sfx}": np.zeros(nk, np.int32)}
+
+    if frame.camera == "pinhole":
+        K = kps_struct(frame.left, keep)
+        out = alloc(K.n)
+        ur = None if u_right is None else keep.add(_c(u_right, np.float32))
+        tk = None if frame.taken_l is None else keep.add(_c(frame.taken_l, np.uint8))
+        c = pinhole_struct(frame.cam)
+        lib.orc_search_last_pinhole(C.byref(p), C.byref(c), C.byref(T), C.byref(TL), C.byref(K), _ptr(ur),
+                                    _ptr(tk), M, _ptr(pos), _ptr(md), _ptr(lo), _ptr(sk),
+                                    *[_ptr(out[k]) for k in keys])
+        return out
+    rig = frame.rig
+    KL, KR = kps_struct(frame.left, keep), kps_struct(frame.right, keep)
+    out = {**alloc(KL.n, "_l"), **alloc(KR.n, "_r")}
+    tl = None if frame.taken_l is None else keep.add(_c(frame.taken_l, np.uint8))
+    tr = None if frame.taken_r is None else keep.add(_c(frame.taken_r, np.uint8))
+    Rrl, trl = keep.add(_c(rig.R_rl, np.float32)), keep.add(_c(rig.t_rl, np.float32))
+    cl, cr = kb8_struct(rig.left), kb8_struct(rig.right)
+    lib.orc_search_last_fisheye(C.byref(p), C.byref(cl), C.byref(cr), _ptr(Rrl), _ptr(trl), rig.b,
+                                C.byref(T), C.byref(TL), C.byref(KL), _ptr(tl), C.byref(KR), _ptr(tr), M,
+                                _ptr(pos), _ptr(md), _ptr(lo), _ptr(sk),
+                                *[_ptr(out[k + "_l"]) for k in keys], *[_ptr(out[k + "_r"]) for k in keys])
+    return out
+
+
+def search_last_camera(params: dict, bounds, kps, u_right, taken, desc, level, proj, motion_: int) -> dict:
+    """f2 search of one camera from given projections (for hand-built cases)."""
+    lib = _lib_handle()
+    keep = _Keep()
+    K = kps_struct(kps, keep)
+    M = len(level)
+    md = keep.add(_c(desc, np.uint8).reshape(-1, 32))
+    lv = keep.add(_c(level, np.int8))
+    pj = keep.add(_c(proj, np.float32).reshape(-1, 4))
+    ur = None if u_right is None else keep.add(_c(u_right, np.float32))
+    tk = None if taken is None else keep.add(_c(taken, np.uint8))
+    out = dict(mp_kp=np.zeros(M, np.int32), mp_d1=np.zeros(M, np.int32), mp_d2=np.zeros(M, np.int32),
+               kp_mp=np.zeros(K.n, np.int32))
+    p = params_struct(params)
+    lib.orc_search_last_camera(C.byref(p), *[float(b) for b in bounds], C.byref(K), _ptr(ur), _ptr(tk), M,
+                               _ptr(md), _ptr(lv), _ptr(pj), motion_,
+                               *[_ptr(out[k]) for k in ("mp_kp", "mp_d1", "mp_d2", "kp_mp")])
+    return out

@@ -834,3 +834,179 @@ void orc_search_fisheye(const orc_params *p, const orc_kb8 *camL, const orc_kb8 
     orc_search_camera(p, camR->min_x, camR->max_x, camR->min_y, camR->max_y, KR, NULL, takenR,
                       M, mp_desc, level_r, proj_r, mp_kp_r, mp_d1_r, mp_d2_r, kp_mp_r);
 }
+
+/* ------------------------------------------------------------------------ */
+/* f2: search by projection of the last frame's points.  The paper runs    */
+/* the same search by projection in the initial pose estimation, adapted,  */
+/* with the previous frame's points as input (sections II-C, IV-E).  The    */
+/* adaptation is a reading of the algorithm family's last-frame search:     */
+/*  - a point is in view if its camera z > 0 and its projection lies in the */
+/*    image bounds (no distance or viewing-angle test); its octave is the   */
+/*    octave of the keypoint that observed it in the last frame; points     */
+/*    with an octave outside [0, S-1] are not searched;                     */
+/*  - radius = th_last * scale[octave];                                     */
+/*  - octave window by the camera motion: with c = R_last O_cur + t_last    */
+/*    (the current centre in last-camera coordinates), forward (c.z > b)    */
+/*    keeps octaves >= the point's, backward (-c.z > b) octaves <= it,      */
+/*    otherwise octave-1 .. octave+1;                                       */
+/*  - accept the best distance d1 <= th_search, without a ratio test;       */
+/*  - the cell window, taken flags, stereo consistency and the conflict     */
+/*    rule are those of a9 and a10.                                         */
+/* ------------------------------------------------------------------------ */
+int orc_motion(const orc_pose *cur, const orc_pose *last, float b)
+{
+    float c[3];
+    transform(last->R, last->t, cur->O, c);
+    if (c[2] > b) return 1;
+    if (-c[2] > b) return -1;
+    return 0;
+}
+
+void orc_search_last_camera(const orc_params *p, float min_x, float max_x, float min_y, float max_y,
+                            const orc_keypoints *K, const float *u_right, const uint8_t *taken,
+                            int M, const uint8_t *mp_desc, const int8_t *level, const float *proj,
+                            int motion, int32_t *mp_kp, int32_t *mp_d1, int32_t *mp_d2,
+                            int32_t *kp_mp)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
+    const float iw = (float)ORC_GRID_COLS / (max_x - min_x);
+    const float ih = (float)ORC_GRID_ROWS / (max_y - min_y);
+    int64_t *owner = (int64_t *)malloc(sizeof(int64_t) * ((size_t)K->n + 1));
+    for (int k = 0; k < K->n; ++k) owner[k] = -1;
+    /* every keypoint's grid cell (a7) */
+    int *kx = (int *)malloc(sizeof(int) * ((size_t)K->n + 1));
+    int *ky = (int *)malloc(sizeof(int) * ((size_t)K->n + 1));
+    for (int k = 0; k < K->n; ++k)
+        if (!orc_grid_cell(K->x[k], K->y[k], min_x, max_x, min_y, max_y, &kx[k], &ky[k])) kx[k] = -1;
+
+    for (int m = 0; m < M; ++m) {
+        mp_kp[m] = -1;
+        mp_d1[m] = -1;
+        mp_d2[m] = -1;
+        const int lv = level[m];
+        if (lv < 0) continue;
+        const float u = proj[4 * m + 0], v = proj[4 * m + 1], ur = proj[4 * m + 2];
+        const float r = p->th_last * sc[lv];
+        const int minLevel = motion > 0 ? lv : (motion < 0 ? 0 : lv - 1);
+        const int maxLevel = motion > 0 ? p->nlevels - 1 : (motion < 0 ? lv : lv + 1);
+        int x0 = (int)floorf((u - min_x - r) * iw);
+        if (x0 < 0) x0 = 0;
+        int x1 = (int)ceilf((u - min_x + r) * iw);
+        if (x1 > ORC_GRID_COLS - 1) x1 = ORC_GRID_COLS - 1;
+        int y0 = (int)floorf((v - min_y - r) * ih);
+        if (y0 < 0) y0 = 0;
+        int y1 = (int)ceilf((v - min_y + r) * ih);
+        if (y1 > ORC_GRID_ROWS - 1) y1 = ORC_GRID_ROWS - 1;
+        if (x0 >= ORC_GRID_COLS || x1 < 0 || y0 >= ORC_GRID_ROWS || y1 < 0) continue;
+        /* the keypoints of the window's cells, in ascending index */
+        int bd = 0, bk = -1, sd = 0, sk = -1;
+        for (int k = 0; k < K->n; ++k) {
+            if (kx[k] < x0 || kx[k] > x1 || ky[k] < y0 || ky[k] > y1) continue;
+            if (K->oct[k] < minLevel || K->oct[k] > maxLevel) continue;
+            if (!(fabsf(K->x[k] - u) < r && fabsf(K->y[k] - v) < r)) continue;
+            if (taken && taken[k]) continue;
+            if (u_right && u_right[k] > 0.0f && fabsf(ur - u_right[k]) > r) continue;
+            const int d = orc_hamming(mp_desc + (size_t)m * ORC_DESC_BYTES, K->desc + (size_t)k * ORC_DESC_BYTES);
+            if (bk < 0 || d < bd) {
+                sd = bd;
+                sk = bk;
+                bd = d;
+                bk = k;
+            } else if (sk < 0 || d < sd) {
+                sd = d;
+                sk = k;
+            }
+        }
+        if (bk < 0) continue;
+        mp_d1[m] = bd;
+        mp_d2[m] = (sk >= 0) ? sd : 256;
+        if (bd > p->th_search) continue;
+        const int64_t key = ((int64_t)bd << 32) | (int64_t)m;
+        if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;
+        mp_kp[m] = bk;
+    }
+    for (int k = 0; k < K->n; ++k) kp_mp[k] = (owner[k] < 0) ? -1 : (int32_t)(owner[k] & 0xffffffff);
+    for (int m = 0; m < M; ++m)
+        if (mp_kp[m] >= 0 && kp_mp[mp_kp[m]] != m) mp_kp[m] = -1;
+    free(ky);
+    free(kx);
+    free(owner);
+}
+
+/* in-view test and projection of a last-frame point (f2) */
+static int last_level(const orc_params *p, const int8_t *last_oct, int m)
+{
+    const int lv = last_oct[m];
+    return (lv >= 0 && lv < p->nlevels) ? lv : -1;
+}
+
+void orc_search_last_pinhole(const orc_params *p, const orc_pinhole *cam, const orc_pose *T,
+                             const orc_pose *T_last, const orc_keypoints *K, const float *u_right,
+                             const uint8_t *taken, int M, const float *pos, const uint8_t *mp_desc,
+                             const int8_t *last_oct, const uint8_t *skip, int8_t *level, float *proj,
+                             int32_t *mp_kp, int32_t *mp_d1, int32_t *mp_d2, int32_t *kp_mp)
+{
+    for (int m = 0; m < M; ++m) {
+        level[m] = -1;
+        for (int c = 0; c < 4; ++c) proj[4 * m + c] = 0.0f;
+        if ((skip && skip[m]) || last_level(p, last_oct, m) < 0) continue;
+        float Pc[3];
+        transform(T->R, T->t, pos + 4 * m, Pc);
+        if (!(Pc[2] > 0.0f)) continue;
+        const float invz = 1.0f / Pc[2];
+        const float u = cam->fx * Pc[0] * invz + cam->cx;
+        const float v = cam->fy * Pc[1] * invz + cam->cy;
+        if (u < cam->min_x || u > cam->max_x || v < cam->min_y || v > cam->max_y) continue;
+        level[m] = (int8_t)last_level(p, last_oct, m);
+        proj[4 * m + 0] = u;
+        proj[4 * m + 1] = v;
+        proj[4 * m + 2] = u - cam->bf * invz;
+    }
+    orc_search_last_camera(p, cam->min_x, cam->max_x, cam->min_y, cam->max_y, K, u_right, taken, M,
+                           mp_desc, level, proj, orc_motion(T, T_last, cam->b), mp_kp, mp_d1, mp_d2,
+                           kp_mp);
+}
+
+void orc_search_last_fisheye(const orc_params *p, const orc_kb8 *camL, const orc_kb8 *camR,
+                             const float *R_rl, const float *t_rl, float b, const orc_pose *T,
+                             const orc_pose *T_last, const orc_keypoints *KL, const uint8_t *takenL,
+                             const orc_keypoints *KR, const uint8_t *takenR, int M, const float *pos,
+                             const uint8_t *mp_desc, const int8_t *last_oct, const uint8_t *skip,
+                             int8_t *level_l, float *proj_l, int32_t *mp_kp_l, int32_t *mp_d1_l,
+                             int32_t *mp_d2_l, int32_t *kp_mp_l,
+                             int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
+                             int32_t *mp_d2_r, int32_t *kp_mp_r)
+{
+    /* right camera pose R_rw = R_rl R_lw, t_rw = R_rl t_lw + t_rl (as in a8) */
+    float Rr[9], tr[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            Rr[3 * i + j] = R_rl[3 * i] * T->R[j] + R_rl[3 * i + 1] * T->R[3 + j] + R_rl[3 * i + 2] * T->R[6 + j];
+        tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2] + t_rl[i];
+    }
+    for (int m = 0; m < M; ++m) {
+        level_l[m] = level_r[m] = -1;
+        for (int c = 0; c < 4; ++c) proj_l[4 * m + c] = proj_r[4 * m + c] = 0.0f;
+        if ((skip && skip[m]) || last_level(p, last_oct, m) < 0) continue;
+        for (int side = 0; side < 2; ++side) {
+            const orc_kb8 *cam = side ? camR : camL;
+            float Pc[3], u, v;
+            transform(side ? Rr : T->R, side ? tr : T->t, pos + 4 * m, Pc);
+            if (!(Pc[2] > 0.0f)) continue;
+            kb8_project(cam, Pc, &u, &v);
+            if (u < cam->min_x || u > cam->max_x || v < cam->min_y || v > cam->max_y) continue;
+            int8_t *lv = side ? level_r : level_l;
+            float *pr = side ? proj_r : proj_l;
+            lv[m] = (int8_t)last_level(p, last_oct, m);
+            pr[4 * m + 0] = u;
+            pr[4 * m + 1] = v;
+            pr[4 * m + 2] = -1.0f;
+        }
+    }
+    const int motion = orc_motion(T, T_last, b);
+    orc_search_last_camera(p, camL->min_x, camL->max_x, camL->min_y, camL->max_y, KL, NULL, takenL, M,
+                           mp_desc, level_l, proj_l, motion, mp_kp_l, mp_d1_l, mp_d2_l, kp_mp_l);
+    orc_search_last_camera(p, camR->min_x, camR->max_x, camR->min_y, camR->max_y, KR, NULL, takenR, M,
+                           mp_desc, level_r, proj_r, motion, mp_kp_r, mp_d1_r, mp_d2_r, kp_mp_r);
+}

@@ -59,6 +59,8 @@ typedef struct {
     float radius_wide;      /* 4.0 px */
     float dist_lo;          /* distance must be >= dist_lo * dmin (0.8) */
     float dist_hi;          /* distance must be <= dist_hi * dmax (1.2) */
+    /* search of the last frame's points (next row f2) */
+    float th_last;          /* radius = th_last * scale[last octave] (7) */
     /* fisheye triangulation (next row f1) */
     int   kb_iters;         /* Newton iterations of the Kannala-Brandt unprojection (10) */
     float min_depth;        /* keep a triangulated point only if its depth > min_depth (1e-4 m) */
@@ -168,6 +170,28 @@ void orc_search_fisheye(const orc_params *p, const orc_kb8 *camL, const orc_kb8 
                         int32_t *mp_d2_l, int32_t *kp_mp_l,
                         int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
                         int32_t *mp_d2_r, int32_t *kp_mp_r);
+
+/* ---- search of the last frame's points (next row f2) ------------------ */
+int orc_motion(const orc_pose *cur, const orc_pose *last, float b);
+void orc_search_last_camera(const orc_params *p, float min_x, float max_x, float min_y, float max_y,
+                            const orc_keypoints *K, const float *u_right, const uint8_t *taken,
+                            int M, const uint8_t *mp_desc, const int8_t *level, const float *proj,
+                            int motion, int32_t *mp_kp, int32_t *mp_d1, int32_t *mp_d2,
+                            int32_t *kp_mp);
+void orc_search_last_pinhole(const orc_params *p, const orc_pinhole *cam, const orc_pose *T,
+                             const orc_pose *T_last, const orc_keypoints *K, const float *u_right,
+                             const uint8_t *taken, int M, const float *pos, const uint8_t *mp_desc,
+                             const int8_t *last_oct, const uint8_t *skip, int8_t *level, float *proj,
+                             int32_t *mp_kp, int32_t *mp_d1, int32_t *mp_d2, int32_t *kp_mp);
+void orc_search_last_fisheye(const orc_params *p, const orc_kb8 *camL, const orc_kb8 *camR,
+                             const float *R_rl, const float *t_rl, float b, const orc_pose *T,
+                             const orc_pose *T_last, const orc_keypoints *KL, const uint8_t *takenL,
+                             const orc_keypoints *KR, const uint8_t *takenR, int M, const float *pos,
+                             const uint8_t *mp_desc, const int8_t *last_oct, const uint8_t *skip,
+                             int8_t *level_l, float *proj_l, int32_t *mp_kp_l, int32_t *mp_d1_l,
+                             int32_t *mp_d2_l, int32_t *kp_mp_l,
+                             int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
+                             int32_t *mp_d2_r, int32_t *kp_mp_r);
 
 #ifdef __cplusplus
 }

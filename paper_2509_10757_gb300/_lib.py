@@ -35,7 +35,7 @@ class ft_params(C.Structure):
                 ("median_factor", f32), ("fisheye_ratio", f32), ("th_search", i32),
                 ("nn_ratio", f32), ("ratio_any_octave", i32), ("search_th", f32),
                 ("view_cos_min", f32), ("view_cos_narrow", f32), ("radius_narrow", f32),
-                ("radius_wide", f32), ("dist_lo", f32), ("dist_hi", f32), ("kb_iters", i32),
+                ("radius_wide", f32), ("dist_lo", f32), ("dist_hi", f32), ("th_last", f32), ("kb_iters", i32),
                 ("min_depth", f32)]
 
 

@@ -156,6 +156,7 @@ ft_status check_params(const ft_params &p)
         return fail(FT_EINVAL, "scale_factor must be >= 1");
     if (!(p.median_factor >= 0.0f)) return fail(FT_EINVAL, "median_factor must be >= 0");
     if (!(p.search_th > 0.0f)) return fail(FT_EINVAL, "search_th must be > 0");
+    if (!(p.th_last > 0.0f) || !std::isfinite(p.th_last)) return fail(FT_EINVAL, "th_last must be > 0");
     if (p.kb_iters < 1 || p.kb_iters > 64) return fail(FT_EINVAL, "kb_iters %d out of [1, 64]", p.kb_iters);
     if (!(p.min_depth >= 0.0f) || !std::isfinite(p.min_depth)) return fail(FT_EINVAL, "min_depth must be >= 0");
     float sc = 1.0f;
@@ -277,6 +278,7 @@ DevParams make_dev_params(const ft_params &p)
     d.radius_narrow = p.radius_narrow;
     d.radius_wide = p.radius_wide;
     d.dist_lo = p.dist_lo;
+    d.th_last = p.th_last;
     d.kb_iters = p.kb_iters;
     d.min_depth = p.min_depth;
     d.dist_hi = p.dist_hi;
@@ -664,6 +666,7 @@ void ft_params_default(ft_params *p)
     p->radius_wide = 4.0f;
     p->dist_lo = 0.8f;
     p->dist_hi = 1.2f;
+    p->th_last = 7.0f;
     p->kb_iters = 10;
     p->min_depth = 1e-4f;
 }

@@ -48,6 +48,7 @@ struct DevParams {
     float sc[FT_MAX_LEVELS], isc[FT_MAX_LEVELS], band_r[FT_MAX_LEVELS];
     float median_factor, fisheye_ratio, nn_ratio, search_th;
     float view_cos_min, view_cos_narrow, radius_narrow, radius_wide, dist_lo, dist_hi;
+    float th_last;
     int kb_iters;
     float min_depth;
     int halo;            // rows a right keypoint's band can reach beyond floor(y), any octave

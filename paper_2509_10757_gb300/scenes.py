@@ -66,6 +66,7 @@ DEFAULT_PARAMS = dict(
     radius_wide=4.0,
     dist_lo=0.8,
     dist_hi=1.2,
+    th_last=7.0,
     kb_iters=10,
     min_depth=1e-4,
 )
@@ -143,6 +144,22 @@ class LocalMap:
     nrm: np.ndarray    # float32 [M, 4]: nx, ny, nz, dmax
     desc: np.ndarray   # uint8 [M, 32]
     skip: np.ndarray   # uint8 [M]
+
+    @property
+    def n(self) -> int:
+        return int(len(self.pos))
+
+
+@dataclass
+class LastFrame:
+    """Points of the last frame to search in the current one: world position
+    (x, y, z, unused), descriptor, the octave of the keypoint that observed
+    the point in the last frame, a skip flag, and the last frame's pose."""
+    pos: np.ndarray    # float32 [M, 4]
+    desc: np.ndarray   # uint8 [M, 32]
+    oct: np.ndarray    # int8 [M]
+    skip: np.ndarray   # uint8 [M]
+    pose: Pose
 
     @property
     def n(self) -> int:
@@ -621,3 +638,35 @@ def served_stream_frame(seed: int, stream: int) -> Frame:
     cam = pinhole_camera(W, H)
     imgs = _pooled_images("served", cam, stream % 4)
     return pinhole_frame(seed * 100_003 + stream, W, H, nl, 0.2, 0.05, m, images=imgs, cam=cam)
+
+
+def last_frame(fr: Frame, seed: int, motion: str = "none", n: int | None = None) -> LastFrame:
+    """Last-frame points for frame `fr`: its local-map points (those placed
+    behind keypoints keep about their keypoint's octave, the others get a
+    random one; a few get an octave outside the pyramid), and a last pose
+    with the current orientation whose centre lies behind ("forward"), ahead
+    of ("backward") or beside ("none") the current one along the viewing
+    axis, 0.3 m away (more than a stereo baseline) or 2 cm for "none"."""
+    rng = np.random.default_rng(seed)
+    m = fr.map
+    M = m.n if n is None else min(n, m.n)
+    oct_ = sample_octaves(rng, M).astype(np.int64)
+    assoc = np.asarray(fr.truth.get("map_kp", np.zeros(0, np.int64))) if fr.truth else np.zeros(0, np.int64)
+    na = min(len(assoc), M)
+    if na:
+        oct_[:na] = np.clip(fr.left.oct[assoc[:na]].astype(np.int64) + rng.integers(-1, 2, na), 0, NLEVELS - 1)
+    bad = rng.random(M) < 0.02
+    oct_[bad] = rng.choice([-1, NLEVELS, 100], bad.sum())
+    R = fr.pose.R.reshape(3, 3).astype(np.float64)
+    O = fr.pose.O.astype(np.float64)
+    axis = R[2]                                     # viewing axis in world coordinates
+    side = R[0]
+    if motion == "forward":
+        O_last = O - 0.3 * axis
+    elif motion == "backward":
+        O_last = O + 0.3 * axis
+    else:
+        O_last = O + 0.02 * side
+    return LastFrame(pos=np.ascontiguousarray(m.pos[:M]), desc=np.ascontiguousarray(m.desc[:M]),
+                     oct=oct_.astype(np.int8), skip=np.ascontiguousarray(m.skip[:M]),
+                     pose=make_pose(R, O_last))

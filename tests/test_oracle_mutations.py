@@ -58,6 +58,18 @@ MUTANTS = [
     ("newton_no_check", "if (!(fabsf(f) <= 2e-6f && dp > 0.0f", "if (!(fabsf(f) <= 2e10f && dp > -1e30f"),
     ("sine_coefficient", "s = -1.66666672e-01f + t2 * s;", "s = -1.66666672e-02f + t2 * s;"),
     ("cosine_coefficient", "c = -0.5f + t2 * c;", "c = -0.25f + t2 * c;"),
+    # search of the last frame's points (next row f2)
+    ("last_forward_window", "const int minLevel = motion > 0 ? lv : (motion < 0 ? 0 : lv - 1);",
+     "const int minLevel = motion > 0 ? lv - 1 : (motion < 0 ? 0 : lv - 1);"),
+    ("last_backward_window", "const int maxLevel = motion > 0 ? p->nlevels - 1 : (motion < 0 ? lv : lv + 1);",
+     "const int maxLevel = motion > 0 ? p->nlevels - 1 : (motion < 0 ? lv + 1 : lv + 1);"),
+    ("last_radius_octave", "const float r = p->th_last * sc[lv];", "const float r = p->th_last * sc[0];"),
+    ("last_motion_sign", "if (-c[2] > b) return -1;", "if (c[2] < b) return -1;"),
+    ("last_ratio_added", "if (bd > p->th_search) continue;\n        const int64_t key = ((int64_t)bd << 32) | (int64_t)m;\n        if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;\n        mp_kp[m] = bk;\n    }\n    for (int k = 0; k < K->n; ++k) kp_mp[k] = (owner[k] < 0) ? -1 : (int32_t)(owner[k] & 0xffffffff);\n    for (int m = 0; m < M; ++m)\n        if (mp_kp[m] >= 0 && kp_mp[mp_kp[m]] != m) mp_kp[m] = -1;\n    free(ky);",
+     "if (bd > p->th_search || (float)bd > 0.8f * (float)mp_d2[m]) continue;\n        const int64_t key = ((int64_t)bd << 32) | (int64_t)m;\n        if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;\n        mp_kp[m] = bk;\n    }\n    for (int k = 0; k < K->n; ++k) kp_mp[k] = (owner[k] < 0) ? -1 : (int32_t)(owner[k] & 0xffffffff);\n    for (int m = 0; m < M; ++m)\n        if (mp_kp[m] >= 0 && kp_mp[mp_kp[m]] != m) mp_kp[m] = -1;\n    free(ky);"),
+    ("last_octave_range", "return (lv >= 0 && lv < p->nlevels) ? lv : -1;", "return (lv >= -1 && lv < p->nlevels) ? (lv < 0 ? 0 : lv) : -1;"),
+    ("last_view_distance", "        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;",
+     "        if (Pc[2] > 8.0f) continue;\n        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;"),
 ]
 
 
@@ -78,7 +90,8 @@ def _run_mutant(tmp, name, old, new):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_stereo.py"),
                         os.path.join(ROOT, "tests", "test_oracle_search.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_triangulation.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_triangulation.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_lastframe.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
