@@ -225,7 +225,27 @@ typedef struct {
     float O_right[3];
 } ft_frame_view;
 
-/* One frame of a batch: stereo matching then search of local points. */
+/* The last frame's points for the search of the last frame (next row f2;
+ * the paper's initial pose estimation runs the same search by projection on
+ * the previous frame's points, sections II-C and IV-E):
+ *   pos  [n][4] world x, y, z and an unused float, 16-byte aligned
+ *   desc [n][32], 16-byte aligned
+ *   oct  [n] octave of the keypoint that observed the point in the last
+ *        frame (points with an octave outside [0, nlevels) are not searched)
+ *   skip [n] nonzero leaves a point out (may be NULL)
+ *   pose the last frame's pose (world -> camera); with the current pose it
+ *        gives the camera's motion along its viewing axis */
+typedef struct {
+    int n;
+    const float *pos;
+    const uint8_t *desc;
+    const int8_t *oct;
+    const uint8_t *skip;
+    ft_pose pose;
+} ft_last_frame_view;
+
+/* One frame of a batch: stereo matching then search of local points (or,
+ * with last non-NULL, of the last frame's points; map is then ignored). */
 typedef struct {
     int camera;                 /* ft_camera_model */
     ft_pinhole pinhole;
@@ -239,6 +259,7 @@ typedef struct {
     ft_stereo_out stereo;               /* pinhole */
     ft_fisheye_out fisheye_out;         /* fisheye */
     ft_search_out search;
+    const ft_last_frame_view *last;     /* HOST struct; NULL: search the local map */
 } ft_frame_job;
 
 /* A ragged batch.  frames points to HOST memory (n entries).  If
@@ -319,6 +340,22 @@ ft_status ft_stereo_match_fisheye(ft_ctx *ctx, void *stream, const ft_params *pa
 ft_status ft_search_local_points(ft_ctx *ctx, void *stream, const ft_params *params,
                                  const ft_frame_view *frame, const ft_pose *Tcw,
                                  const ft_map_view *map, ft_search_out *out);
+
+/* Search of the last frame's points for one frame (next row f2): the
+ * search by projection of the paper's initial pose estimation (sections
+ * II-C, IV-E), adapted as the algorithm family does it (a reading): a point
+ * is in view if it lies in front of the camera and projects inside the image
+ * (no distance or viewing-angle test); its search radius is th_last *
+ * scale[oct]; the candidate octaves are >= oct if the camera moved forward
+ * by more than the stereo baseline along its viewing axis since the last
+ * frame, <= oct if it moved backward, oct-1..oct+1 otherwise; the best
+ * distance is accepted if <= th_search, without a ratio test; the grid
+ * window, taken flags, stereo consistency (pinhole u_right) and conflict
+ * resolution are those of the local-map search.  Outputs as
+ * ft_search_local_points, with level = the point's octave and proj[3] = 0. */
+ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *params,
+                               const ft_frame_view *frame, const ft_pose *Tcw,
+                               const ft_last_frame_view *last, ft_search_out *out);
 
 /* Stereo matching followed by the search, for a ragged batch of frames, in
  * one persistent fused launch (CUDA-graph replayed per batch-shape bucket if

@@ -102,13 +102,17 @@ class ft_frame_view(C.Structure):
                 ("taken_left", vp), ("taken_right", vp), ("O_right", f32 * 3)]
 
 
+class ft_last_frame_view(C.Structure):
+    _fields_ = [("n", i32), ("pos", vp), ("desc", vp), ("oct", vp), ("skip", vp), ("pose", ft_pose)]
+
+
 class ft_frame_job(C.Structure):
     _fields_ = [("camera", i32), ("pinhole", ft_pinhole), ("fisheye", ft_fisheye_rig),
                 ("left", ft_keypoints), ("right", ft_keypoints), ("pyr_left", ft_pyramid),
                 ("pyr_right", ft_pyramid), ("taken_left", vp), ("taken_right", vp),
                 ("pose", ft_pose), ("O_right", f32 * 3), ("map", ft_map_view),
                 ("stereo", ft_stereo_out), ("fisheye_out", ft_fisheye_out),
-                ("search", ft_search_out)]
+                ("search", ft_search_out), ("last", C.POINTER(ft_last_frame_view))]
 
 
 class ft_batch(C.Structure):
@@ -184,6 +188,9 @@ SIGNATURES = [
     ("ft_search_local_points", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_frame_view),
                                      C.POINTER(ft_pose), C.POINTER(ft_map_view),
                                      C.POINTER(ft_search_out)]),
+    ("ft_search_last_frame", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_frame_view),
+                                   C.POINTER(ft_pose), C.POINTER(ft_last_frame_view),
+                                   C.POINTER(ft_search_out)]),
     ("ft_track_batch", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch)]),
     ("ft_autotune", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch), i32,
                           C.POINTER(ft_tuning)]),

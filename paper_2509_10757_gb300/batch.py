@@ -38,8 +38,8 @@ class _Layout:
         return off
 
 
-def _input_arrays(f, fr):
-    """(key, array) pairs of frame `f`'s inputs."""
+def _input_arrays(f, fr, last=None):
+    """(key, array) pairs of frame `f`'s inputs (and of its last frame's points)."""
     out = [((f, "lx"), fr.left.x), ((f, "ly"), fr.left.y), ((f, "loct"), fr.left.oct),
            ((f, "ldesc"), fr.left.desc), ((f, "rx"), fr.right.x), ((f, "ry"), fr.right.y),
            ((f, "roct"), fr.right.oct), ((f, "rdesc"), fr.right.desc),
@@ -53,10 +53,13 @@ def _input_arrays(f, fr):
         out.append(((f, "taken_r"), fr.taken_r))
     out += [((f, "pos"), fr.map.pos), ((f, "nrm"), fr.map.nrm), ((f, "mdesc"), fr.map.desc),
             ((f, "skip"), fr.map.skip)]
+    if last is not None:
+        out += [((f, "lf_pos"), last.pos), ((f, "lf_desc"), last.desc), ((f, "lf_oct"), last.oct),
+                ((f, "lf_skip"), last.skip)]
     return out
 
 
-def _output_specs(f, fr):
+def _output_specs(f, fr, last=None):
     nl, nr, m = fr.left.n, fr.right.n, fr.map.n
     spec = []
     if fr.camera == "pinhole":
@@ -71,6 +74,11 @@ def _output_specs(f, fr):
         spec += [((f, f"level_{s}"), np.int8, (m,)), ((f, f"proj_{s}"), np.float32, (m, 4))]
         spec += [((f, f"{k}_{s}"), np.int32, (m,)) for k in ("mp_kp", "mp_d1", "mp_d2")]
         spec += [((f, f"kp_mp_{s}"), np.int32, (nk,))]
+    if last is not None:
+        for s, nk in sides:
+            spec += [((f, f"lf_level_{s}"), np.int8, (last.n,)), ((f, f"lf_proj_{s}"), np.float32, (last.n, 4))]
+            spec += [((f, f"lf_{k}_{s}"), np.int32, (last.n,)) for k in ("mp_kp", "mp_d1", "mp_d2")]
+            spec += [((f, f"lf_kp_mp_{s}"), np.int32, (nk,))]
     return spec
 
 
@@ -125,18 +133,22 @@ def pose_struct(pose) -> L.ft_pose:
 class PackedBatch:
     """Inputs and outputs of a list of generated frames, packed for the GPU."""
 
-    def __init__(self, frames, device: str | torch.device = "cuda", pin: bool = True):
+    def __init__(self, frames, device: str | torch.device = "cuda", pin: bool = True, lasts=None):
+        """lasts: optional per-frame scenes.LastFrame (or None); a frame with
+        one gets the last frame's points packed too, its batch job searches
+        them instead of the local map, and its results go to the lf_* outputs."""
         self.frames = list(frames)
+        self.lasts = list(lasts) if lasts is not None else [None] * len(self.frames)
         self.device = torch.device(device)
         self.lin = _Layout()
         self.lout = _Layout()
         arrays = []
         for f, fr in enumerate(self.frames):
-            for key, a in _input_arrays(f, fr):
+            for key, a in _input_arrays(f, fr, self.lasts[f]):
                 a = np.ascontiguousarray(a)
                 self.lin.add(key, a.dtype, a.shape)
                 arrays.append(a)
-            for key, dt, shape in _output_specs(f, fr):
+            for key, dt, shape in _output_specs(f, fr, self.lasts[f]):
                 self.lout.add(key, dt, shape)
         self.host_in = torch.empty(self.lin.size, dtype=torch.uint8, pin_memory=pin)
         self.host_out = torch.empty(self.lout.size, dtype=torch.uint8, pin_memory=pin)
@@ -147,6 +159,8 @@ class PackedBatch:
         self.dev_out = torch.empty(self.lout.size, dtype=torch.uint8, device=self.device)
         self.in_base = self.dev_in.data_ptr()
         self.out_base = self.dev_out.data_ptr()
+        self.last_views = [self.last_view(f) if self.lasts[f] is not None else None
+                           for f in range(len(self.frames))]
         self.jobs = (L.ft_frame_job * max(1, len(self.frames)))()
         for f in range(len(self.frames)):
             self.jobs[f] = self.job(f)
@@ -203,12 +217,21 @@ class PackedBatch:
         s.xyz = self.pout(f, "xyz")
         return s
 
-    def search_out(self, f) -> L.ft_search_out:
+    def search_out(self, f, prefix: str = "") -> L.ft_search_out:
         s = L.ft_search_out()
         for side, dst in (("l", s.left), ("r", s.right)):
-            if self.has_out(f, f"level_{side}"):
+            if self.has_out(f, f"{prefix}level_{side}"):
                 for k in ("level", "proj", "mp_kp", "mp_d1", "mp_d2", "kp_mp"):
-                    setattr(dst, k, self.pout(f, f"{k}_{side}"))
+                    setattr(dst, k, self.pout(f, f"{prefix}{k}_{side}"))
+        return s
+
+    def last_view(self, f) -> L.ft_last_frame_view:
+        last = self.lasts[f]
+        s = L.ft_last_frame_view()
+        s.n = last.n
+        s.pos, s.desc = self.pin_(f, "lf_pos"), self.pin_(f, "lf_desc")
+        s.oct, s.skip = self.pin_(f, "lf_oct"), self.pin_(f, "lf_skip")
+        s.pose = pose_struct(last.pose)
         return s
 
     def frame_view(self, f, u_right: bool = True) -> L.ft_frame_view:
@@ -242,6 +265,9 @@ class PackedBatch:
         j.pose = pose_struct(fr.pose)
         j.map = self.map_view(f)
         j.search = self.search_out(f)
+        if self.last_views[f] is not None:
+            j.last = C.pointer(self.last_views[f])
+            j.search = self.search_out(f, "lf_")
         if fr.camera == "pinhole":
             j.camera = L.FT_CAMERA_PINHOLE
             j.pinhole = pinhole_struct(fr.cam)
@@ -366,6 +392,19 @@ def run_search(ctx: Context, pb: PackedBatch, f: int, params: L.ft_params | None
     r = ctx.lib.ft_search_local_points(ctx.ptr, stream_handle(stream), p, C.byref(fv),
                                        C.byref(pose), C.byref(mv), C.byref(out))
     L.check(r, "ft_search_local_points")
+
+
+def run_search_last(ctx: Context, pb: PackedBatch, f: int, params: L.ft_params | None = None,
+                    stream=None, u_right: bool = True):
+    """Per-frame search of the last frame's points (pb built with lasts)."""
+    fv = pb.frame_view(f, u_right=u_right)
+    pose = pose_struct(pb.frames[f].pose)
+    lv = pb.last_views[f]
+    out = pb.search_out(f, "lf_")
+    p = C.byref(params) if params is not None else None
+    r = ctx.lib.ft_search_last_frame(ctx.ptr, stream_handle(stream), p, C.byref(fv), C.byref(pose),
+                                     C.byref(lv), C.byref(out))
+    L.check(r, "ft_search_last_frame")
 
 
 def run_batch(ctx: Context, pb: PackedBatch, params: L.ft_params | None = None, stream=None,

@@ -105,7 +105,23 @@ struct Job {
     ft_fisheye_out fo{};
     ft_search_out so{};
     const float *u_right_in = nullptr;
+    int search_mode = 0;                  // 0: local map; 1: the last frame's points (map.nrm unused)
+    const int8_t *last_oct = nullptr;
+    ft_pose last_pose{};
 };
+
+// the map view and mode of a last-frame search
+void set_last(Job &j, const ft_last_frame_view &l)
+{
+    j.search_mode = 1;
+    j.map = ft_map_view{};
+    j.map.n = l.n;
+    j.map.pos = l.pos;
+    j.map.desc = l.desc;
+    j.map.skip = l.skip;
+    j.last_oct = l.oct;
+    j.last_pose = l.pose;
+}
 
 }  // namespace
 
@@ -235,10 +251,15 @@ ft_status check_job(const Job &j, const ft_params &p)
     if (j.do_search) {
         const ft_map_view &m = j.map;
         if (m.n < 0 || m.n >= FT_MAX_MAP_POINTS) return fail(FT_EINVAL, "map: n=%d out of range", m.n);
-        if (m.n > 0) {
+        if (m.n > 0 && j.search_mode == 0) {
             if (!m.pos || !m.nrm || !m.desc) return fail(FT_EINVAL, "map: NULL array");
             if (!aligned16(m.pos) || !aligned16(m.nrm) || !aligned16(m.desc))
                 return fail(FT_EALIGN, "map: pos/nrm/desc not 16-byte aligned");
+        }
+        if (m.n > 0 && j.search_mode == 1) {
+            if (!m.pos || !m.desc || !j.last_oct) return fail(FT_EINVAL, "last frame: NULL array");
+            if (!aligned16(m.pos) || !aligned16(m.desc))
+                return fail(FT_EALIGN, "last frame: pos/desc not 16-byte aligned");
         }
         const int ncam = j.camera == FT_CAMERA_FISHEYE ? 2 : 1;
         for (int c = 0; c < ncam; ++c) {
@@ -475,6 +496,11 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             F.nrm = reinterpret_cast<const float4 *>(j.map.nrm);
             F.mdesc = reinterpret_cast<const uint4 *>(j.map.desc);
             F.skip = j.map.skip;
+            F.search_mode = j.search_mode;
+            F.last_oct = j.last_oct;
+            for (int i = 0; i < 9; ++i) F.last_R[i] = j.last_pose.R[i];
+            for (int i = 0; i < 3; ++i) F.last_t[i] = j.last_pose.t[i];
+            F.base = j.camera == FT_CAMERA_PINHOLE ? j.pin.b : j.rig.b;
             F.search_tile = std::max(kThreads, tune.search_tile / kThreads * kThreads);
             F.resolve_tile = std::max(kThreads, tune.resolve_tile / kThreads * kThreads);
             for (int c = 0; c < F.ncam; ++c) {
@@ -852,6 +878,31 @@ ft_status ft_search_local_points(ft_ctx *ctx, void *stream, const ft_params *par
     return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
 }
 
+ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *params,
+                               const ft_frame_view *frame, const ft_pose *Tcw, const ft_last_frame_view *last,
+                               ft_search_out *out)
+{
+    if (!ctx || !frame || !Tcw || !last || !out) return fail(FT_EINVAL, "ft_search_last_frame: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    Job j;
+    j.camera = frame->camera;
+    j.do_search = true;
+    j.pin = frame->pinhole;
+    j.rig = frame->fisheye;
+    j.left = frame->left;
+    j.right = frame->right;
+    j.u_right_in = frame->u_right;
+    j.taken_l = frame->taken_left;
+    j.taken_r = frame->taken_right;
+    j.pose = *Tcw;
+    for (int i = 0; i < 3; ++i) j.O_right[i] = frame->O_right[i];
+    set_last(j, *last);
+    j.so = *out;
+    return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
+}
+
 static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
 {
     if (!batch || batch->n < 0 || (batch->n > 0 && !batch->frames))
@@ -879,6 +930,7 @@ static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
         j.fo = s.fisheye_out;
         j.so = s.search;
         j.u_right_in = s.camera == FT_CAMERA_PINHOLE ? s.stereo.u_right : nullptr;
+        if (s.last) set_last(j, *s.last);
     }
     return FT_OK;
 }

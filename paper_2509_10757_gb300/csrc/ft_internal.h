@@ -109,6 +109,10 @@ struct FrameDev {
     float kbl[8], kbr[8];          // fx, fy, cx, cy, k1..k4 of the left and right fisheye cameras
     // search
     const float *u_right_in;       // stereo consistency input (NULL: none)
+    int search_mode;               // 0: local map; 1: the last frame's points
+    const int8_t *last_oct;        // last mode: octave of each point's last observation
+    float last_R[9], last_t[3];    // last mode: the last frame's pose
+    float base;                    // stereo baseline (the motion test of the last mode)
     float R_rl[9], t_rl[3];        // fisheye rig (right camera pose is composed on the device)
     CamDev cam[2];
     const float4 *pos, *nrm;

@@ -1213,8 +1213,9 @@ __device__ __forceinline__ bool distance_scale(const DevParams &P, const float *
     return true;
 }
 
-__device__ bool project(const DevParams &P, const CamDev &C, const float *pose, float4 pos,
-                        float4 nrm, float &u, float &v, float &ur, float &vc, int &level)
+// a8 without the distance and viewing tests: camera z > 0 and the
+// projection inside the image bounds
+__device__ bool project_uv(const CamDev &C, const float *pose, float4 pos, float &u, float &v, float &ur)
 {
     float x, y, z;
     transform(pose, pos, x, y, z);
@@ -1247,29 +1248,50 @@ __device__ bool project(const DevParams &P, const CamDev &C, const float *pose, 
         if (v < C.miny || v > C.maxy) return false;
         ur = -1.0f;
     }
-    return distance_scale(P, C.O, pos, nrm, vc, level);
+    return true;
+}
+
+__device__ bool project(const DevParams &P, const CamDev &C, const float *pose, float4 pos,
+                        float4 nrm, float &u, float &v, float &ur, float &vc, int &level)
+{
+    return project_uv(C, pose, pos, u, v, ur) && distance_scale(P, C.O, pos, nrm, vc, level);
 }
 
 // One map point against the keypoints of its search window.  kStaged: the
 // camera's cell-ordered records and descriptors sit in shared memory.
+// motion: for a last-frame search, +1 / -1 / 0 for a camera that moved
+// forward / backward / neither along its viewing axis (f2).
 template <bool kStaged>
 __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C, const SmemSearch &Q,
-                             float iw, float ih, int m)
+                             float iw, float ih, int m, int motion)
 {
     const float *pose = Q.pose;
+    const bool last = F.search_mode != 0;
     int lvl = -1, d1 = -1, d2 = -1, kp = -1;
     float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool skipped = F.skip != nullptr && __ldg(F.skip + m) != 0;
+    const int loct = last ? (int)__ldg(F.last_oct + m) : 0;
+    const bool skipped = (F.skip != nullptr && __ldg(F.skip + m) != 0) || (last && (loct < 0 || loct >= P.nlevels));
     if (!skipped) {
-        const float4 pos = __ldg(F.pos + m), nrm = __ldg(F.nrm + m);
-        float u, v, ur, vc;
-        int level;
-        if (project(P, C, pose, pos, nrm, u, v, ur, vc, level)) {
+        const float4 pos = __ldg(F.pos + m);
+        float u, v, ur, vc = 0.0f;
+        int level = loct;
+        const bool in_view = last ? project_uv(C, pose, pos, u, v, ur)
+                                  : project(P, C, pose, pos, __ldg(F.nrm + m), u, v, ur, vc, level);
+        if (in_view) {
             lvl = level;
             pj = make_float4(u, v, ur, vc);
-            float r = (vc > P.view_cos_narrow) ? P.radius_narrow : P.radius_wide;
-            r = fmul(r, P.search_th);
-            r = fmul(r, P.sc[level]);
+            float r;
+            int min_oct = level - 1, max_oct = level;
+            if (last) {
+                // f2: radius of the last octave, octave window by the motion
+                r = fmul(P.th_last, P.sc[level]);
+                min_oct = motion > 0 ? level : (motion < 0 ? 0 : level - 1);
+                max_oct = motion > 0 ? P.nlevels - 1 : (motion < 0 ? level : level + 1);
+            } else {
+                r = (vc > P.view_cos_narrow) ? P.radius_narrow : P.radius_wide;
+                r = fmul(r, P.search_th);
+                r = fmul(r, P.sc[level]);
+            }
             const float du = fsub(u, C.minx), dv = fsub(v, C.miny);
             const int x0 = max(f2i(floorf(fmul(fsub(du, r), iw))), 0);
             const int x1 = min(f2i(ceilf(fmul(fadd(du, r), iw))), FT_GRID_COLS - 1);
@@ -1304,7 +1326,7 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                         oct = (int)(int8_t)((z >> 20) & 0xffu);
                         taken = (z >> 28) != 0;
                         urk = g.w;
-                        if (oct < level - 1 || oct > level) continue;
+                        if (oct < min_oct || oct > max_oct) continue;
                         const float distx = fsub(gx, u), disty = fsub(gy, v);
                         if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
                         if (taken) continue;
@@ -1330,7 +1352,7 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                     d2 = second != kNoKey ? (int)(second >> 20) : 256;
                     if (d1 <= P.th_search) {
                         const int k1 = (int)(best & 0xfffffu);
-                        const bool ratio = P.ratio_any_octave || oct1 == oct2;
+                        const bool ratio = !last && (P.ratio_any_octave || oct1 == oct2);
                         if (!(ratio && (float)d1 > fmul(P.nn_ratio, (float)d2))) {
                             atomicMin(C.owner + k1, ((unsigned long long)d1 << 32) | (unsigned)m);
                             kp = k1;
@@ -1398,10 +1420,20 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         const int m1 = min(F.nm, m0 + F.search_tile);
         const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
         const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
+        int motion = 0;
+        if (F.search_mode != 0) {
+            // the current (left) camera centre in the last frame's camera
+            // coordinates; its z against the baseline (f2)
+            const float *O = F.cam[0].O;
+            const float cz =
+                fadd(fadd(fadd(fmul(F.last_R[6], O[0]), fmul(F.last_R[7], O[1])), fmul(F.last_R[8], O[2])),
+                     F.last_t[2]);
+            motion = cz > F.base ? 1 : (-cz > F.base ? -1 : 0);
+        }
         if (staged) {
-            for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, iw, ih, m);
+            for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, iw, ih, m, motion);
         } else {
-            for (int m = m0 + tid; m < m1; m += kThreads) search_point<false>(B.p, F, C, Q, iw, ih, m);
+            for (int m = m0 + tid; m < m1; m += kThreads) search_point<false>(B.p, F, C, Q, iw, ih, m, motion);
         }
         mark(B, 1);
     } else {

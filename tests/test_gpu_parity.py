@@ -392,3 +392,83 @@ def test_host_checks_reject_bad_arguments(ctx, lib):
         assert lib.ft_track_batch(small.ptr, stream_handle(), None, C.byref(b)) == lib.FT_ENOMEM
     finally:
         small.close()
+
+
+# ---------------------------------------------------------------- search of the last frame (f2)
+def _check_last(pb, f, st, what):
+    fr, last = pb.frames[f], pb.lasts[f]
+    ref = orc.search_last_frame(_oracle_params(), fr, last, st["u_right"] if fr.camera == "pinhole" else None)
+    out = pb.outputs(f)
+    got = {k[3:]: v for k, v in out.items() if k.startswith("lf_")}
+    if fr.camera == "pinhole":
+        assert_search_equal(got, ref, "l", None, what)
+    else:
+        assert_search_equal(got, ref, "l", "l", what)
+        assert_search_equal(got, ref, "r", "r", what)
+    return ref
+
+
+@pytest.mark.parametrize("motion", ["forward", "backward", "none"])
+def test_last_frame_search_per_call(ctx, lib, motion):
+    from paper_2509_10757_gb300.batch import PackedBatch, run_search_last, run_stereo
+    frames = [scenes.single_pinhole(30), scenes.fisheye_frame(31)]
+    lasts = [scenes.last_frame(fr, 32 + i, motion) for i, fr in enumerate(frames)]
+    pb = PackedBatch(frames, lasts=lasts)
+    pb.upload()
+    pb.clear_outputs()
+    for f in range(len(frames)):
+        run_stereo(ctx, pb, f)
+        run_search_last(ctx, pb, f)
+    pb.download()
+    assert ctx.sync_status() == 0
+    for f, fr in enumerate(frames):
+        st = orc.stereo_frame(_oracle_params(), fr)
+        ref = _check_last(pb, f, st, f"last-frame {motion} frame {f}: ")
+        key = "mp_kp" if fr.camera == "pinhole" else "mp_kp_l"
+        assert (ref[key] >= 0).sum() > 100
+
+
+def test_last_frame_search_batched_with_local_map_frames(ctx, lib):
+    # a batch mixing frames that search their local map with frames that
+    # search their last frame's points (stereo first in both)
+    frames = scenes.pinhole_batch(seed=3, n_frames=6) + [scenes.fisheye_frame(33), scenes.fisheye_frame(34)]
+    motions = ["forward", None, "backward", "none", None, "forward", "backward", None]
+    lasts = [None if mo is None else scenes.last_frame(fr, 40 + i, mo)
+             for i, (fr, mo) in enumerate(zip(frames, motions))]
+    from paper_2509_10757_gb300.batch import PackedBatch, run_batch
+    pb = PackedBatch(frames, lasts=lasts)
+    pb.upload()
+    pb.clear_outputs()
+    run_batch(ctx, pb)
+    pb.download()
+    assert ctx.sync_status() == 0
+    for f, fr in enumerate(frames):
+        st = orc.stereo_frame(_oracle_params(), fr)
+        if fr.camera == "pinhole":
+            assert_stereo_equal(pb.outputs(f), st, f"frame {f}: ")
+        else:
+            assert_fisheye_equal(pb.outputs(f), st, f"frame {f}: ")
+        if lasts[f] is None:
+            check_frame(pb, f, what="mixed batch")
+        else:
+            _check_last(pb, f, st, f"mixed batch frame {f}: ")
+
+
+def test_last_frame_search_edge_cases(ctx, lib):
+    from paper_2509_10757_gb300.batch import PackedBatch, run_search_last, run_stereo
+    fr = scenes.single_pinhole(35)
+    empty = scenes.last_frame(fr, 36, "none", n=0)
+    bad = scenes.last_frame(fr, 37, "forward", n=50)
+    bad.oct[:] = np.int8(-1)
+    bad.oct[::7] = np.int8(8)
+    for last in (empty, bad):
+        pb = PackedBatch([fr], lasts=[last])
+        pb.upload()
+        pb.clear_outputs()
+        run_stereo(ctx, pb, 0)
+        run_search_last(ctx, pb, 0)
+        pb.download()
+        assert ctx.sync_status() == 0
+        st = orc.stereo_frame(_oracle_params(), fr)
+        ref = _check_last(pb, 0, st, "edge: ")
+        assert np.all(ref["level"] == -1)
