@@ -40,6 +40,10 @@ L2_FLUSH_BYTES = 256 << 20
 PATCH_BYTES = 121 + 231          # left 11x11 patch + right 11x21 strip per refined match
 KP_BYTES = 4 + 4 + 1 + 32        # x, y, octave, descriptor
 MP_BYTES = 16 + 16 + 32 + 1      # pos+dmin, normal+dmax, descriptor, skip flag
+LAST_BYTES = 16 + 32 + 1 + 1     # last-frame point: pos, descriptor, octave, skip flag
+STEREO_OUT_BYTES = 6 * 4         # best_r, dist, sad_shift, sad_best, u_right, depth
+FISHEYE_OUT_BYTES = 3 * 4 + 4 + 16   # r_idx, d1, d2, depth, point
+SEARCH_OUT_BYTES = 1 + 16 + 3 * 4    # level, projection, mp_kp, mp_d1, mp_d2 (+4 B kp_mp per keypoint)
 
 
 # ---------------------------------------------------------------- distributed helpers
@@ -175,14 +179,24 @@ def profiled_traffic() -> float | None:
 
 def algorithmic_bytes(pb) -> int:
     """Bytes the fused launch must move at minimum: every keypoint record,
-    taken flag and map record once, one left patch + right strip per refined
-    match, and every output once."""
-    total = pb.out_bytes
+    taken flag and searched point record once, one left patch + right strip
+    per refined match, and every output it writes once."""
+    total = 0
     for f, fr in enumerate(pb.frames):
         out = pb.outputs(f)
-        total += KP_BYTES * (fr.left.n + fr.right.n) + fr.left.n + MP_BYTES * fr.map.n
+        last = pb.lasts[f]
+        nl, nr = fr.left.n, fr.right.n
+        total += KP_BYTES * (nl + nr) + nl
         if fr.camera == "pinhole":
             total += PATCH_BYTES * int(np.count_nonzero(out["sad_shift"] != -128))
+            total += STEREO_OUT_BYTES * nl
+            cams = (nl,)
+        else:
+            total += nr + FISHEYE_OUT_BYTES * nl
+            cams = (nl, nr)
+        m = fr.map.n if last is None else last.n
+        total += (MP_BYTES if last is None else LAST_BYTES) * m
+        total += sum(SEARCH_OUT_BYTES * m + 4 * nk for nk in cams)
     return total
 
 
@@ -458,7 +472,7 @@ def fisheye_pairs(frames) -> int:
     return n
 
 
-def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_bytes: int) -> dict:
+def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_bytes: int, lasts=None) -> dict:
     """One fused launch per step over `frames` (graph replay, autotuned tiles,
     L2 flushed between steps): launch time, throughput and the HBM roofline."""
     import ctypes as C
@@ -468,7 +482,7 @@ def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_byte
     from paper_2509_10757_gb300 import _lib as L
     from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch, stream_handle
 
-    pb = PackedBatch(frames, device=dev)
+    pb = PackedBatch(frames, device=dev, lasts=lasts)
     pb.upload()
     ctx = Context(device=local_rank, arena_bytes=arena_bytes, max_frames=max(len(frames), 1), use_graphs=True)
     stream = torch.cuda.Stream(device=dev)
@@ -495,6 +509,8 @@ def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_byte
     pb.download()
     alg = algorithmic_bytes(pb)
     kp, mp = units_of(frames)
+    if lasts is not None:
+        mp = sum(l.n if l is not None else fr.map.n for fr, l in zip(frames, lasts))
     mean_s = statistics.mean(ms) / 1e3
     peaks = measured_peaks()
     out = {"frames": len(frames), "ms_per_launch": mean_s * 1e3,
@@ -570,6 +586,16 @@ def run_configs(args, local_rank):
                      "peak_source": "152 SMs x 16 popcounts/clk x 2070 MHz"}
     lines.append({"workload": "fisheye batch: 32 frames 512x512 KB8, 1500 keypoints (60% overlap), "
                               "6000 map points", **r})
+
+    # the batched workload with each frame searching its last frame's points
+    # (stereo first; the search of the paper's initial pose estimation)
+    frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
+    lasts = [scenes.last_frame(fr, 900 + i, ("forward", "backward", "none")[i % 3]) for i, fr in enumerate(frames)]
+    r = time_batch(frames, steps=max(50, min(args.steps, 1000)), warmup=max(3, args.warmup), dev=dev,
+                   local_rank=local_rank, arena_bytes=512 << 20, lasts=lasts)
+    lines.append({"workload": "batched pinhole, last-frame search: 64 frames 752x480, stereo then the search "
+                              "of the last frame's points (2000-5000 per frame, motions forward/backward/none)",
+                  **r})
 
     # 1080p stress: batch sweep (16 distinct frames, repeated to fill a batch)
     base = scenes.stress_batch(seed=0, n_frames=16)
