@@ -99,9 +99,9 @@ typedef struct {
 } ft_keypoints;
 
 /* Image pyramid: level l is width[l] x height[l] uint8 with row pitch[l]
- * bytes (pitch >= width).  Every level pointer must be 4-byte aligned and
- * every pitch a multiple of 4 (rows are read as 32-bit words; FT_EALIGN
- * otherwise). */
+ * bytes (pitch >= width).  Every level pointer must be 16-byte aligned and
+ * every pitch a multiple of 16 (patch rows are copied in 16-byte chunks;
+ * FT_EALIGN otherwise). */
 typedef struct {
     int nlevels;
     const uint8_t *data[FT_MAX_LEVELS];

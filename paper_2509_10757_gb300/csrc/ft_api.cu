@@ -198,8 +198,8 @@ ft_status check_pyramid(const ft_pyramid &p, int nlevels, const char *what)
         if (p.width[l] <= 0 || p.height[l] <= 0 || p.pitch[l] < p.width[l])
             return fail(FT_EINVAL, "%s: level %d has bad size %dx%d pitch %d", what, l, p.width[l],
                         p.height[l], p.pitch[l]);
-        if ((reinterpret_cast<uintptr_t>(p.data[l]) & 3u) || (p.pitch[l] & 3))
-            return fail(FT_EALIGN, "%s: level %d needs a 4-byte aligned pointer and pitch (pitch %d)", what, l,
+        if ((reinterpret_cast<uintptr_t>(p.data[l]) & 15u) || (p.pitch[l] & 15))
+            return fail(FT_EALIGN, "%s: level %d needs a 16-byte aligned pointer and pitch (pitch %d)", what, l,
                         p.pitch[l]);
     }
     return FT_OK;

@@ -173,15 +173,15 @@ struct RefineJob {
 
 constexpr int kGroup = 4;                       // lanes per left keypoint in the Hamming phase
 constexpr int kGroups = kThreads / kGroup;      // left keypoints in flight per CTA
-constexpr int kSadChunk = 64;                   // matches refined per round
-constexpr int kWordsL = 4;                      // 32-bit words holding a left patch row (11 bytes)
-constexpr int kWordsR = 6;                      // words holding a right strip row (21 bytes)
+constexpr int kSadChunk = 32;                   // matches refined per round
+constexpr int kChunksL = 2;                     // 16-byte chunks holding a left patch row (11 bytes)
+constexpr int kChunksR = 3;                     // chunks holding a right strip row (21 bytes)
 
-// patches of one refinement round as the raw 32-bit words of their rows
-// (copied asynchronously; the bytes start at offset (column & 3))
+// patches of one refinement round as the raw 16-byte chunks of their rows
+// (copied asynchronously; a row's bytes start at offset (column & 15))
 struct PatchBuf {
-    unsigned l[kSadChunk][2 * kW + 1][kWordsL];
-    unsigned r[kSadChunk][2 * kW + 1][kWordsR];
+    uint4 l[kSadChunk][2 * kW + 1][kChunksL];
+    uint4 r[kSadChunk][2 * kW + 1][kChunksR];
 };
 // left keypoints of a pass (Hamming phase)
 struct LeftBuf {
@@ -687,33 +687,29 @@ __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &
     const int tid = threadIdx.x;
     constexpr int kRows = 2 * kW + 1;
     for (int q = tid; q < nc * kShifts; q += kThreads) S.sad[q / kShifts][q % kShifts] = 0;
-    // asynchronous copies of the 32-bit words holding every patch row; a
-    // match has ten word slots (four of a left row, six of a right row) and
-    // one thread per slot walks the 11 rows, so that consecutive lanes copy
-    // consecutive words and one warp copy touches few cache lines.  Level
-    // pointers and pitches are 4-byte aligned (checked on the host): a row's
-    // words start at its column rounded down to a multiple of 4 and never
-    // leave the level image.  One memory latency for the whole round.
-    constexpr int kSlots = kWordsL + kWordsR;
+    // asynchronous copies of the 16-byte chunks holding every patch row; a
+    // match has five chunk slots (two of a left row, three of a right row)
+    // and one thread per slot walks the 11 rows.  Level pointers and pitches
+    // are 16-byte aligned (checked on the host): a row's chunks start at its
+    // column rounded down to a multiple of 16 and end within the row's pitch.
+    constexpr int kSlots = kChunksL + kChunksR;
     for (int q = tid; q < nc * kSlots; q += kThreads) {
         const int mm = q / kSlots, w = q - mm * kSlots;
-        const bool right = w >= kWordsL;
-        const int k = right ? w - kWordsL : w;
+        const bool right = w >= kChunksL;
+        const int k = right ? w - kChunksL : w;
         const RefineJob &J = S.ref[r0 + mm];
         const int col = right ? J.ur0 - kL - kW : J.ul - kW;
         const int len = right ? kStripW : 2 * kW + 1;
-        if (k > (((col & 3) + len - 1) >> 2)) continue;     // the word holds none of the row's bytes
+        if (k > (((col & 15) + len - 1) >> 4)) continue;    // the chunk holds none of the row's bytes
         const int pitch = right ? F.rp[J.l] : F.lp[J.l];
-        const uint8_t *row0 = (right ? F.pyrR[J.l] : F.pyrL[J.l]) + (size_t)(J.vl - kW) * pitch;
-        const unsigned *src = reinterpret_cast<const unsigned *>(row0) + (col >> 2) + k;
+        const uint8_t *src = (right ? F.pyrR[J.l] : F.pyrL[J.l]) + (size_t)(J.vl - kW) * pitch + (col & ~15) + 16 * k;
         const unsigned dst = (unsigned)__cvta_generic_to_shared(right ? &S.u.patch.r[mm][0][k]
                                                                        : &S.u.patch.l[mm][0][k]);
-        const unsigned dstep = 4u * (right ? kWordsR : kWordsL);
-        const int sstep = pitch >> 2;
+        const unsigned dstep = 16u * (right ? kChunksR : kChunksL);
 #pragma unroll
         for (int row = 0; row < kRows; ++row)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + row * dstep),
-                         "l"(src + (size_t)row * sstep)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + row * dstep),
+                         "l"(src + (size_t)row * pitch)
                          : "memory");
     }
     // the grid record of each match (the search reads the right coordinate there)
@@ -727,21 +723,24 @@ __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &
     for (int q = tid; q < nc * kRows; q += kThreads) {
         const int dy = q / nc, m = q - dy * nc;
         const RefineJob &J = S.ref[r0 + m];
-        const int offl = 8 * ((J.ul - kW) & 3), offr = 8 * ((J.ur0 - kL - kW) & 3);
-        const unsigned *ql = S.u.patch.l[m][dy];
-        const unsigned *qr = S.u.patch.r[m][dy];
-        const unsigned *qc = S.u.patch.r[m][kW];
+        const int ol = (J.ul - kW) & 15, orr = (J.ur0 - kL - kW) & 15;
+        // the rows as 32-bit words; byte b of a row is byte (o + b) of its chunks
+        const unsigned *ql = reinterpret_cast<const unsigned *>(S.u.patch.l[m][dy]) + (ol >> 2);
+        const unsigned *qr = reinterpret_cast<const unsigned *>(S.u.patch.r[m][dy]) + (orr >> 2);
+        const unsigned *qc = reinterpret_cast<const unsigned *>(S.u.patch.r[m][kW]) + (orr >> 2);
+        const unsigned *qlc = reinterpret_cast<const unsigned *>(S.u.patch.l[m][kW]) + (ol >> 2);
+        const int sl = 8 * (ol & 3), sr = 8 * (orr & 3);
         // realigned words: byte b of the row is byte b & 3 of word b >> 2
         unsigned wl[3], wr[6], wc[4];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) wl[k] = __funnelshift_r(ql[k], ql[k + 1], offl);
+        for (int k = 0; k < 3; ++k) wl[k] = __funnelshift_r(ql[k], ql[k + 1], sl);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) wr[k] = __funnelshift_r(qr[k], k + 1 < kWordsR ? qr[k + 1] : 0u, offr);
+        for (int k = 0; k < 6; ++k) wr[k] = __funnelshift_r(qr[k], qr[k + 1], sr);
 #pragma unroll
-        for (int k = 1; k < 4; ++k) wc[k] = __funnelshift_r(qc[k], k + 1 < kWordsR ? qc[k + 1] : 0u, offr);
+        for (int k = 1; k < 4; ++k) wc[k] = __funnelshift_r(qc[k], qc[k + 1], sr);
         // left row minus the left centre, right row, and the centres of the
         // 11 right patches (bytes 5..15 of the right centre row)
-        const int cl = (int)((__funnelshift_r(S.u.patch.l[m][kW][1], S.u.patch.l[m][kW][2], offl) >> 8) & 0xff);
+        const int cl = (int)((__funnelshift_r(qlc[1], qlc[2], sl) >> 8) & 0xff);
         int lc[2 * kW + 1], rv[kStripW], cr[kShifts];
 #pragma unroll
         for (int b = 0; b < 2 * kW + 1; ++b) lc[b] = (int)((wl[b >> 2] >> (8 * (b & 3))) & 0xff) - cl;

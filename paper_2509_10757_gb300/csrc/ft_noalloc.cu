@@ -125,8 +125,8 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
         for (int l = 0; l < p.nlevels; ++l)
             if (!py->data[l] || py->width[l] <= 0 || py->height[l] <= 0 || py->pitch[l] < py->width[l])
                 return fail(FT_EINVAL, "pyramid level %d is missing or has a bad size", l);
-            else if ((reinterpret_cast<uintptr_t>(py->data[l]) & 3u) || (py->pitch[l] & 3))
-                return fail(FT_EALIGN, "pyramid level %d needs a 4-byte aligned pointer and pitch", l);
+            else if ((reinterpret_cast<uintptr_t>(py->data[l]) & 15u) || (py->pitch[l] & 15))
+                return fail(FT_EALIGN, "pyramid level %d needs a 16-byte aligned pointer and pitch", l);
     }
     if (L.n > 0 && (!out->best_r || !out->dist || !out->sad_shift || !out->sad_best || !out->u_right || !out->depth))
         return fail(FT_EINVAL, "NULL output array");

@@ -376,8 +376,9 @@ def test_host_checks_reject_bad_arguments(ctx, lib):
     assert "level 3" in lib.last_error()
     st.pyr_left.data[3] = pb.pin_(0, "pyrL3")
     pitch = st.pyr_left.pitch[2]
-    st.pyr_left.pitch[2] = pitch + 1                 # rows must be 4-byte aligned
-    assert call() == lib.FT_EALIGN
+    for bad in (pitch + 1, pitch + 4):               # rows must be 16-byte aligned
+        st.pyr_left.pitch[2] = bad
+        assert call() == lib.FT_EALIGN
     st.pyr_left.pitch[2] = pitch
     assert call() == lib.FT_OK
     assert ctx.sync_status() == 0
