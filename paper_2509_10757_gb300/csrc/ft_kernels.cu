@@ -223,9 +223,10 @@ struct SmemFish {
 constexpr int kMedianSmem = 8192;               // left keypoints whose SADs the median keeps on chip
 
 struct SmemMedian {
-    int hist[256];
+    int hist[256], hist2[256];          // high bytes; low bytes within the median's high byte
     int count, bin, before;
     int vals[kMedianSmem];
+    int gp[kMedianSmem];               // grid record of each left keypoint (searched frames)
 };
 
 constexpr int kSearchStage = 1536;              // keypoints of one camera the search keeps on chip
@@ -828,23 +829,28 @@ __device__ __forceinline__ int median_value(const FrameDev &F, const SmemMedian 
     return on_chip ? M.vals[i] : __ldcg(F.sad_best + i);
 }
 
-__device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedian &M, int *s_flag)
+__device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedian &M, bool grid_ok)
 {
     const DevParams &P = B.p;
     const int tid = threadIdx.x;
     // a search in this launch reads the final right coordinates from the
-    // grid records: a rejected match takes its coordinate back there too
-    const bool rec = F.wait_stereo && F.u_right_in != nullptr &&
-                     wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
+    // grid records (the strip waited for the grid step): a rejected match
+    // takes its coordinate back there too
+    const bool rec = F.wait_stereo && F.u_right_in != nullptr && grid_ok;
     const bool on_chip = F.nl <= kMedianSmem;
-    if (on_chip)
-        for (int i = tid; i < F.nl; i += kThreads) M.vals[i] = __ldcg(F.sad_best + i);
-    for (int b = tid; b < 256; b += kThreads) M.hist[b] = 0;
+    for (int b = tid; b < 256; b += kThreads) M.hist[b] = M.hist2[b] = 0;
     if (tid == 0) M.count = 0;
     __syncthreads();
+    // one pass over the values (kept on chip with each keypoint's grid
+    // record when they fit): the count and the histogram of the high bytes
     int local = 0;
+#pragma unroll 4
     for (int i = tid; i < F.nl; i += kThreads) {
-        const int x = median_value(F, M, on_chip, i);
+        const int x = __ldcg(F.sad_best + i);
+        if (on_chip) {
+            M.vals[i] = x;
+            if (rec) M.gp[i] = __ldcg(F.cam[0].gpos + i);
+        }
         if (x >= 0) {
             atomicAdd(&M.hist[(x >> 8) & 255], 1);
             ++local;
@@ -860,15 +866,12 @@ __device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedia
     __syncthreads();
     const int hi = M.bin;
     const int k2 = k - M.before;
-    __syncthreads();
-    for (int b = tid; b < 256; b += kThreads) M.hist[b] = 0;
-    __syncthreads();
     for (int i = tid; i < F.nl; i += kThreads) {
         const int x = median_value(F, M, on_chip, i);
-        if (x >= 0 && ((x >> 8) & 255) == hi) atomicAdd(&M.hist[x & 255], 1);
+        if (x >= 0 && ((x >> 8) & 255) == hi) atomicAdd(&M.hist2[x & 255], 1);
     }
     __syncthreads();
-    if (tid < 32) select_bin(M.hist, k2, &M.bin, &M.before);
+    if (tid < 32) select_bin(M.hist2, k2, &M.bin, &M.before);
     __syncthreads();
     const int median = (hi << 8) | M.bin;
     const float th = fmul(P.median_factor, (float)median);
@@ -880,7 +883,7 @@ __device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedia
             F.u_right[i] = -1.0f;
             F.depth[i] = -1.0f;
             if (rec) {
-                const int pos = __ldcg(C.gpos + i);
+                const int pos = on_chip ? M.gp[i] : __ldcg(C.gpos + i);
                 if (pos >= 0) reinterpret_cast<float *>(C.gkp + pos)[3] = -1.0f;
             }
         }
@@ -896,8 +899,9 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     // a search in this launch reads each refined match's right coordinate
     // from the grid record, written here once the grid step is done
     const bool rec = F.wait_stereo && F.u_right_in != nullptr;
-    if (wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag, rec ? &F.ctr[C_GRID_DONE] : nullptr,
-                 (unsigned)F.n_grid_items)) {
+    const bool ready = wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag, rec ? &F.ctr[C_GRID_DONE] : nullptr,
+                                (unsigned)F.n_grid_items);
+    if (ready) {
         const int H = F.H;
         const int r_lo = strip * F.strip_rows;
         const int r_hi = min(H, r_lo + F.strip_rows);
@@ -973,7 +977,7 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
         }
     }
     if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
-        median_reject(B, F, U.m, s_flag);
+        median_reject(B, F, U.m, ready);
         __threadfence();
         __syncthreads();
         mark(B, 3);
