@@ -173,7 +173,7 @@ struct RefineJob {
 
 constexpr int kGroup = 4;                       // lanes per left keypoint in the Hamming phase
 constexpr int kGroups = kThreads / kGroup;      // left keypoints in flight per CTA
-constexpr int kSadChunk = 32;                   // matches refined per round
+constexpr int kSadChunk = 64;                   // matches refined per round
 constexpr int kChunksL = 2;                     // 16-byte chunks holding a left patch row (11 bytes)
 constexpr int kChunksR = 3;                     // chunks holding a right strip row (21 bytes)
 
@@ -189,12 +189,18 @@ struct LeftBuf {
     uint4 ldesc[2 * kThreads];
 };
 
-struct SmemStereo {
+// what the Hamming phase reads: the staged right window and the pass's left
+// keypoints
+struct StageBuf {
     float4 rkp[kStageCap];             // staged right keypoints sorted by (octave, row)
-    uint4 sdesc[2 * kStageCap];
-    union {                            // the pass's left keypoints are dead once the
-        LeftBuf left;                  // Hamming phase is over; the patches reuse them
-        PatchBuf patch;
+    uint4 sdesc[2 * kStageCap];        // their descriptors in row order
+    LeftBuf left;
+};
+
+struct SmemStereo {
+    union {                            // the window and the left keypoints are dead once
+        StageBuf st;                   // the Hamming phase is over; the patches reuse them
+        PatchBuf patch;                // (a strip with a second pass stages its window again)
     } u;
     RefineJob ref[kThreads];
     int gp[kSadChunk];                 // grid record of each match of the round (-1: none)
@@ -572,7 +578,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
         float xi = 0.0f, yi = 0.0f;
         int oi = 0, i = 0;
         if (have) {
-            const float4 L = S.u.left.lkp[t];
+            const float4 L = S.u.st.left.lkp[t];
             xi = L.x;
             yi = L.y;
             i = __float_as_int(L.z);
@@ -581,7 +587,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
             const float minU = fsub(xi, maxD);
             const float maxU = fsub(xi, 0.0f);
             if (!(yi < 0.0f) && row < F.H && !(maxU < 0.0f)) {
-                const uint4 a0 = S.u.left.ldesc[2 * t], a1 = S.u.left.ldesc[2 * t + 1];
+                const uint4 a0 = S.u.st.left.ldesc[2 * t], a1 = S.u.st.left.ldesc[2 * t + 1];
                 if (staged) {
                     // candidate octaves oi-1 .. oi+1, each over the rows its band can reach
                     const int olo = max(oi - 1, 0), ohi = min(oi + 1, kOctBuckets - 1);
@@ -591,13 +597,13 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                         const int rb = min(row + h, w_a + nrows - 1) - w_a;
                         const int e1 = S.bptr[o * nrows + rb + 1];
                         for (int e = S.bptr[o * nrows + ra] + sub; e < e1; e += kGroup) {
-                            const float4 g = S.rkp[e];
+                            const float4 g = S.u.st.rkp[e];
                             const int oj = rec_octave(g.w);
                             if (oj < oi - 1 || oj > oi + 1) continue;
                             if (!band_has(g.y, row)) continue;
                             if (g.x < minU || g.x > maxU) continue;
                             const int at = __float_as_int(g.z);
-                            const unsigned k = ((unsigned)ham8(a0, a1, S.sdesc[2 * at], S.sdesc[2 * at + 1]) << 20) |
+                            const unsigned k = ((unsigned)ham8(a0, a1, S.u.st.sdesc[2 * at], S.u.st.sdesc[2 * at + 1]) << 20) |
                                                (unsigned)rec_index(g.w);
                             if (k < key) {
                                 key = k;
@@ -890,6 +896,43 @@ __device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedia
     }
 }
 
+// Stage the row-sorted right keypoints of window rows [w_a, w_a + nrows)
+// in shared memory, re-bucketed by (octave, row) so that a left keypoint
+// visits only its octaves; their descriptors keep row order (a staged record
+// carries its row-order position) and arrive by asynchronous copies that the
+// caller waits for.
+__device__ __forceinline__ void stage_window(const FrameDev &F, SmemStereo &S, int w_a, int nrows, int e_base,
+                                             int n_st)
+{
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 2 * n_st; e += kThreads) cp_async16(&S.u.st.sdesc[e], F.rs_desc + 2 * e_base + e);
+    constexpr int Q = kStageCap / kThreads;
+    const int nb = kOctBuckets * nrows;
+    for (int b = tid; b <= nb; b += kThreads) S.bptr[b] = 0;
+    __syncthreads();
+    float4 g[Q];
+    int bucket[Q], rank[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int e = q * kThreads + tid;
+        if (e < n_st) {
+            g[q] = __ldcg(F.rs_kp + e_base + e);
+            bucket[q] = clampi(rec_octave(g[q].w), 0, kOctBuckets - 1) * nrows + (__float_as_int(g[q].z) - w_a);
+            rank[q] = atomicAdd(&S.bptr[bucket[q]], 1);
+        }
+    }
+    __syncthreads();
+    block_scan(S.bptr, S.bptr, nb + 1, S.warp_sums);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int e = q * kThreads + tid;
+        if (e < n_st) {
+            g[q].z = __int_as_float(e);          // row-order position: its descriptor
+            S.u.st.rkp[S.bptr[bucket[q]] + rank[q]] = g[q];
+        }
+    }
+}
+
 __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int strip, Smem &U,
                                     int *s_flag)
 {
@@ -905,8 +948,7 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
         const int H = F.H;
         const int r_lo = strip * F.strip_rows;
         const int r_hi = min(H, r_lo + F.strip_rows);
-        // stage the row-sorted right keypoints of rows [w_a, w_b], re-bucketed
-        // by (octave, row) so that a left keypoint visits only its octaves
+        // the window of right keypoint rows [w_a, w_b] the strip's bands can reach
         const int w_a = max(r_lo - P.halo, 0);
         const int w_b = min(r_hi - 1 + P.halo, H - 1);
         const int nrows = w_b - w_a + 1;
@@ -915,57 +957,21 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
         const int l_lo = __ldcg(F.row_ptr_l + r_lo), l_hi = __ldcg(F.row_ptr_l + r_hi);
         const int n_st = e_end - e_base;
         const bool staged = n_st <= kStageCap && nrows <= kWinRows && P.nlevels <= kOctBuckets;
-        // asynchronous copies, in flight during the bucketing below: the first
-        // pass's left keypoints and (staged) the window's right descriptors in
-        // row order (a staged record keeps its row-order position)
-        if (tid < min(kThreads, l_hi - l_lo)) {
-            cp_async16(&S.u.left.lkp[tid], F.ls_kp + l_lo + tid);
-            cp_async16(&S.u.left.ldesc[2 * tid], F.ls_desc + 2 * (l_lo + tid));
-            cp_async16(&S.u.left.ldesc[2 * tid + 1], F.ls_desc + 2 * (l_lo + tid) + 1);
-        }
-        if (staged)
-            for (int e = tid; e < 2 * n_st; e += kThreads) cp_async16(&S.sdesc[e], F.rs_desc + 2 * e_base + e);
-        if (staged) {
-            constexpr int Q = kStageCap / kThreads;
-            const int nb = kOctBuckets * nrows;
-            for (int b = tid; b <= nb; b += kThreads) S.bptr[b] = 0;
-            __syncthreads();
-            float4 g[Q];
-            int bucket[Q], rank[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int e = q * kThreads + tid;
-                if (e < n_st) {
-                    g[q] = __ldcg(F.rs_kp + e_base + e);
-                    bucket[q] = clampi(rec_octave(g[q].w), 0, kOctBuckets - 1) * nrows +
-                                (__float_as_int(g[q].z) - w_a);
-                    rank[q] = atomicAdd(&S.bptr[bucket[q]], 1);
-                }
-            }
-            __syncthreads();
-            block_scan(S.bptr, S.bptr, nb + 1, S.warp_sums);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int e = q * kThreads + tid;
-                if (e < n_st) {
-                    g[q].z = __int_as_float(e);          // row-order position: its descriptor
-                    S.rkp[S.bptr[bucket[q]] + rank[q]] = g[q];
-                }
-            }
-        }
         if (tid == 0) S.nref = 0;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        mark(B, 0);
         for (int pass = l_lo; pass < l_hi; pass += kThreads) {
-            // the pass's left keypoints, one thread each, into shared memory
-            // (the first pass's are already there)
+            // the pass's left keypoints arrive by asynchronous copies while the
+            // window is staged (again for a later pass: the previous pass's
+            // patches overwrote it)
             const int npass = min(kThreads, l_hi - pass);
-            if (pass != l_lo && tid < npass) {
-                S.u.left.lkp[tid] = __ldcg(F.ls_kp + pass + tid);
-                S.u.left.ldesc[2 * tid] = __ldcg(F.ls_desc + 2 * (pass + tid));
-                S.u.left.ldesc[2 * tid + 1] = __ldcg(F.ls_desc + 2 * (pass + tid) + 1);
+            if (tid < npass) {
+                cp_async16(&S.u.st.left.lkp[tid], F.ls_kp + pass + tid);
+                cp_async16(&S.u.st.left.ldesc[2 * tid], F.ls_desc + 2 * (pass + tid));
+                cp_async16(&S.u.st.left.ldesc[2 * tid + 1], F.ls_desc + 2 * (pass + tid) + 1);
             }
+            if (staged) stage_window(F, S, w_a, nrows, e_base, n_st);
+            asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
+            mark(B, 0);
             hamming_phase(P, F, S, npass, staged, w_a, nrows, e_base);
             __syncthreads();
             mark(B, 1);
