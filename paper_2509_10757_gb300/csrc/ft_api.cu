@@ -451,7 +451,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 }
                 F.strip_rows = sr;
                 n_stereo = (F.H + sr - 1) / sr;
-                F.rowsort = 2;
+                F.rowsort = kRowSortItems;
                 F.row_ptr_l = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
                 F.row_ptr_r = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)(F.H + 1)));
                 F.ls_kp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)F.nl));

@@ -210,8 +210,11 @@ struct SmemStereo {
     int nref;
 };
 
+constexpr int kSortParts = kRowSortItems / 2;   // work items per side of a frame's row sort
+
 struct SmemRows {
-    int cnt[kMaxRows + 1];
+    int cnt[kSortParts][kMaxRows + 1];  // per-part row counts, then this part's write cursors
+    int tot[kMaxRows + 1];              // row totals, then row starts
     int warp_sums[kWarps];
 };
 
@@ -423,118 +426,107 @@ __device__ __forceinline__ int own_row(float y, int H)
 }
 
 // Right keypoints are bucketed by floor(y) clamped to the image, left
-// keypoints by the row they search, (int)y clamped to the image.  The two
-// sorts are separate work items so they run side by side.
-__device__ void rowsort_right_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
+// keypoints by the row they search, (int)y clamped to the image.  Each side's
+// sort is split over kSortParts work items that run side by side: every part
+// counts all keypoints per row and per part, and scatters only its own
+// contiguous share, starting each row after the parts before it.
+__device__ __forceinline__ int sort_row(bool right, float y, int H)
 {
-    const int tid = threadIdx.x, H = F.H;
-    for (int r = tid; r <= H; r += kThreads) S.cnt[r] = 0;
-    __syncthreads();
-    for (int base = 0; base < F.nr; base += kBatch * kThreads) {
-        float y[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int j = base + u * kThreads + tid;
-            y[u] = j < F.nr ? __ldg(F.ry + j) : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (base + u * kThreads + tid < F.nr) atomicAdd(&S.cnt[clampi(floor_row(y[u]), 0, H - 1)], 1);
-    }
-    __syncthreads();
-    mark(B, 0);
-    const int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
-    for (int r = tid; r < H; r += kThreads) F.row_ptr_r[r] = S.cnt[r];
-    if (tid == 0) F.row_ptr_r[H] = total;
-    __syncthreads();
-    mark(B, 1);
-    for (int base = 0; base < F.nr; base += kScatter * kThreads) {
-        float x[kScatter], y[kScatter];
-        int oct[kScatter];
-        uint4 d0[kScatter], d1[kScatter];
-#pragma unroll
-        for (int u = 0; u < kScatter; ++u) {
-            const int j = min(base + u * kThreads + tid, F.nr - 1);
-            x[u] = __ldg(F.rx + j);
-            y[u] = __ldg(F.ry + j);
-            oct[u] = __ldg(F.roct + j);
-            d0[u] = __ldg(F.rdesc + 2 * j);
-            d1[u] = __ldg(F.rdesc + 2 * j + 1);
-        }
-#pragma unroll
-        for (int u = 0; u < kScatter; ++u) {
-            const int j = base + u * kThreads + tid;
-            if (j >= F.nr) continue;
-            const int row = clampi(floor_row(y[u]), 0, H - 1);
-            const int pos = atomicAdd(&S.cnt[row], 1);
-            // the rows this keypoint lists: floor(y - r) .. ceil(y + r), r = 2 scale[oct],
-            // clamped to the image (computed once here, tested per candidate later;
-            // an empty band stays empty: lo in [0, H], hi in [-1, H - 1])
-            const float r = B.p.band_r[clampi(oct[u], 0, B.p.nlevels - 1)];
-            const int lo = min(max(f2i(floorf(fsub(y[u], r))), 0), H);
-            const int hi = max(min(f2i(ceilf(fadd(y[u], r))), H - 1), -1);
-            F.rs_kp[pos] = make_float4(x[u], __int_as_float(lo | (hi << 16)), __int_as_float(row),
-                                       __int_as_float(j | ((oct[u] & 0xff) << 20)));
-            F.rs_desc[2 * pos] = d0[u];
-            F.rs_desc[2 * pos + 1] = d1[u];
-        }
-    }
-    mark(B, 2);
-    signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
-    mark(B, 3);
+    return right ? clampi(floor_row(y), 0, H - 1) : own_row(y, H);
 }
 
-__device__ void rowsort_left_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, int *s_flag)
+__device__ void rowsort_item(const BatchHeader &B, const FrameDev &F, SmemRows &S, bool right, int part,
+                             int *s_flag)
 {
     const int tid = threadIdx.x, H = F.H;
-    for (int r = tid; r <= H; r += kThreads) S.cnt[r] = 0;
+    const int n = right ? F.nr : F.nl;
+    const float *ys = right ? F.ry : F.ly;
+    const int share = (n + kSortParts - 1) / kSortParts;
+    for (int r = tid; r <= H; r += kThreads)
+        for (int p = 0; p < kSortParts; ++p) S.cnt[p][r] = 0;
     __syncthreads();
-    for (int base = 0; base < F.nl; base += kBatch * kThreads) {
+    for (int base = 0; base < n; base += kBatch * kThreads) {
         float y[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int i = base + u * kThreads + tid;
-            y[u] = i < F.nl ? __ldg(F.ly + i) : 0.0f;
+            y[u] = i < n ? __ldg(ys + i) : 0.0f;
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (base + u * kThreads + tid < F.nl) atomicAdd(&S.cnt[own_row(y[u], H)], 1);
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = base + u * kThreads + tid;
+            if (i < n) atomicAdd(&S.cnt[i / share][sort_row(right, y[u], H)], 1);
+        }
     }
     __syncthreads();
     mark(B, 0);
-    const int total = block_scan(S.cnt, S.cnt, H, S.warp_sums);
-    for (int r = tid; r < H; r += kThreads) F.row_ptr_l[r] = S.cnt[r];
-    if (tid == 0) F.row_ptr_l[H] = total;
+    for (int r = tid; r < H; r += kThreads) {
+        int t = 0;
+        for (int p = 0; p < kSortParts; ++p) t += S.cnt[p][r];
+        S.tot[r] = t;
+    }
+    __syncthreads();
+    const int total = block_scan(S.tot, S.tot, H, S.warp_sums);
+    // this part's write cursor per row: the row's start plus the earlier parts' counts
+    for (int r = tid; r < H; r += kThreads) {
+        int c = S.tot[r];
+        for (int p = 0; p < part; ++p) c += S.cnt[p][r];
+        S.cnt[part][r] = c;
+    }
+    if (part == 0) {
+        int *row_ptr = right ? F.row_ptr_r : F.row_ptr_l;
+        for (int r = tid; r < H; r += kThreads) row_ptr[r] = S.tot[r];
+        if (tid == 0) row_ptr[H] = total;
+    }
     __syncthreads();
     mark(B, 1);
-    // a row-ordered copy of the keypoints and their descriptors, so that the
-    // stereo strips read their left keypoints contiguously (all loads of a
-    // batch are issued before its shared-memory atomics)
-    for (int base = 0; base < F.nl; base += kScatter * kThreads) {
+    // the part's share: records (right: x, band rows, row, index | octave;
+    // left: x, y, index, octave) and descriptors in row order, so that the
+    // stereo strips read them contiguously (all loads of a batch are issued
+    // before its shared-memory atomics)
+    const int i0 = part * share, i1 = min(n, i0 + share);
+    const float *xs = right ? F.rx : F.lx;
+    const int8_t *os = right ? F.roct : F.loct;
+    const uint4 *ds = right ? F.rdesc : F.ldesc;
+    float4 *rec_out = right ? F.rs_kp : F.ls_kp;
+    uint4 *desc_out = right ? F.rs_desc : F.ls_desc;
+    for (int base = i0; base < i1; base += kScatter * kThreads) {
         float x[kScatter], y[kScatter];
         int oct[kScatter];
         uint4 d0[kScatter], d1[kScatter];
 #pragma unroll
         for (int u = 0; u < kScatter; ++u) {
-            const int i = min(base + u * kThreads + tid, F.nl - 1);
-            x[u] = __ldg(F.lx + i);
-            y[u] = __ldg(F.ly + i);
-            oct[u] = __ldg(F.loct + i);
-            d0[u] = __ldg(F.ldesc + 2 * i);
-            d1[u] = __ldg(F.ldesc + 2 * i + 1);
+            const int i = min(base + u * kThreads + tid, i1 - 1);
+            x[u] = __ldg(xs + i);
+            y[u] = __ldg(ys + i);
+            oct[u] = __ldg(os + i);
+            d0[u] = __ldg(ds + 2 * i);
+            d1[u] = __ldg(ds + 2 * i + 1);
         }
 #pragma unroll
         for (int u = 0; u < kScatter; ++u) {
             const int i = base + u * kThreads + tid;
-            if (i >= F.nl) continue;
-            const int pos = atomicAdd(&S.cnt[own_row(y[u], H)], 1);
-            F.ls_kp[pos] = make_float4(x[u], y[u], __int_as_float(i), __int_as_float(oct[u]));
-            F.ls_desc[2 * pos] = d0[u];
-            F.ls_desc[2 * pos + 1] = d1[u];
+            if (i >= i1) continue;
+            const int row = sort_row(right, y[u], H);
+            const int pos = atomicAdd(&S.cnt[part][row], 1);
+            if (right) {
+                // the rows this keypoint lists: floor(y - r) .. ceil(y + r), r = 2 scale[oct],
+                // clamped to the image (computed once here, tested per candidate later;
+                // an empty band stays empty: lo in [0, H], hi in [-1, H - 1])
+                const float r = B.p.band_r[clampi(oct[u], 0, B.p.nlevels - 1)];
+                const int lo = min(max(f2i(floorf(fsub(y[u], r))), 0), H);
+                const int hi = max(min(f2i(ceilf(fadd(y[u], r))), H - 1), -1);
+                rec_out[pos] = make_float4(x[u], __int_as_float(lo | (hi << 16)), __int_as_float(row),
+                                           __int_as_float(i | ((oct[u] & 0xff) << 20)));
+            } else {
+                rec_out[pos] = make_float4(x[u], y[u], __int_as_float(i), __int_as_float(oct[u]));
+            }
+            desc_out[2 * pos] = d0[u];
+            desc_out[2 * pos + 1] = d1[u];
         }
     }
     mark(B, 2);
-    signal_count(&F.ctr[C_ROWS_DONE], 2u, s_flag);
+    signal_count(&F.ctr[C_ROWS_DONE], (unsigned)F.rowsort, s_flag);
     mark(B, 3);
 }
 
@@ -942,7 +934,7 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     // a search in this launch reads each refined match's right coordinate
     // from the grid record, written here once the grid step is done
     const bool rec = F.wait_stereo && F.u_right_in != nullptr;
-    const bool ready = wait_geq(B, &F.ctr[C_ROWS_DONE], 2u, s_flag, rec ? &F.ctr[C_GRID_DONE] : nullptr,
+    const bool ready = wait_geq(B, &F.ctr[C_ROWS_DONE], (unsigned)F.rowsort, s_flag, rec ? &F.ctr[C_GRID_DONE] : nullptr,
                                 (unsigned)F.n_grid_items);
     if (ready) {
         const int H = F.H;
@@ -1555,8 +1547,7 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
         switch (kind) {
         case K_INDEX:
             if (tile < F.rowsort) {
-                if (tile == 0) rowsort_left_item(B, F, U.r, &s_flag);
-                else rowsort_right_item(B, F, U.r, &s_flag);
+                rowsort_item(B, F, U.r, tile >= kSortParts, tile % kSortParts, &s_flag);
             } else {
                 grid_item(B, F, tile - F.rowsort, U.g, &s_flag);
             }
