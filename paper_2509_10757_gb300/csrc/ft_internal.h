@@ -30,7 +30,7 @@ constexpr int kRefineChunk = 64;                    // matches refined per SAD r
 constexpr int kFishChunk = 512;                     // right descriptors staged per chunk
 constexpr int kFoldResolveMax = 8192;               // frames up to this size resolve in their last search item
 constexpr int kCounters = 8;                        // per-frame counters (u32)
-constexpr int kRowSortItems = 4;                    // row-sort work items per pinhole frame (2 per side)
+constexpr int kRowSortItems = 6;                    // row-sort work items per pinhole frame (3 per side)
 
 enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
 

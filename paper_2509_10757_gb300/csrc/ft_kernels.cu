@@ -932,10 +932,9 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
     const DevParams &P = B.p;
     const int tid = threadIdx.x;
     // a search in this launch reads each refined match's right coordinate
-    // from the grid record, written here once the grid step is done
+    // from the grid record, written once the grid step is done
     const bool rec = F.wait_stereo && F.u_right_in != nullptr;
-    const bool ready = wait_geq(B, &F.ctr[C_ROWS_DONE], (unsigned)F.rowsort, s_flag, rec ? &F.ctr[C_GRID_DONE] : nullptr,
-                                (unsigned)F.n_grid_items);
+    bool ready = wait_geq(B, &F.ctr[C_ROWS_DONE], (unsigned)F.rowsort, s_flag);
     if (ready) {
         const int H = F.H;
         const int r_lo = strip * F.strip_rows;
@@ -965,16 +964,22 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
             __syncthreads();
             mark(B, 0);
             hamming_phase(P, F, S, npass, staged, w_a, nrows, e_base);
-            __syncthreads();
+            // the refinement writes the grid records: the grid step must be done
+            if (rec && pass == l_lo) ready = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
+            else __syncthreads();
             mark(B, 1);
             const int nref = S.nref;
-            for (int r0 = 0; r0 < nref; r0 += kSadChunk) refine_round(P, F, S, r0, min(kSadChunk, nref - r0), rec);
+            for (int r0 = 0; r0 < nref; r0 += kSadChunk)
+                refine_round(P, F, S, r0, min(kSadChunk, nref - r0), rec && ready);
             if (tid == 0) S.nref = 0;
             __syncthreads();
             mark(B, 2);
         }
     }
     if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
+        // the rejection writes grid records too (this strip may have had no
+        // keypoints to refine, so it has not waited for the grid step yet)
+        if (rec && ready) ready = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
         median_reject(B, F, U.m, ready);
         __threadfence();
         __syncthreads();
