@@ -527,6 +527,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 fill_cam_kps(C, c ? j.right : j.left, c ? j.taken_r : j.taken_l);
                 fill_cam_out(C, c ? j.so.right : j.so.left);
                 C.cell_ptr = reinterpret_cast<int *>(carve(sizeof(int) * (kCells + 1)));
+                C.cell16 = reinterpret_cast<uint16_t *>(carve(sizeof(uint16_t) * (kCells + 1)));
                 C.gkp = reinterpret_cast<float4 *>(carve(sizeof(float4) * (size_t)C.nk));
                 C.gdesc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)C.nk));
                 C.gpos = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)C.nk));

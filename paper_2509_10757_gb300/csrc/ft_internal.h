@@ -74,6 +74,7 @@ struct CamDev {
     float4 *proj;
     int *mp_kp, *mp_d1, *mp_d2, *kp_mp;
     int *cell_ptr;                 // [kCells + 1]
+    uint16_t *cell16;              // [kCells + 1] the same starts in 16 bits (nk < 65536), 16-byte aligned
     float4 *gkp;                   // [nk] keypoints in cell order: x, y,
                                    // index | octave << 20 | taken << 28, right coordinate (or -1)
     uint4 *gdesc;                  // [2 * nk]

@@ -240,12 +240,14 @@ struct SmemMedian {
 
 constexpr int kSearchStage = 1536;              // keypoints of one camera the search keeps on chip
 
+constexpr int kCell16Bytes = (2 * (kCells + 1) + 15) / 16 * 16;   // 16-bit cell starts, whole chunks
+
 // a camera's keypoints in cell order, staged for the search of one tile:
-// x, y, index | octave << 20 | taken << 28, right coordinate (or -1)
+// records (x, y, index | octave << 20 | taken << 28, right coordinate or -1)
+// then descriptors, and, when they fit behind them, the 16-bit cell starts
 struct SmemSearch {
     float pose[12];
-    float4 rec[kSearchStage];
-    uint4 desc[2 * kSearchStage];
+    uint4 buf[kSearchStage * 3];
 };
 
 union Smem {
@@ -369,8 +371,14 @@ __device__ void grid_item(const BatchHeader &B, const FrameDev &F, int cam, Smem
     __syncthreads();
     mark(B, 0);
     const int total = block_scan(G.cnt, G.cnt, kCells, G.warp_sums);
-    for (int c = tid; c < kCells; c += kThreads) C.cell_ptr[c] = G.cnt[c];
-    if (tid == 0) C.cell_ptr[kCells] = total;
+    for (int c = tid; c < kCells; c += kThreads) {
+        C.cell_ptr[c] = G.cnt[c];
+        C.cell16[c] = (uint16_t)G.cnt[c];      // read only for frames of fewer than 65536 keypoints
+    }
+    if (tid == 0) {
+        C.cell_ptr[kCells] = total;
+        C.cell16[kCells] = (uint16_t)total;
+    }
     __syncthreads();
     mark(B, 1);
     // the record's right coordinate: a stereo step in this launch fills it
@@ -1269,9 +1277,11 @@ __device__ bool project(const DevParams &P, const CamDev &C, const float *pose, 
 // forward / backward / neither along its viewing axis (f2).
 template <bool kStaged>
 __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C, const SmemSearch &Q,
-                             float iw, float ih, int m, int motion)
+                             const uint16_t *scell, float iw, float ih, int m, int motion)
 {
     const float *pose = Q.pose;
+    const float4 *srec = reinterpret_cast<const float4 *>(Q.buf);
+    const uint4 *sdesc = Q.buf + C.nk;
     const bool last = F.search_mode != 0;
     int lvl = -1, d1 = -1, d2 = -1, kp = -1;
     float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1309,8 +1319,14 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                 unsigned best = kNoKey, second = kNoKey;
                 int oct1 = -1, oct2 = -1;
                 for (int cy = y0; cy <= y1; ++cy) {
-                    const int e0 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x0);
-                    const int e1 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x1 + 1);
+                    int e0, e1;
+                    if (kStaged && scell != nullptr) {
+                        e0 = scell[cy * FT_GRID_COLS + x0];
+                        e1 = scell[cy * FT_GRID_COLS + x1 + 1];
+                    } else {
+                        e0 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x0);
+                        e1 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x1 + 1);
+                    }
                     for (int e = e0; e < e1; ++e) {
                         int oct, k;
                         bool taken;
@@ -1318,7 +1334,7 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                         uint4 b0, b1;
                         float4 g;
                         if (kStaged) {
-                            g = Q.rec[e];
+                            g = srec[e];
                         } else {
                             // the keypoint record and its descriptor are fetched together
                             g = __ldcg(C.gkp + e);
@@ -1338,8 +1354,8 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                         if (taken) continue;
                         if (check_ur && urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
                         if (kStaged) {
-                            b0 = Q.desc[2 * e];
-                            b1 = Q.desc[2 * e + 1];
+                            b0 = sdesc[2 * e];
+                            b1 = sdesc[2 * e + 1];
                         }
                         const unsigned key = ((unsigned)ham8(q0, q1, b0, b1) << 20) | (unsigned)k;
                         if (key < best) {
@@ -1409,15 +1425,15 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         // records is copied but never read)
         const int nk = C.nk;
         const bool staged = nk <= kSearchStage;
+        // the 16-bit cell starts too when they fit behind the descriptors
+        const bool cells = staged && 48 * nk + kCell16Bytes <= (int)sizeof(Q.buf);
+        const uint16_t *scell = cells ? reinterpret_cast<const uint16_t *>(Q.buf + 3 * nk) : nullptr;
         if (staged) {
-            const unsigned srec = (unsigned)__cvta_generic_to_shared(Q.rec);
-            const unsigned sdesc = (unsigned)__cvta_generic_to_shared(Q.desc);
-            for (int e = tid; e < nk; e += kThreads)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(srec + 16u * e), "l"(C.gkp + e)
-                             : "memory");
-            for (int e = tid; e < 2 * nk; e += kThreads)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdesc + 16u * e), "l"(C.gdesc + e)
-                             : "memory");
+            for (int e = tid; e < nk; e += kThreads) cp_async16(Q.buf + e, C.gkp + e);
+            for (int e = tid; e < 2 * nk; e += kThreads) cp_async16(Q.buf + nk + e, C.gdesc + e);
+            if (cells)
+                for (int c = tid; c < kCell16Bytes / 16; c += kThreads)
+                    cp_async16(Q.buf + 3 * nk + c, reinterpret_cast<const uint4 *>(C.cell16) + c);
             asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
@@ -1437,9 +1453,10 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
             motion = cz > F.base ? 1 : (-cz > F.base ? -1 : 0);
         }
         if (staged) {
-            for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, iw, ih, m, motion);
+            for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, scell, iw, ih, m, motion);
         } else {
-            for (int m = m0 + tid; m < m1; m += kThreads) search_point<false>(B.p, F, C, Q, iw, ih, m, motion);
+            for (int m = m0 + tid; m < m1; m += kThreads)
+                search_point<false>(B.p, F, C, Q, nullptr, iw, ih, m, motion);
         }
         mark(B, 1);
     } else {

@@ -155,10 +155,11 @@ def test_stress_frames(ctx, lib):
 
 
 def test_search_keypoints_on_chip_boundary(ctx, lib):
-    # the search keeps up to 1536 keypoints of a camera in shared memory and
-    # reads larger frames from device memory: both sides of the boundary,
-    # fused (right coordinates from the stereo step) and per call
-    frames = [scenes.pinhole_frame(40 + n, 752, 480, n, 0.2, 0.05, 3000) for n in (1535, 1536, 1537)]
+    # the search keeps up to 1536 keypoints of a camera in shared memory (and
+    # the grid's 16-bit cell starts too up to 1407 keypoints) and reads larger
+    # frames from device memory: both sides of each boundary, fused (right
+    # coordinates from the stereo step) and per call
+    frames = [scenes.pinhole_frame(40 + n, 752, 480, n, 0.2, 0.05, 3000) for n in (1407, 1408, 1536, 1537)]
     frames.append(scenes.fisheye_frame(43, 1536, n_map=3000))
     frames.append(scenes.fisheye_frame(44, 1537, n_map=3000))
     pb = run_fused(ctx, frames)
