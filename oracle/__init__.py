@@ -139,6 +139,8 @@ def _lib_handle():
             lib.orc_triangulate.argtypes = [vp, vp, vp, vp, C.c_float, vp]
             lib.orc_fisheye_triangulate.argtypes = [P(OrcParams), P(OrcKB8), P(OrcKB8), vp, vp,
                                                     P(OrcKeypoints), P(OrcKeypoints), vp, vp, vp]
+            lib.orc_pyramid_sizes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, vp, vp]
+            lib.orc_resample_level.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int]
             lib.orc_motion.restype = C.c_int
             lib.orc_motion.argtypes = [P(OrcPose), P(OrcPose), C.c_float]
             lib.orc_search_last_camera.argtypes = [P(OrcParams), C.c_float, C.c_float, C.c_float,
@@ -606,3 +608,25 @@ def search_last_camera(params: dict, bounds, kps, u_right, taken, desc, level, p
                                _ptr(md), _ptr(lv), _ptr(pj), motion_,
                                *[_ptr(out[k]) for k in ("mp_kp", "mp_d1", "mp_d2", "kp_mp")])
     return out
+
+
+def pyramid_sizes(W: int, H: int, nlevels: int = 8, s: float = 1.2):
+    """f3: (widths, heights) of the pyramid levels."""
+    w = np.zeros(nlevels, np.int32)
+    h = np.zeros(nlevels, np.int32)
+    _lib_handle().orc_pyramid_sizes(W, H, nlevels, s, _ptr(w), _ptr(h))
+    return [int(v) for v in w], [int(v) for v in h]
+
+
+def resample_level(img, w: int, h: int) -> np.ndarray:
+    """f3: one pyramid level from level 0."""
+    src = _c(img, np.uint8)
+    out = np.zeros((h, w), np.uint8)
+    _lib_handle().orc_resample_level(_ptr(src), src.shape[1], src.shape[0], src.strides[0], _ptr(out), w, h, w)
+    return out
+
+
+def build_pyramid(img, nlevels: int = 8, s: float = 1.2) -> list:
+    """f3: the pyramid of a level-0 image (level 0 itself first)."""
+    ws, hs = pyramid_sizes(img.shape[1], img.shape[0], nlevels, s)
+    return [np.ascontiguousarray(img, np.uint8)] + [resample_level(img, ws[l], hs[l]) for l in range(1, nlevels)]

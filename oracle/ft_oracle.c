@@ -1010,3 +1010,55 @@ void orc_search_last_fisheye(const orc_params *p, const orc_kb8 *camL, const orc
     orc_search_last_camera(p, camR->min_x, camR->max_x, camR->min_y, camR->max_y, KR, NULL, takenR, M,
                            mp_desc, level_r, proj_r, motion, mp_kp_r, mp_d1_r, mp_d2_r, kp_mp_r);
 }
+
+/* ------------------------------------------------------------------------ */
+/* f3 (pyramid part): the image pyramid built from level 0.  The paper runs */
+/* ORB extraction on the GPU so that the pyramid, most of stereo matching's */
+/* input, never crosses the bus (section IV-B); it prints no resampling.     */
+/* Reading (each level straight from level 0, as the family resizes):      */
+/*  - level l is round(W / scale[l]) x round(H / scale[l]) (FP32 division);  */
+/*  - output pixel (x, y) samples level 0 at xs = (x + 0.5) * (W / w) - 0.5, */
+/*    ys likewise, each clamped to [0, W-1] / [0, H-1], bilinearly:         */
+/*    with x0 = floor(xs), x1 = min(x0 + 1, W - 1), fx = xs - x0 (same in y),*/
+/*    top = I(x0,y0)(1-fx) + I(x1,y0) fx, bottom likewise on y1,            */
+/*    value = top (1-fy) + bottom fy, rounded half to even and clamped to   */
+/*    [0, 255]; FP32, in this order.                                         */
+/* ------------------------------------------------------------------------ */
+void orc_pyramid_sizes(int W, int H, int nlevels, float s, int *w, int *h)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(nlevels, s, sc, isc);
+    for (int l = 0; l < nlevels; ++l) {
+        w[l] = (int)roundf((float)W / sc[l]);
+        h[l] = (int)roundf((float)H / sc[l]);
+    }
+}
+
+void orc_resample_level(const uint8_t *src, int W, int H, int pitch, uint8_t *dst, int w, int h, int dpitch)
+{
+    const float sx = (float)W / (float)w, sy = (float)H / (float)h;
+    for (int y = 0; y < h; ++y) {
+        float ys = ((float)y + 0.5f) * sy - 0.5f;
+        if (ys < 0.0f) ys = 0.0f;
+        if (ys > (float)(H - 1)) ys = (float)(H - 1);
+        const int y0 = (int)floorf(ys);
+        const int y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+        const float fy = ys - (float)y0;
+        for (int x = 0; x < w; ++x) {
+            float xs = ((float)x + 0.5f) * sx - 0.5f;
+            if (xs < 0.0f) xs = 0.0f;
+            if (xs > (float)(W - 1)) xs = (float)(W - 1);
+            const int x0 = (int)floorf(xs);
+            const int x1 = x0 + 1 < W ? x0 + 1 : W - 1;
+            const float fx = xs - (float)x0;
+            const float p00 = src[(size_t)y0 * pitch + x0], p01 = src[(size_t)y0 * pitch + x1];
+            const float p10 = src[(size_t)y1 * pitch + x0], p11 = src[(size_t)y1 * pitch + x1];
+            const float top = p00 * (1.0f - fx) + p01 * fx;
+            const float bot = p10 * (1.0f - fx) + p11 * fx;
+            float v = rintf(top * (1.0f - fy) + bot * fy);
+            if (v < 0.0f) v = 0.0f;
+            if (v > 255.0f) v = 255.0f;
+            dst[(size_t)y * dpitch + x] = (uint8_t)v;
+        }
+    }
+}

@@ -171,6 +171,10 @@ void orc_search_fisheye(const orc_params *p, const orc_kb8 *camL, const orc_kb8 
                         int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
                         int32_t *mp_d2_r, int32_t *kp_mp_r);
 
+/* ---- image pyramid (next row f3, its pyramid part) ------------------- */
+void orc_pyramid_sizes(int W, int H, int nlevels, float s, int *w, int *h);
+void orc_resample_level(const uint8_t *src, int W, int H, int pitch, uint8_t *dst, int w, int h, int dpitch);
+
 /* ---- search of the last frame's points (next row f2) ------------------ */
 int orc_motion(const orc_pose *cur, const orc_pose *last, float b);
 void orc_search_last_camera(const orc_params *p, float min_x, float max_x, float min_y, float max_y,

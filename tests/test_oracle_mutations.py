@@ -68,6 +68,13 @@ MUTANTS = [
     ("last_ratio_added", "if (bd > p->th_search) continue;\n        const int64_t key = ((int64_t)bd << 32) | (int64_t)m;\n        if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;\n        mp_kp[m] = bk;\n    }\n    for (int k = 0; k < K->n; ++k) kp_mp[k] = (owner[k] < 0) ? -1 : (int32_t)(owner[k] & 0xffffffff);\n    for (int m = 0; m < M; ++m)\n        if (mp_kp[m] >= 0 && kp_mp[mp_kp[m]] != m) mp_kp[m] = -1;\n    free(ky);",
      "if (bd > p->th_search || (float)bd > 0.8f * (float)mp_d2[m]) continue;\n        const int64_t key = ((int64_t)bd << 32) | (int64_t)m;\n        if (owner[bk] < 0 || key < owner[bk]) owner[bk] = key;\n        mp_kp[m] = bk;\n    }\n    for (int k = 0; k < K->n; ++k) kp_mp[k] = (owner[k] < 0) ? -1 : (int32_t)(owner[k] & 0xffffffff);\n    for (int m = 0; m < M; ++m)\n        if (mp_kp[m] >= 0 && kp_mp[mp_kp[m]] != m) mp_kp[m] = -1;\n    free(ky);"),
     ("last_octave_range", "return (lv >= 0 && lv < p->nlevels) ? lv : -1;", "return (lv >= -1 && lv < p->nlevels) ? (lv < 0 ? 0 : lv) : -1;"),
+    # image pyramid (next row f3)
+    ("pyr_half_pixel", "float xs = ((float)x + 0.5f) * sx - 0.5f;", "float xs = (float)x * sx;"),
+    ("pyr_weights_swapped", "const float top = p00 * (1.0f - fx) + p01 * fx;",
+     "const float top = p00 * fx + p01 * (1.0f - fx);"),
+    ("pyr_no_y_weight", "const float fy = ys - (float)y0;", "const float fy = 0.0f;"),
+    ("pyr_size_floor", "w[l] = (int)roundf((float)W / sc[l]);", "w[l] = (int)((float)W / sc[l]);"),
+    ("pyr_round_floor", "float v = rintf(top * (1.0f - fy) + bot * fy);", "float v = floorf(top * (1.0f - fy) + bot * fy);"),
     ("last_view_distance", "        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;",
      "        if (Pc[2] > 8.0f) continue;\n        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;"),
 ]
@@ -91,7 +98,8 @@ def _run_mutant(tmp, name, old, new):
                         os.path.join(ROOT, "tests", "test_oracle_stereo.py"),
                         os.path.join(ROOT, "tests", "test_oracle_search.py"),
                         os.path.join(ROOT, "tests", "test_oracle_triangulation.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_lastframe.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_lastframe.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pyramid.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
