@@ -260,6 +260,9 @@ typedef struct {
     ft_fisheye_out fisheye_out;         /* fisheye */
     ft_search_out search;
     const ft_last_frame_view *last;     /* HOST struct; NULL: search the local map */
+    int build_pyramids;                 /* pinhole: nonzero = levels 1.. of pyr_left and pyr_right
+                                           are built on the device from level 0 before the stereo
+                                           step reads them (see ft_build_pyramid) */
 } ft_frame_job;
 
 /* A ragged batch.  frames points to HOST memory (n entries).  If
@@ -356,6 +359,22 @@ ft_status ft_search_local_points(ft_ctx *ctx, void *stream, const ft_params *par
 ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *params,
                                const ft_frame_view *frame, const ft_pose *Tcw,
                                const ft_last_frame_view *last, ft_search_out *out);
+
+/* Sizes of the pyramid levels of a width x height level 0 (next row f3, its
+ * pyramid part): level l is round(width / scale[l]) x round(height /
+ * scale[l]) with scale[l] the FP32 product of scale_factor (params NULL =
+ * defaults).  Host function; w and h receive params->nlevels values. */
+ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *w, int *h);
+
+/* Build levels 1..nlevels-1 of a pyramid from its level 0 on the device (the
+ * paper runs ORB extraction, which produces the pyramid, on the GPU so that
+ * the pyramid never crosses the bus; section IV-B).  Level l samples level 0
+ * bilinearly at xs = (x + 0.5) * (W / w) - 0.5 (and ys likewise), clamped to
+ * the image, in FP32 (this order: top = I00 (1-fx) + I01 fx, bottom likewise,
+ * value = top (1-fy) + bottom fy), rounded half to even.  The caller owns
+ * every level (sizes from ft_pyramid_sizes; 16-byte aligned, pitches
+ * multiples of 16); levels 1.. are written.  Asynchronous on the stream. */
+ft_status ft_build_pyramid(ft_ctx *ctx, void *stream, const ft_params *params, const ft_pyramid *pyr);
 
 /* Stereo matching followed by the search, for a ragged batch of frames, in
  * one persistent fused launch (CUDA-graph replayed per batch-shape bucket if

@@ -112,7 +112,8 @@ class ft_frame_job(C.Structure):
                 ("pyr_right", ft_pyramid), ("taken_left", vp), ("taken_right", vp),
                 ("pose", ft_pose), ("O_right", f32 * 3), ("map", ft_map_view),
                 ("stereo", ft_stereo_out), ("fisheye_out", ft_fisheye_out),
-                ("search", ft_search_out), ("last", C.POINTER(ft_last_frame_view))]
+                ("search", ft_search_out), ("last", C.POINTER(ft_last_frame_view)),
+                ("build_pyramids", i32)]
 
 
 class ft_batch(C.Structure):
@@ -191,6 +192,8 @@ SIGNATURES = [
     ("ft_search_last_frame", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_frame_view),
                                    C.POINTER(ft_pose), C.POINTER(ft_last_frame_view),
                                    C.POINTER(ft_search_out)]),
+    ("ft_pyramid_sizes", i32, [i32, i32, C.POINTER(ft_params), vp, vp]),
+    ("ft_build_pyramid", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_pyramid)]),
     ("ft_track_batch", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch)]),
     ("ft_autotune", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch), i32,
                           C.POINTER(ft_tuning)]),

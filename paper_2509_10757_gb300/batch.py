@@ -38,16 +38,18 @@ class _Layout:
         return off
 
 
-def _input_arrays(f, fr, last=None):
-    """(key, array) pairs of frame `f`'s inputs (and of its last frame's points)."""
+def _input_arrays(f, fr, last=None, device_pyramids=False):
+    """(key, array) pairs of frame `f`'s inputs (and of its last frame's
+    points); with device_pyramids only level 0 of each pyramid is an input."""
     out = [((f, "lx"), fr.left.x), ((f, "ly"), fr.left.y), ((f, "loct"), fr.left.oct),
            ((f, "ldesc"), fr.left.desc), ((f, "rx"), fr.right.x), ((f, "ry"), fr.right.y),
            ((f, "roct"), fr.right.oct), ((f, "rdesc"), fr.right.desc),
            ((f, "taken_l"), fr.taken_l)]
     if fr.camera == "pinhole":
-        for l, img in enumerate(fr.pyr_left):
+        nl = 1 if device_pyramids else len(fr.pyr_left)
+        for l, img in enumerate(fr.pyr_left[:nl]):
             out.append(((f, f"pyrL{l}"), pad_rows(img)))
-        for l, img in enumerate(fr.pyr_right):
+        for l, img in enumerate(fr.pyr_right[:nl]):
             out.append(((f, f"pyrR{l}"), pad_rows(img)))
     else:
         out.append(((f, "taken_r"), fr.taken_r))
@@ -133,18 +135,23 @@ def pose_struct(pose) -> L.ft_pose:
 class PackedBatch:
     """Inputs and outputs of a list of generated frames, packed for the GPU."""
 
-    def __init__(self, frames, device: str | torch.device = "cuda", pin: bool = True, lasts=None):
+    def __init__(self, frames, device: str | torch.device = "cuda", pin: bool = True, lasts=None,
+                 device_pyramids: bool = False):
         """lasts: optional per-frame scenes.LastFrame (or None); a frame with
         one gets the last frame's points packed too, its batch job searches
-        them instead of the local map, and its results go to the lf_* outputs."""
+        them instead of the local map, and its results go to the lf_* outputs.
+        device_pyramids: pinhole frames carry only level 0 of their images;
+        levels 1.. live in a device buffer the launch fills (ft_frame_job
+        build_pyramids), with the sizes ft_pyramid_sizes gives."""
         self.frames = list(frames)
         self.lasts = list(lasts) if lasts is not None else [None] * len(self.frames)
+        self.device_pyramids = device_pyramids
         self.device = torch.device(device)
         self.lin = _Layout()
         self.lout = _Layout()
         arrays = []
         for f, fr in enumerate(self.frames):
-            for key, a in _input_arrays(f, fr, self.lasts[f]):
+            for key, a in _input_arrays(f, fr, self.lasts[f], device_pyramids):
                 a = np.ascontiguousarray(a)
                 self.lin.add(key, a.dtype, a.shape)
                 arrays.append(a)
@@ -159,6 +166,17 @@ class PackedBatch:
         self.dev_out = torch.empty(self.lout.size, dtype=torch.uint8, device=self.device)
         self.in_base = self.dev_in.data_ptr()
         self.out_base = self.dev_out.data_ptr()
+        # device-built pyramid levels 1.. (16-byte aligned rows)
+        self.lpyr = _Layout()
+        if device_pyramids:
+            for f, fr in enumerate(self.frames):
+                if fr.camera != "pinhole":
+                    continue
+                for side, levels in (("L", fr.pyr_left), ("R", fr.pyr_right)):
+                    for l in range(1, len(levels)):
+                        h, w = levels[l].shape
+                        self.lpyr.add((f, f"pyr{side}{l}"), np.uint8, (h, (w + 15) // 16 * 16))
+        self.dev_pyr = torch.empty(max(self.lpyr.size, 1), dtype=torch.uint8, device=self.device)
         self.last_views = [self.last_view(f) if self.lasts[f] is not None else None
                            for f in range(len(self.frames))]
         self.jobs = (L.ft_frame_job * max(1, len(self.frames)))()
@@ -191,10 +209,22 @@ class PackedBatch:
         s = L.ft_pyramid()
         s.nlevels = len(levels)
         for l, img in enumerate(levels):
-            s.data[l] = self.pin_(f, f"pyr{side}{l}")
+            key = (f, f"pyr{side}{l}")
+            if l > 0 and self.device_pyramids:
+                s.data[l] = self.dev_pyr.data_ptr() + self.lpyr.items[self.lpyr.index[key]][1]
+            else:
+                s.data[l] = self.pin_(f, f"pyr{side}{l}")
             s.height[l], s.width[l] = img.shape
             s.pitch[l] = pad_rows(img[:1]).shape[1]
         return s
+
+    def device_level(self, f, side: str, l: int) -> np.ndarray:
+        """A device-built level (levels >= 1 with device_pyramids) copied to the host."""
+        key, off, dt, shape = self.lpyr.items[self.lpyr.index[(f, f"pyr{side}{l}")]]
+        n = int(np.prod(shape))
+        a = self.dev_pyr[off:off + n].cpu().numpy().reshape(shape)
+        w = (self.frames[f].pyr_left if side == "L" else self.frames[f].pyr_right)[l].shape[1]
+        return a[:, :w]
 
     def map_view(self, f) -> L.ft_map_view:
         s = L.ft_map_view()
@@ -273,6 +303,7 @@ class PackedBatch:
             j.pinhole = pinhole_struct(fr.cam)
             j.pyr_left, j.pyr_right = self.pyramid(f, "L"), self.pyramid(f, "R")
             j.stereo = self.stereo_out(f)
+            j.build_pyramids = 1 if self.device_pyramids else 0
         else:
             j.camera = L.FT_CAMERA_FISHEYE
             j.fisheye = rig_struct(fr.rig)

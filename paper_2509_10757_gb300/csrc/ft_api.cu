@@ -105,6 +105,8 @@ struct Job {
     ft_fisheye_out fo{};
     ft_search_out so{};
     const float *u_right_in = nullptr;
+    int build_pyr = 0;                    // levels 1.. built on the device from level 0: bit 0 the left
+                                          // pyramid, bit 1 the right one
     int search_mode = 0;                  // 0: local map; 1: the last frame's points (map.nrm unused)
     const int8_t *last_oct = nullptr;
     ft_pose last_pose{};
@@ -143,7 +145,8 @@ struct ft_ctx {
     bool have_last = false;
     bool use_graphs = false;
     cudaStream_t capture_stream = nullptr;
-    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM, slot)
+    std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM, slot,
+                                                                        //  pyramid frames)
     std::map<Bucket, ft_tuning> tuning;
     uint64_t launches = 0;
     unsigned debug_flags = 0;
@@ -190,6 +193,18 @@ ft_status check_kps(const ft_keypoints &k, const char *what)
     return FT_OK;
 }
 
+// level sizes of a device-built pyramid: round(size / scale[l]), scale[l]
+// the FP32 product of the scale factor (the device table's values)
+void pyramid_sizes(int W, int H, const ft_params &p, int *w, int *h)
+{
+    float sc = 1.0f;
+    for (int l = 0; l < p.nlevels; ++l) {
+        if (l > 0) sc = sc * p.scale_factor;
+        w[l] = (int)std::round((float)W / sc);
+        h[l] = (int)std::round((float)H / sc);
+    }
+}
+
 ft_status check_pyramid(const ft_pyramid &p, int nlevels, const char *what)
 {
     if (p.nlevels < nlevels) return fail(FT_EINVAL, "%s: %d levels, need %d", what, p.nlevels, nlevels);
@@ -217,6 +232,19 @@ ft_status check_job(const Job &j, const ft_params &p)
     if ((s = check_kps(j.left, "left keypoints")) != FT_OK) return s;
     if (j.camera == FT_CAMERA_FISHEYE || j.do_stereo)
         if ((s = check_kps(j.right, "right keypoints")) != FT_OK) return s;
+    if (j.build_pyr) {
+        if (j.camera != FT_CAMERA_PINHOLE) return fail(FT_EINVAL, "pyramids are built for pinhole frames only");
+        const ft_pyramid *pp[2] = {&j.pyr_l, &j.pyr_r};
+        for (const ft_pyramid *py : pp) {
+            if ((s = check_pyramid(*py, p.nlevels, "pyramid")) != FT_OK) return s;
+            int w[FT_MAX_LEVELS], h[FT_MAX_LEVELS];
+            pyramid_sizes(py->width[0], py->height[0], p, w, h);
+            for (int l = 1; l < p.nlevels; ++l)
+                if (py->width[l] != w[l] || py->height[l] != h[l])
+                    return fail(FT_EINVAL, "pyramid level %d is %dx%d, a built level is %dx%d", l, py->width[l],
+                                py->height[l], w[l], h[l]);
+        }
+    }
     if (j.camera == FT_CAMERA_PINHOLE) {
         if (j.pin.width <= 0 || j.pin.height <= 0) return fail(FT_EINVAL, "pinhole: bad image size");
         if (j.do_search) {
@@ -422,7 +450,8 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             F.H = j.pin.height;
             F.b = j.pin.b;
             F.bf = j.pin.bf;
-            if (j.do_stereo) {
+            F.build_pyr = j.build_pyr;
+            if (j.do_stereo || j.build_pyr) {
                 for (int l = 0; l < params.nlevels; ++l) {
                     F.pyrL[l] = j.pyr_l.data[l];
                     F.lw[l] = j.pyr_l.width[l];
@@ -433,6 +462,8 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                     F.rh[l] = j.pyr_r.height[l];
                     F.rp[l] = j.pyr_r.pitch[l];
                 }
+            }
+            if (j.do_stereo) {
                 F.best_r = j.st.best_r;
                 F.dist = j.st.dist;
                 F.sad_shift = j.st.sad_shift;
@@ -588,9 +619,9 @@ ft_status finish_call(ft_ctx *ctx, cudaStream_t s)
 }
 
 ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int slot, int grid,
-                    size_t copy_bytes, cudaGraphExec_t *out)
+                    size_t copy_bytes, int pyr_frames, cudaGraphExec_t *out)
 {
-    const auto key = std::make_tuple(frames_p2, cps, slot);
+    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
@@ -601,7 +632,9 @@ ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int sl
     cudaGraph_t g = nullptr;
     FT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e1 = cudaMemcpyAsync(table_dev, ctx->staging[slot], copy_bytes, cudaMemcpyHostToDevice, cs);
-    const cudaError_t e2 = launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), grid, cs);
+    const cudaError_t e0 = launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, cs);
+    const cudaError_t e2 = e0 != cudaSuccess ? e0 : launch_fused(reinterpret_cast<const BatchHeader *>(table_dev),
+                                                                 grid, cs);
     const cudaError_t e3 = cudaStreamEndCapture(cs, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -649,20 +682,30 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
     if ((s = order_stream(ctx, stream)) != FT_OK) return s;
     const int cps = tune.ctas_per_sm > 0 ? std::min(tune.ctas_per_sm, ctx->occ) : ctx->occ;
     const int grid_max = ctx->sm_count * cps;
-    if (items > 0) {
-        if (allow_graph && ctx->use_graphs) {
+    // frames that build their pyramids first run the pyramid kernel
+    int pyr_frames = 0;
+    for (size_t f = 0; f < jobs.size(); ++f)
+        if (jobs[f].build_pyr) pyr_frames = (int)f + 1;
+    if (items > 0 || pyr_frames > 0) {
+        if (allow_graph && ctx->use_graphs && items > 0) {
             const int fp2 = bk.frames_p2;
             const size_t copy = std::max(bytes, table_layout(fp2).total);
             cudaGraphExec_t exec = nullptr;
             if ((s = get_graph(ctx, table_dev, fp2, cps, slot, grid_max, std::min(copy, ctx->table_cap),
-                               &exec)) != FT_OK)
+                               pyr_frames > 0 ? fp2 : 0, &exec)) != FT_OK)
                 return s;
             FT_CUDA(cudaGraphLaunch(exec, stream));
         } else {
             FT_CUDA(cudaMemcpyAsync(table_dev, ctx->staging[slot], bytes, cudaMemcpyHostToDevice, stream));
-            FT_CUDA(launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), std::min(items, grid_max), stream));
+            if (pyr_frames > 0) {
+                FT_CUDA(launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, stream));
+                ctx->launches += 1;
+            }
+            if (items > 0)
+                FT_CUDA(launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), std::min(items, grid_max),
+                                     stream));
         }
-        ctx->launches += 1;
+        if (items > 0) ctx->launches += 1;
     }
     FT_CUDA(cudaEventRecord(ctx->slot_done[slot], stream));
     return finish_call(ctx, stream);
@@ -904,6 +947,34 @@ ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *param
     return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
 }
 
+ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *w, int *h)
+{
+    if (!w || !h || width <= 0 || height <= 0) return fail(FT_EINVAL, "ft_pyramid_sizes: bad argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    ft_status s = check_params(p);
+    if (s != FT_OK) return s;
+    pyramid_sizes(width, height, p, w, h);
+    return FT_OK;
+}
+
+ft_status ft_build_pyramid(ft_ctx *ctx, void *stream, const ft_params *params, const ft_pyramid *pyr)
+{
+    if (!ctx || !pyr) return fail(FT_EINVAL, "ft_build_pyramid: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    Job j;
+    j.camera = FT_CAMERA_PINHOLE;
+    j.build_pyr = 1;           // one image: the left side names it
+    j.pin.width = pyr->width[0];
+    j.pin.height = pyr->height[0];
+    j.pyr_l = *pyr;
+    j.pyr_r = *pyr;
+    return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
+}
+
 static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
 {
     if (!batch || batch->n < 0 || (batch->n > 0 && !batch->frames))
@@ -932,6 +1003,7 @@ static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
         j.so = s.search;
         j.u_right_in = s.camera == FT_CAMERA_PINHOLE ? s.stereo.u_right : nullptr;
         if (s.last) set_last(j, *s.last);
+        j.build_pyr = s.build_pyramids != 0 ? 3 : 0;
     }
     return FT_OK;
 }

@@ -111,6 +111,7 @@ struct FrameDev {
     float kbl[8], kbr[8];          // fx, fy, cx, cy, k1..k4 of the left and right fisheye cameras
     // search
     const float *u_right_in;       // stereo consistency input (NULL: none)
+    int build_pyr;                 // levels 1.. built from level 0 before the launch: bit 0 left, bit 1 right
     int search_mode;               // 0: local map; 1: the last frame's points
     const int8_t *last_oct;        // last mode: octave of each point's last observation
     float last_R[9], last_t[3];    // last mode: the last frame's pose
@@ -149,6 +150,8 @@ struct BatchHeader {
 // Launch helpers implemented in ft_kernels.cu (host-callable).
 namespace ft {
 cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stream);
+// levels 1.. of the pyramids of the frames that build them (before the fused launch)
+cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream);
 int fused_smem_bytes();
 cudaError_t fused_occupancy(int *ctas_per_sm);
 const void *fused_kernel_ptr();

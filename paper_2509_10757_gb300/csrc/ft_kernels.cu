@@ -1603,6 +1603,69 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
 
 }  // namespace
 
+// ---------------------------------------------------------------- f3: image pyramid
+// Block (x, y): y = frame * 2 * (FT_MAX_LEVELS - 1) + side * (FT_MAX_LEVELS - 1)
+// + level - 1; the x blocks stride the level's rows.  Each thread computes
+// four neighbouring pixels of a row and stores them as one 32-bit word
+// (pitches are multiples of 16; bytes past the level's width are zero).
+constexpr int kPyrLevelSlots = FT_MAX_LEVELS - 1;
+constexpr int kPyrRowBlocks = 16;
+
+__global__ void __launch_bounds__(256) ft_pyramid_kernel(const BatchHeader *__restrict__ hdr)
+{
+    const int f = blockIdx.y / (2 * kPyrLevelSlots);
+    const int r = blockIdx.y - f * 2 * kPyrLevelSlots;
+    const int side = r / kPyrLevelSlots, l = 1 + r % kPyrLevelSlots;
+    if (f >= hdr->nframes || l >= hdr->p.nlevels) return;
+    const FrameDev &F = hdr->frames[f];
+    if (!(F.build_pyr & (1 << side))) return;
+    const uint8_t *src = side ? F.pyrR[0] : F.pyrL[0];
+    const int W = side ? F.rw[0] : F.lw[0], H = side ? F.rh[0] : F.lh[0], sp = side ? F.rp[0] : F.lp[0];
+    uint8_t *dst = const_cast<uint8_t *>(side ? F.pyrR[l] : F.pyrL[l]);
+    const int w = side ? F.rw[l] : F.lw[l], h = side ? F.rh[l] : F.lh[l], dp = side ? F.rp[l] : F.lp[l];
+    const float sx = fdiv((float)W, (float)w), sy = fdiv((float)H, (float)h);
+    for (int x4 = 4 * (int)threadIdx.x; x4 < w; x4 += 4 * (int)blockDim.x) {
+        int c0[4], c1[4];
+        float fx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float xs = fsub(fmul(fadd((float)(x4 + j), 0.5f), sx), 0.5f);
+            xs = fminf(fmaxf(xs, 0.0f), (float)(W - 1));
+            c0[j] = f2i(floorf(xs));
+            c1[j] = min(c0[j] + 1, W - 1);
+            fx[j] = fsub(xs, (float)c0[j]);
+        }
+        for (int y = blockIdx.x; y < h; y += gridDim.x) {
+            float ys = fsub(fmul(fadd((float)y, 0.5f), sy), 0.5f);
+            ys = fminf(fmaxf(ys, 0.0f), (float)(H - 1));
+            const int y0 = f2i(floorf(ys));
+            const int y1 = min(y0 + 1, H - 1);
+            const float fy = fsub(ys, (float)y0);
+            const uint8_t *r0 = src + (size_t)y0 * sp, *r1 = src + (size_t)y1 * sp;
+            unsigned word = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (x4 + j >= w) continue;
+                const float p00 = (float)__ldg(r0 + c0[j]), p01 = (float)__ldg(r0 + c1[j]);
+                const float p10 = (float)__ldg(r1 + c0[j]), p11 = (float)__ldg(r1 + c1[j]);
+                const float top = fadd(fmul(p00, fsub(1.0f, fx[j])), fmul(p01, fx[j]));
+                const float bot = fadd(fmul(p10, fsub(1.0f, fx[j])), fmul(p11, fx[j]));
+                const float v = rintf(fadd(fmul(top, fsub(1.0f, fy)), fmul(bot, fy)));
+                word |= (unsigned)f2i(fminf(fmaxf(v, 0.0f), 255.0f)) << (8 * j);
+            }
+            *reinterpret_cast<unsigned *>(dst + (size_t)y * dp + x4) = word;
+        }
+    }
+}
+
+cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream)
+{
+    if (nframes <= 0) return cudaSuccess;
+    const dim3 grid(kPyrRowBlocks, (unsigned)(nframes * 2 * kPyrLevelSlots));
+    ft_pyramid_kernel<<<grid, 256, 0, stream>>>(dev_hdr);
+    return cudaGetLastError();
+}
+
 int fused_smem_bytes() { return (int)sizeof(Smem); }
 
 const void *fused_kernel_ptr() { return (const void *)ft_fused_kernel; }

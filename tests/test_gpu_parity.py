@@ -474,3 +474,56 @@ def test_last_frame_search_edge_cases(ctx, lib):
         st = orc.stereo_frame(_oracle_params(), fr)
         ref = _check_last(pb, 0, st, "edge: ")
         assert np.all(ref["level"] == -1)
+
+
+# ---------------------------------------------------------------- device-built pyramids (f3)
+def _with_oracle_pyramids(fr):
+    return dataclasses.replace(fr, pyr_left=orc.build_pyramid(fr.pyr_left[0]),
+                               pyr_right=orc.build_pyramid(fr.pyr_right[0]))
+
+
+def test_device_pyramids_in_the_batch(ctx, lib):
+    # pinhole frames that upload only level 0 of their images: the launch
+    # builds levels 1.. first; levels and results equal the oracle's on the
+    # oracle-built pyramids (fisheye frames in the same batch are untouched)
+    from paper_2509_10757_gb300.batch import PackedBatch, run_batch
+    frames = scenes.pinhole_batch(seed=5, n_frames=5) + [scenes.fisheye_frame(50)]
+    pb = PackedBatch(frames, device_pyramids=True)
+    pb.upload()
+    pb.clear_outputs()
+    run_batch(ctx, pb)
+    pb.download()
+    assert ctx.sync_status() == 0
+    for f, fr in enumerate(frames):
+        if fr.camera != "pinhole":
+            check_frame(pb, f, what="device pyramids")
+            continue
+        ref = _with_oracle_pyramids(fr)
+        for side, levels in (("L", ref.pyr_left), ("R", ref.pyr_right)):
+            for l in range(1, len(levels)):
+                assert np.array_equal(pb.device_level(f, side, l), levels[l]), (f, side, l)
+        out = pb.outputs(f)
+        st, se = orc.track_frame(_oracle_params(), ref)
+        assert_stereo_equal(out, st, f"device pyramids frame {f}: ")
+        assert_search_equal(out, se, "l", None, f"device pyramids frame {f}: ")
+
+
+def test_build_pyramid_per_call_and_size_check(ctx, lib):
+    from paper_2509_10757_gb300.batch import PackedBatch, stream_handle
+    fr = scenes.pinhole_frame(51, W=640, H=480, n_left=300, n_map=300)
+    pb = PackedBatch([fr], device_pyramids=True)
+    pb.upload()
+    pyr = pb.pyramid(0, "R")
+    lib.check(ctx.lib.ft_build_pyramid(ctx.ptr, stream_handle(), None, C.byref(pyr)), "ft_build_pyramid")
+    torch.cuda.synchronize()
+    ref = orc.build_pyramid(fr.pyr_right[0])
+    for l in range(1, len(ref)):
+        assert np.array_equal(pb.device_level(0, "R", l), ref[l]), l
+    # the library's sizes are the oracle's
+    w = (C.c_int * 8)()
+    h = (C.c_int * 8)()
+    lib.check(ctx.lib.ft_pyramid_sizes(640, 480, None, w, h), "ft_pyramid_sizes")
+    assert (list(w), list(h)) == tuple(map(list, orc.pyramid_sizes(640, 480)))
+    # a level of another size is refused before anything runs
+    pyr.width[3] += 1
+    assert ctx.lib.ft_build_pyramid(ctx.ptr, stream_handle(), None, C.byref(pyr)) == lib.FT_EINVAL
