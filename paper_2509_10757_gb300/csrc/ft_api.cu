@@ -239,6 +239,8 @@ ft_status check_job(const Job &j, const ft_params &p)
             if ((s = check_pyramid(*py, p.nlevels, "pyramid")) != FT_OK) return s;
             int w[FT_MAX_LEVELS], h[FT_MAX_LEVELS];
             pyramid_sizes(py->width[0], py->height[0], p, w, h);
+            if (p.nlevels > 1 && w[1] > 4096)
+                return fail(FT_EINVAL, "a device-built level may be at most 4096 pixels wide (level 1 is %d)", w[1]);
             for (int l = 1; l < p.nlevels; ++l)
                 if (py->width[l] != w[l] || py->height[l] != h[l])
                     return fail(FT_EINVAL, "pyramid level %d is %dx%d, a built level is %dx%d", l, py->width[l],

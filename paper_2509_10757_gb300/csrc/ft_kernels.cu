@@ -1605,14 +1605,19 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
 
 // ---------------------------------------------------------------- f3: image pyramid
 // Block (x, y): y = frame * 2 * (FT_MAX_LEVELS - 1) + side * (FT_MAX_LEVELS - 1)
-// + level - 1; the x blocks stride the level's rows.  Each thread computes
-// four neighbouring pixels of a row and stores them as one 32-bit word
-// (pitches are multiples of 16; bytes past the level's width are zero).
+// + level - 1; the x blocks split the level's rows into contiguous bands.
+// The source column and weight of every output column are computed once per
+// block into shared memory; each warp then takes rows, its lanes the row's
+// 32-bit output words (four neighbouring pixels, stored together: pitches
+// are multiples of 16, bytes past the level's width are zero).
 constexpr int kPyrLevelSlots = FT_MAX_LEVELS - 1;
-constexpr int kPyrRowBlocks = 16;
+constexpr int kPyrBlocks = 16;
+constexpr int kPyrMaxWidth = 4096;                  // widest level built on the device
 
 __global__ void __launch_bounds__(256) ft_pyramid_kernel(const BatchHeader *__restrict__ hdr)
 {
+    __shared__ int s_c0[kPyrMaxWidth];
+    __shared__ float s_fx[kPyrMaxWidth];
     const int f = blockIdx.y / (2 * kPyrLevelSlots);
     const int r = blockIdx.y - f * 2 * kPyrLevelSlots;
     const int side = r / kPyrLevelSlots, l = 1 + r % kPyrLevelSlots;
@@ -1623,34 +1628,38 @@ __global__ void __launch_bounds__(256) ft_pyramid_kernel(const BatchHeader *__re
     const int W = side ? F.rw[0] : F.lw[0], H = side ? F.rh[0] : F.lh[0], sp = side ? F.rp[0] : F.lp[0];
     uint8_t *dst = const_cast<uint8_t *>(side ? F.pyrR[l] : F.pyrL[l]);
     const int w = side ? F.rw[l] : F.lw[l], h = side ? F.rh[l] : F.lh[l], dp = side ? F.rp[l] : F.lp[l];
+    if (w > kPyrMaxWidth) return;                   // refused on the host
     const float sx = fdiv((float)W, (float)w), sy = fdiv((float)H, (float)h);
-    for (int x4 = 4 * (int)threadIdx.x; x4 < w; x4 += 4 * (int)blockDim.x) {
-        int c0[4], c1[4];
-        float fx[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float xs = fsub(fmul(fadd((float)(x4 + j), 0.5f), sx), 0.5f);
-            xs = fminf(fmaxf(xs, 0.0f), (float)(W - 1));
-            c0[j] = f2i(floorf(xs));
-            c1[j] = min(c0[j] + 1, W - 1);
-            fx[j] = fsub(xs, (float)c0[j]);
-        }
-        for (int y = blockIdx.x; y < h; y += gridDim.x) {
-            float ys = fsub(fmul(fadd((float)y, 0.5f), sy), 0.5f);
-            ys = fminf(fmaxf(ys, 0.0f), (float)(H - 1));
-            const int y0 = f2i(floorf(ys));
-            const int y1 = min(y0 + 1, H - 1);
-            const float fy = fsub(ys, (float)y0);
-            const uint8_t *r0 = src + (size_t)y0 * sp, *r1 = src + (size_t)y1 * sp;
+    for (int x = threadIdx.x; x < w; x += blockDim.x) {
+        float xs = fsub(fmul(fadd((float)x, 0.5f), sx), 0.5f);
+        xs = fminf(fmaxf(xs, 0.0f), (float)(W - 1));
+        const int c0 = f2i(floorf(xs));
+        s_c0[x] = c0;
+        s_fx[x] = fsub(xs, (float)c0);
+    }
+    __syncthreads();
+    const int wq = (w + 3) >> 2;                       // words per output row
+    const int band = (h + gridDim.x - 1) / gridDim.x;
+    const int ya = (int)blockIdx.x * band, yb = min(h, ya + band);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int y = ya + warp; y < yb; y += nwarps) {
+        float ys = fsub(fmul(fadd((float)y, 0.5f), sy), 0.5f);
+        ys = fminf(fmaxf(ys, 0.0f), (float)(H - 1));
+        const int y0 = f2i(floorf(ys));
+        const int y1 = min(y0 + 1, H - 1);
+        const float fy = fsub(ys, (float)y0), gy = fsub(1.0f, fy);
+        const uint8_t *r0 = src + (size_t)y0 * sp, *r1 = src + (size_t)y1 * sp;
+        for (int q = lane; q < wq; q += 32) {
+            const int x4 = 4 * q;
             unsigned word = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (x4 + j >= w) continue;
-                const float p00 = (float)__ldg(r0 + c0[j]), p01 = (float)__ldg(r0 + c1[j]);
-                const float p10 = (float)__ldg(r1 + c0[j]), p11 = (float)__ldg(r1 + c1[j]);
-                const float top = fadd(fmul(p00, fsub(1.0f, fx[j])), fmul(p01, fx[j]));
-                const float bot = fadd(fmul(p10, fsub(1.0f, fx[j])), fmul(p11, fx[j]));
-                const float v = rintf(fadd(fmul(top, fsub(1.0f, fy)), fmul(bot, fy)));
+                const int c0 = s_c0[x4 + j], c1 = min(c0 + 1, W - 1);
+                const float fx = s_fx[x4 + j], gx = fsub(1.0f, fx);
+                const float top = fadd(fmul((float)__ldg(r0 + c0), gx), fmul((float)__ldg(r0 + c1), fx));
+                const float bot = fadd(fmul((float)__ldg(r1 + c0), gx), fmul((float)__ldg(r1 + c1), fx));
+                const float v = rintf(fadd(fmul(top, gy), fmul(bot, fy)));
                 word |= (unsigned)f2i(fminf(fmaxf(v, 0.0f), 255.0f)) << (8 * j);
             }
             *reinterpret_cast<unsigned *>(dst + (size_t)y * dp + x4) = word;
@@ -1661,7 +1670,7 @@ __global__ void __launch_bounds__(256) ft_pyramid_kernel(const BatchHeader *__re
 cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream)
 {
     if (nframes <= 0) return cudaSuccess;
-    const dim3 grid(kPyrRowBlocks, (unsigned)(nframes * 2 * kPyrLevelSlots));
+    const dim3 grid(kPyrBlocks, (unsigned)(nframes * 2 * kPyrLevelSlots));
     ft_pyramid_kernel<<<grid, 256, 0, stream>>>(dev_hdr);
     return cudaGetLastError();
 }
