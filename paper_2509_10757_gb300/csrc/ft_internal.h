@@ -124,7 +124,8 @@ struct FrameDev {
     // work decomposition
     int strip_rows, n_stereo_items, fisheye_tile;
     int search_tile, resolve_tile;
-    int rowsort;                   // 2: index items 0 and 1 are the left and right row sorts
+    int rowsort;                   // row-sort index items (kRowSortItems: the first half the left
+                                   // keypoints, the second half the right ones), 0 without stereo
     int fold_resolve;              // 1: the last search item of a camera writes the final tables
     int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]

@@ -565,7 +565,7 @@ __device__ __forceinline__ void write_stereo(const FrameDev &F, int i, int best,
 // reduce to the smallest (distance, right index); lane 0 of the group queues
 // the match for refinement or writes the final "no match" outputs.
 __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo &S, int npass,
-                              bool staged, int w_a, int nrows, int e_base)
+                              bool staged, int w_a, int nrows)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane & (kGroup - 1), gw = lane / kGroup;
@@ -971,7 +971,7 @@ __device__ void stereo_pinhole_item(const BatchHeader &B, const FrameDev &F, int
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
             mark(B, 0);
-            hamming_phase(P, F, S, npass, staged, w_a, nrows, e_base);
+            hamming_phase(P, F, S, npass, staged, w_a, nrows);
             // the refinement writes the grid records: the grid step must be done
             if (rec && pass == l_lo) ready = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
             else __syncthreads();
