@@ -1327,45 +1327,41 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                         e0 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x0);
                         e1 = __ldcg(C.cell_ptr + cy * FT_GRID_COLS + x1 + 1);
                     }
-                    for (int e = e0; e < e1; ++e) {
-                        int oct, k;
-                        bool taken;
-                        float gx, gy, urk;
-                        uint4 b0, b1;
-                        float4 g;
-                        if (kStaged) {
-                            g = srec[e];
-                        } else {
-                            // the keypoint record and its descriptor are fetched together
-                            g = __ldcg(C.gkp + e);
-                            b0 = __ldcg(C.gdesc + 2 * e);
-                            b1 = __ldcg(C.gdesc + 2 * e + 1);
+                    // records in device memory arrive kBatchRec at a time (one
+                    // round trip), the descriptors of those that pass the tests after
+                    constexpr int kBatchRec = kStaged ? 1 : 4;
+                    for (int eb = e0; eb < e1; eb += kBatchRec) {
+                        float4 gb[kBatchRec];
+#pragma unroll
+                        for (int q = 0; q < kBatchRec; ++q) {
+                            if (kStaged) gb[q] = srec[eb + q];
+                            else gb[q] = eb + q < e1 ? __ldcg(C.gkp + eb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                        const unsigned z = __float_as_uint(g.z);
-                        gx = g.x;
-                        gy = g.y;
-                        k = (int)(z & 0xfffffu);
-                        oct = (int)(int8_t)((z >> 20) & 0xffu);
-                        taken = (z >> 28) != 0;
-                        urk = g.w;
-                        if (oct < min_oct || oct > max_oct) continue;
-                        const float distx = fsub(gx, u), disty = fsub(gy, v);
-                        if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
-                        if (taken) continue;
-                        if (check_ur && urk > 0.0f && fabsf(fsub(ur, urk)) > r) continue;
-                        if (kStaged) {
-                            b0 = sdesc[2 * e];
-                            b1 = sdesc[2 * e + 1];
-                        }
-                        const unsigned key = ((unsigned)ham8(q0, q1, b0, b1) << 20) | (unsigned)k;
-                        if (key < best) {
-                            second = best;
-                            oct2 = oct1;
-                            best = key;
-                            oct1 = oct;
-                        } else if (key < second) {
-                            second = key;
-                            oct2 = oct;
+#pragma unroll
+                        for (int q = 0; q < kBatchRec; ++q) {
+                            const int e = eb + q;
+                            if (e >= e1) break;
+                            const float4 g = gb[q];
+                            const unsigned z = __float_as_uint(g.z);
+                            const int k = (int)(z & 0xfffffu);
+                            const int oct = (int)(int8_t)((z >> 20) & 0xffu);
+                            if (oct < min_oct || oct > max_oct) continue;
+                            const float distx = fsub(g.x, u), disty = fsub(g.y, v);
+                            if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
+                            if (z >> 28) continue;                         // taken
+                            if (check_ur && g.w > 0.0f && fabsf(fsub(ur, g.w)) > r) continue;
+                            const uint4 b0 = kStaged ? sdesc[2 * e] : __ldcg(C.gdesc + 2 * e);
+                            const uint4 b1 = kStaged ? sdesc[2 * e + 1] : __ldcg(C.gdesc + 2 * e + 1);
+                            const unsigned key = ((unsigned)ham8(q0, q1, b0, b1) << 20) | (unsigned)k;
+                            if (key < best) {
+                                second = best;
+                                oct2 = oct1;
+                                best = key;
+                                oct1 = oct;
+                            } else if (key < second) {
+                                second = key;
+                                oct2 = oct;
+                            }
                         }
                     }
                 }
