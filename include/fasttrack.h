@@ -99,9 +99,10 @@ typedef struct {
 } ft_keypoints;
 
 /* Image pyramid: level l is width[l] x height[l] uint8 with row pitch[l]
- * bytes (pitch >= width).  Every level pointer must be 16-byte aligned and
- * every pitch a multiple of 16 (patch rows are copied in 16-byte chunks;
- * FT_EALIGN otherwise). */
+ * bytes (pitch >= width); the buffer of a level spans height x pitch bytes
+ * (rows are read in aligned 4- and 16-byte words up to the pitch).  Every
+ * level pointer must be 16-byte aligned and every pitch a multiple of 16
+ * (patch rows are copied in 16-byte chunks; FT_EALIGN otherwise). */
 typedef struct {
     int nlevels;
     const uint8_t *data[FT_MAX_LEVELS];
@@ -373,7 +374,8 @@ ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *
  * the image, in FP32 (this order: top = I00 (1-fx) + I01 fx, bottom likewise,
  * value = top (1-fy) + bottom fy), rounded half to even.  The caller owns
  * every level (sizes from ft_pyramid_sizes; 16-byte aligned, pitches
- * multiples of 16); levels 1.. are written.  Asynchronous on the stream. */
+ * multiples of 16); levels 1.. are written, each row up to its width rounded
+ * up to 4 (bytes past the width are zero).  Asynchronous on the stream. */
 ft_status ft_build_pyramid(ft_ctx *ctx, void *stream, const ft_params *params, const ft_pyramid *pyr);
 
 /* Stereo matching followed by the search, for a ragged batch of frames, in

@@ -145,8 +145,9 @@ struct ft_ctx {
     bool have_last = false;
     bool use_graphs = false;
     cudaStream_t capture_stream = nullptr;
-    std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM, slot,
-                                                                        //  pyramid frames)
+    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM,
+                                                                             //  slot, pyramid frames,
+                                                                             //  pyramid blocks per image)
     std::map<Bucket, ft_tuning> tuning;
     uint64_t launches = 0;
     unsigned debug_flags = 0;
@@ -239,8 +240,6 @@ ft_status check_job(const Job &j, const ft_params &p)
             if ((s = check_pyramid(*py, p.nlevels, "pyramid")) != FT_OK) return s;
             int w[FT_MAX_LEVELS], h[FT_MAX_LEVELS];
             pyramid_sizes(py->width[0], py->height[0], p, w, h);
-            if (p.nlevels > 1 && w[1] > 4096)
-                return fail(FT_EINVAL, "a device-built level may be at most 4096 pixels wide (level 1 is %d)", w[1]);
             for (int l = 1; l < p.nlevels; ++l)
                 if (py->width[l] != w[l] || py->height[l] != h[l])
                     return fail(FT_EINVAL, "pyramid level %d is %dx%d, a built level is %dx%d", l, py->width[l],
@@ -621,9 +620,9 @@ ft_status finish_call(ft_ctx *ctx, cudaStream_t s)
 }
 
 ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int slot, int grid,
-                    size_t copy_bytes, int pyr_frames, cudaGraphExec_t *out)
+                    size_t copy_bytes, int pyr_frames, int pyr_blocks, cudaGraphExec_t *out)
 {
-    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames);
+    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames, pyr_blocks);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
@@ -634,7 +633,7 @@ ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int sl
     cudaGraph_t g = nullptr;
     FT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e1 = cudaMemcpyAsync(table_dev, ctx->staging[slot], copy_bytes, cudaMemcpyHostToDevice, cs);
-    const cudaError_t e0 = launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, cs);
+    const cudaError_t e0 = launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_blocks, cs);
     const cudaError_t e2 = e0 != cudaSuccess ? e0 : launch_fused(reinterpret_cast<const BatchHeader *>(table_dev),
                                                                  grid, cs);
     const cudaError_t e3 = cudaStreamEndCapture(cs, &g);
@@ -684,23 +683,38 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
     if ((s = order_stream(ctx, stream)) != FT_OK) return s;
     const int cps = tune.ctas_per_sm > 0 ? std::min(tune.ctas_per_sm, ctx->occ) : ctx->occ;
     const int grid_max = ctx->sm_count * cps;
-    // frames that build their pyramids first run the pyramid kernel
-    int pyr_frames = 0;
+    // frames that build their pyramids first run the pyramid kernel, one
+    // block per virtual block of the largest image (the blocks of a smaller
+    // image exit; a graph replayed for larger images strides)
+    int pyr_frames = 0, pyr_blocks = 1;
     for (size_t f = 0; f < jobs.size(); ++f)
         if (jobs[f].build_pyr) pyr_frames = (int)f + 1;
+    if (pyr_frames > 0) {
+        int most = 1;
+        for (int f = 0; f < pyr_frames; ++f)
+            for (int side = 0; side < 2; ++side) {
+                if (!(jobs[f].build_pyr & (1 << side))) continue;
+                const ft_pyramid &py = side ? jobs[f].pyr_r : jobs[f].pyr_l;
+                int n = 0;
+                for (int l = 1; l < params.nlevels; ++l) n += pyr_vblocks(py.width[l], py.height[l]);
+                most = std::max(most, n);
+            }
+        pyr_blocks = most;
+    }
     if (items > 0 || pyr_frames > 0) {
         if (allow_graph && ctx->use_graphs && items > 0) {
             const int fp2 = bk.frames_p2;
             const size_t copy = std::max(bytes, table_layout(fp2).total);
             cudaGraphExec_t exec = nullptr;
             if ((s = get_graph(ctx, table_dev, fp2, cps, slot, grid_max, std::min(copy, ctx->table_cap),
-                               pyr_frames > 0 ? fp2 : 0, &exec)) != FT_OK)
+                               pyr_frames > 0 ? fp2 : 0, pyr_blocks, &exec)) != FT_OK)
                 return s;
             FT_CUDA(cudaGraphLaunch(exec, stream));
         } else {
             FT_CUDA(cudaMemcpyAsync(table_dev, ctx->staging[slot], bytes, cudaMemcpyHostToDevice, stream));
             if (pyr_frames > 0) {
-                FT_CUDA(launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, stream));
+                FT_CUDA(launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_blocks,
+                                        stream));
                 ctx->launches += 1;
             }
             if (items > 0)

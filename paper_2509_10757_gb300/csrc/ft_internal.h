@@ -31,6 +31,16 @@ constexpr int kFishChunk = 512;                     // right descriptors staged 
 constexpr int kFoldResolveMax = 8192;               // frames up to this size resolve in their last search item
 constexpr int kCounters = 8;                        // per-frame counters (u32)
 constexpr int kRowSortItems = 6;                    // row-sort work items per pinhole frame (3 per side)
+constexpr int kPyrRows = 16;                        // output rows one pyramid thread walks
+constexpr int kPyrThreads = 256;                    // threads per pyramid block
+
+// Pyramid work of one level: threads are (band of kPyrRows rows) x (quad of
+// four columns), grouped kPyrThreads to a virtual block.
+__host__ __device__ inline int pyr_vblocks(int w, int h)
+{
+    const long long t = (long long)((w + 3) >> 2) * ((h + kPyrRows - 1) / kPyrRows);
+    return (int)((t + kPyrThreads - 1) / kPyrThreads);
+}
 
 enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
 
@@ -151,8 +161,9 @@ struct BatchHeader {
 // Launch helpers implemented in ft_kernels.cu (host-callable).
 namespace ft {
 cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stream);
-// levels 1.. of the pyramids of the frames that build them (before the fused launch)
-cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream);
+// levels 1.. of the pyramids of the frames that build them (before the fused
+// launch); blocks_per_image blocks stride over each image's virtual blocks
+cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, int blocks_per_image, cudaStream_t stream);
 int fused_smem_bytes();
 cudaError_t fused_occupancy(int *ctas_per_sm);
 const void *fused_kernel_ptr();

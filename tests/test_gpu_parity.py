@@ -527,3 +527,45 @@ def test_build_pyramid_per_call_and_size_check(ctx, lib):
     # a level of another size is refused before anything runs
     pyr.width[3] += 1
     assert ctx.lib.ft_build_pyramid(ctx.ptr, stream_handle(), None, C.byref(pyr)) == lib.FT_EINVAL
+
+
+@pytest.mark.parametrize("W,H,nlevels,scale,seed", [(752, 480, 8, 1.2, 752), (333, 77, 8, 1.2, 1),
+                                                     (6000, 37, 6, 1.3, 2), (17, 9, 3, 1.5, 3),
+                                                     (641, 203, 5, 2.0, 4), (2, 3, 4, 1.2, 5),
+                                                     (1000, 1000, 4, 3.5, 6)])
+def test_build_pyramid_shapes_and_scales(ctx, lib, W, H, nlevels, scale, seed):
+    # odd widths (ragged last quads), flat and tiny images, a level wider than
+    # 4096, and scale factors whose levels take one 8-byte source window per
+    # four output pixels, one per pair and one per pixel; level 0's row
+    # padding holds junk the result must not depend on, levels 1.. start as
+    # junk and must come out zero past their width.  The first image has a
+    # pixel (level 5, row 9, column 225) whose value is an exact tie, 177.5,
+    # only when both products are rounded before the sum: a fused
+    # multiply-add there gives 177 instead of 178.
+    from paper_2509_10757_gb300.batch import stream_handle
+    rng = np.random.default_rng(seed)
+    img = rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+    ref = orc.build_pyramid(img, nlevels, scale)
+    p = _params(lib, {"nlevels": nlevels, "scale_factor": scale})
+    pyr = lib.ft_pyramid()
+    pyr.nlevels = nlevels
+    bufs = []
+    for l, lev in enumerate(ref):
+        h, w = lev.shape
+        pitch = (w + 15) // 16 * 16
+        host = rng.integers(0, 256, size=(h, pitch), dtype=np.uint8)
+        if l == 0:
+            host[:, :w] = lev
+        t = torch.from_numpy(host.reshape(-1)).cuda()
+        bufs.append(t)
+        pyr.data[l] = t.data_ptr()
+        pyr.width[l], pyr.height[l], pyr.pitch[l] = w, h, pitch
+    lib.check(ctx.lib.ft_build_pyramid(ctx.ptr, stream_handle(), C.byref(p), C.byref(pyr)), "ft_build_pyramid")
+    torch.cuda.synchronize()
+    for l in range(1, nlevels):
+        h, w = ref[l].shape
+        got = bufs[l].cpu().numpy().reshape(h, -1)
+        bad = np.argwhere(got[:, :w] != ref[l])
+        assert len(bad) == 0, (l, len(bad), bad[:4].tolist())
+        w4 = (w + 3) // 4 * 4
+        assert not got[:, w:w4].any(), l

@@ -65,3 +65,50 @@ def test_agrees_with_the_generator_resampling():
         d = pyr[l].astype(int) - fr.pyr_left[l].astype(int)
         assert np.all(np.abs(d) <= 1), l
         assert np.mean(d != 0) < 0.005, l
+
+
+def _round_f32(q):
+    """The float32 nearest to the exact rational q >= 0, ties to even."""
+    from fractions import Fraction
+    if q == 0:
+        return np.float32(0)
+    e = math.floor(math.log2(q))
+    while Fraction(2) ** e > q:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= q:
+        e += 1
+    ulp = Fraction(2) ** (e - 23)
+    m = q / ulp
+    lo = math.floor(m)
+    r = m - lo
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and lo % 2 == 1):
+        lo += 1
+    return np.float32(float(lo * ulp))
+
+
+def test_products_are_rounded_before_the_sum():
+    # One pixel of a seeded 752x480 image (level 5, row 9, column 225) whose
+    # value is an exact tie, 177.5, when top (1-fy) and bottom fy are each
+    # rounded to FP32 before their sum (178 after rounding half to even); a
+    # fused multiply-add of the first product into the sum gives 177.49998
+    # (177).  Exact rational arithmetic decides both, and the oracle (built
+    # without contraction) must give 178.
+    from fractions import Fraction
+    f32 = np.float32
+    rng = np.random.default_rng(752)
+    img = rng.integers(0, 256, size=(480, 752), dtype=np.uint8)
+    ws, hs = orc.pyramid_sizes(752, 480, 8, 1.2)
+    w, h, y, x = ws[5], hs[5], 9, 225
+    sx, sy = f32(752) / f32(w), f32(480) / f32(h)
+    xs = min(max((f32(x) + f32(0.5)) * sx - f32(0.5), f32(0)), f32(751))
+    ys = min(max((f32(y) + f32(0.5)) * sy - f32(0.5), f32(0)), f32(479))
+    x0, y0 = int(np.floor(xs)), int(np.floor(ys))
+    fx, fy = f32(xs - f32(x0)), f32(ys - f32(y0))
+    gx, gy = f32(1) - fx, f32(1) - fy
+    top = f32(f32(f32(img[y0, x0]) * gx) + f32(f32(img[y0, x0 + 1]) * fx))
+    bot = f32(f32(f32(img[y0 + 1, x0]) * gx) + f32(f32(img[y0 + 1, x0 + 1]) * fx))
+    F = lambda v: Fraction(float(v))
+    separate = _round_f32(F(_round_f32(F(top) * F(gy))) + F(_round_f32(F(bot) * F(fy))))
+    fused = _round_f32(F(top) * F(gy) + F(_round_f32(F(bot) * F(fy))))
+    assert separate == f32(177.5) and fused < f32(177.5)
+    assert orc.resample_level(img, w, h)[y, x] == 178
