@@ -835,6 +835,8 @@ __device__ __forceinline__ int median_value(const FrameDev &F, const SmemMedian 
     return on_chip ? M.vals[i] : __ldcg(F.sad_best + i);
 }
 
+constexpr int kMedianBatch = 8;   // values a thread loads at once in the median's first pass
+
 __device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedian &M, bool grid_ok)
 {
     const DevParams &P = B.p;
@@ -848,18 +850,29 @@ __device__ void median_reject(const BatchHeader &B, const FrameDev &F, SmemMedia
     if (tid == 0) M.count = 0;
     __syncthreads();
     // one pass over the values (kept on chip with each keypoint's grid
-    // record when they fit): the count and the histogram of the high bytes
+    // record when they fit): the count and the histogram of the high bytes;
+    // a thread loads kMedianBatch values before it stores or counts any
     int local = 0;
-#pragma unroll 4
-    for (int i = tid; i < F.nl; i += kThreads) {
-        const int x = __ldcg(F.sad_best + i);
-        if (on_chip) {
-            M.vals[i] = x;
-            if (rec) M.gp[i] = __ldcg(F.cam[0].gpos + i);
+    for (int i0 = tid; i0 < F.nl; i0 += kThreads * kMedianBatch) {
+        int xv[kMedianBatch], gv[kMedianBatch];
+#pragma unroll
+        for (int u = 0; u < kMedianBatch; ++u) {
+            const int i = i0 + u * kThreads;
+            xv[u] = i < F.nl ? __ldcg(F.sad_best + i) : -1;
+            gv[u] = on_chip && rec && i < F.nl ? __ldcg(F.cam[0].gpos + i) : -1;
         }
-        if (x >= 0) {
-            atomicAdd(&M.hist[(x >> 8) & 255], 1);
-            ++local;
+#pragma unroll
+        for (int u = 0; u < kMedianBatch; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i >= F.nl) continue;
+            if (on_chip) {
+                M.vals[i] = xv[u];
+                if (rec) M.gp[i] = gv[u];
+            }
+            if (xv[u] >= 0) {
+                atomicAdd(&M.hist[(xv[u] >> 8) & 255], 1);
+                ++local;
+            }
         }
     }
     local = __reduce_add_sync(kFull, local);
@@ -1391,6 +1404,13 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
 {
     const int cam = tile < F.n_search_items[0] ? 0 : 1;
     const int t = cam ? tile - F.n_search_items[0] : tile;
+    // the tile's map point records do not depend on the stereo step: ask L2
+    // for them before waiting for it
+    for (int m = t * F.search_tile + (int)threadIdx.x; m < min(F.nm, (t + 1) * F.search_tile); m += kThreads) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(F.pos + m));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(F.mdesc + 2 * m));
+        if (F.search_mode == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(F.nrm + m));
+    }
     bool ok = true;
     if (F.wait_stereo) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
     if (ok) ok = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
@@ -1478,21 +1498,45 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
 
 // ---------------------------------------------------------------- K_RESOLVE
 // Final tables for entries [i0, i1): a map point keeps its keypoint only if
-// it owns it; a keypoint gets its owner (or -1).
+// it owns it; a keypoint gets its owner (or -1).  A thread takes kResolveBatch
+// entries at a time and issues all their loads before any store, so a
+// range's dependent reads (map point -> keypoint -> owner) cost two L2 round
+// trips per batch rather than per entry.
+constexpr int kResolveBatch = 8;
+
 __device__ void resolve_range(const CamDev &C, int nm, int i0, int i1)
 {
-    for (int m = i0 + threadIdx.x; m < min(i1, nm); m += kThreads) {
-        const int k = __ldcg(C.mp_kp + m);
-        if (k >= C.nk) {
-            C.mp_kp[m] = -1;                 // never written by a search item
-        } else if (k >= 0) {
-            const unsigned long long own = __ldcg(C.owner + k);
-            if ((unsigned)(own & 0xffffffffull) != (unsigned)m) C.mp_kp[m] = -1;
+    const int me = min(i1, nm), ke = min(i1, C.nk);
+    for (int m0 = i0 + (int)threadIdx.x; m0 < me; m0 += kThreads * kResolveBatch) {
+        int kk[kResolveBatch];
+#pragma unroll
+        for (int u = 0; u < kResolveBatch; ++u) {
+            const int m = m0 + u * kThreads;
+            kk[u] = m < me ? __ldcg(C.mp_kp + m) : -1;
+        }
+        unsigned own[kResolveBatch];
+#pragma unroll
+        for (int u = 0; u < kResolveBatch; ++u)
+            own[u] = kk[u] >= 0 && kk[u] < C.nk ? (unsigned)(__ldcg(C.owner + kk[u]) & 0xffffffffull) : 0u;
+#pragma unroll
+        for (int u = 0; u < kResolveBatch; ++u) {
+            const int m = m0 + u * kThreads;
+            if (m >= me || kk[u] < 0) continue;
+            if (kk[u] >= C.nk || own[u] != (unsigned)m) C.mp_kp[m] = -1;   // never written / not the owner
         }
     }
-    for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) {
-        const unsigned long long own = __ldcg(C.owner + k);
-        C.kp_mp[k] = own == ~0ull ? -1 : (int)(own & 0xffffffffull);
+    for (int k0 = i0 + (int)threadIdx.x; k0 < ke; k0 += kThreads * kResolveBatch) {
+        unsigned long long own[kResolveBatch];
+#pragma unroll
+        for (int u = 0; u < kResolveBatch; ++u) {
+            const int k = k0 + u * kThreads;
+            own[u] = k < ke ? __ldcg(C.owner + k) : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kResolveBatch; ++u) {
+            const int k = k0 + u * kThreads;
+            if (k < ke) C.kp_mp[k] = own[u] == ~0ull ? -1 : (int)(own[u] & 0xffffffffull);
+        }
     }
 }
 
