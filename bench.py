@@ -349,9 +349,13 @@ def run_profile(args, local_rank):
     print(json.dumps({"profile_run": "ok", "launches": args.warmup + args.steps}), flush=True)
 
 
-def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batch: int, seed: int = 0):
+def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batch: int, seed: int = 0,
+               images: bool = False):
     """Drive the served loop with Poisson arrivals (rate_hz per stream) for
-    `seconds`; returns throughput, latency percentiles and dropped frames."""
+    `seconds`; returns throughput, latency percentiles and dropped frames.
+    images: every pinhole request carries its level-0 images (copied at
+    submit, pyramid rebuilt on the device in the batch) instead of the
+    streams' pyramids being uploaded once."""
     import ctypes as C
 
     from paper_2509_10757_gb300.batch import HostFrame, stream_desc_of
@@ -370,13 +374,13 @@ def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batc
             h = HostFrame(fr)
             sid = C.c_int()
             L.check(L.ft_server_open_stream(srv, C.byref(desc), C.byref(sid)), "open_stream")
-            if fr.camera == "pinhole":
+            if fr.camera == "pinhole" and not images:
                 pl, pr = h.pyramids()
                 L.check(L.ft_server_set_pyramids(srv, sid.value, C.byref(pl), C.byref(pr)), "pyramids")
             L.check(L.ft_server_set_map(srv, sid.value, C.byref(h.map_view())), "map")
             hosts.append(h)
             sids.append(sid.value)
-        reqs = [h.request(sid, 0) for h, sid in zip(hosts, sids)]
+        reqs = [h.request(sid, 0, images=images and h.frame.camera == "pinhole") for h, sid in zip(hosts, sids)]
         units = [fr.left.n + fr.map.n for fr in frames]
         rng = np.random.default_rng(seed)
         arrivals = []
@@ -429,7 +433,7 @@ def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batc
     t_first = min((a for _, a, _ in done), default=0.0)
     span = max((t_last - t_first) / 1e6, wall)
     served_units = sum(units[sids.index(sid)] for sid, _, _ in done)
-    return {"value": served_units / span, "unit": UNIT, "offered_hz": rate_hz * len(frames),
+    return {"value": served_units / span, "unit": UNIT, "offered_hz": rate_hz * len(frames), "images": images,
             "completed": len(done), "dropped": dropped[0], "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_batch": stats.frames_launched / max(1, stats.batches),
             "slots": n_slots, "max_batch": max_batch, "seconds": seconds}
@@ -453,6 +457,7 @@ def run_served(args, local_rank, seconds: float = 4.0, streams: int = 256):
     out["served_30hz"] = serve_load(frames, L, 30.0, seconds, n_slots=3, max_batch=64)
     out["plain_30hz"] = serve_load(frames, L, 30.0, seconds, n_slots=1, max_batch=1)
     out["served_120hz"] = serve_load(frames, L, 120.0, seconds, n_slots=3, max_batch=64)
+    out["served_30hz_images"] = serve_load(frames, L, 30.0, seconds, n_slots=3, max_batch=64, images=True)
     return out
 
 

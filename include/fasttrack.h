@@ -434,8 +434,9 @@ ft_status ft_read_trace(ft_ctx *ctx, ft_trace_record *out, int max, int *n);
  * block for its resident state (both pyramids, the local map, the per-frame
  * keypoint block and the result block); a stream that does not fit is
  * refused with FT_EBUSY until others close.  Requests (one frame: keypoints,
- * descriptors, taken flags and pose, all in host memory) are copied into
- * the stream's pinned staging at submit.  A scheduler thread fills free
+ * descriptors, taken flags, pose and optionally the frame's level-0 images,
+ * all in host memory) are copied into the stream's pinned staging at
+ * submit.  A scheduler thread fills free
  * slots -- n_slots contexts, each with its own arena and CUDA stream -- with
  * batches of up to max_batch pending requests in arrival order, at most one
  * per stream and none of a stream whose previous request is still running;
@@ -469,7 +470,16 @@ typedef struct {
     int max_left, max_right, max_map;
 } ft_stream_desc;
 
-/* One frame of a stream (all pointers in host memory; taken may be NULL). */
+/* One frame of a stream (all pointers in host memory; taken may be NULL).
+ * image_left / image_right (pinhole streams; both or neither): this frame's
+ * level-0 images, level_width[0] x level_height[0] bytes with row pitch
+ * image_pitch (>= the width).  They are copied at submit into the stream's
+ * pinned staging; at launch they replace the stream's resident level 0 and
+ * levels 1.. are rebuilt on the device from it in the same batch (as
+ * ft_build_pyramid), so the stream's level sizes must be those of
+ * ft_pyramid_sizes for level 0 under the server's parameters (FT_EINVAL
+ * otherwise).  NULL: the frame uses the resident pyramids as they are (set
+ * by ft_server_set_pyramids or by an earlier frame's images). */
 typedef struct {
     int stream_id;
     uint64_t tag;
@@ -477,6 +487,8 @@ typedef struct {
     const uint8_t *taken_left, *taken_right;
     ft_pose pose;
     float O_right[3];
+    const uint8_t *image_left, *image_right;
+    int image_pitch;
 } ft_request;
 
 /* Host copies of one request's results (valid until the stream's second

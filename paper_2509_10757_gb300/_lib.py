@@ -153,7 +153,8 @@ class ft_stream_desc(C.Structure):
 class ft_request(C.Structure):
     _fields_ = [("stream_id", i32), ("tag", C.c_uint64), ("left", ft_keypoints),
                 ("right", ft_keypoints), ("taken_left", vp), ("taken_right", vp),
-                ("pose", ft_pose), ("O_right", f32 * 3)]
+                ("pose", ft_pose), ("O_right", f32 * 3), ("image_left", vp), ("image_right", vp),
+                ("image_pitch", i32)]
 
 
 class ft_results(C.Structure):

@@ -485,9 +485,14 @@ class HostFrame:
         if frame.camera == "pinhole":
             self.pyr = [[c(x, np.uint8) for x in frame.pyr_left], [c(x, np.uint8) for x in frame.pyr_right]]
 
-    def request(self, sid: int, tag: int) -> L.ft_request:
+    def request(self, sid: int, tag: int, images: bool = False) -> L.ft_request:
+        """The frame as a served request; images: it carries its level-0
+        images (the server rebuilds the pyramid levels on the device)."""
         r = L.ft_request()
         r.stream_id, r.tag = sid, tag
+        if images:
+            a, b = self.pyr[0][0], self.pyr[1][0]
+            r.image_left, r.image_right, r.image_pitch = a.ctypes.data, b.ctypes.data, a.strides[0]
         r.left = L.ft_keypoints(self.frame.left.n, self.lx.ctypes.data, self.ly.ctypes.data,
                                 self.lo.ctypes.data, self.ld.ctypes.data)
         r.right = L.ft_keypoints(self.frame.right.n, self.rx.ctypes.data, self.ry.ctypes.data,

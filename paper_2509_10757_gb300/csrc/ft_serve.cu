@@ -5,8 +5,10 @@
 // device pool of that size and gives each admitted stream a block holding its
 // resident state (both pyramids, the local map, the per-frame keypoint block
 // and the output block).  A request carries one frame's keypoints, taken
-// flags and pose in host memory; submit packs them into the stream's pinned
-// staging buffer.  A scheduler thread fills free slots (a slot = an ft_ctx
+// flags and pose in host memory, and optionally the frame's two level-0
+// images; submit packs them into the stream's pinned staging buffers.  A
+// request with images replaces the resident level 0 at launch, and the batch
+// rebuilds that stream's levels 1.. on the device before it matches.  A scheduler thread fills free slots (a slot = an ft_ctx
 // with its own arena and CUDA stream) with batches of pending requests, at
 // most one per stream, in arrival order: one host-to-device copy per
 // request, one ft_track_batch launch per batch, one device-to-host copy of
@@ -172,6 +174,8 @@ struct StreamState {
     char *h_dyn[2] = {nullptr, nullptr};   // pinned staging of two requests
     int dyn_used[2] = {0, 0};
     char *h_out[2] = {nullptr, nullptr};   // pinned copies of two results
+    char *h_img[2] = {nullptr, nullptr};   // pinned level-0 images of two requests (left, then right;
+                                           // allocated at the first request that carries images)
     int next_out = 0;
     bool in_flight = false;
     int queued = 0;
@@ -180,6 +184,7 @@ struct StreamState {
 struct Request {
     uint64_t tag = 0;
     int sid = -1, buf = 0, nl = 0, nr = 0;
+    bool images = false;           // level-0 images staged in h_img[buf]
     ft_pose pose{};
     float O_right[3] = {0, 0, 0};
     double t_submit = 0;
@@ -323,6 +328,7 @@ ft_frame_job job_of(const StreamState &S, const Request &r)
             j.pyr_left.pitch[l] = j.pyr_right.pitch[l] = (int)level_pitch(d, l);
         }
     }
+    j.build_pyramids = r.images ? 1 : 0;
     j.pose = r.pose;
     for (int i = 0; i < 3; ++i) j.O_right[i] = r.O_right[i];
     j.map = ft_map_view{S.map_n, reinterpret_cast<float *>(S.dev + S.o_pos), reinterpret_cast<float *>(S.dev + S.o_nrm),
@@ -351,6 +357,16 @@ ft_status launch(ft_server *s, Slot &sl)
         const DynLayout D = dyn_layout(r.nl, r.nr);
         if (cudaMemcpyAsync(S.dev + S.o_dyn, S.h_dyn[r.buf], D.bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
             return fail(FT_ECUDA, "server: upload failed");
+        if (r.images) {
+            // the stream's previous request has completed (one in flight per
+            // stream), so its level 0 may be overwritten
+            const size_t b0 = level_pitch(S.desc, 0) * (size_t)S.desc.level_height[0];
+            if (cudaMemcpyAsync(S.dev + S.o_pyrL[0], S.h_img[r.buf], b0, cudaMemcpyHostToDevice, sl.stream) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(S.dev + S.o_pyrR[0], S.h_img[r.buf] + b0, b0, cudaMemcpyHostToDevice, sl.stream) !=
+                    cudaSuccess)
+                return fail(FT_ECUDA, "server: image upload failed");
+        }
         jobs.push_back(job_of(S, r));
     }
     ft_batch b{};
@@ -523,6 +539,7 @@ void ft_server_destroy(ft_server *s)
         for (int b = 0; b < 2; ++b) {
             if (S.h_dyn[b]) cudaFreeHost(S.h_dyn[b]);
             if (S.h_out[b]) cudaFreeHost(S.h_out[b]);
+            if (S.h_img[b]) cudaFreeHost(S.h_img[b]);
         }
     }
     if (s->pool_mem) cudaFree(s->pool_mem);
@@ -600,6 +617,7 @@ ft_status ft_server_close_stream(ft_server *s, int sid)
     for (int b = 0; b < 2; ++b) {
         if (S.h_dyn[b]) cudaFreeHost(S.h_dyn[b]);
         if (S.h_out[b]) cudaFreeHost(S.h_out[b]);
+        if (S.h_img[b]) cudaFreeHost(S.h_img[b]);
     }
     S = StreamState();
     s->stats.streams_open -= 1;
@@ -664,7 +682,10 @@ ft_status ft_server_submit(ft_server *s, const ft_request *req)
     r.nr = req->right.n;
     r.pose = req->pose;
     for (int i = 0; i < 3; ++i) r.O_right[i] = req->O_right[i];
-    char *dst = nullptr;
+    r.images = req->image_left != nullptr || req->image_right != nullptr;
+    char *dst = nullptr, *img = nullptr;
+    int W0 = 0, H0 = 0;
+    size_t lp0 = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (r.sid < 0 || r.sid >= (int)s->streams.size() || !s->streams[r.sid].open)
@@ -672,6 +693,20 @@ ft_status ft_server_submit(ft_server *s, const ft_request *req)
         StreamState &S = s->streams[r.sid];
         if (r.nl < 0 || r.nl > S.desc.max_left || r.nr < 0 || r.nr > S.desc.max_right)
             return fail(FT_EINVAL, "request of %d/%d keypoints exceeds the stream's capacity", r.nl, r.nr);
+        if (r.images) {
+            if (S.desc.camera != FT_CAMERA_PINHOLE) return fail(FT_EINVAL, "stream %d has no pyramids", r.sid);
+            if (!req->image_left || !req->image_right) return fail(FT_EINVAL, "request images: both or neither");
+            W0 = S.desc.level_width[0];
+            H0 = S.desc.level_height[0];
+            if (req->image_pitch < W0) return fail(FT_EINVAL, "image pitch %d below the width %d", req->image_pitch, W0);
+            int w[FT_MAX_LEVELS], h[FT_MAX_LEVELS];
+            if (ft_pyramid_sizes(W0, H0, &s->params, w, h) != FT_OK) return FT_EINVAL;
+            for (int l = 1; l < S.desc.nlevels; ++l)
+                if (w[l] != S.desc.level_width[l] || h[l] != S.desc.level_height[l])
+                    return fail(FT_EINVAL, "stream level %d is %dx%d; built from level 0 it is %dx%d", l,
+                                S.desc.level_width[l], S.desc.level_height[l], w[l], h[l]);
+            lp0 = level_pitch(S.desc, 0);
+        }
         r.buf = -1;
         for (int b = 0; b < 2; ++b)
             if (!S.dyn_used[b]) {
@@ -679,8 +714,14 @@ ft_status ft_server_submit(ft_server *s, const ft_request *req)
                 break;
             }
         if (r.buf < 0) return fail(FT_EBUSY, "stream %d already has two requests waiting", r.sid);
+        if (r.images && !s->dry && !S.h_img[r.buf] &&
+            cudaMallocHost(&S.h_img[r.buf], 2 * lp0 * (size_t)H0) != cudaSuccess) {
+            S.h_img[r.buf] = nullptr;
+            return fail(FT_ENOMEM, "pinned image staging for stream %d could not be allocated", r.sid);
+        }
         S.dyn_used[r.buf] = 1;
         dst = S.h_dyn[r.buf];
+        img = S.h_img[r.buf];
     }
     if (!s->dry) {
         const DynLayout D = dyn_layout(r.nl, r.nr);
@@ -699,6 +740,13 @@ ft_status ft_server_submit(ft_server *s, const ft_request *req)
         else if (r.nl) std::memset(dst + D.tl, 0, (size_t)r.nl);
         if (req->taken_right) cp(D.tr, req->taken_right, (size_t)r.nr);
         else if (r.nr) std::memset(dst + D.tr, 0, (size_t)r.nr);
+        if (r.images) {
+            const uint8_t *src[2] = {req->image_left, req->image_right};
+            for (int k = 0; k < 2; ++k)
+                for (int y = 0; y < H0; ++y)
+                    std::memcpy(img + (size_t)k * lp0 * H0 + (size_t)y * lp0,
+                                src[k] + (size_t)y * (size_t)req->image_pitch, (size_t)W0);
+        }
     }
     r.t_submit = now_us();
     {

@@ -4,7 +4,9 @@ completions instead of GPU work (the failure and timing are made on the
 host).  Checks: admission refuses a stream the budget cannot hold and
 accepts it once another stream closes; a stream's requests complete in
 submit order and never overlap; batches never exceed max_batch and hold at
-most one request per stream; every request completes."""
+most one request per stream; every request completes; requests with level-0
+images are checked at submit (pinhole streams only, both images, a pitch of
+at least the width, stream levels of the sizes the device would build)."""
 import ctypes as C
 import time
 
@@ -133,5 +135,40 @@ def test_every_request_completes_under_load(L, frames):
         assert len(done) == n and len({d[0] for d in done}) == n
         lat = sorted(d[4] - d[2] for d in done)
         assert lat[0] >= 200.0 * 0.9
+    finally:
+        L.ft_server_destroy(s)
+
+
+def test_request_images_are_checked_at_submit(L, frames):
+    import numpy as np
+
+    from paper_2509_10757_gb300.batch import HostFrame, stream_desc_of
+    s = make_server(L)
+    try:
+        pin, fish = frames[0], frames[3]
+        st, sp = open_stream(L, s, pin)
+        assert st == L.FT_OK
+        st, sf = open_stream(L, s, fish)
+        assert st == L.FT_OK
+        bad = stream_desc_of(pin)
+        bad.level_width[3] += 1                      # not the size built from level 0
+        sb = C.c_int(-1)
+        assert L.ft_server_open_stream(s, C.byref(bad), C.byref(sb)) == L.FT_OK
+        hp, hf = HostFrame(pin), HostFrame(fish)
+        img = np.zeros_like(pin.pyr_left[0])
+        r = hp.request(sp, 1, images=True)
+        r.image_right = None                         # one image only
+        assert L.ft_server_submit(s, C.byref(r)) == L.FT_EINVAL
+        r = hp.request(sp, 2, images=True)
+        r.image_pitch = img.shape[1] - 1             # pitch below the width
+        assert L.ft_server_submit(s, C.byref(r)) == L.FT_EINVAL
+        r = hf.request(sf, 3)
+        r.image_left = r.image_right = img.ctypes.data
+        r.image_pitch = img.shape[1]                 # a fisheye stream has no pyramid
+        assert L.ft_server_submit(s, C.byref(r)) == L.FT_EINVAL
+        assert L.ft_server_submit(s, C.byref(hp.request(sb.value, 4, images=True))) == L.FT_EINVAL
+        assert L.ft_server_submit(s, C.byref(hp.request(sb.value, 5))) == L.FT_OK   # no images: accepted
+        assert L.ft_server_submit(s, C.byref(hp.request(sp, 6, images=True))) == L.FT_OK
+        assert sorted(t for t, *_ in drain(L, s, 2)) == [5, 6]
     finally:
         L.ft_server_destroy(s)
