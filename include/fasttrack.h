@@ -298,7 +298,7 @@ typedef struct ft_ctx ft_ctx;
 typedef struct {
     int strip_rows;         /* image rows per pinhole stereo work item */
     int search_tile;        /* map points per search work item (multiple of 256) */
-    int fisheye_tile;       /* left keypoints per fisheye work item (256 or 512) */
+    int fisheye_tile;       /* left keypoints per fisheye work item (64, or 128 for any larger value) */
     int resolve_tile;       /* entries per conflict-resolution item */
     int ctas_per_sm;        /* persistent CTAs per SM (0: occupancy limit) */
 } ft_tuning;

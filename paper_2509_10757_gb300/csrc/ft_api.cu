@@ -163,7 +163,7 @@ ft_tuning default_tuning()
     ft_tuning t{};
     t.strip_rows = 32;
     t.search_tile = 512;
-    t.fisheye_tile = 256;
+    t.fisheye_tile = 128;
     t.resolve_tile = 2048;
     t.ctas_per_sm = 0;
     return t;
@@ -513,7 +513,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 F.fd2 = j.fo.d2;
                 F.fdepth = j.fo.depth;
                 F.fxyz = reinterpret_cast<float4 *>(j.fo.depth ? j.fo.xyz : nullptr);
-                F.fisheye_tile = tune.fisheye_tile >= 512 ? 512 : 256;
+                F.fisheye_tile = tune.fisheye_tile >= kFishTileMax ? kFishTileMax : kFishTileMax / 2;
                 n_stereo = (F.nl + F.fisheye_tile - 1) / F.fisheye_tile;
             }
         }
@@ -1091,7 +1091,7 @@ ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const 
     // delays do not pick the winner.
     const int strips[] = {16, 32, 64};
     const int tiles[] = {256, 512, 1024};
-    const int fish[] = {256, 512};
+    const int fish[] = {64, 128};
     const int occs[] = {ctx->occ, std::max(1, ctx->occ / 2)};
     std::vector<ft_tuning> cand;
     for (int a : strips)

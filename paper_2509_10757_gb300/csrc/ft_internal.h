@@ -28,6 +28,7 @@ constexpr int kWinRows = 192;                       // rows of a stereo item's s
 constexpr int kOctBuckets = 8;                      // octaves a staged window separates
 constexpr int kRefineChunk = 64;                    // matches refined per SAD round
 constexpr int kFishChunk = 512;                     // right descriptors staged per chunk
+constexpr int kFishTileMax = 128;                   // left keypoints per fisheye item, at most
 constexpr int kFoldResolveMax = 8192;               // frames up to this size resolve in their last search item
 constexpr int kCounters = 8;                        // per-frame counters (u32)
 constexpr int kRowSortItems = 6;                    // row-sort work items per pinhole frame (3 per side)

@@ -223,10 +223,15 @@ struct SmemGrid {
     int warp_sums[kWarps];
 };
 
+constexpr int kFishGroup = 4;                    // lanes sharing one left keypoint (each scans a quarter)
+constexpr int kFishSlots = kThreads / kFishGroup; // left keypoints per pass
+static_assert(kFishTileMax % kFishSlots == 0, "a fisheye item is a whole number of passes");
+
 struct SmemFish {
     uint4 desc[2 * kFishChunk];
     int idx[kFishChunk];
-    int count;
+    int act[kFishTileMax];   // the item's left keypoints inside the overlap
+    int count, nact;
 };
 
 constexpr int kMedianSmem = 8192;               // left keypoints whose SADs the median keeps on chip
@@ -1135,30 +1140,39 @@ __device__ void triangulate_match(const DevParams &P, const FrameDev &F, int i, 
 __device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U,
                                     int *s_flag)
 {
+    // The item's left keypoints inside the overlap are compacted into a list;
+    // kFishGroup lanes share each one, lane g comparing it with the staged
+    // right overlap descriptors g, g + kFishGroup, ...; the lanes' top-2 keys
+    // (distance << 20 | right index, all distinct) merge by shuffles into the
+    // top-2 of the whole scan.
     SmemFish &S = U.f;
     const DevParams &P = B.p;
     const int tid = threadIdx.x;
-    constexpr int Q = 2;            // left keypoints per thread (fisheye_tile <= 512)
+    const int g = tid & (kFishGroup - 1), slot = tid / kFishGroup;
+    const int i0 = tile * F.fisheye_tile, i1 = min(F.nl, i0 + F.fisheye_tile);
+    if (tid == 0) S.nact = 0;
+    __syncthreads();
+    for (int i = i0 + tid; i < i1; i += kThreads) {
+        const float x = __ldg(F.lx + i);
+        if (x >= F.lap_l0 && x <= F.lap_l1) S.act[atomicAdd(&S.nact, 1)] = i;
+    }
+    __syncthreads();
+    const int nact = S.nact;
+    constexpr int Q = kFishTileMax / kFishSlots;    // passes: left keypoints per lane group
     int idx[Q];
-    bool act[Q];
     uint4 a0[Q], a1[Q];
     unsigned best[Q], second[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        idx[q] = tile * F.fisheye_tile + q * kThreads + tid;
-        act[q] = false;
+        const int a = q * kFishSlots + slot;
+        idx[q] = a < nact ? S.act[a] : -1;
         best[q] = second[q] = kNoKey;
-        if (q * kThreads < F.fisheye_tile && idx[q] < F.nl) {
-            const float x = __ldg(F.lx + idx[q]);
-            act[q] = x >= F.lap_l0 && x <= F.lap_l1;
-            if (act[q]) {
-                a0[q] = __ldg(F.ldesc + 2 * idx[q]);
-                a1[q] = __ldg(F.ldesc + 2 * idx[q] + 1);
-            }
+        if (idx[q] >= 0) {
+            a0[q] = __ldg(F.ldesc + 2 * idx[q]);
+            a1[q] = __ldg(F.ldesc + 2 * idx[q] + 1);
         }
     }
-    const bool any = __syncthreads_or(act[0] || act[1]);
-    if (any) {
+    if (nact > 0) {
         for (int c0 = 0; c0 < F.nr; c0 += kFishChunk) {
             if (tid == 0) S.count = 0;
             __syncthreads();
@@ -1174,14 +1188,13 @@ __device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int
             }
             __syncthreads();
             const int cnt = S.count;
-            if (act[0] || act[1]) {
-                for (int e = 0; e < cnt; ++e) {
+            if (idx[0] >= 0) {
+                for (int e = g; e < cnt; e += kFishGroup) {
                     const uint4 b0 = S.desc[2 * e], b1 = S.desc[2 * e + 1];
                     const unsigned j = (unsigned)S.idx[e];
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        if (act[q]) top2_push(((unsigned)ham8(a0[q], a1[q], b0, b1) << 20) | j, best[q], second[q]);
-                    }
+                    for (int q = 0; q < Q; ++q)
+                        if (idx[q] >= 0) top2_push(((unsigned)ham8(a0[q], a1[q], b0, b1) << 20) | j, best[q], second[q]);
                 }
             }
             __syncthreads();
@@ -1189,18 +1202,35 @@ __device__ void stereo_fisheye_item(const BatchHeader &B, const FrameDev &F, int
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        if (q * kThreads < F.fisheye_tile && idx[q] < F.nl) {
-            int r = -1, d1 = -1, d2 = -1;
-            if (act[q] && best[q] != kNoKey) {
-                d1 = (int)(best[q] >> 20);
+#pragma unroll
+        for (int off = 1; off < kFishGroup; off <<= 1) {
+            const unsigned ob = __shfl_xor_sync(kFull, best[q], off), os = __shfl_xor_sync(kFull, second[q], off);
+            second[q] = min(min(second[q], os), max(best[q], ob));
+            best[q] = min(best[q], ob);
+        }
+        if (idx[q] >= 0 && g == 0) {
+            int r = -1, d2 = 256;
+            const int d1 = best[q] != kNoKey ? (int)(best[q] >> 20) : -1;
+            if (best[q] != kNoKey) {
                 d2 = second[q] != kNoKey ? (int)(second[q] >> 20) : 256;
                 if ((float)d1 < fmul(P.fisheye_ratio, (float)d2)) r = (int)(best[q] & 0xfffffu);
+            } else {
+                d2 = -1;
             }
             F.r_idx[idx[q]] = r;
             F.fd1[idx[q]] = d1;
             F.fd2[idx[q]] = d2;
             if (F.fdepth) triangulate_match(P, F, idx[q], r);
         }
+    }
+    // the item's keypoints outside the overlap: no match
+    for (int i = i0 + tid; i < i1; i += kThreads) {
+        const float x = __ldg(F.lx + i);
+        if (x >= F.lap_l0 && x <= F.lap_l1) continue;
+        F.r_idx[i] = -1;
+        F.fd1[i] = -1;
+        F.fd2[i] = -1;
+        if (F.fdepth) triangulate_match(P, F, i, -1);
     }
     if (signal_count(&F.ctr[C_STEREO_DONE], (unsigned)F.n_stereo_items, s_flag)) {
         if (tid == 0 && !(B.debug_flags & kDebugWithholdStereoReady))
