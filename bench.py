@@ -644,39 +644,70 @@ def run_gpu(args, rank, world, local_rank):
                 "ft_autotune")
     torch.cuda.synchronize(dev)
 
-    def step():
-        run_batch(ctx, pb, stream=stream)
+    # Headline: a stream of batches.  Two contexts, each with its own copy of
+    # the batch's device buffers and its own stream, take alternate launches,
+    # so one launch's CTAs start while the other's last frames finish their
+    # dependency chains (row sort -> strips -> median -> search).  No L2
+    # flush: a launch reads 127 MB of inputs and the two buffer sets alternate
+    # (the same buffers come back after ~270 MB of other traffic, 2x L2).
+    ctx2 = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES, use_graphs=True)
+    pb2 = PackedBatch(frames, device=dev)
+    pb2.upload()
+    stream2 = torch.cuda.Stream(device=dev)
+    L.check(ctx2.lib.ft_set_tuning(ctx2.ptr, C.byref(pb2.batch()), C.byref(best)), "ft_set_tuning")
+    lanes = [(ctx, pb, stream), (ctx2, pb2, stream2)]
 
-    # warm-up (graph capture happens on the first call)
-    for _ in range(args.warmup):
-        step()
+    def step(i):
+        c, bt, st = lanes[i & 1]
+        with torch.cuda.stream(st):
+            run_batch(c, bt, stream=st)
+
+    # warm-up on both lanes (graph capture happens on the first calls)
+    for i in range(max(args.warmup, 2)):
+        step(i)
     torch.cuda.synchronize(dev)
-    assert ctx.sync_status() == 0
+    assert ctx.sync_status() == 0 and ctx2.sync_status() == 0
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local_rank)
-    launches0 = ctx.launches()
+    launches0 = ctx.launches() + ctx2.launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize(dev)
+    t0.record(stream)
+    stream2.wait_event(t0)
     for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(i & 0xff)                  # evict L2 (256 MB write) between steps
-            starts[i].record(stream)
-            step()
-            stops[i].record(stream)
+        step(i)
+    stream.wait_stream(stream2)
+    t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
-    launches = ctx.launches() - launches0
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
-    assert ctx.sync_status() == 0
-    local_s = sum(step_ms) / 1e3
-    job_s = max_over_ranks(local_s, world, dev)
+    launches = ctx.launches() + ctx2.launches() - launches0
+    assert ctx.sync_status() == 0 and ctx2.sync_status() == 0
+    job_s = max_over_ranks(t0.elapsed_time(t1) / 1e3, world, dev)
     units = sum_over_ranks(float(args.steps * (kp_units + mp_units)), world, dev)
     value = units / job_s
     ms_per_step = 1e3 * job_s / args.steps
+
+    # The single launch (one context, one stream, L2 flushed before each
+    # launch, each launch timed alone): the kernel's duration for its
+    # roofline and the launch latency.
+    n_serial = min(args.steps, 2000)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
+    torch.cuda.synchronize(dev)
+    for i in range(n_serial):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)                  # evict L2 (256 MB write) between launches
+            starts[i].record(stream)
+            run_batch(ctx, pb, stream=stream)
+            stops[i].record(stream)
+    torch.cuda.synchronize(dev)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    assert ctx.sync_status() == 0
+    serial_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    serial_units = sum_over_ranks(float(n_serial * (kp_units + mp_units)), world, dev)
 
     # outputs of the last step, for the algorithmic byte count
     pb.download()
@@ -722,11 +753,10 @@ def run_gpu(args, rank, world, local_rank):
     # the host waits for step i-2's results (now in pinned host memory)
     # before it issues step i.  No L2 flush: each step's inputs arrive over
     # the bus, and the two buffer sets (~170 MB touched per step) exceed L2.
-    ctx2 = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES, use_graphs=True)
     L.check(ctx2.lib.ft_set_tuning(ctx2.ptr, C.byref(pbd.batch()), C.byref(best)), "ft_set_tuning")
     pbd2 = PackedBatch(frames, device=dev, device_pyramids=True)
     pbd2.upload()
-    lanes = [(ctx, pbd, stream), (ctx2, pbd2, torch.cuda.Stream(device=dev))]
+    lanes = [(ctx, pbd, stream), (ctx2, pbd2, stream2)]
 
     def e2e_pipelined(n):
         done = [None] * n
@@ -798,8 +828,17 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32/f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_launch": FRAMES, "global_batch": FRAMES * world,
-                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}",
+                   "streams": "two contexts on two streams take alternate launches (each with its own "
+                              "copy of the batch's device buffers)",
+                   "l2": "not flushed in the timed region: inputs larger than L2 (a launch reads 127 MB; "
+                         "the two buffer sets alternate, so a launch's inputs return after ~270 MB of "
+                         "other traffic); the serial form flushes (256 MB write) before every launch",
                    "cuda_graph": True, "tuning": ctx_tuning},
+        "serial": {"value": serial_units / serial_s, "ms_per_launch": statistics.mean(step_ms),
+                   "steps": n_serial,
+                   "form": "one context, one stream, L2 flushed before each launch, each launch timed "
+                           "alone (the kernel duration the roofline uses)"},
         "components": {"stereo_keypoints_per_s": kp_units * world * args.steps / job_s,
                        "map_point_searches_per_s": mp_units * world * args.steps / job_s},
         "latency_ms": {"batch_p50": float(np.percentile(step_ms, 50)),
