@@ -650,11 +650,18 @@ def run_gpu(args, rank, world, local_rank):
     # dependency chains (row sort -> strips -> median -> search).  No L2
     # flush: a launch reads 127 MB of inputs and the two buffer sets alternate
     # (the same buffers come back after ~270 MB of other traffic, 2x L2).
+    # The launch shapes come from the stream autotuner (a candidate is timed
+    # as a run of launches alternating between the two contexts); the single
+    # launch below keeps the shapes of the single-launch autotuner.
     ctx2 = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES, use_graphs=True)
     pb2 = PackedBatch(frames, device=dev)
     pb2.upload()
     stream2 = torch.cuda.Stream(device=dev)
-    L.check(ctx2.lib.ft_set_tuning(ctx2.ptr, C.byref(pb2.batch()), C.byref(best)), "ft_set_tuning")
+    best_stream = L.ft_tuning()
+    L.check(ctx.lib.ft_autotune_stream(ctx.ptr, ctx2.ptr, stream_handle(stream), stream_handle(stream2), None,
+                                       C.byref(pb.batch()), C.byref(pb2.batch()), 3, C.byref(best_stream)),
+            "ft_autotune_stream")
+    torch.cuda.synchronize(dev)
     lanes = [(ctx, pb, stream), (ctx2, pb2, stream2)]
 
     def step(i):
@@ -694,6 +701,9 @@ def run_gpu(args, rank, world, local_rank):
     # launch, each launch timed alone): the kernel's duration for its
     # roofline and the launch latency.
     n_serial = min(args.steps, 2000)
+    L.check(ctx.lib.ft_set_tuning(ctx.ptr, C.byref(pb.batch()), C.byref(best)), "ft_set_tuning")
+    for _ in range(3):
+        run_batch(ctx, pb, stream=stream)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(n_serial)]
     torch.cuda.synchronize(dev)
@@ -739,6 +749,7 @@ def run_gpu(args, rank, world, local_rank):
         return ms
 
     n_e2e = max(3, args.steps // 2)
+    L.check(ctx.lib.ft_set_tuning(ctx.ptr, C.byref(pbd.batch()), C.byref(best)), "ft_set_tuning")
     e2e_run(pbd, 3)
     e2e_ms = e2e_run(pbd, n_e2e)
     e2e_up_ms = e2e_run(pb, n_e2e)
@@ -753,7 +764,8 @@ def run_gpu(args, rank, world, local_rank):
     # the host waits for step i-2's results (now in pinned host memory)
     # before it issues step i.  No L2 flush: each step's inputs arrive over
     # the bus, and the two buffer sets (~170 MB touched per step) exceed L2.
-    L.check(ctx2.lib.ft_set_tuning(ctx2.ptr, C.byref(pbd.batch()), C.byref(best)), "ft_set_tuning")
+    for c in (ctx, ctx2):
+        L.check(c.lib.ft_set_tuning(c.ptr, C.byref(pbd.batch()), C.byref(best_stream)), "ft_set_tuning")
     pbd2 = PackedBatch(frames, device=dev, device_pyramids=True)
     pbd2.upload()
     lanes = [(ctx, pbd, stream), (ctx2, pbd2, stream2)]
@@ -818,8 +830,10 @@ def run_gpu(args, rank, world, local_rank):
     served = None
     if rank == 0 and world == 1 and not args.no_served:
         served = run_served(args, local_rank, seconds=3.0)
-    ctx_tuning = {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
-                  "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm}
+    def tuning_of(t):
+        return {"strip_rows": t.strip_rows, "search_tile": t.search_tile, "fisheye_tile": t.fisheye_tile,
+                "ctas_per_sm": t.ctas_per_sm}
+    ctx_tuning = tuning_of(best_stream)
     ctx.close()
     if rank != 0:
         return
@@ -834,9 +848,10 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "not flushed in the timed region: inputs larger than L2 (a launch reads 127 MB; "
                          "the two buffer sets alternate, so a launch's inputs return after ~270 MB of "
                          "other traffic); the serial form flushes (256 MB write) before every launch",
-                   "cuda_graph": True, "tuning": ctx_tuning},
+                   "cuda_graph": True, "tuning": ctx_tuning,
+                   "tuning_from": "ft_autotune_stream (the serial form: ft_autotune)"},
         "serial": {"value": serial_units / serial_s, "ms_per_launch": statistics.mean(step_ms),
-                   "steps": n_serial,
+                   "steps": n_serial, "tuning": tuning_of(best),
                    "form": "one context, one stream, L2 flushed before each launch, each launch timed "
                            "alone (the kernel duration the roofline uses)"},
         "components": {"stereo_keypoints_per_s": kp_units * world * args.steps / job_s,

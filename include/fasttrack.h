@@ -389,6 +389,19 @@ ft_status ft_track_batch(ft_ctx *ctx, void *stream, const ft_params *params, con
 ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch,
                       int iters, ft_tuning *best);
 
+/* Time candidate launch shapes for a stream of batches and keep the fastest
+ * in both contexts for the batches' bucket.  A candidate runs as a sequence
+ * of launches alternating between context a on stream_a and context b on
+ * stream_b (each with its own arena, so one launch's CTAs start while the
+ * other's last frames finish); its score is the sequence's time divided by
+ * its launches (4 * iters of them, then 16 * iters three times for the four
+ * best).  Shapes that make a single launch short can lose here: longer work
+ * items waste less when another launch fills the tail.  batch_a and batch_b
+ * (for instance two buffer sets of the same frames) must fall in the same
+ * bucket (FT_EINVAL otherwise); *best receives the winner (may be NULL). */
+ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_b, const ft_params *params,
+                             const ft_batch *batch_a, const ft_batch *batch_b, int iters, ft_tuning *best);
+
 /* Set / get the launch shape used for a batch's bucket. */
 ft_status ft_set_tuning(ft_ctx *ctx, const ft_batch *batch, const ft_tuning *t);
 ft_status ft_get_tuning(ft_ctx *ctx, const ft_batch *batch, ft_tuning *t);

@@ -1163,6 +1163,103 @@ ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const 
     return s;
 }
 
+ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_b, const ft_params *params,
+                             const ft_batch *batch_a, const ft_batch *batch_b, int iters, ft_tuning *best)
+{
+    if (!a || !b || !batch_a || !batch_b || a == b) return fail(FT_EINVAL, "ft_autotune_stream: bad argument");
+    if (a->device != b->device) return fail(FT_EINVAL, "ft_autotune_stream: contexts on different devices");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    std::vector<Job> ja, jb;
+    ft_status s = jobs_of_batch(batch_a, ja);
+    if (s != FT_OK) return s;
+    if ((s = jobs_of_batch(batch_b, jb)) != FT_OK) return s;
+    const Bucket bk = bucket_of(ja);
+    const Bucket bk2 = bucket_of(jb);
+    if (bk < bk2 || bk2 < bk) return fail(FT_EINVAL, "ft_autotune_stream: the two batches fall in different buckets");
+    if (iters < 1) iters = 3;
+    cudaStream_t sa = (cudaStream_t)stream_a, sb = (cudaStream_t)stream_b;
+    FT_CUDA(cudaSetDevice(a->device));
+    // the same candidates as ft_autotune; a candidate's score is the time of
+    // a run of launches alternating between the two contexts, divided by the
+    // launches (the form where one launch fills the other's tail)
+    const int occ = std::min(a->occ, b->occ);
+    const int strips[] = {16, 32, 64};
+    const int tiles[] = {256, 512, 1024};
+    const int fish[] = {64, 128};
+    const int occs[] = {occ, std::max(1, occ / 2)};
+    std::vector<ft_tuning> cand;
+    for (int x : strips)
+        for (int y : tiles)
+            for (int z : fish)
+                for (int o : occs) {
+                    ft_tuning t = default_tuning();
+                    t.strip_rows = x;
+                    t.search_tile = y;
+                    t.fisheye_tile = z;
+                    t.ctas_per_sm = o;
+                    cand.push_back(t);
+                }
+    cudaEvent_t e0 = nullptr, e1 = nullptr, eb = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaEventCreate(&eb) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return fail(FT_ECUDA, "autotune: cannot create events");
+    }
+    auto run = [&](const ft_tuning &t, int n, float *per_launch_ms) -> ft_status {
+        ft_status r;
+        if (cudaEventRecord(e0, sa) != cudaSuccess || cudaStreamWaitEvent(sb, e0, 0) != cudaSuccess)
+            return fail(FT_ECUDA, "autotune: event record failed");
+        for (int i = 0; i < n; ++i) {
+            const bool second = (i & 1) != 0;
+            if ((r = submit(second ? b : a, second ? sb : sa, p, second ? jb : ja, &t, false)) != FT_OK) return r;
+        }
+        if (cudaEventRecord(eb, sb) != cudaSuccess || cudaStreamWaitEvent(sa, eb, 0) != cudaSuccess ||
+            cudaEventRecord(e1, sa) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+            return fail(FT_ECUDA, "autotune: event sync failed");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *per_launch_ms = ms / (float)n;
+        return FT_OK;
+    };
+    std::vector<std::pair<float, int>> score;
+    for (size_t k = 0; k < cand.size() && s == FT_OK; ++k) {
+        float ms = 0;
+        if ((s = run(cand[k], 2, &ms)) != FT_OK) break;          // untimed: the first launches of a shape
+        if ((s = run(cand[k], 4 * iters, &ms)) != FT_OK) break;
+        score.push_back({ms, (int)k});
+    }
+    if (s == FT_OK) {
+        // the four best again, in turn, each run four times as long
+        std::sort(score.begin(), score.end());
+        const int top = std::min<int>(4, (int)score.size());
+        std::vector<float> again((size_t)top, 0.0f);
+        for (int round = 0; round < 3 && s == FT_OK; ++round)
+            for (int q = 0; q < top && s == FT_OK; ++q) {
+                float ms = 0;
+                if ((s = run(cand[score[q].second], 16 * iters, &ms)) == FT_OK) again[q] += ms;
+            }
+        if (s == FT_OK) {
+            int win = score[0].second;
+            float win_ms = 1e30f;
+            for (int q = 0; q < top; ++q)
+                if (again[q] < win_ms) {
+                    win_ms = again[q];
+                    win = score[q].second;
+                }
+            a->tuning[bk] = cand[win];
+            b->tuning[bk] = cand[win];
+            if (best) *best = cand[win];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(eb);
+    return s;
+}
+
 ft_status ft_save_tuning(ft_ctx *ctx, const char *path)
 {
     if (!ctx || !path) return fail(FT_EINVAL, "ft_save_tuning: NULL argument");

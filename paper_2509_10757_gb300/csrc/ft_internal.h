@@ -31,7 +31,7 @@ constexpr int kFishChunk = 512;                     // right descriptors staged 
 constexpr int kFishTileMax = 128;                   // left keypoints per fisheye item, at most
 constexpr int kFoldResolveMax = 8192;               // frames up to this size resolve in their last search item
 constexpr int kCounters = 8;                        // per-frame counters (u32)
-constexpr int kRowSortItems = 6;                    // row-sort work items per pinhole frame (3 per side)
+constexpr int kRowSortItems = 4;                    // row-sort work items per pinhole frame (2 per side)
 constexpr int kPyrRows = 16;                        // output rows one pyramid thread walks
 constexpr int kPyrThreads = 256;                    // threads per pyramid block
 

@@ -335,6 +335,47 @@ def test_autotune_and_table_roundtrip(ctx, lib, tmp_path):
         check_frame(out, f, what="tuned")
 
 
+def test_autotune_stream_sets_both_contexts(ctx, lib):
+    # the stream autotuner times candidates as launches alternating between
+    # two contexts; both keep the winner, results are the oracle's, and it
+    # refuses one context twice or batches of different buckets
+    import torch as _t
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch, stream_handle
+    frames = scenes.pinhole_batch(seed=2, n_frames=4)
+    pa, pb2 = PackedBatch(frames), PackedBatch(frames)
+    pa.upload()
+    pb2.upload()
+    ctx2 = Context(arena_bytes=1 << 28, max_frames=8)
+    try:
+        s1, s2 = _t.cuda.Stream(), _t.cuda.Stream()
+        best = lib.ft_tuning()
+        ba, bb = pa.batch(), pb2.batch()
+        lib.check(lib.ft_autotune_stream(ctx.ptr, ctx2.ptr, stream_handle(s1), stream_handle(s2), None,
+                                         C.byref(ba), C.byref(bb), 1, C.byref(best)), "autotune_stream")
+        assert best.strip_rows in (16, 32, 64) and best.search_tile in (256, 512, 1024)
+        for c in (ctx, ctx2):
+            got = lib.ft_tuning()
+            lib.check(lib.ft_get_tuning(c.ptr, C.byref(ba), C.byref(got)), "get")
+            assert (got.strip_rows, got.search_tile, got.fisheye_tile, got.ctas_per_sm) == \
+                (best.strip_rows, best.search_tile, best.fisheye_tile, best.ctas_per_sm)
+        assert lib.ft_autotune_stream(ctx.ptr, ctx.ptr, stream_handle(s1), stream_handle(s2), None,
+                                      C.byref(ba), C.byref(bb), 1, None) == lib.FT_EINVAL
+        other = PackedBatch(scenes.pinhole_batch(seed=3, n_frames=9))
+        other.upload()
+        assert lib.ft_autotune_stream(ctx.ptr, ctx2.ptr, stream_handle(s1), stream_handle(s2), None,
+                                      C.byref(ba), C.byref(other.batch()), 1, None) == lib.FT_EINVAL
+        _t.cuda.synchronize()
+        for c, p in ((ctx, pa), (ctx2, pb2)):
+            p.clear_outputs()
+            run_batch(c, p)
+            p.download()
+            assert c.sync_status() == 0
+            for f in range(len(frames)):
+                check_frame(p, f, what="stream-tuned")
+    finally:
+        ctx2.close()
+
+
 # ---------------------------------------------------------------- failures reported, never trapped
 def test_bounded_wait_reports_timeout_and_context_recovers(lib):
     from paper_2509_10757_gb300.batch import Context
