@@ -1072,6 +1072,29 @@ ft_status ft_get_tuning(ft_ctx *ctx, const ft_batch *batch, ft_tuning *t)
     return FT_OK;
 }
 
+// The launch shapes both autotuners try: strip rows 16/32/64, search tile
+// 256/512/1024, fisheye tile 64/128, all or half of the resident CTAs per SM.
+static std::vector<ft_tuning> tuning_candidates(int occ)
+{
+    const int strips[] = {16, 32, 64};
+    const int tiles[] = {256, 512, 1024};
+    const int fish[] = {64, 128};
+    const int occs[] = {occ, std::max(1, occ / 2)};
+    std::vector<ft_tuning> cand;
+    for (int a : strips)
+        for (int b : tiles)
+            for (int c : fish)
+                for (int o : occs) {
+                    ft_tuning t = default_tuning();
+                    t.strip_rows = a;
+                    t.search_tile = b;
+                    t.fisheye_tile = c;
+                    t.ctas_per_sm = o;
+                    cand.push_back(t);
+                }
+    return cand;
+}
+
 ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch, int iters,
                       ft_tuning *best)
 {
@@ -1089,22 +1112,7 @@ ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const 
     // untimed launch) and ranked by its median; the four best are then
     // re-timed in turn, four times as often, so that clock drift and one-off
     // delays do not pick the winner.
-    const int strips[] = {16, 32, 64};
-    const int tiles[] = {256, 512, 1024};
-    const int fish[] = {64, 128};
-    const int occs[] = {ctx->occ, std::max(1, ctx->occ / 2)};
-    std::vector<ft_tuning> cand;
-    for (int a : strips)
-        for (int b : tiles)
-            for (int c : fish)
-                for (int o : occs) {
-                    ft_tuning t = default_tuning();
-                    t.strip_rows = a;
-                    t.search_tile = b;
-                    t.fisheye_tile = c;
-                    t.ctas_per_sm = o;
-                    cand.push_back(t);
-                }
+    const std::vector<ft_tuning> cand = tuning_candidates(ctx->occ);
     const int slots = 4 * iters;
     std::vector<cudaEvent_t> ev(2 * (size_t)slots, nullptr);
     for (auto &e : ev)
@@ -1184,23 +1192,7 @@ ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_
     // the same candidates as ft_autotune; a candidate's score is the time of
     // a run of launches alternating between the two contexts, divided by the
     // launches (the form where one launch fills the other's tail)
-    const int occ = std::min(a->occ, b->occ);
-    const int strips[] = {16, 32, 64};
-    const int tiles[] = {256, 512, 1024};
-    const int fish[] = {64, 128};
-    const int occs[] = {occ, std::max(1, occ / 2)};
-    std::vector<ft_tuning> cand;
-    for (int x : strips)
-        for (int y : tiles)
-            for (int z : fish)
-                for (int o : occs) {
-                    ft_tuning t = default_tuning();
-                    t.strip_rows = x;
-                    t.search_tile = y;
-                    t.fisheye_tile = z;
-                    t.ctas_per_sm = o;
-                    cand.push_back(t);
-                }
+    const std::vector<ft_tuning> cand = tuning_candidates(std::min(a->occ, b->occ));
     cudaEvent_t e0 = nullptr, e1 = nullptr, eb = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaEventCreate(&eb) != cudaSuccess) {
