@@ -376,6 +376,36 @@ def test_autotune_stream_sets_both_contexts(ctx, lib):
         ctx2.close()
 
 
+def test_two_contexts_overlapping_launches(ctx, lib):
+    # the headline form: two contexts on two streams launch alternately with
+    # no synchronisation between them, so their persistent kernels overlap;
+    # each context's results stay the oracle's
+    import torch as _t
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch
+    fa = scenes.pinhole_batch(seed=6, n_frames=6)
+    fb = scenes.pinhole_batch(seed=7, n_frames=6)
+    pa, pb2 = PackedBatch(fa), PackedBatch(fb)
+    pa.upload()
+    pb2.upload()
+    pa.clear_outputs()
+    pb2.clear_outputs()
+    ctx2 = Context(arena_bytes=1 << 28, max_frames=8, use_graphs=True)
+    try:
+        s1, s2 = _t.cuda.Stream(), _t.cuda.Stream()
+        for i in range(12):
+            c, p, st = (ctx, pa, s1) if i % 2 == 0 else (ctx2, pb2, s2)
+            with _t.cuda.stream(st):
+                run_batch(c, p, stream=st)
+        _t.cuda.synchronize()
+        assert ctx.sync_status() == 0 and ctx2.sync_status() == 0
+        for p, frames in ((pa, fa), (pb2, fb)):
+            p.download()
+            for f in range(len(frames)):
+                check_frame(p, f, what="overlapped")
+    finally:
+        ctx2.close()
+
+
 # ---------------------------------------------------------------- failures reported, never trapped
 def test_bounded_wait_reports_timeout_and_context_recovers(lib):
     from paper_2509_10757_gb300.batch import Context
