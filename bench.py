@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+LANES = 3                       # contexts taking the headline launches in turn
 METRIC = "matched keypoints/sec + map-point searches/sec on 1 GB300; p50/p99 frame latency, served vs plain"
 UNIT = "keypoints+map points/s"
 WORKLOAD = ("batched pinhole stereo + local-map search: 64 frames per fused launch, 752x480, "
@@ -624,7 +625,7 @@ def run_gpu(args, rank, world, local_rank):
     from paper_2509_10757_gb300 import _lib as L
     from paper_2509_10757_gb300 import build as B
     from paper_2509_10757_gb300 import scenes
-    from paper_2509_10757_gb300.batch import (Context, PackedBatch, run_batch, run_search,
+    from paper_2509_10757_gb300.batch import (Context, PackedBatch, autotune_stream, run_batch, run_search,
                                               run_stereo, stream_handle)
 
     torch.cuda.set_device(local_rank)
@@ -644,54 +645,54 @@ def run_gpu(args, rank, world, local_rank):
                 "ft_autotune")
     torch.cuda.synchronize(dev)
 
-    # Headline: a stream of batches.  Two contexts, each with its own copy of
-    # the batch's device buffers and its own stream, take alternate launches,
-    # so one launch's CTAs start while the other's last frames finish their
-    # dependency chains (row sort -> strips -> median -> search).  No L2
-    # flush: a launch reads 127 MB of inputs and the two buffer sets alternate
-    # (the same buffers come back after ~270 MB of other traffic, 2x L2).
-    # The launch shapes come from the stream autotuner (a candidate is timed
-    # as a run of launches alternating between the two contexts); the single
-    # launch below keeps the shapes of the single-launch autotuner.
-    ctx2 = Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES, use_graphs=True)
-    pb2 = PackedBatch(frames, device=dev)
-    pb2.upload()
-    stream2 = torch.cuda.Stream(device=dev)
-    best_stream = L.ft_tuning()
-    L.check(ctx.lib.ft_autotune_stream(ctx.ptr, ctx2.ptr, stream_handle(stream), stream_handle(stream2), None,
-                                       C.byref(pb.batch()), C.byref(pb2.batch()), 3, C.byref(best_stream)),
-            "ft_autotune_stream")
+    # Headline: a stream of batches.  LANES contexts, each with its own copy
+    # of the batch's device buffers and its own stream, take the launches in
+    # turn, so later launches' CTAs start while earlier ones' last frames
+    # finish their dependency chains (row sort -> strips -> median ->
+    # search).  No L2 flush: a launch reads 127 MB of inputs and the buffer
+    # sets take turns (the same buffers come back after ~400 MB of other
+    # traffic, 3x L2).  The launch shapes come from the stream autotuner (a
+    # candidate is timed as a run of launches taken by the contexts in turn);
+    # the single launch below keeps the shapes of the single-launch autotuner.
+    extra = [(Context(device=local_rank, arena_bytes=512 << 20, max_frames=FRAMES, use_graphs=True),
+              PackedBatch(frames, device=dev), torch.cuda.Stream(device=dev)) for _ in range(LANES - 1)]
+    for _, b2, _ in extra:
+        b2.upload()
+    lanes = [(ctx, pb, stream)] + extra
+    ctx2, stream2 = extra[0][0], extra[0][2]
+    best_stream = autotune_stream([c for c, _, _ in lanes], [st for _, _, st in lanes], [b for _, b, _ in lanes])
     torch.cuda.synchronize(dev)
-    lanes = [(ctx, pb, stream), (ctx2, pb2, stream2)]
 
     def step(i):
-        c, bt, st = lanes[i & 1]
+        c, bt, st = lanes[i % LANES]
         with torch.cuda.stream(st):
             run_batch(c, bt, stream=st)
 
-    # warm-up on both lanes (graph capture happens on the first calls)
-    for i in range(max(args.warmup, 2)):
+    # warm-up on every lane (graph capture happens on the first calls)
+    for i in range(max(args.warmup, LANES)):
         step(i)
     torch.cuda.synchronize(dev)
-    assert ctx.sync_status() == 0 and ctx2.sync_status() == 0
+    assert all(c.sync_status() == 0 for c, _, _ in lanes)
 
     clocks = ClockSampler(local_rank)
-    launches0 = ctx.launches() + ctx2.launches()
+    launches0 = sum(c.launches() for c, _, _ in lanes)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize(dev)
     t0.record(stream)
-    stream2.wait_event(t0)
+    for _, _, st in extra:
+        st.wait_event(t0)
     for i in range(args.steps):
         step(i)
-    stream.wait_stream(stream2)
+    for _, _, st in extra:
+        stream.wait_stream(st)
     t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
-    launches = ctx.launches() + ctx2.launches() - launches0
-    assert ctx.sync_status() == 0 and ctx2.sync_status() == 0
+    launches = sum(c.launches() for c, _, _ in lanes) - launches0
+    assert all(c.sync_status() == 0 for c, _, _ in lanes)
     job_s = max_over_ranks(t0.elapsed_time(t1) / 1e3, world, dev)
     units = sum_over_ranks(float(args.steps * (kp_units + mp_units)), world, dev)
     value = units / job_s
@@ -795,7 +796,8 @@ def run_gpu(args, rank, world, local_rank):
     pipe_s = max_over_ranks(e2e_pipelined(n_pipe) / 1e3, world, dev)
     pipe_units = sum_over_ranks(float(n_pipe * (kp_units + mp_units)), world, dev)
     assert ctx2.sync_status() == 0
-    ctx2.close()
+    for c, _, _ in extra:
+        c.close()
 
     # the device-resident launch with the pyramids built on the device first
     pyr_ms = []
@@ -843,11 +845,12 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32/f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_launch": FRAMES, "global_batch": FRAMES * world,
                    "parallelism": f"replicas x{world}",
-                   "streams": "two contexts on two streams take alternate launches (each with its own "
-                              "copy of the batch's device buffers)",
+                   "streams": f"{LANES} contexts on {LANES} streams take the launches in turn (each with its "
+                              "own copy of the batch's device buffers)",
                    "l2": "not flushed in the timed region: inputs larger than L2 (a launch reads 127 MB; "
-                         "the two buffer sets alternate, so a launch's inputs return after ~270 MB of "
-                         "other traffic); the serial form flushes (256 MB write) before every launch",
+                         f"the {LANES} buffer sets take turns, so a launch's inputs return after "
+                         f"~{135 * (LANES - 1)} MB of other traffic); the serial form flushes (256 MB write) "
+                         "before every launch",
                    "cuda_graph": True, "tuning": ctx_tuning,
                    "tuning_from": "ft_autotune_stream (the serial form: ft_autotune)"},
         "serial": {"value": serial_units / serial_s, "ms_per_launch": statistics.mean(step_ms),

@@ -385,22 +385,26 @@ ft_status ft_build_pyramid(ft_ctx *ctx, void *stream, const ft_params *params, c
 ft_status ft_track_batch(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch);
 
 /* Time candidate launch shapes on this batch (iters runs each) and keep the
- * fastest for the batch's bucket; *best receives it (may be NULL). */
+ * fastest for the batch's bucket; *best receives it (may be NULL).  The
+ * candidates: strip rows 16/32/64, search tile 256/512/1024, fisheye tile
+ * 64/128, every count of CTAs per SM up to the resident maximum. */
 ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch,
                       int iters, ft_tuning *best);
 
 /* Time candidate launch shapes for a stream of batches and keep the fastest
- * in both contexts for the batches' bucket.  A candidate runs as a sequence
- * of launches alternating between context a on stream_a and context b on
- * stream_b (each with its own arena, so one launch's CTAs start while the
- * other's last frames finish); its score is the sequence's time divided by
- * its launches (4 * iters of them, then 16 * iters three times for the four
- * best).  Shapes that make a single launch short can lose here: longer work
- * items waste less when another launch fills the tail.  batch_a and batch_b
- * (for instance two buffer sets of the same frames) must fall in the same
- * bucket (FT_EINVAL otherwise); *best receives the winner (may be NULL). */
-ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_b, const ft_params *params,
-                             const ft_batch *batch_a, const ft_batch *batch_b, int iters, ft_tuning *best);
+ * in every context for the batches' bucket.  A candidate runs as a sequence
+ * of launches taken by the n contexts in turn, context i on streams[i] with
+ * batches[i] (each context with its own arena and each batch with its own
+ * buffers, so later launches start while earlier ones' last frames finish);
+ * its score is the sequence's time divided by its launches (4 * iters * n of
+ * them, then 16 * iters * n three times for the four best).  Shapes that
+ * make a single launch short can lose here: longer work items waste less
+ * when another launch fills the tail, and fewer CTAs per SM leave room for
+ * the next launch.  2 <= n <= 16 distinct contexts on one device; every batch
+ * must fall in the same bucket (FT_EINVAL otherwise); *best receives the
+ * winner (may be NULL). */
+ft_status ft_autotune_stream(ft_ctx *const *ctxs, void *const *streams, int n, const ft_params *params,
+                             const ft_batch *const *batches, int iters, ft_tuning *best);
 
 /* Set / get the launch shape used for a batch's bucket. */
 ft_status ft_set_tuning(ft_ctx *ctx, const ft_batch *batch, const ft_tuning *t);

@@ -198,8 +198,8 @@ SIGNATURES = [
     ("ft_track_batch", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch)]),
     ("ft_autotune", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch), i32,
                           C.POINTER(ft_tuning)]),
-    ("ft_autotune_stream", i32, [vp, vp, vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch), C.POINTER(ft_batch), i32,
-                                 C.POINTER(ft_tuning)]),
+    ("ft_autotune_stream", i32, [C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(ft_params),
+                                 C.POINTER(C.POINTER(ft_batch)), i32, C.POINTER(ft_tuning)]),
     ("ft_set_tuning", i32, [vp, C.POINTER(ft_batch), C.POINTER(ft_tuning)]),
     ("ft_get_tuning", i32, [vp, C.POINTER(ft_batch), C.POINTER(ft_tuning)]),
     ("ft_save_tuning", i32, [vp, C.c_char_p]),

@@ -447,6 +447,20 @@ def run_batch(ctx: Context, pb: PackedBatch, params: L.ft_params | None = None, 
             "ft_track_batch")
 
 
+def autotune_stream(ctxs, streams, pbs, iters: int = 3, params: L.ft_params | None = None) -> L.ft_tuning:
+    """ft_autotune_stream over the contexts, streams and batches given in
+    turn; returns the chosen launch shape (kept in every context)."""
+    n = len(ctxs)
+    cs = (C.c_void_p * n)(*[c.ptr for c in ctxs])
+    ss = (C.c_void_p * n)(*[stream_handle(s).value for s in streams])
+    keep = [pb.batch() for pb in pbs]
+    bs = (C.POINTER(L.ft_batch) * n)(*[C.pointer(b) for b in keep])
+    best = L.ft_tuning()
+    p = C.byref(params) if params is not None else None
+    L.check(ctxs[0].lib.ft_autotune_stream(cs, ss, n, p, bs, iters, C.byref(best)), "ft_autotune_stream")
+    return best
+
+
 # ---------------------------------------------------------------- served loop marshalling
 def stream_desc_of(frame, slack: float = 1.0) -> L.ft_stream_desc:
     """Stream description for frames shaped like `frame` (capacities scaled by slack)."""

@@ -1073,13 +1073,15 @@ ft_status ft_get_tuning(ft_ctx *ctx, const ft_batch *batch, ft_tuning *t)
 }
 
 // The launch shapes both autotuners try: strip rows 16/32/64, search tile
-// 256/512/1024, fisheye tile 64/128, all or half of the resident CTAs per SM.
+// 256/512/1024, fisheye tile 64/128, and every count of CTAs per SM from the
+// resident maximum down to one (fewer leave room for a concurrent launch).
 static std::vector<ft_tuning> tuning_candidates(int occ)
 {
     const int strips[] = {16, 32, 64};
     const int tiles[] = {256, 512, 1024};
     const int fish[] = {64, 128};
-    const int occs[] = {occ, std::max(1, occ / 2)};
+    std::vector<int> occs;
+    for (int o = std::max(1, occ); o >= 1; --o) occs.push_back(o);
     std::vector<ft_tuning> cand;
     for (int a : strips)
         for (int b : tiles)
@@ -1171,56 +1173,71 @@ ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const 
     return s;
 }
 
-ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_b, const ft_params *params,
-                             const ft_batch *batch_a, const ft_batch *batch_b, int iters, ft_tuning *best)
+ft_status ft_autotune_stream(ft_ctx *const *ctxs, void *const *streams, int n, const ft_params *params,
+                             const ft_batch *const *batches, int iters, ft_tuning *best)
 {
-    if (!a || !b || !batch_a || !batch_b || a == b) return fail(FT_EINVAL, "ft_autotune_stream: bad argument");
-    if (a->device != b->device) return fail(FT_EINVAL, "ft_autotune_stream: contexts on different devices");
+    if (!ctxs || !streams || !batches || n < 2 || n > 16) return fail(FT_EINVAL, "ft_autotune_stream: bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !batches[i]) return fail(FT_EINVAL, "ft_autotune_stream: NULL context or batch %d", i);
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(FT_EINVAL, "ft_autotune_stream: contexts on different devices");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return fail(FT_EINVAL, "ft_autotune_stream: context %d given twice", i);
+    }
     ft_params p;
     if (params) p = *params;
     else ft_params_default(&p);
-    std::vector<Job> ja, jb;
-    ft_status s = jobs_of_batch(batch_a, ja);
+    std::vector<std::vector<Job>> jobs((size_t)n);
+    ft_status s = FT_OK;
+    for (int i = 0; i < n && s == FT_OK; ++i) s = jobs_of_batch(batches[i], jobs[(size_t)i]);
     if (s != FT_OK) return s;
-    if ((s = jobs_of_batch(batch_b, jb)) != FT_OK) return s;
-    const Bucket bk = bucket_of(ja);
-    const Bucket bk2 = bucket_of(jb);
-    if (bk < bk2 || bk2 < bk) return fail(FT_EINVAL, "ft_autotune_stream: the two batches fall in different buckets");
-    if (iters < 1) iters = 3;
-    cudaStream_t sa = (cudaStream_t)stream_a, sb = (cudaStream_t)stream_b;
-    FT_CUDA(cudaSetDevice(a->device));
-    // the same candidates as ft_autotune; a candidate's score is the time of
-    // a run of launches alternating between the two contexts, divided by the
-    // launches (the form where one launch fills the other's tail)
-    const std::vector<ft_tuning> cand = tuning_candidates(std::min(a->occ, b->occ));
-    cudaEvent_t e0 = nullptr, e1 = nullptr, eb = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
-        cudaEventCreate(&eb) != cudaSuccess) {
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
-        return fail(FT_ECUDA, "autotune: cannot create events");
+    const Bucket bk = bucket_of(jobs[0]);
+    int occ = ctxs[0]->occ;
+    for (int i = 1; i < n; ++i) {
+        const Bucket bi = bucket_of(jobs[(size_t)i]);
+        if (bk < bi || bi < bk) return fail(FT_EINVAL, "ft_autotune_stream: batches fall in different buckets");
+        occ = std::min(occ, ctxs[i]->occ);
     }
-    auto run = [&](const ft_tuning &t, int n, float *per_launch_ms) -> ft_status {
-        ft_status r;
-        if (cudaEventRecord(e0, sa) != cudaSuccess || cudaStreamWaitEvent(sb, e0, 0) != cudaSuccess)
-            return fail(FT_ECUDA, "autotune: event record failed");
-        for (int i = 0; i < n; ++i) {
-            const bool second = (i & 1) != 0;
-            if ((r = submit(second ? b : a, second ? sb : sa, p, second ? jb : ja, &t, false)) != FT_OK) return r;
+    if (iters < 1) iters = 3;
+    FT_CUDA(cudaSetDevice(ctxs[0]->device));
+    // the same candidates as ft_autotune; a candidate's score is the time of
+    // a run of launches taken by the contexts in turn, divided by the
+    // launches (the form where later launches fill earlier ones' tails)
+    const std::vector<ft_tuning> cand = tuning_candidates(occ);
+    std::vector<cudaEvent_t> ev((size_t)n + 1, nullptr);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(FT_ECUDA, "autotune: cannot create events");
         }
-        if (cudaEventRecord(eb, sb) != cudaSuccess || cudaStreamWaitEvent(sa, eb, 0) != cudaSuccess ||
-            cudaEventRecord(e1, sa) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+    cudaStream_t s0 = (cudaStream_t)streams[0];
+    auto run = [&](const ft_tuning &t, int launches, float *per_launch_ms) -> ft_status {
+        ft_status r;
+        if (cudaEventRecord(ev[0], s0) != cudaSuccess) return fail(FT_ECUDA, "autotune: event record failed");
+        for (int i = 1; i < n; ++i)
+            if (cudaStreamWaitEvent((cudaStream_t)streams[i], ev[0], 0) != cudaSuccess)
+                return fail(FT_ECUDA, "autotune: stream wait failed");
+        for (int i = 0; i < launches; ++i) {
+            const int c = i % n;
+            if ((r = submit(ctxs[c], (cudaStream_t)streams[c], p, jobs[(size_t)c], &t, false)) != FT_OK) return r;
+        }
+        for (int i = 1; i < n; ++i)
+            if (cudaEventRecord(ev[(size_t)i], (cudaStream_t)streams[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(s0, ev[(size_t)i], 0) != cudaSuccess)
+                return fail(FT_ECUDA, "autotune: event record failed");
+        if (cudaEventRecord(ev[(size_t)n], s0) != cudaSuccess || cudaEventSynchronize(ev[(size_t)n]) != cudaSuccess)
             return fail(FT_ECUDA, "autotune: event sync failed");
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        *per_launch_ms = ms / (float)n;
+        cudaEventElapsedTime(&ms, ev[0], ev[(size_t)n]);
+        *per_launch_ms = ms / (float)launches;
         return FT_OK;
     };
     std::vector<std::pair<float, int>> score;
     for (size_t k = 0; k < cand.size() && s == FT_OK; ++k) {
         float ms = 0;
-        if ((s = run(cand[k], 2, &ms)) != FT_OK) break;          // untimed: the first launches of a shape
-        if ((s = run(cand[k], 4 * iters, &ms)) != FT_OK) break;
+        if ((s = run(cand[k], n, &ms)) != FT_OK) break;              // untimed: the first launches of a shape
+        if ((s = run(cand[k], 4 * iters * n, &ms)) != FT_OK) break;
         score.push_back({ms, (int)k});
     }
     if (s == FT_OK) {
@@ -1231,7 +1248,7 @@ ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_
         for (int round = 0; round < 3 && s == FT_OK; ++round)
             for (int q = 0; q < top && s == FT_OK; ++q) {
                 float ms = 0;
-                if ((s = run(cand[score[q].second], 16 * iters, &ms)) == FT_OK) again[q] += ms;
+                if ((s = run(cand[score[q].second], 16 * iters * n, &ms)) == FT_OK) again[q] += ms;
             }
         if (s == FT_OK) {
             int win = score[0].second;
@@ -1241,14 +1258,11 @@ ft_status ft_autotune_stream(ft_ctx *a, ft_ctx *b, void *stream_a, void *stream_
                     win_ms = again[q];
                     win = score[q].second;
                 }
-            a->tuning[bk] = cand[win];
-            b->tuning[bk] = cand[win];
+            for (int i = 0; i < n; ++i) ctxs[i]->tuning[bk] = cand[win];
             if (best) *best = cand[win];
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(eb);
+    for (auto &e : ev) cudaEventDestroy(e);
     return s;
 }
 

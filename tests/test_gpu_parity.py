@@ -335,37 +335,45 @@ def test_autotune_and_table_roundtrip(ctx, lib, tmp_path):
         check_frame(out, f, what="tuned")
 
 
-def test_autotune_stream_sets_both_contexts(ctx, lib):
-    # the stream autotuner times candidates as launches alternating between
-    # two contexts; both keep the winner, results are the oracle's, and it
-    # refuses one context twice or batches of different buckets
+def test_autotune_stream_sets_every_context(ctx, lib):
+    # the stream autotuner times candidates as launches taken in turn by
+    # three contexts; each keeps the winner, results are the oracle's, and it
+    # refuses a context given twice, fewer than two, or batches of different
+    # buckets
     import torch as _t
-    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch, stream_handle
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, autotune_stream, run_batch, stream_handle
     frames = scenes.pinhole_batch(seed=2, n_frames=4)
-    pa, pb2 = PackedBatch(frames), PackedBatch(frames)
-    pa.upload()
-    pb2.upload()
-    ctx2 = Context(arena_bytes=1 << 28, max_frames=8)
+    pbs = [PackedBatch(frames) for _ in range(3)]
+    for p in pbs:
+        p.upload()
+    extra = [Context(arena_bytes=1 << 28, max_frames=8) for _ in range(2)]
+    ctxs = [ctx] + extra
     try:
-        s1, s2 = _t.cuda.Stream(), _t.cuda.Stream()
-        best = lib.ft_tuning()
-        ba, bb = pa.batch(), pb2.batch()
-        lib.check(lib.ft_autotune_stream(ctx.ptr, ctx2.ptr, stream_handle(s1), stream_handle(s2), None,
-                                         C.byref(ba), C.byref(bb), 1, C.byref(best)), "autotune_stream")
+        streams = [_t.cuda.Stream() for _ in range(3)]
+        best = autotune_stream(ctxs, streams, pbs, iters=1)
         assert best.strip_rows in (16, 32, 64) and best.search_tile in (256, 512, 1024)
-        for c in (ctx, ctx2):
+        assert 1 <= best.ctas_per_sm <= 3
+        ba = pbs[0].batch()
+        for c in ctxs:
             got = lib.ft_tuning()
             lib.check(lib.ft_get_tuning(c.ptr, C.byref(ba), C.byref(got)), "get")
             assert (got.strip_rows, got.search_tile, got.fisheye_tile, got.ctas_per_sm) == \
                 (best.strip_rows, best.search_tile, best.fisheye_tile, best.ctas_per_sm)
-        assert lib.ft_autotune_stream(ctx.ptr, ctx.ptr, stream_handle(s1), stream_handle(s2), None,
-                                      C.byref(ba), C.byref(bb), 1, None) == lib.FT_EINVAL
+
+        def call(cs, ps):
+            n = len(cs)
+            keep = [p.batch() for p in ps]
+            return lib.ft_autotune_stream((C.c_void_p * n)(*[c.ptr for c in cs]),
+                                          (C.c_void_p * n)(*[stream_handle(st).value for st in streams[:n]]), n,
+                                          None, (C.POINTER(lib.ft_batch) * n)(*[C.pointer(b) for b in keep]), 1,
+                                          None)
+        assert call([ctx, ctx], pbs[:2]) == lib.FT_EINVAL
+        assert call([ctx], pbs[:1]) == lib.FT_EINVAL
         other = PackedBatch(scenes.pinhole_batch(seed=3, n_frames=9))
         other.upload()
-        assert lib.ft_autotune_stream(ctx.ptr, ctx2.ptr, stream_handle(s1), stream_handle(s2), None,
-                                      C.byref(ba), C.byref(other.batch()), 1, None) == lib.FT_EINVAL
+        assert call([ctx, extra[0]], [pbs[0], other]) == lib.FT_EINVAL
         _t.cuda.synchronize()
-        for c, p in ((ctx, pa), (ctx2, pb2)):
+        for c, p in zip(ctxs, pbs):
             p.clear_outputs()
             run_batch(c, p)
             p.download()
@@ -373,7 +381,8 @@ def test_autotune_stream_sets_both_contexts(ctx, lib):
             for f in range(len(frames)):
                 check_frame(p, f, what="stream-tuned")
     finally:
-        ctx2.close()
+        for c in extra:
+            c.close()
 
 
 def test_two_contexts_overlapping_launches(ctx, lib):
