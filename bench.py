@@ -888,7 +888,12 @@ def run_gpu(args, rank, world, local_rank):
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "ft_fused_kernel"},
+                     "kernel": "ft_fused_kernel",
+                     "duration": "mean CUDA-event time of a single launch timed alone (the serial form)",
+                     "stream": {"achieved": alg_bytes / (job_s / args.steps) / 1e9,
+                                "frac": alg_bytes / (job_s / args.steps) / 1e9 / peaks["hbm_gbs"],
+                                "duration": "the headline's timed region divided by its launches "
+                                            "(launches overlap)"}},
         "gpu_launches": launches,
         "clocks": clk,
     }
