@@ -211,6 +211,32 @@ def test_parameter_variants(ctx, lib, overrides):
 
 
 # ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_randomized_batches(ctx, lib, seed):
+    # seeded random ragged batches: pinhole images from 64x48 to 1280x720
+    # (multiples of 16), 0-3000 left keypoints with 0-50 % distractors, 0-6000
+    # map points, descriptor flip rates up to 15 %, a quarter fisheye frames
+    # with 20-90 % overlap, and one parameter set per batch; every frame
+    # equals the oracle's result for it alone
+    rng = np.random.default_rng(900 + seed)
+    frames = []
+    for _ in range(10):
+        if rng.random() < 0.25:
+            frames.append(scenes.fisheye_frame(int(rng.integers(1 << 30)), n_left=int(rng.integers(0, 2500)),
+                                               overlap_frac=float(rng.uniform(0.2, 0.9)),
+                                               flip_p=float(rng.uniform(0, 0.15)), n_map=int(rng.integers(0, 6000))))
+        else:
+            W, H = int(rng.integers(4, 81)) * 16, int(rng.integers(3, 46)) * 16
+            frames.append(scenes.pinhole_frame(int(rng.integers(1 << 30)), W=W, H=H,
+                                               n_left=int(rng.integers(0, 3000)),
+                                               distractor_frac=float(rng.uniform(0, 0.5)),
+                                               flip_p=float(rng.uniform(0, 0.15)), n_map=int(rng.integers(0, 6000))))
+    overrides = [{}, {"search_th": 2.0}, {"ratio_any_octave": 1}, {"th_stereo": 50, "th_search": 80}][seed]
+    out = run_fused(ctx, frames, params=overrides, lib=lib)
+    for f in range(len(frames)):
+        check_frame(out, f, params=overrides, what=f"random batch {seed}")
+
+
 def _shrink(fr, nl=None, nr=None, m=None):
     fr = dataclasses.replace(fr)
     def cut(k, n):
