@@ -1813,30 +1813,15 @@ __device__ __forceinline__ void pyr_band(const uint8_t *__restrict__ src, int sp
     const int left = w - 4 * q;
     const unsigned mask = left >= 4 ? 0xffffffffu : (1u << (8 * left)) - 1u;
     const f32x2 rnd = f2_splat(kRound23);
-    float top[4] = {0.0f, 0.0f, 0.0f, 0.0f}, bot[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    int cy0 = -1, cy1 = -1;
+    // Rows in pairs: the two register arrays swap roles, so the new bottom
+    // row's interpolation always goes into the array whose contents are dead,
+    // and the top row is the previous bottom row unless it was skipped (then
+    // it is interpolated in place): no copies between the arrays.
+    float ha[4], hb[4];
+    int cy1 = -1;
     const int ya = band * kPyrRows, yb = min(h, ya + kPyrRows);
     uint8_t *out = dst + 4 * q;
-    for (int y = ya; y < yb; ++y) {
-        int y0, y1;
-        float fy, gy;
-        pyr_row(y, sy, H, y0, y1, fy, gy);
-        if (y0 != cy0) {
-            if (y0 == cy1) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) top[j] = bot[j];
-            } else {
-                pyr_hrow<NW>((size_t)y0 * sp, C, top);
-            }
-        }
-        if (y1 == y0) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bot[j] = top[j];
-        } else if (y1 != cy1) {
-            pyr_hrow<NW>((size_t)y1 * sp, C, bot);
-        }
-        cy0 = y0;
-        cy1 = y1;
+    auto emit = [&](int y, const float (&top)[4], const float (&bot)[4], float fy, float gy) {
         float v[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[j] = fadd(fmul(top[j], gy), fmul(bot[j], fy));
@@ -1845,6 +1830,23 @@ __device__ __forceinline__ void pyr_band(const uint8_t *__restrict__ src, int sp
         f2_unpack(f2_add(f2_pack(__float_as_uint(v[2]), __float_as_uint(v[3])), rnd), r2, r3);
         const unsigned word = __byte_perm(__byte_perm(r0, r1, 0x0040), __byte_perm(r2, r3, 0x0040), 0x5410);
         *reinterpret_cast<unsigned *>(out + (size_t)y * dp) = word & mask;
+    };
+    for (int y = ya; y < yb; y += 2) {
+        int y0, y1;
+        float fy, gy;
+        // even row: top in ha, bottom into hb
+        pyr_row(y, sy, H, y0, y1, fy, gy);
+        pyr_hrow<NW>((size_t)y1 * sp, C, hb);
+        if (y0 != cy1) pyr_hrow<NW>((size_t)y0 * sp, C, ha);
+        cy1 = y1;
+        emit(y, ha, hb, fy, gy);
+        if (y + 1 >= yb) break;
+        // odd row: top in hb, bottom into ha
+        pyr_row(y + 1, sy, H, y0, y1, fy, gy);
+        pyr_hrow<NW>((size_t)y1 * sp, C, ha);
+        if (y0 != cy1) pyr_hrow<NW>((size_t)y0 * sp, C, hb);
+        cy1 = y1;
+        emit(y + 1, hb, ha, fy, gy);
     }
 }
 
