@@ -20,6 +20,10 @@
  *     a10 a keypoint claimed by several map points keeps the smallest
  *         (distance, map point index); map points are searched independently
  *         as the paper states (section IV-E).
+ *   and the next steps around them:
+ *     f1  triangulation of the fisheye matches (section II-B)
+ *     f2  search by projection of the last frame's points (sections II-C, IV-E)
+ *     f3  the image pyramid built from level 0 (section IV-B)
  * The paper prints none of the constants; each is a parameter (orc_params).
  */
 #include "ft_oracle.h"
@@ -516,8 +520,8 @@ int orc_project_kb8(const orc_params *p, const orc_kb8 *cam, const float *R, con
 }
 
 /* ------------------------------------------------------------------------ */
-/* f1: fisheye triangulation.  The paper matches fisheye keypoints "to       */
-/* calculate depth" (section II-B) and says nothing more; the reading here:  */
+/* f1: fisheye triangulation.  The paper says only that stereo matches      */
+/* serve to compute depth (section II-B); the reading here:                 */
 /*  - unprojection of a Kannala-Brandt pixel: m = ((u-cx)/fx, (v-cy)/fy),    */
 /*    theta_d = |m|; theta solves theta*(1+k1 t+k2 t^2+k3 t^3+k4 t^4) =      */
 /*    theta_d (t = theta^2) by kb_iters Newton steps from theta = theta_d,   */
