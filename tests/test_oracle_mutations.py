@@ -75,6 +75,7 @@ MUTANTS = [
     ("pyr_no_y_weight", "const float fy = ys - (float)y0;", "const float fy = 0.0f;"),
     ("pyr_size_floor", "w[l] = (int)roundf((float)W / sc[l]);", "w[l] = (int)((float)W / sc[l]);"),
     ("pyr_round_floor", "float v = rintf(top * (1.0f - fy) + bot * fy);", "float v = floorf(top * (1.0f - fy) + bot * fy);"),
+    ("pyr_fused_vertical", "float v = rintf(top * (1.0f - fy) + bot * fy);", "float v = rintf(fmaf(top, 1.0f - fy, bot * fy));"),
     ("last_view_distance", "        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;",
      "        if (Pc[2] > 8.0f) continue;\n        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;"),
 ]
