@@ -221,6 +221,43 @@ def time_oracle(frames, budget_s: float) -> dict:
                       f"single thread, {dt:.1f} s"}
 
 
+def _oracle_share(share):
+    """One process of the all-cores oracle timing: its share of the frames,
+    cycled until the time budget runs out."""
+    frames, budget_s = share
+    import oracle as orc
+    from paper_2509_10757_gb300.scenes import DEFAULT_PARAMS
+    p = dict(DEFAULT_PARAMS)
+    units, done = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        fr = frames[done % len(frames)]
+        orc.track_frame(p, fr)
+        units += fr.left.n + fr.map.n
+        done += 1
+    return units, done, time.perf_counter() - t0
+
+
+def time_oracle_all_cores(frames, budget_s: float) -> dict:
+    """The same oracle spread over every host core: one process per core (a
+    spawned pool: the parent holds a CUDA context), each cycling its share of
+    the frames for the time budget."""
+    import multiprocessing as mp
+
+    import oracle as orc
+    orc.build()
+    n = max(1, os.cpu_count() or 1)
+    shares = [(frames[i::n] or frames, budget_s) for i in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_share, shares)
+    units = sum(r[0] for r in res)
+    done = sum(r[1] for r in res)
+    wall = max(r[2] for r in res)
+    return {"value": units / wall, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{done} frames of the batched workload over {n} processes (one per core), "
+                      f"{wall:.1f} s each"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle as it stands, timed on host cores."""
     if rank != 0:
@@ -603,6 +640,18 @@ def run_configs(args, local_rank):
                               "of the last frame's points (2000-5000 per frame, motions forward/backward/none)",
                   **r})
 
+    # the batched workload on five seeds (five runs per configuration, as the
+    # paper reports), single launches with the single-launch shapes
+    runs = []
+    for sd in range(5):
+        r = time_batch(scenes.pinhole_batch(seed=sd, n_frames=FRAMES), steps=min(args.steps, 1000),
+                       warmup=max(3, args.warmup), dev=dev, local_rank=local_rank, arena_bytes=512 << 20)
+        runs.append({"seed": sd, "ms_per_launch": r["ms_per_launch"], "value": r["value"], "tuning": r["tuning"]})
+    vals = [x["value"] for x in runs]
+    lines.append({"workload": "batched pinhole, 64 frames 752x480, seeds 0-4 (single launch, L2 flushed)",
+                  "runs": runs, "mean": statistics.mean(vals), "min": min(vals), "max": max(vals),
+                  "unit": UNIT})
+
     # 1080p stress: batch sweep (16 distinct frames, repeated to fill a batch)
     base = scenes.stress_batch(seed=0, n_frames=16)
     sweep = []
@@ -829,6 +878,7 @@ def run_gpu(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(frames, budget_s=12.0)
+        cpu["all_cores"] = time_oracle_all_cores(frames, budget_s=8.0)
     served = None
     if rank == 0 and world == 1 and not args.no_served:
         served = run_served(args, local_rank, seconds=3.0)
