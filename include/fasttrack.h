@@ -367,6 +367,13 @@ ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *param
  * defaults).  Host function; w and h receive params->nlevels values. */
 ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *w, int *h);
 
+/* Measure the current device's 32-bit popcount rate (popcounts per second):
+ * a kernel of eight independent popcount chains per thread on every SM,
+ * timed with events on the stream (best of three runs after one warm-up).
+ * The denominator of the popcount roofline of the Hamming searches; not part
+ * of the paper's method.  Allocates and frees 4 KB of device memory. */
+ft_status ft_measure_popcount(void *stream, double *popc_per_s);
+
 /* Build levels 1..nlevels-1 of a pyramid from its level 0 on the device (the
  * paper runs ORB extraction, which produces the pyramid, on the GPU so that
  * the pyramid never crosses the bus; section IV-B).  Level l samples level 0

@@ -194,6 +194,7 @@ SIGNATURES = [
                                    C.POINTER(ft_pose), C.POINTER(ft_last_frame_view),
                                    C.POINTER(ft_search_out)]),
     ("ft_pyramid_sizes", i32, [i32, i32, C.POINTER(ft_params), vp, vp]),
+    ("ft_measure_popcount", i32, [vp, C.POINTER(C.c_double)]),
     ("ft_build_pyramid", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_pyramid)]),
     ("ft_track_batch", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch)]),
     ("ft_autotune", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch), i32,

@@ -729,6 +729,30 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
 
 }  // namespace
 
+namespace {
+
+// Popcount-only work for the popcount roofline: eight independent chains of
+// 32-bit popcounts per thread (enough to keep the pipe busy), folded into one
+// value the kernel writes so that nothing is optimised away.
+constexpr int kPopcIters = 4096;
+
+__global__ void __launch_bounds__(256) popcount_rate_kernel(unsigned seed, unsigned *sink)
+{
+    unsigned v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = seed * (threadIdx.x + 1u) + 0x9e3779b9u * (unsigned)k + blockIdx.x;
+    for (int i = 0; i < kPopcIters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = (unsigned)__popc(v[k]) + (v[k] << 1);
+    }
+    unsigned x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x ^= v[k];
+    if (x == 0x12345678u) sink[blockIdx.x & 1023] = x;
+}
+
+}  // namespace
+
 void ft::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
 // ======================================================================== C ABI
@@ -972,6 +996,38 @@ ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *
     ft_status s = check_params(p);
     if (s != FT_OK) return s;
     pyramid_sizes(width, height, p, w, h);
+    return FT_OK;
+}
+
+ft_status ft_measure_popcount(void *stream, double *popc_per_s)
+{
+    if (!popc_per_s) return fail(FT_EINVAL, "ft_measure_popcount: NULL argument");
+    int dev = 0, sms = 0;
+    FT_CUDA(cudaGetDevice(&dev));
+    FT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned *sink = nullptr;
+    FT_CUDA(cudaMalloc(&sink, 1024 * sizeof(unsigned)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int blocks = sms * 8;
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {      // the first run warms up
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) popcount_rate_kernel<<<blocks, 256, 0, st>>>(0x2545f491u + rep, sink);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0) best_ms = std::min(best_ms, ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return fail(FT_ECUDA, "ft_measure_popcount: %s", cudaGetErrorString(e));
+    *popc_per_s = (double)blocks * 256.0 * kPopcIters * 8.0 / (best_ms * 1e-3);
     return FT_OK;
 }
 
