@@ -441,6 +441,16 @@ def test_two_contexts_overlapping_launches(ctx, lib):
         ctx2.close()
 
 
+def test_measure_popcount(lib):
+    # the popcount roofline's denominator: a plausible rate (between a tenth
+    # and twice 16 popcounts per SM per clock at 2 GHz) and a refused NULL
+    v = C.c_double(0.0)
+    lib.check(lib.load().ft_measure_popcount(None, C.byref(v)), "ft_measure_popcount")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0.1 * sms * 16 * 2e9 < v.value < 2.0 * sms * 16 * 2e9
+    assert lib.load().ft_measure_popcount(None, None) == lib.FT_EINVAL
+
+
 # ---------------------------------------------------------------- failures reported, never trapped
 def test_bounded_wait_reports_timeout_and_context_recovers(lib):
     from paper_2509_10757_gb300.batch import Context
