@@ -575,7 +575,10 @@ ft_status ft_server_get_stats(ft_server *s, ft_server_stats *stats);
  *
  * Limits: at most 16384 left and 16384 right keypoints and 4096 image rows
  * per call; larger frames are rejected with FT_EINVAL and a message in
- * ft_last_error().
+ * ft_last_error().  params are checked as by every other entry point
+ * (FT_EINVAL before any device work).  The call copies its work table from
+ * a buffer on the host stack, so a stream that is being captured is refused
+ * with FT_EINVAL.
  *
  * The first call on a device looks up the array's device address and the
  * kernel's launch shape for that device (with the device current); make that

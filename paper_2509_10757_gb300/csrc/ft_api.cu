@@ -169,7 +169,10 @@ ft_tuning default_tuning()
     return t;
 }
 
-ft_status check_params(const ft_params &p)
+}  // namespace
+
+// parameter checks shared by every entry point (ft_noalloc.cu included)
+ft_status ft::check_params(const ft_params &p)
 {
     if (p.nlevels < 1 || p.nlevels > FT_MAX_LEVELS) return fail(FT_EINVAL, "nlevels %d out of [1, 16]", p.nlevels);
     if (!(p.scale_factor >= 1.0f) || !std::isfinite(p.scale_factor))
@@ -184,6 +187,8 @@ ft_status check_params(const ft_params &p)
     if (!(2.0f * sc < 1.0e6f)) return fail(FT_EINVAL, "scale_factor^(nlevels-1) = %g is too large", sc);
     return FT_OK;
 }
+
+namespace {
 
 ft_status check_kps(const ft_keypoints &k, const char *what)
 {
@@ -303,7 +308,9 @@ ft_status check_job(const Job &j, const ft_params &p)
     return FT_OK;
 }
 
-DevParams make_dev_params(const ft_params &p)
+}  // namespace
+
+DevParams ft::make_dev_params(const ft_params &p)
 {
     DevParams d{};
     d.nlevels = p.nlevels;
@@ -342,6 +349,25 @@ DevParams make_dev_params(const ft_params &p)
     }
     return d;
 }
+
+// Strip height of the pinhole stereo items: at most `want` rows and the
+// image height; the staged window (strip + 2 halo rows) must fit kWinRows
+// rows, and the right keypoints it is expected to hold (at the frame's mean
+// density) 3/4 of the shared-memory stage.
+int ft::stereo_strip_rows(int want, int H, int nr, int halo)
+{
+    int sr = std::max(1, want);
+    sr = std::min(sr, std::max(1, H));
+    sr = std::min(sr, std::max(1, kWinRows - 2 * halo));
+    if (nr > 0) {
+        const double per_row = (double)nr / (double)std::max(1, H);
+        const int cap_rows = (int)(0.75 * kStageCap / per_row) - 2 * halo;
+        sr = std::max(1, std::min(sr, cap_rows));
+    }
+    return sr;
+}
+
+namespace {
 
 Bucket bucket_of(const std::vector<Job> &jobs)
 {
@@ -471,16 +497,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 F.sad_best = j.st.sad_best;
                 F.u_right = j.st.u_right;
                 F.depth = j.st.depth;
-                // strip height: the expected right keypoints of the strip's
-                // window (strip + 2 halo rows) must fit the shared-memory stage
-                int sr = std::max(1, tune.strip_rows);
-                sr = std::min(sr, std::max(1, F.H));
-                sr = std::min(sr, std::max(1, kWinRows - 2 * halo));
-                if (F.nr > 0) {
-                    const double per_row = (double)F.nr / (double)std::max(1, F.H);
-                    const int cap_rows = (int)(0.75 * kStageCap / per_row) - 2 * halo;
-                    sr = std::max(1, std::min(sr, cap_rows));
-                }
+                const int sr = stereo_strip_rows(tune.strip_rows, F.H, F.nr, halo);
                 F.strip_rows = sr;
                 n_stereo = (F.H + sr - 1) / sr;
                 F.rowsort = kRowSortItems;

@@ -170,4 +170,8 @@ cudaError_t fused_occupancy(int *ctas_per_sm);
 const void *fused_kernel_ptr();
 // set the text ft_last_error() returns on this thread (ft_api.cu)
 void set_last_error(const char *msg);
+// host checks and derived tables shared by the entry points (ft_api.cu)
+ft_status check_params(const ft_params &p);   // FT_EINVAL + ft_last_error() text on a bad field
+DevParams make_dev_params(const ft_params &p);
+int stereo_strip_rows(int want, int H, int nr, int halo);
 }  // namespace ft

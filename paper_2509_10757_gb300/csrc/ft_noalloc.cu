@@ -40,7 +40,7 @@ constexpr int kNoAllocMaxRows = kMaxRows;       // level-0 image height
 constexpr size_t kNoAllocScratchBytes = (size_t)2 << 20;
 constexpr int kMaxDevices = 64;
 
-// The scratch memory: 1 MiB per device, resident from library load to exit.
+// The scratch memory: 2 MiB per device, resident from library load to exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 struct DeviceSetup {
@@ -102,8 +102,9 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     ft_params p;
     if (params) p = *params;
     else ft_params_default(&p);
-    if (p.nlevels < 1 || p.nlevels > FT_MAX_LEVELS) return fail(FT_EINVAL, "nlevels %d out of [1, 16]", p.nlevels);
-    if (!(p.scale_factor >= 1.0f) || !std::isfinite(p.scale_factor)) return fail(FT_EINVAL, "bad scale_factor");
+    // the same parameter checks as every context entry point
+    const ft_status pst = check_params(p);
+    if (pst != FT_OK) return pst;
     const ft_keypoints &L = frame->left, &R = frame->right;
     if (L.n < 0 || R.n < 0) return fail(FT_EINVAL, "negative keypoint count");
     if (L.n > kNoAllocMaxKeypoints || R.n > kNoAllocMaxKeypoints)
@@ -131,8 +132,17 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     if (L.n > 0 && (!out->best_r || !out->dist || !out->sad_shift || !out->sad_best || !out->u_right || !out->depth))
         return fail(FT_EINVAL, "NULL output array");
 
+    // The work table is copied from a stack buffer (pageable memory), which a
+    // stream capture cannot record: refuse a capturing stream up front rather
+    // than fail in the middle of the caller's capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) return fail(FT_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(FT_EINVAL, "ft_stereo_match_pinhole_noalloc: the stream is capturing");
+
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(FT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     DeviceSetup *S = nullptr;
     ft_status st = setup_device(dev, &S);
@@ -176,34 +186,7 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     std::memset(host, 0, table_bytes);
     unsigned char *d = S->scratch;
     BatchHeader &B = *reinterpret_cast<BatchHeader *>(host + o_hdr);
-    DevParams &P = B.p;
-    P.nlevels = p.nlevels;
-    P.th_stereo = p.th_stereo;
-    P.th_search = p.th_search;
-    P.ratio_any_octave = p.ratio_any_octave;
-    float sc = 1.0f, rmax = 0.0f;
-    for (int l = 0; l < FT_MAX_LEVELS; ++l) {
-        if (l > 0 && l < p.nlevels) sc = sc * p.scale_factor;
-        P.sc[l] = sc;
-        P.isc[l] = 1.0f / sc;
-        P.band_r[l] = 2.0f * sc;
-        if (l < p.nlevels) rmax = std::max(rmax, P.band_r[l]);
-    }
-    P.median_factor = p.median_factor;
-    P.fisheye_ratio = p.fisheye_ratio;
-    P.nn_ratio = p.nn_ratio;
-    P.search_th = p.search_th;
-    P.view_cos_min = p.view_cos_min;
-    P.view_cos_narrow = p.view_cos_narrow;
-    P.radius_narrow = p.radius_narrow;
-    P.radius_wide = p.radius_wide;
-    P.dist_lo = p.dist_lo;
-    P.dist_hi = p.dist_hi;
-    P.halo = (int)std::ceil(rmax) + 3;
-    for (int o = 0; o < FT_MAX_LEVELS; ++o) {
-        P.halo_oct[o] = (int)std::ceil(P.band_r[std::min(o + 1, p.nlevels - 1)]) + 3;
-        P.halo_c[o] = (int)std::ceil(P.band_r[std::min(o, p.nlevels - 1)]) + 3;
-    }
+    B.p = make_dev_params(p);
     B.nframes = 1;
     B.prefix = reinterpret_cast<const int *>(d + o_prefix);
     B.frames = reinterpret_cast<const FrameDev *>(d + o_frame);
@@ -250,13 +233,8 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     F.ls_desc = reinterpret_cast<uint4 *>(d + o_lds);
     F.rs_kp = reinterpret_cast<float4 *>(d + o_rkp);
     F.rs_desc = reinterpret_cast<uint4 *>(d + o_rds);
-    // strips of 32 rows, fewer if the expected right keypoints of a window
-    // would overflow the shared-memory stage
-    int sr = std::min(32, H);
-    if (R.n > 0) {
-        const double per_row = (double)R.n / (double)H;
-        sr = std::max(1, std::min(sr, (int)(0.75 * kStageCap / per_row) - 2 * P.halo));
-    }
+    // strips of 32 rows (the context's default), shortened by the same rule
+    const int sr = stereo_strip_rows(32, H, R.n, B.p.halo);
     F.strip_rows = sr;
     F.n_stereo_items = (H + sr - 1) / sr;
     F.rowsort = kRowSortItems;

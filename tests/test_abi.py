@@ -82,3 +82,19 @@ def test_create_fails_cleanly_without_a_device(lib):
     assert st in (lib.FT_ECUDA, lib.FT_EINVAL)
     assert not ctx.value
     assert lib.last_error()
+
+
+def test_noalloc_checks_params_before_any_device_work(lib):
+    """The allocation-free entry point applies the same parameter checks as
+    the context entry points and returns before any CUDA call: a scale table
+    whose top level overflows the band arithmetic (10^10) and a negative
+    median factor are refused with FT_EINVAL, here on a machine without a GPU."""
+    so = lib.load()
+    cam, st, out = lib.ft_pinhole(), lib.ft_stereo_frame(), lib.ft_stereo_out()
+    cam.width, cam.height, cam.b = 752, 480, 0.11
+    bad = [dict(scale_factor=10.0, nlevels=11), dict(median_factor=-1.0), dict(nlevels=0)]
+    for over in bad:
+        p = lib.default_params(over)
+        r = so.ft_stereo_match_pinhole_noalloc(None, C.byref(p), C.byref(cam), C.byref(st), C.byref(out), None)
+        assert r == lib.FT_EINVAL, over
+        assert lib.last_error(), over

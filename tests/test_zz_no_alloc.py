@@ -5,16 +5,16 @@ memory while they run (a deadline-bound tracking loop, a process that
 reserved all device memory up front, a host framework that forbids foreign
 allocations): it needs no context and keeps its scratch in a fixed device
 array inside the library.  Its results must equal those of
-ft_stereo_match_pinhole, call after call (the shared scratch keeps the
-previous call's contents, so a second call checks that nothing stale leaks
-into the next result).  This file is collected last so that a failure here
-never hides another test's result.
+ft_stereo_match_pinhole and those of the CPU oracle, call after call (the
+shared scratch keeps the previous call's contents, so a second call checks
+that nothing stale leaks into the next result).  This file is collected
+last so that a failure here never hides another test's result.
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 
+import oracle as orc
 from paper_2509_10757_gb300 import scenes
 from tests.gpu_common import assert_stereo_equal, stereo_view
 
@@ -57,13 +57,35 @@ def test_noalloc_equals_context_entry_point_twice(lib):
     finally:
         ctx.close()
     status = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    oracle_ref = [orc.stereo_frame(dict(scenes.DEFAULT_PARAMS), fr) for fr in frames]
     for call in range(2):
         for f in range(len(frames)):
             pb.clear_outputs(0x3c + call)
             lib.check(_noalloc(lib, pb, f, status), "ft_stereo_match_pinhole_noalloc")
             pb.download()
             assert int(status.item()) == 0
-            assert_stereo_equal(stereo_view(pb.outputs(f)), ref[f], f"call {call} frame {f}: ")
+            got = stereo_view(pb.outputs(f))
+            assert_stereo_equal(got, ref[f], f"call {call} frame {f} (context entry point): ")
+            assert_stereo_equal(got, oracle_ref[f], f"call {call} frame {f} (oracle): ")
+
+
+def test_noalloc_calls_leave_device_memory_unchanged(lib):
+    """After the first call on the device (which may load the library's
+    module and so reserve the array), further calls take no device memory:
+    the free-memory figure of the device is the same before and after them."""
+    from paper_2509_10757_gb300.batch import PackedBatch
+    pb = PackedBatch([scenes.single_pinhole(24)])
+    pb.upload()
+    status = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    lib.check(_noalloc(lib, pb, 0, status), "ft_stereo_match_pinhole_noalloc")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        lib.check(_noalloc(lib, pb, 0, status), "ft_stereo_match_pinhole_noalloc")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device free memory changed by {free0 - free1} bytes over three calls"
+    assert int(status.item()) == 0
 
 
 def test_noalloc_rejects_frames_above_its_limit(lib):
