@@ -147,6 +147,33 @@ def test_fisheye_batch_full_size(ctx, lib):
         check_frame(pb, f, what="fisheye batch")
 
 
+def test_fisheye_rotated_rig_local_map_and_last_frame(ctx, lib):
+    """A rig whose right camera is rotated 15 degrees from the left one: the
+    right camera's pose (T_rl T_lw) and centre matter to every right-camera
+    projection, distance and viewing angle, in the local-map search and in
+    the last-frame search."""
+    from paper_2509_10757_gb300.batch import PackedBatch, run_batch
+    from tests.test_oracle_fisheye_rig import rotated_rig
+    frames = [scenes.fisheye_frame(60 + i, n_left=1500, n_map=6000, rig=rotated_rig(5 + i)) for i in range(4)]
+    pb = run_fused(ctx, frames)
+    for f in range(len(frames)):
+        out, _, se = check_frame(pb, f, what="rotated rig")
+        assert (se["mp_kp_r"] >= 0).sum() > 200
+    lasts = [scenes.last_frame(fr, 70 + i, mo) for i, (fr, mo) in
+             enumerate(zip(frames, ["forward", "backward", "none", "none"]))]
+    pb = PackedBatch(frames, lasts=lasts)
+    pb.upload()
+    pb.clear_outputs()
+    run_batch(ctx, pb)
+    pb.download()
+    assert ctx.sync_status() == 0
+    for f, fr in enumerate(frames):
+        st = orc.stereo_frame(_oracle_params(), fr)
+        assert_fisheye_equal(pb.outputs(f), st, f"rotated rig frame {f}: ")
+        ref = _check_last(pb, f, st, f"rotated rig last-frame {f}: ")
+        assert (ref["mp_kp_r"] >= 0).sum() > 50
+
+
 def test_stress_frames(ctx, lib):
     frames = scenes.stress_batch(seed=0, n_frames=2, n_map=100_000)
     pb = run_fused(ctx, frames)

@@ -76,6 +76,18 @@ MUTANTS = [
     ("pyr_size_floor", "w[l] = (int)roundf((float)W / sc[l]);", "w[l] = (int)((float)W / sc[l]);"),
     ("pyr_round_floor", "float v = rintf(top * (1.0f - fy) + bot * fy);", "float v = floorf(top * (1.0f - fy) + bot * fy);"),
     ("pyr_fused_vertical", "float v = rintf(top * (1.0f - fy) + bot * fy);", "float v = rintf(fmaf(top, 1.0f - fy, bot * fy));"),
+    # right fisheye camera of the search (T_rw = T_rl T_lw, centre O_right)
+    ("right_R_transposed", "Rr[3 * i + j] = R_rl[3 * i + 0] * T->R[0 + j] + R_rl[3 * i + 1] * T->R[3 + j] +\n                            R_rl[3 * i + 2] * T->R[6 + j];",
+     "Rr[3 * i + j] = R_rl[0 + i] * T->R[0 + j] + R_rl[3 + i] * T->R[3 + j] +\n                            R_rl[6 + i] * T->R[6 + j];"),
+    ("right_t_dropped", "R_rl[3 * i + 2] * T->t[2] + t_rl[i];\n    }\n    for (int m = 0; m < M; ++m) {\n        int lv;",
+     "R_rl[3 * i + 2] * T->t[2];\n    }\n    for (int m = 0; m < M; ++m) {\n        int lv;"),
+    ("right_centre_is_left", "orc_project_kb8(p, camR, Rr, tr, O_right,", "orc_project_kb8(p, camR, Rr, tr, T->O,"),
+    ("last_right_R_transposed",
+     "Rr[3 * i + j] = R_rl[3 * i] * T->R[j] + R_rl[3 * i + 1] * T->R[3 + j] + R_rl[3 * i + 2] * T->R[6 + j];",
+     "Rr[3 * i + j] = R_rl[i] * T->R[j] + R_rl[3 + i] * T->R[3 + j] + R_rl[6 + i] * T->R[6 + j];"),
+    ("last_right_t_dropped",
+     "tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2] + t_rl[i];",
+     "tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2];"),
     ("last_view_distance", "        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;",
      "        if (Pc[2] > 8.0f) continue;\n        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;"),
 ]
@@ -100,7 +112,9 @@ def _run_mutant(tmp, name, old, new):
                         os.path.join(ROOT, "tests", "test_oracle_search.py"),
                         os.path.join(ROOT, "tests", "test_oracle_triangulation.py"),
                         os.path.join(ROOT, "tests", "test_oracle_lastframe.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pyramid.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pyramid.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_fisheye_rig.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_mirror.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
