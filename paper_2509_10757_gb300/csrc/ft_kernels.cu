@@ -659,9 +659,13 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                 const int ul = f2i(roundf(fmul(xi, P.isc[l])));
                 const int vl = f2i(roundf(fmul(yi, P.isc[l])));
                 const int ur0 = f2i(roundf(fmul(xb, P.isc[l])));
-                const bool inside = vl - kW >= 0 && vl + kW <= F.lh[l] - 1 && vl + kW <= F.rh[l] - 1 &&
-                                    ul - kW >= 0 && ul + kW <= F.lw[l] - 1 &&
-                                    ur0 - kL - kW >= 0 && ur0 + kL + kW <= F.rw[l] - 1;
+                // windows inside both level images.  ul, vl and ur0 saturate at
+                // INT_MAX / INT_MIN for coordinates of 2^31 and more (or +-inf), so
+                // they are compared with the bounds and never offset: ul + kW would
+                // wrap negative and let a window 2 GB past the level through.
+                const bool inside = vl >= kW && vl <= F.lh[l] - 1 - kW && vl <= F.rh[l] - 1 - kW &&
+                                    ul >= kW && ul <= F.lw[l] - 1 - kW &&
+                                    ur0 >= kL + kW && ur0 <= F.rw[l] - 1 - kL - kW;
                 if (inside) {
                     // the lanes ask L2 for the patch rows now, so that the
                     // refinement's copies find them there

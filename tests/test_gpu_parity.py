@@ -320,6 +320,44 @@ def test_keypoints_on_image_borders(ctx, lib):
     check_frame(pb, 0, what="borders")
 
 
+def test_keypoints_at_huge_coordinates_are_not_refined(ctx, lib):
+    """Keypoints whose x is 3e9 or +inf (with right partners of the same
+    descriptor at the same place) are matched by the Hamming step but have no
+    SAD window inside the level images: their level coordinates saturate at
+    INT_MAX on the device, and the window test must reject them rather than
+    let the addition of the window half-widths wrap around.  They lie outside
+    the search grid, so every other result is the oracle's on the frame
+    without them."""
+    fr = scenes.single_pinhole(19)
+    st, se = orc.track_frame(_oracle_params(), fr)
+    rng = np.random.default_rng(19)
+    xs = np.array([3e9, np.inf, 3e9], np.float32)
+    ys = np.array([100.0, 200.0, 300.0], np.float32)
+    octs = np.array([0, 0, 3], np.int8)
+    desc = scenes.random_desc(rng, len(xs))
+    nl, nr = fr.left.n, fr.right.n
+    big = dataclasses.replace(
+        fr,
+        left=scenes.Keypoints(x=np.concatenate([fr.left.x, xs]), y=np.concatenate([fr.left.y, ys]),
+                              oct=np.concatenate([fr.left.oct, octs]), desc=np.concatenate([fr.left.desc, desc])),
+        right=scenes.Keypoints(x=np.concatenate([fr.right.x, xs]), y=np.concatenate([fr.right.y, ys]),
+                               oct=np.concatenate([fr.right.oct, octs]),
+                               desc=np.concatenate([fr.right.desc, desc])),
+        taken_l=np.concatenate([fr.taken_l, np.zeros(len(xs), np.uint8)]))
+    pb = run_fused(ctx, [big])
+    out = pb.outputs(0)
+    base = {k: (v[:nl] if k in ("best_r", "dist", "sad_shift", "sad_best", "u_right", "depth", "kp_mp_l")
+                else v) for k, v in out.items()}
+    assert_stereo_equal(base, st, "huge coordinates (other keypoints): ")
+    assert_search_equal(base, se, "l", None, "huge coordinates (map points): ")
+    assert np.array_equal(out["best_r"][nl:], nr + np.arange(len(xs)))
+    assert np.all(out["dist"][nl:] == 0)
+    assert np.all(out["sad_shift"][nl:] == lib.FT_NO_SHIFT)
+    assert np.all(out["sad_best"][nl:] == -1)
+    assert np.all(out["u_right"][nl:] == -1.0) and np.all(out["depth"][nl:] == -1.0)
+    assert np.all(out["kp_mp_l"][nl:] == -1)
+
+
 def test_dense_rows_fall_back_to_scan(ctx, lib):
     # thousands of right keypoints on a few rows overflow the shared-memory stage
     fr = scenes.single_pinhole(10)
