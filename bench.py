@@ -91,23 +91,28 @@ def barrier(world: int):
 
 # ---------------------------------------------------------------- measurement helpers
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while running."""
+    """Samples nvidia-smi clocks and throttle reasons while running.  The
+    sampler runs from before the warm-up to after the last timed form; mark()
+    names the time windows of individual forms, and stop() reports the whole
+    run and each marked window."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host time, csv line)
         self.thread = None
+        self.windows = {}        # name -> [t0, t1]
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -117,21 +122,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        if self.thread:
-            self.thread.join(timeout=5)
+    def mark(self, name: str, begin: bool):
+        w = self.windows.setdefault(name, [None, None])
+        w[0 if begin else 1] = time.time()
+
+    @staticmethod
+    def _summary(rows) -> dict:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for _, line in rows:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -146,6 +147,29 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        out = self._summary(self.lines)
+        out["period_ms"] = self.PERIOD_MS
+        out["span"] = "from before the warm-up to after the last timed form"
+        win = {}
+        for name, (a, b) in self.windows.items():
+            if a is None or b is None:
+                continue
+            rows = [r for r in self.lines if a <= r[0] <= b]
+            win[name] = {k: v for k, v in self._summary(rows).items() if k in ("sm_mhz", "samples", "reasons")}
+        if win:
+            out["windows"] = win
+        return out
 
 
 def measured_peaks() -> dict:
@@ -477,10 +501,31 @@ def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batc
             "slots": n_slots, "max_batch": max_batch, "seconds": seconds}
 
 
+SERVED_RATES_HZ = (30.0, 60.0, 120.0, 240.0)      # per stream, batched server (3 slots, up to 64 frames)
+PLAIN_RATES_HZ = (2.0, 4.0, 8.0, 12.0, 16.0, 30.0)  # per stream, plain form (1 slot, 1 frame per launch)
+P99_BOUNDS_MS = (1.0, 33.0)                         # 1 ms, and one frame period at 30 Hz
+MAX_DROP_FRAC = 0.001
+
+
+def equal_p99(points: list, bound_ms: float) -> dict | None:
+    """The highest throughput among sweep points whose p99 latency is within
+    the bound and that dropped (almost) nothing; dropped frames never count
+    as throughput (the value counts completed frames only)."""
+    ok = [p for p in points if p["p99_ms"] <= bound_ms
+          and p["dropped"] <= MAX_DROP_FRAC * (p["completed"] + p["dropped"])]
+    if not ok:
+        return None
+    b = max(ok, key=lambda p: p["value"])
+    return {"value": b["value"], "offered_hz_per_stream": b["offered_hz"] / 256.0, "p50_ms": b["p50_ms"],
+            "p99_ms": b["p99_ms"], "dropped": b["dropped"], "completed": b["completed"]}
+
+
 def run_served(args, local_rank, seconds: float = 4.0, streams: int = 256):
-    """Served mixed streams: 256 camera streams of uneven shapes, Poisson 30 Hz
-    each, resident state, HBM-budget admission; the batched server against
-    the plain form (one frame per launch, one slot)."""
+    """Served mixed streams: 256 camera streams of uneven shapes, Poisson
+    arrivals, resident state, HBM-budget admission.  The batched server and
+    the plain form (one frame per launch, one slot) are each swept over the
+    offered load; each form's throughput at equal p99 latency is the highest
+    throughput it sustains with p99 within the bound and no drops."""
     import torch
 
     from paper_2509_10757_gb300 import _lib as L
@@ -492,10 +537,23 @@ def run_served(args, local_rank, seconds: float = 4.0, streams: int = 256):
     frames = [scenes.served_stream_frame(0, s) for s in range(streams)]
     out = {"workload": "served mixed streams: 256 camera streams (640x480, 752x480, 1280x720 pinhole, "
                        "512x512 fisheye), 500-4000 keypoints, 1k-20k map points, Poisson arrivals"}
-    out["served_30hz"] = serve_load(frames, L, 30.0, seconds, n_slots=3, max_batch=64)
-    out["plain_30hz"] = serve_load(frames, L, 30.0, seconds, n_slots=1, max_batch=1)
-    out["served_120hz"] = serve_load(frames, L, 120.0, seconds, n_slots=3, max_batch=64)
+    served = [serve_load(frames, L, hz, seconds, n_slots=3, max_batch=64) for hz in SERVED_RATES_HZ]
+    plain = [serve_load(frames, L, hz, seconds, n_slots=1, max_batch=1) for hz in PLAIN_RATES_HZ]
+    out["served_30hz"] = served[0]
+    out["plain_30hz"] = plain[-1]
     out["served_30hz_images"] = serve_load(frames, L, 30.0, seconds, n_slots=3, max_batch=64, images=True)
+    out["sweep"] = {"served": served, "plain": plain}
+    eq = {}
+    for bound in P99_BOUNDS_MS:
+        a, b = equal_p99(served, bound), equal_p99(plain, bound)
+        eq[f"p99_le_{bound:g}ms"] = {"served": a, "plain": b,
+                                    "served_over_plain": (a["value"] / b["value"]) if a and b else None}
+    out["equal_p99"] = {**eq, "rule": f"highest throughput of a sweep point with p99 <= bound and dropped <= "
+                                      f"{MAX_DROP_FRAC:g} of submitted; offered loads per stream: served "
+                                      f"{list(SERVED_RATES_HZ)} Hz, plain {list(PLAIN_RATES_HZ)} Hz; "
+                                      f"{seconds:g} s per point",
+                        "note": "the served sweep's top rate is the highest the submitting host loop was "
+                                "run at, not the server's limit"}
     return out
 
 
@@ -567,6 +625,45 @@ def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_byte
     return out
 
 
+def fisheye_result(steps: int, warmup: int, dev, local_rank: int) -> dict:
+    """The fisheye batch (32 frames of 512x512 KB8, 1500 keypoints, 60 % in
+    the overlap, 6000 map points) as one fused launch per step, with the
+    popcount roofline of its overlap brute force: 8 popcounts per descriptor
+    pair against the device's measured popcount rate."""
+    import ctypes as C
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300 import scenes
+    frames = scenes.fisheye_batch(seed=0, n_frames=32)
+    r = time_batch(frames, steps=steps, warmup=warmup, dev=dev, local_rank=local_rank, arena_bytes=512 << 20)
+    pairs = fisheye_pairs(frames)
+    measured = C.c_double(0.0)
+    L.check(L.load().ft_measure_popcount(None, C.byref(measured)), "ft_measure_popcount")
+    nominal = 152 * POPC_PER_SM_CLK * 2070e6
+    achieved = pairs * POPC_PER_PAIR / (r["ms_per_launch"] / 1e3)
+    r["popcount"] = {"bound": "alu", "pairs_per_launch": pairs, "achieved_popc_per_s": achieved,
+                     "peak_popc_per_s": measured.value, "frac": achieved / measured.value,
+                     "peak_source": "measured on this device by ft_measure_popcount (popcount-only kernel)",
+                     "nominal_popc_per_s": nominal, "nominal_source": "152 SMs x 16 popcounts/clk x 2070 MHz",
+                     "duration": "mean CUDA-event time of a single launch timed alone, L2 flushed before it"}
+    return {"workload": "fisheye batch: 32 frames 512x512 KB8, 1500 keypoints (60% overlap), "
+                        "6000 map points", **r}
+
+
+_STRESS_BASE: list = []
+
+
+def stress_result(n: int, steps: int, warmup: int, dev, local_rank: int) -> dict:
+    """The 1080p stress batch (8000 keypoints, 100k map points per frame, 8 %
+    flips, 40 % distractors) of n frames, 16 distinct frames repeated."""
+    from paper_2509_10757_gb300 import scenes
+    if not _STRESS_BASE:
+        _STRESS_BASE.extend(scenes.stress_batch(seed=0, n_frames=16))
+    frames = [_STRESS_BASE[i % len(_STRESS_BASE)] for i in range(n)]
+    return time_batch(frames, steps=steps, warmup=warmup, dev=dev, local_rank=local_rank,
+                      arena_bytes=(64 << 20) + n * (24 << 20))
+
+
 def run_configs(args, local_rank):
     """The other workloads, one JSON line each: single pinhole frames (per-frame
     latency over 1000 frames, plain calls and a one-frame fused launch), the
@@ -617,23 +714,7 @@ def run_configs(args, local_rank):
                   "plain": lat["plain"], "fused_one_frame": lat["fused"]})
 
     # fisheye batch: 32 frames of 512x512, 1500 keypoints, 6000 map points
-    frames = scenes.fisheye_batch(seed=0, n_frames=32)
-    r = time_batch(frames, steps=max(50, min(args.steps, 500)), warmup=max(3, args.warmup), dev=dev,
-                   local_rank=local_rank, arena_bytes=512 << 20)
-    pairs = fisheye_pairs(frames)
-    import ctypes as C
-
-    from paper_2509_10757_gb300 import _lib as L
-    measured = C.c_double(0.0)
-    L.check(L.load().ft_measure_popcount(None, C.byref(measured)), "ft_measure_popcount")
-    nominal = 152 * POPC_PER_SM_CLK * 2070e6
-    achieved = pairs * POPC_PER_PAIR / (r["ms_per_launch"] / 1e3)
-    r["popcount"] = {"pairs_per_launch": pairs, "achieved_popc_per_s": achieved,
-                     "peak_popc_per_s": measured.value, "frac": achieved / measured.value,
-                     "peak_source": "measured on this device by ft_measure_popcount (popcount-only kernel)",
-                     "nominal_popc_per_s": nominal, "nominal_source": "152 SMs x 16 popcounts/clk x 2070 MHz"}
-    lines.append({"workload": "fisheye batch: 32 frames 512x512 KB8, 1500 keypoints (60% overlap), "
-                              "6000 map points", **r})
+    lines.append(fisheye_result(max(50, min(args.steps, 500)), max(3, args.warmup), dev, local_rank))
 
     # the batched workload with each frame searching its last frame's points
     # (stereo first; the search of the paper's initial pose estimation)
@@ -658,13 +739,10 @@ def run_configs(args, local_rank):
                   "unit": UNIT})
 
     # 1080p stress: batch sweep (16 distinct frames, repeated to fill a batch)
-    base = scenes.stress_batch(seed=0, n_frames=16)
     sweep = []
     for n in (1, 2, 4, 8, 16, 32, 64, 128):
-        frames = [base[i % len(base)] for i in range(n)]
         steps = max(20, min(args.steps, 2000 // n))
-        sweep.append(time_batch(frames, steps=steps, warmup=max(3, args.warmup), dev=dev,
-                                local_rank=local_rank, arena_bytes=(64 << 20) + n * (24 << 20)))
+        sweep.append(stress_result(n, steps, max(3, args.warmup), dev, local_rank))
     lines.append({"workload": "stress 1920x1080, 8000 keypoints, 100k map points per frame; batch sweep",
                   "sweep": sweep})
     for ln in lines:
@@ -722,16 +800,18 @@ def run_gpu(args, rank, world, local_rank):
         with torch.cuda.stream(st):
             run_batch(c, bt, stream=st)
 
+    # clocks are sampled from here (before the warm-up) to after the last timed form
+    clocks = ClockSampler(local_rank)
+    clocks.start()
     # warm-up on every lane (graph capture happens on the first calls)
     for i in range(max(args.warmup, LANES)):
         step(i)
     torch.cuda.synchronize(dev)
     assert all(c.sync_status() == 0 for c, _, _ in lanes)
 
-    clocks = ClockSampler(local_rank)
     launches0 = sum(c.launches() for c, _, _ in lanes)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks.start()
+    clocks.mark("headline", True)
     barrier(world)
     torch.cuda.synchronize(dev)
     t0.record(stream)
@@ -744,7 +824,7 @@ def run_gpu(args, rank, world, local_rank):
     t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
-    clk = clocks.stop()
+    clocks.mark("headline", False)
     launches = sum(c.launches() for c, _, _ in lanes) - launches0
     assert all(c.sync_status() == 0 for c, _, _ in lanes)
     job_s = max_over_ranks(t0.elapsed_time(t1) / 1e3, world, dev)
@@ -880,13 +960,27 @@ def run_gpu(args, rank, world, local_rank):
         plain_ms.append(p0.elapsed_time(p1))
     plain_units = sum(frames[f].left.n + frames[f].map.n for f in range(nplain))
 
+    # the other batched workloads of the scope, one fused launch per step:
+    # the fisheye batch (popcount roofline) and the 1080p stress batch of 32
+    clocks.mark("fisheye", True)
+    fisheye = fisheye_result(max(20, min(args.steps, 300)), max(3, args.warmup), dev, local_rank)
+    clocks.mark("fisheye", False)
+    clocks.mark("stress", True)
+    stress = stress_result(32, max(10, min(args.steps, 60)), max(3, args.warmup), dev, local_rank)
+    clocks.mark("stress", False)
+    stress["workload"] = ("stress: 32 frames 1920x1080 per launch, 8000 keypoints, 100k map points "
+                          "(grid 64x48), 8% flips, 40% distractors (16 distinct frames, each twice)")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(frames, budget_s=12.0)
         cpu["all_cores"] = time_oracle_all_cores(frames, budget_s=8.0)
     served = None
     if rank == 0 and world == 1 and not args.no_served:
-        served = run_served(args, local_rank, seconds=3.0)
+        clocks.mark("served", True)
+        served = run_served(args, local_rank, seconds=2.0)
+        clocks.mark("served", False)
+    clk = clocks.stop()
     def tuning_of(t):
         return {"strip_rows": t.strip_rows, "search_tile": t.search_tile, "fisheye_tile": t.fisheye_tile,
                 "ctas_per_sm": t.ctas_per_sm}
@@ -949,6 +1043,8 @@ def run_gpu(args, rank, world, local_rank):
                                 "frac": alg_bytes / (job_s / args.steps) / 1e9 / peaks["hbm_gbs"],
                                 "duration": "the headline's timed region divided by its launches "
                                             "(launches overlap)"}},
+        "fisheye": fisheye,
+        "stress": stress,
         "gpu_launches": launches,
         "clocks": clk,
     }
