@@ -56,6 +56,8 @@ class OrcParams(C.Structure):
         ("view_cos_narrow", C.c_float), ("radius_narrow", C.c_float),
         ("radius_wide", C.c_float), ("dist_lo", C.c_float), ("dist_hi", C.c_float),
         ("th_last", C.c_float), ("kb_iters", C.c_int), ("min_depth", C.c_float),
+        ("po_rounds", C.c_int), ("po_iters", C.c_int), ("po_chi2_mono", C.c_float),
+        ("po_chi2_stereo", C.c_float), ("po_huber", C.c_int),
     ]
 
 
@@ -172,6 +174,13 @@ def _lib_handle():
                                                P(OrcPose), vp, P(OrcKeypoints), vp,
                                                P(OrcKeypoints), vp, C.c_int, vp, vp, vp, vp,
                                                vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_se3_exp.argtypes = [vp, vp, vp]
+            lib.orc_pose_residual.restype = C.c_int
+            lib.orc_pose_residual.argtypes = [P(OrcPinhole), vp, vp, vp, vp, C.c_int, vp, vp]
+            lib.orc_optimize_pose_pinhole.restype = C.c_int
+            lib.orc_optimize_pose_pinhole.argtypes = [P(OrcParams), P(OrcPinhole), P(OrcPose),
+                                                      P(OrcKeypoints), vp, C.c_int, vp, vp, vp, vp, vp,
+                                                      vp, vp]
             _lib = lib
     return _lib
 
@@ -630,3 +639,53 @@ def build_pyramid(img, nlevels: int = 8, s: float = 1.2) -> list:
     """f3: the pyramid of a level-0 image (level 0 itself first)."""
     ws, hs = pyramid_sizes(img.shape[1], img.shape[0], nlevels, s)
     return [np.ascontiguousarray(img, np.uint8)] + [resample_level(img, ws[l], hs[l]) for l in range(1, nlevels)]
+
+
+# --------------------------------------------------------------------------
+# f4: pose optimization (double precision)
+# --------------------------------------------------------------------------
+def se3_exp(d6):
+    """exp of a twist d = (w, v): (R_d, V) as 3x3 arrays."""
+    d = _c(d6, np.float64)
+    R = np.zeros(9, np.float64)
+    V = np.zeros(9, np.float64)
+    _lib_handle().orc_se3_exp(_ptr(d), _ptr(R), _ptr(V))
+    return R.reshape(3, 3), V.reshape(3, 3)
+
+
+def pose_residual(cam, R, t, P, obs, stereo: bool):
+    """(in front, residual e [3], Jacobian [3][6]) of one observation."""
+    Rd = _c(np.asarray(R, np.float64).reshape(9), np.float64)
+    td = _c(t, np.float64)
+    Pw = _c(list(P) + [0.0] * (4 - len(P)), np.float32)
+    ob = _c(list(obs) + [0.0] * (3 - len(obs)), np.float64)
+    e = np.zeros(3, np.float64)
+    J = np.zeros(18, np.float64)
+    c = pinhole_struct(cam)
+    ok = _lib_handle().orc_pose_residual(C.byref(c), _ptr(Rd), _ptr(td), _ptr(Pw), _ptr(ob), int(stereo),
+                                         _ptr(e), _ptr(J))
+    return bool(ok), e, J.reshape(3, 6)
+
+
+def optimize_pose(params: dict, cam, pose, kps, u_right, pos, mp_kp) -> dict:
+    """f4 for a pinhole frame: the refined pose (R, t, double), per map point
+    inlier flags (1, 0, -1 unmatched) and final chi2, the number of inliers,
+    the smallest relative distance of a classification's chi2 to its
+    threshold, and the rounds run."""
+    lib = _lib_handle()
+    keep = _Keep()
+    K = kps_struct(kps, keep)
+    P = keep.add(_c(pos, np.float32).reshape(-1, 4))
+    M = len(P)
+    mk = keep.add(_c(mp_kp, np.int32))
+    ur = None if u_right is None else keep.add(_c(u_right, np.float32))
+    Rt = np.zeros(12, np.float64)
+    inl = np.zeros(M, np.int8)
+    c2 = np.zeros(M, np.float64)
+    margin = C.c_double(0.0)
+    rounds = C.c_int(0)
+    p, c, T = params_struct(params), pinhole_struct(cam), pose_struct(pose)
+    n = lib.orc_optimize_pose_pinhole(C.byref(p), C.byref(c), C.byref(T), C.byref(K), _ptr(ur), M, _ptr(P),
+                                      _ptr(mk), _ptr(Rt), _ptr(inl), _ptr(c2), C.byref(margin), C.byref(rounds))
+    return dict(R=Rt[:9].reshape(3, 3).copy(), t=Rt[9:].copy(), inlier=inl, chi2=c2, n_inliers=int(n),
+                min_margin=margin.value, rounds=rounds.value)

@@ -1066,3 +1066,215 @@ void orc_resample_level(const uint8_t *src, int W, int H, int pitch, uint8_t *ds
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* f4: pose optimization.  The paper's tracking refines the camera pose     */
+/* with all the map points its search found in the frame (section II-D);    */
+/* FastTrack switches the step off (section IV-F).  The reading, the        */
+/* algorithm family's motion-only optimization, in double precision:       */
+/*  - observations: a map point m matched to keypoint k = mp_kp[m] >= 0     */
+/*    is observed at (x_k, y_k) and, when u_right[k] >= 0, also at the      */
+/*    right coordinate u_right[k] (three residuals; else two).  Its weight  */
+/*    is w = 1 / scale[oct_k]^2 (scale from the FP32 table).                */
+/*  - the pose starts at the search's pose; every observation starts as an  */
+/*    inlier.                                                               */
+/*  - po_rounds rounds; a round runs only while at least 3 observations are */
+/*    inliers.  It takes po_iters Gauss-Newton steps over the inliers that  */
+/*    lie in front of the camera (z > 0): residual e = observation -        */
+/*    projection, chi2 = w |e|^2, Huber factor h = 1 if chi2 <= th else     */
+/*    sqrt(th / chi2) (th the threshold of the observation's kind; h = 1    */
+/*    without Huber); H += h w J^T J, g += h w J^T e, J the derivative of   */
+/*    the projection for a perturbation exp(d) multiplied on the left of    */
+/*    the pose; d solves H d = g (Cholesky; if H is not positive definite   */
+/*    the optimization stops with the current pose); the pose becomes       */
+/*    exp(d) (R, t).                                                        */
+/*  - after each round every observation is classified again at the new     */
+/*    pose: an outlier if z <= 0 or chi2 > th, else an inlier.              */
+/*  - exp(d), d = (w, v): theta = |w|, R_d = I + a [w]x + b [w]x^2,          */
+/*    V = I + b [w]x + c [w]x^2, a = sin(theta)/theta,                       */
+/*    b = (1 - cos(theta))/theta^2, c = (theta - sin(theta))/theta^3, and   */
+/*    below theta = 0.01 their series 1 - theta^2/6, 1/2 - theta^2/24,      */
+/*    1/6 - theta^2/120; then R <- R_d R, t <- R_d t + V v.                 */
+/* ------------------------------------------------------------------------ */
+static void mat3_mul(const double *A, const double *B, double *C)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+void orc_se3_exp(const double *d6, double *R9, double *V9)
+{
+    const double *w = d6;
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double th = sqrt(th2);
+    double a, b, c;
+    if (th < 0.01) {
+        a = 1.0 - th2 / 6.0;
+        b = 0.5 - th2 / 24.0;
+        c = 1.0 / 6.0 - th2 / 120.0;
+    } else {
+        a = sin(th) / th;
+        b = (1.0 - cos(th)) / th2;
+        c = (th - sin(th)) / (th2 * th);
+    }
+    const double W[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    double W2[9];
+    mat3_mul(W, W, W2);
+    for (int i = 0; i < 9; ++i) {
+        const double id = (i % 4 == 0) ? 1.0 : 0.0;
+        R9[i] = id + a * W[i] + b * W2[i];
+        V9[i] = id + b * W[i] + c * W2[i];
+    }
+}
+
+/* Residual e = obs - projection of world point Pw at pose (R, t) and its
+ * Jacobian J (rows u, v[, u_right], 6 columns: rotation then translation of
+ * the left perturbation).  Returns 0 if the point is not in front (z <= 0). */
+int orc_pose_residual(const orc_pinhole *cam, const double *R9, const double *t3, const float *Pw,
+                      const double *obs3, int stereo, double *e3, double *J18)
+{
+    const double P[3] = {Pw[0], Pw[1], Pw[2]};
+    double Pc[3];
+    for (int i = 0; i < 3; ++i) Pc[i] = R9[3 * i] * P[0] + R9[3 * i + 1] * P[1] + R9[3 * i + 2] * P[2] + t3[i];
+    const double x = Pc[0], y = Pc[1], z = Pc[2];
+    if (!(z > 0.0)) return 0;
+    const double fx = cam->fx, fy = cam->fy, cx = cam->cx, cy = cam->cy, bf = cam->bf;
+    const double iz = 1.0 / z, iz2 = iz * iz;
+    const double u = fx * x * iz + cx, v = fy * y * iz + cy;
+    e3[0] = obs3[0] - u;
+    e3[1] = obs3[1] - v;
+    e3[2] = stereo ? obs3[2] - (u - bf * iz) : 0.0;
+    /* d projection / d Pc */
+    const double D[9] = {fx * iz, 0.0, -fx * x * iz2,
+                         0.0, fy * iz, -fy * y * iz2,
+                         fx * iz, 0.0, -fx * x * iz2 + bf * iz2};
+    /* d Pc / d (w, v) = [ -[Pc]x | I ] */
+    const double S[18] = {0.0, z, -y, 1.0, 0.0, 0.0,
+                          -z, 0.0, x, 0.0, 1.0, 0.0,
+                          y, -x, 0.0, 0.0, 0.0, 1.0};
+    const int rows = stereo ? 3 : 2;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 6; ++c)
+            J18[6 * r + c] = r < rows ? D[3 * r] * S[c] + D[3 * r + 1] * S[6 + c] + D[3 * r + 2] * S[12 + c] : 0.0;
+    return 1;
+}
+
+/* Solve H d = g for symmetric positive definite H (6x6) by Cholesky. */
+static int solve6(const double *H, const double *g, double *d)
+{
+    double Lm[36] = {0};
+    for (int j = 0; j < 6; ++j) {
+        double s = H[6 * j + j];
+        for (int k = 0; k < j; ++k) s -= Lm[6 * j + k] * Lm[6 * j + k];
+        if (!(s > 0.0)) return 0;
+        Lm[6 * j + j] = sqrt(s);
+        for (int i = j + 1; i < 6; ++i) {
+            double q = H[6 * i + j];
+            for (int k = 0; k < j; ++k) q -= Lm[6 * i + k] * Lm[6 * j + k];
+            Lm[6 * i + j] = q / Lm[6 * j + j];
+        }
+    }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = g[i];
+        for (int k = 0; k < i; ++k) s -= Lm[6 * i + k] * y[k];
+        y[i] = s / Lm[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= Lm[6 * k + i] * d[k];
+        d[i] = s / Lm[6 * i + i];
+    }
+    return 1;
+}
+
+int orc_optimize_pose_pinhole(const orc_params *p, const orc_pinhole *cam, const orc_pose *T0,
+                              const orc_keypoints *K, const float *u_right, int M, const float *pos,
+                              const int32_t *mp_kp, double *Rt12, int8_t *inlier, double *chi2,
+                              double *min_margin, int *rounds_run)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
+    double R[9], t[3];
+    for (int i = 0; i < 9; ++i) R[i] = T0->R[i];
+    for (int i = 0; i < 3; ++i) t[i] = T0->t[i];
+    double margin = INFINITY;
+    int rounds = 0;
+    for (int m = 0; m < M; ++m) {
+        inlier[m] = (mp_kp[m] >= 0 && mp_kp[m] < K->n) ? 1 : -1;
+        chi2[m] = -1.0;
+    }
+    for (int round = 0; round < p->po_rounds; ++round) {
+        int n_in = 0;
+        for (int m = 0; m < M; ++m) n_in += inlier[m] == 1;
+        if (n_in < 3) break;
+        int ok = 1;
+        for (int it = 0; it < p->po_iters && ok; ++it) {
+            double H[36] = {0}, g[6] = {0};
+            for (int m = 0; m < M; ++m) {
+                if (inlier[m] != 1) continue;
+                const int k = mp_kp[m];
+                const int oct = K->oct[k];
+                const double s = (oct >= 0 && oct < p->nlevels) ? (double)sc[oct] : 1.0;
+                const double w = 1.0 / (s * s);
+                const int stereo = u_right != NULL && u_right[k] >= 0.0f;
+                const double obs[3] = {K->x[k], K->y[k], stereo ? (double)u_right[k] : 0.0};
+                double e[3], J[18];
+                if (!orc_pose_residual(cam, R, t, pos + 4 * m, obs, stereo, e, J)) continue;
+                const double c2 = w * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+                const double th = stereo ? p->po_chi2_stereo : p->po_chi2_mono;
+                const double h = (!p->po_huber || c2 <= th) ? 1.0 : sqrt(th / c2);
+                const int rows = stereo ? 3 : 2;
+                for (int a = 0; a < 6; ++a) {
+                    for (int r = 0; r < rows; ++r) g[a] += h * w * J[6 * r + a] * e[r];
+                    for (int b2 = 0; b2 < 6; ++b2)
+                        for (int r = 0; r < rows; ++r) H[6 * a + b2] += h * w * J[6 * r + a] * J[6 * r + b2];
+                }
+            }
+            double d[6], Rd[9], V[9];
+            if (!solve6(H, g, d)) {
+                ok = 0;
+                break;
+            }
+            orc_se3_exp(d, Rd, V);
+            double Rn[9], tn[3];
+            mat3_mul(Rd, R, Rn);
+            for (int i = 0; i < 3; ++i)
+                tn[i] = Rd[3 * i] * t[0] + Rd[3 * i + 1] * t[1] + Rd[3 * i + 2] * t[2] +
+                        V[3 * i] * d[3] + V[3 * i + 1] * d[4] + V[3 * i + 2] * d[5];
+            memcpy(R, Rn, sizeof(R));
+            memcpy(t, tn, sizeof(t));
+        }
+        ++rounds;
+        /* classify every observation at the new pose */
+        for (int m = 0; m < M; ++m) {
+            if (inlier[m] < 0) continue;
+            const int k = mp_kp[m];
+            const int oct = K->oct[k];
+            const double s = (oct >= 0 && oct < p->nlevels) ? (double)sc[oct] : 1.0;
+            const int stereo = u_right != NULL && u_right[k] >= 0.0f;
+            const double obs[3] = {K->x[k], K->y[k], stereo ? (double)u_right[k] : 0.0};
+            const double th = stereo ? p->po_chi2_stereo : p->po_chi2_mono;
+            double e[3], J[18];
+            if (!orc_pose_residual(cam, R, t, pos + 4 * m, obs, stereo, e, J)) {
+                inlier[m] = 0;
+                chi2[m] = INFINITY;
+                continue;
+            }
+            const double c2 = (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) / (s * s);
+            chi2[m] = c2;
+            inlier[m] = c2 > th ? 0 : 1;
+            const double mg = fabs(c2 - th) / th;
+            if (mg < margin) margin = mg;
+        }
+        if (!ok) break;
+    }
+    for (int i = 0; i < 9; ++i) Rt12[i] = R[i];
+    for (int i = 0; i < 3; ++i) Rt12[9 + i] = t[i];
+    int n_in = 0;
+    for (int m = 0; m < M; ++m) n_in += inlier[m] == 1;
+    if (min_margin) *min_margin = margin;
+    if (rounds_run) *rounds_run = rounds;
+    return n_in;
+}

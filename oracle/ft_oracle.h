@@ -21,7 +21,9 @@
  *
  * Floating point: FP32, each operation in the order written here, compiled
  * with -ffp-contract=off so no multiply-add is fused.  Division and sqrtf are
- * IEEE correctly rounded.  Integer work (Hamming, SAD) is exact.
+ * IEEE correctly rounded.  Integer work (Hamming, SAD) is exact.  The pose
+ * optimization (next row f4) alone runs in double precision: the library
+ * computes it in FP32 and is compared with a stated tolerance.
  */
 #ifndef FT_ORACLE_H
 #define FT_ORACLE_H
@@ -64,6 +66,12 @@ typedef struct {
     /* fisheye triangulation (next row f1) */
     int   kb_iters;         /* Newton iterations of the Kannala-Brandt unprojection (10) */
     float min_depth;        /* keep a triangulated point only if its depth > min_depth (1e-4 m) */
+    /* pose optimization (next row f4) */
+    int   po_rounds;        /* classification rounds (4) */
+    int   po_iters;         /* Gauss-Newton steps per round (10) */
+    float po_chi2_mono;     /* outlier above this chi2, two residuals (5.991) */
+    float po_chi2_stereo;   /* outlier above this chi2, three residuals (7.815) */
+    int   po_huber;         /* Huber weights with delta^2 = the threshold (1) or none (0) */
 } orc_params;
 
 typedef struct {
@@ -196,6 +204,15 @@ void orc_search_last_fisheye(const orc_params *p, const orc_kb8 *camL, const orc
                              int32_t *mp_d2_l, int32_t *kp_mp_l,
                              int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
                              int32_t *mp_d2_r, int32_t *kp_mp_r);
+
+/* ---- pose optimization (next row f4), double precision ---------------- */
+void orc_se3_exp(const double *d6, double *R9, double *V9);
+int orc_pose_residual(const orc_pinhole *cam, const double *R9, const double *t3, const float *Pw,
+                      const double *obs3, int stereo, double *e3, double *J18);
+int orc_optimize_pose_pinhole(const orc_params *p, const orc_pinhole *cam, const orc_pose *T0,
+                              const orc_keypoints *K, const float *u_right, int M, const float *pos,
+                              const int32_t *mp_kp, double *Rt12, int8_t *inlier, double *chi2,
+                              double *min_margin, int *rounds_run);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,11 @@ DEFAULT_PARAMS = dict(
     th_last=7.0,
     kb_iters=10,
     min_depth=1e-4,
+    po_rounds=4,
+    po_iters=10,
+    po_chi2_mono=5.991,
+    po_chi2_stereo=7.815,
+    po_huber=1,
 )
 
 

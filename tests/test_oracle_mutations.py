@@ -88,6 +88,17 @@ MUTANTS = [
     ("last_right_t_dropped",
      "tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2] + t_rl[i];",
      "tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2];"),
+    # pose optimization (next row f4)
+    ("pose_jacobian_sign", "const double S[18] = {0.0, z, -y, 1.0, 0.0, 0.0,", "const double S[18] = {0.0, -z, y, 1.0, 0.0, 0.0,"),
+    ("pose_stereo_bf_sign", "-fx * x * iz2 + bf * iz2};", "-fx * x * iz2 - bf * iz2};"),
+    ("pose_weight_not_squared", "const double w = 1.0 / (s * s);", "const double w = 1.0 / s;"),
+    ("pose_huber_no_sqrt", "c2 <= th) ? 1.0 : sqrt(th / c2);", "c2 <= th) ? 1.0 : th / c2;"),
+    ("pose_right_multiplied", "mat3_mul(Rd, R, Rn);", "mat3_mul(R, Rd, Rn);"),
+    ("pose_exp_series_sign", "a = 1.0 - th2 / 6.0;", "a = 1.0 + th2 / 6.0;"),
+    ("pose_exp_v_coefficient", "V9[i] = id + b * W[i] + c * W2[i];", "V9[i] = id + a * W[i] + c * W2[i];"),
+    ("pose_stereo_threshold", "const double th = stereo ? p->po_chi2_stereo : p->po_chi2_mono;\n            double e[3], J[18];",
+     "const double th = p->po_chi2_mono;\n            double e[3], J[18];"),
+    ("pose_min_three", "if (n_in < 3) break;", "if (n_in < 2) break;"),
     ("last_view_distance", "        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;",
      "        if (Pc[2] > 8.0f) continue;\n        level[m] = (int8_t)last_level(p, last_oct, m);\n        proj[4 * m + 0] = u;"),
 ]
@@ -114,7 +125,8 @@ def _run_mutant(tmp, name, old, new):
                         os.path.join(ROOT, "tests", "test_oracle_lastframe.py"),
                         os.path.join(ROOT, "tests", "test_oracle_pyramid.py"),
                         os.path.join(ROOT, "tests", "test_oracle_fisheye_rig.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_mirror.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_mirror.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pose.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
