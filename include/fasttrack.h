@@ -87,6 +87,11 @@ typedef struct {
     int   kb_iters;         /* fisheye triangulation: Newton steps of the
                                Kannala-Brandt unprojection (10), in [1, 64] */
     float min_depth;        /* fisheye triangulation: keep depth > 1e-4 m */
+    int   po_rounds;        /* pose optimization: classification rounds (4), in [1, 16] */
+    int   po_iters;         /* pose optimization: Gauss-Newton steps per round (10), in [1, 64] */
+    float po_chi2_mono;     /* pose optimization: outlier above this chi2, 2 residuals (5.991) */
+    float po_chi2_stereo;   /* pose optimization: outlier above this chi2, 3 residuals (7.815) */
+    int   po_huber;         /* pose optimization: Huber weights (1) or plain least squares (0) */
 } ft_params;
 
 /* Keypoints of one image (level-0 pixel coordinates).  desc is [n][32]

@@ -36,7 +36,8 @@ class ft_params(C.Structure):
                 ("nn_ratio", f32), ("ratio_any_octave", i32), ("search_th", f32),
                 ("view_cos_min", f32), ("view_cos_narrow", f32), ("radius_narrow", f32),
                 ("radius_wide", f32), ("dist_lo", f32), ("dist_hi", f32), ("th_last", f32), ("kb_iters", i32),
-                ("min_depth", f32)]
+                ("min_depth", f32), ("po_rounds", i32), ("po_iters", i32), ("po_chi2_mono", f32),
+                ("po_chi2_stereo", f32), ("po_huber", i32)]
 
 
 class ft_keypoints(C.Structure):

@@ -182,6 +182,11 @@ ft_status ft::check_params(const ft_params &p)
     if (!(p.th_last > 0.0f) || !std::isfinite(p.th_last)) return fail(FT_EINVAL, "th_last must be > 0");
     if (p.kb_iters < 1 || p.kb_iters > 64) return fail(FT_EINVAL, "kb_iters %d out of [1, 64]", p.kb_iters);
     if (!(p.min_depth >= 0.0f) || !std::isfinite(p.min_depth)) return fail(FT_EINVAL, "min_depth must be >= 0");
+    if (p.po_rounds < 1 || p.po_rounds > 16) return fail(FT_EINVAL, "po_rounds %d out of [1, 16]", p.po_rounds);
+    if (p.po_iters < 1 || p.po_iters > 64) return fail(FT_EINVAL, "po_iters %d out of [1, 64]", p.po_iters);
+    if (!(p.po_chi2_mono > 0.0f) || !std::isfinite(p.po_chi2_mono) || !(p.po_chi2_stereo > 0.0f) ||
+        !std::isfinite(p.po_chi2_stereo))
+        return fail(FT_EINVAL, "pose optimization chi2 thresholds must be finite and > 0");
     float sc = 1.0f;
     for (int l = 1; l < p.nlevels; ++l) sc = sc * p.scale_factor;
     if (!(2.0f * sc < 1.0e6f)) return fail(FT_EINVAL, "scale_factor^(nlevels-1) = %g is too large", sc);
@@ -796,6 +801,11 @@ void ft_params_default(ft_params *p)
     p->th_last = 7.0f;
     p->kb_iters = 10;
     p->min_depth = 1e-4f;
+    p->po_rounds = 4;
+    p->po_iters = 10;
+    p->po_chi2_mono = 5.991f;
+    p->po_chi2_stereo = 7.815f;
+    p->po_huber = 1;
 }
 
 const char *ft_last_error(void) { return g_last_error.c_str(); }
