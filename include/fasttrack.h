@@ -216,6 +216,18 @@ typedef struct {
     ft_search_cam_out right;   /* fisheye frames only */
 } ft_search_out;
 
+/* Pose optimization output of one pinhole frame (next row f4):
+ *   Rt        [12] refined pose: R (row-major, world -> camera) then t
+ *   inlier    [M] 1 inlier, 0 outlier after the last round, -1 unmatched
+ *             map point (M = the map's points)
+ *   n_inliers [1] number of inliers
+ * All three are device pointers. */
+typedef struct {
+    float *Rt;
+    int8_t *inlier;
+    int32_t *n_inliers;
+} ft_pose_out;
+
 /* A frame as seen by the search step.  Pinhole: left keypoints only, with
  * u_right from stereo matching (NULL: no stereo consistency check).
  * Fisheye: left and right keypoints, each camera with its own grid; O_right
@@ -269,6 +281,9 @@ typedef struct {
     int build_pyramids;                 /* pinhole: nonzero = levels 1.. of pyr_left and pyr_right
                                            are built on the device from level 0 before the stereo
                                            step reads them (see ft_build_pyramid) */
+    const ft_pose_out *pose_out;        /* HOST struct; pinhole frames: non-NULL = optimize the pose
+                                           over the search's matches after the search (see
+                                           ft_optimize_pose); NULL: no pose optimization */
 } ft_frame_job;
 
 /* A ragged batch.  frames points to HOST memory (n entries).  If
@@ -365,6 +380,30 @@ ft_status ft_search_local_points(ft_ctx *ctx, void *stream, const ft_params *par
 ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *params,
                                const ft_frame_view *frame, const ft_pose *Tcw,
                                const ft_last_frame_view *last, ft_search_out *out);
+
+/* Pose optimization of one pinhole frame (next row f4): the refinement of
+ * the camera pose with all the map points the search found in the frame
+ * (section II-D; FastTrack switches it off, section IV-F).  The method is a
+ * reading of the algorithm family's motion-only optimization:
+ *   - observations: map point m with match k = mp_kp[m] (0 <= k < left.n) is
+ *     observed at (left.x[k], left.y[k]) and, if frame->u_right is not NULL
+ *     and u_right[k] >= 0, also at u_right[k] (a stereo observation, three
+ *     residuals; else two).  Weight 1 / scale[left.oct[k]]^2.
+ *   - po_rounds rounds, each run only while at least 3 observations are
+ *     inliers (all are at the start): po_iters Gauss-Newton steps over the
+ *     inliers in front of the camera with Huber weights (po_huber; delta^2 =
+ *     po_chi2_mono or po_chi2_stereo), the update exp(d) multiplied on the
+ *     left of the pose; then every observation is classified again: outlier
+ *     if behind the camera or chi2 above its threshold.  A step whose normal
+ *     matrix is not positive definite ends the optimization after that
+ *     round's classification.
+ * FP32 on the device, one work item per frame.  Inputs: frame->pinhole,
+ * frame->left, frame->u_right (may be NULL), Tcw (the starting pose),
+ * map->pos ([n][4], 16-byte aligned; the rest of the map is not read) and
+ * mp_kp ([map->n] device int32, the search's matches).  Outputs: out. */
+ft_status ft_optimize_pose(ft_ctx *ctx, void *stream, const ft_params *params,
+                           const ft_frame_view *frame, const ft_pose *Tcw, const ft_map_view *map,
+                           const int32_t *mp_kp, const ft_pose_out *out);
 
 /* Sizes of the pyramid levels of a width x height level 0 (next row f3, its
  * pyramid part): level l is round(width / scale[l]) x round(height /

@@ -107,6 +107,10 @@ class ft_last_frame_view(C.Structure):
     _fields_ = [("n", i32), ("pos", vp), ("desc", vp), ("oct", vp), ("skip", vp), ("pose", ft_pose)]
 
 
+class ft_pose_out(C.Structure):
+    _fields_ = [("Rt", vp), ("inlier", vp), ("n_inliers", vp)]
+
+
 class ft_frame_job(C.Structure):
     _fields_ = [("camera", i32), ("pinhole", ft_pinhole), ("fisheye", ft_fisheye_rig),
                 ("left", ft_keypoints), ("right", ft_keypoints), ("pyr_left", ft_pyramid),
@@ -114,7 +118,7 @@ class ft_frame_job(C.Structure):
                 ("pose", ft_pose), ("O_right", f32 * 3), ("map", ft_map_view),
                 ("stereo", ft_stereo_out), ("fisheye_out", ft_fisheye_out),
                 ("search", ft_search_out), ("last", C.POINTER(ft_last_frame_view)),
-                ("build_pyramids", i32)]
+                ("build_pyramids", i32), ("pose_out", C.POINTER(ft_pose_out))]
 
 
 class ft_batch(C.Structure):
@@ -194,6 +198,8 @@ SIGNATURES = [
     ("ft_search_last_frame", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_frame_view),
                                    C.POINTER(ft_pose), C.POINTER(ft_last_frame_view),
                                    C.POINTER(ft_search_out)]),
+    ("ft_optimize_pose", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_frame_view), C.POINTER(ft_pose),
+                               C.POINTER(ft_map_view), vp, C.POINTER(ft_pose_out)]),
     ("ft_pyramid_sizes", i32, [i32, i32, C.POINTER(ft_params), vp, vp]),
     ("ft_measure_popcount", i32, [vp, C.POINTER(C.c_double)]),
     ("ft_build_pyramid", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_pyramid)]),

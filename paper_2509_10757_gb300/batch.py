@@ -61,9 +61,13 @@ def _input_arrays(f, fr, last=None, device_pyramids=False):
     return out
 
 
-def _output_specs(f, fr, last=None):
+def _output_specs(f, fr, last=None, pose=False):
     nl, nr, m = fr.left.n, fr.right.n, fr.map.n
     spec = []
+    if pose and fr.camera == "pinhole":
+        npts = last.n if last is not None else m
+        spec += [((f, "po_Rt"), np.float32, (12,)), ((f, "po_inlier"), np.int8, (npts,)),
+                 ((f, "po_n"), np.int32, (1,))]
     if fr.camera == "pinhole":
         spec += [((f, k), np.int32, (nl,)) for k in ("best_r", "dist", "sad_shift", "sad_best")]
         spec += [((f, "u_right"), np.float32, (nl,)), ((f, "depth"), np.float32, (nl,))]
@@ -136,13 +140,15 @@ class PackedBatch:
     """Inputs and outputs of a list of generated frames, packed for the GPU."""
 
     def __init__(self, frames, device: str | torch.device = "cuda", pin: bool = True, lasts=None,
-                 device_pyramids: bool = False):
+                 device_pyramids: bool = False, pose: bool = False):
         """lasts: optional per-frame scenes.LastFrame (or None); a frame with
         one gets the last frame's points packed too, its batch job searches
         them instead of the local map, and its results go to the lf_* outputs.
         device_pyramids: pinhole frames carry only level 0 of their images;
         levels 1.. live in a device buffer the launch fills (ft_frame_job
-        build_pyramids), with the sizes ft_pyramid_sizes gives."""
+        build_pyramids), with the sizes ft_pyramid_sizes gives.
+        pose: pinhole frames get pose optimization outputs (po_Rt, po_inlier,
+        po_n) and their batch jobs optimize the pose after the search."""
         self.frames = list(frames)
         self.lasts = list(lasts) if lasts is not None else [None] * len(self.frames)
         self.device_pyramids = device_pyramids
@@ -155,7 +161,7 @@ class PackedBatch:
                 a = np.ascontiguousarray(a)
                 self.lin.add(key, a.dtype, a.shape)
                 arrays.append(a)
-            for key, dt, shape in _output_specs(f, fr, self.lasts[f]):
+            for key, dt, shape in _output_specs(f, fr, self.lasts[f], pose):
                 self.lout.add(key, dt, shape)
         self.host_in = torch.empty(self.lin.size, dtype=torch.uint8, pin_memory=pin)
         self.host_out = torch.empty(self.lout.size, dtype=torch.uint8, pin_memory=pin)
@@ -179,6 +185,8 @@ class PackedBatch:
         self.dev_pyr = torch.empty(max(self.lpyr.size, 1), dtype=torch.uint8, device=self.device)
         self.last_views = [self.last_view(f) if self.lasts[f] is not None else None
                            for f in range(len(self.frames))]
+        self.pose_outs = [self.pose_out(f) if self.has_out(f, "po_Rt") else None
+                          for f in range(len(self.frames))]
         self.jobs = (L.ft_frame_job * max(1, len(self.frames)))()
         for f in range(len(self.frames)):
             self.jobs[f] = self.job(f)
@@ -255,6 +263,11 @@ class PackedBatch:
                     setattr(dst, k, self.pout(f, f"{prefix}{k}_{side}"))
         return s
 
+    def pose_out(self, f) -> L.ft_pose_out:
+        s = L.ft_pose_out()
+        s.Rt, s.inlier, s.n_inliers = self.pout(f, "po_Rt"), self.pout(f, "po_inlier"), self.pout(f, "po_n")
+        return s
+
     def last_view(self, f) -> L.ft_last_frame_view:
         last = self.lasts[f]
         s = L.ft_last_frame_view()
@@ -304,6 +317,8 @@ class PackedBatch:
             j.pyr_left, j.pyr_right = self.pyramid(f, "L"), self.pyramid(f, "R")
             j.stereo = self.stereo_out(f)
             j.build_pyramids = 1 if self.device_pyramids else 0
+            if self.pose_outs[f] is not None:
+                j.pose_out = C.pointer(self.pose_outs[f])
         else:
             j.camera = L.FT_CAMERA_FISHEYE
             j.fisheye = rig_struct(fr.rig)
@@ -436,6 +451,20 @@ def run_search_last(ctx: Context, pb: PackedBatch, f: int, params: L.ft_params |
     r = ctx.lib.ft_search_last_frame(ctx.ptr, stream_handle(stream), p, C.byref(fv), C.byref(pose),
                                      C.byref(lv), C.byref(out))
     L.check(r, "ft_search_last_frame")
+
+
+def run_pose(ctx: Context, pb: PackedBatch, f: int, params: L.ft_params | None = None, stream=None,
+             u_right: bool = True):
+    """ft_optimize_pose on frame f (pinhole): its local-map search matches
+    (mp_kp_l) from the frame's starting pose, with its stereo u_right."""
+    fr = pb.frames[f]
+    fv = pb.frame_view(f, u_right=u_right)
+    pose = pose_struct(fr.pose)
+    mv = pb.map_view(f)
+    out = pb.pose_outs[f]
+    L.check(ctx.lib.ft_optimize_pose(ctx.ptr, stream_handle(stream), C.byref(params) if params is not None else None,
+                                     C.byref(fv), C.byref(pose), C.byref(mv), C.c_void_p(pb.pout(f, "mp_kp_l")),
+                                     C.byref(out)), "ft_optimize_pose")
 
 
 def run_batch(ctx: Context, pb: PackedBatch, params: L.ft_params | None = None, stream=None,

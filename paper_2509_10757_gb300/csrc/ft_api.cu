@@ -110,6 +110,9 @@ struct Job {
     int search_mode = 0;                  // 0: local map; 1: the last frame's points (map.nrm unused)
     const int8_t *last_oct = nullptr;
     ft_pose last_pose{};
+    bool do_pose = false;                 // pose optimization after the search (pinhole)
+    ft_pose_out po{};
+    const int32_t *po_mp_kp = nullptr;    // matches when the call does no search
 };
 
 // the map view and mode of a last-frame search
@@ -287,6 +290,16 @@ ft_status check_job(const Job &j, const ft_params &p)
     } else {
         return fail(FT_EINVAL, "unknown camera model %d", j.camera);
     }
+    if (j.do_pose) {
+        if (j.camera != FT_CAMERA_PINHOLE) return fail(FT_EINVAL, "pose optimization: pinhole frames only");
+        const ft_map_view &m = j.map;
+        if (m.n < 0 || m.n >= FT_MAX_MAP_POINTS) return fail(FT_EINVAL, "map: n=%d out of range", m.n);
+        if (!j.po.Rt || !j.po.n_inliers || (m.n > 0 && !j.po.inlier))
+            return fail(FT_EINVAL, "pose output: NULL array");
+        if (m.n > 0 && (!m.pos || !aligned16(m.pos))) return fail(FT_EALIGN, "map: pos NULL or not 16-byte aligned");
+        if (!j.do_search && m.n > 0 && !j.po_mp_kp) return fail(FT_EINVAL, "pose optimization: NULL mp_kp");
+        if (!j.do_search && (s = check_kps(j.left, "left keypoints")) != FT_OK) return s;
+    }
     if (j.do_search) {
         const ft_map_view &m = j.map;
         if (m.n < 0 || m.n >= FT_MAX_MAP_POINTS) return fail(FT_EINVAL, "map: n=%d out of range", m.n);
@@ -344,6 +357,11 @@ DevParams ft::make_dev_params(const ft_params &p)
     d.kb_iters = p.kb_iters;
     d.min_depth = p.min_depth;
     d.dist_hi = p.dist_hi;
+    d.po_rounds = p.po_rounds;
+    d.po_iters = p.po_iters;
+    d.po_huber = p.po_huber;
+    d.po_chi2_mono = p.po_chi2_mono;
+    d.po_chi2_stereo = p.po_chi2_stereo;
     // a right keypoint's band reaches rows within ceil(r) + 2 of floor(y); +1 margin
     d.halo = (int)std::ceil(rmax) + 3;
     // a left keypoint of octave o only meets right octaves up to o + 1
@@ -466,7 +484,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
         F.wait_stereo = j.wait_stereo;
         F.nl = j.left.n;
         F.nr = j.right.n;
-        F.nm = j.do_search ? j.map.n : 0;
+        F.nm = (j.do_search || j.do_pose) ? j.map.n : 0;
         F.lx = j.left.x;
         F.ly = j.left.y;
         F.loct = j.left.oct;
@@ -599,6 +617,33 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             }
             F.n_grid_items = F.ncam;
         }
+        int n_pose = 0;
+        if (j.do_pose) {
+            CamDev &C = F.cam[0];
+            if (!j.do_search) {
+                // the standalone call: the camera, pose and keypoints the
+                // search would have set up
+                C.model = FT_CAMERA_PINHOLE;
+                C.fx = j.pin.fx;
+                C.fy = j.pin.fy;
+                C.cx = j.pin.cx;
+                C.cy = j.pin.cy;
+                C.bf = j.pin.bf;
+                for (int i = 0; i < 9; ++i) C.R[i] = j.pose.R[i];
+                for (int i = 0; i < 3; ++i) C.t[i] = j.pose.t[i];
+                fill_cam_kps(C, j.left, nullptr);
+                F.u_right_in = j.u_right_in;
+                F.pos = reinterpret_cast<const float4 *>(j.map.pos);
+            }
+            F.do_pose = 1;
+            F.po_mp_kp = j.do_search ? j.so.left.mp_kp : j.po_mp_kp;
+            F.po_Rt = j.po.Rt;
+            F.po_inlier = j.po.inlier;
+            F.po_n = j.po.n_inliers;
+            F.po_list = reinterpret_cast<float4 *>(carve(sizeof(float4) * 2 * (size_t)std::max(F.nm, 1)));
+            F.n_resolve_signals = j.do_search ? (F.fold_resolve ? F.ncam : n_resolve[0] + n_resolve[1]) : 0;
+            n_pose = 1;
+        }
         n_index = F.rowsort + F.n_grid_items;
         if (scratch > ctx->arena_bytes)
             return fail(FT_ENOMEM, "arena of %zu bytes too small for this batch (needs %zu)", ctx->arena_bytes, scratch);
@@ -608,7 +653,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
         F.n_resolve_items[0] = n_resolve[0];
         F.n_resolve_items[1] = n_resolve[1];
         const int per_kind[K_KINDS] = {n_index, n_stereo, n_search[0] + n_search[1],
-                                       n_resolve[0] + n_resolve[1]};
+                                       n_resolve[0] + n_resolve[1], n_pose};
         for (int k = 0; k < K_KINDS; ++k) {
             prefix[k * (n + 1) + f] = counts[k];
             counts[k] += per_kind[k];
@@ -1014,6 +1059,26 @@ ft_status ft_search_last_frame(ft_ctx *ctx, void *stream, const ft_params *param
     return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
 }
 
+ft_status ft_optimize_pose(ft_ctx *ctx, void *stream, const ft_params *params, const ft_frame_view *frame,
+                           const ft_pose *Tcw, const ft_map_view *map, const int32_t *mp_kp, const ft_pose_out *out)
+{
+    if (!ctx || !frame || !Tcw || !map || !out) return fail(FT_EINVAL, "ft_optimize_pose: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    Job j;
+    j.camera = frame->camera;
+    j.do_pose = true;
+    j.pin = frame->pinhole;
+    j.left = frame->left;
+    j.u_right_in = frame->u_right;
+    j.pose = *Tcw;
+    j.map = *map;
+    j.po = *out;
+    j.po_mp_kp = mp_kp;
+    return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
+}
+
 ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *w, int *h)
 {
     if (!w || !h || width <= 0 || height <= 0) return fail(FT_EINVAL, "ft_pyramid_sizes: bad argument");
@@ -1103,6 +1168,10 @@ static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
         j.u_right_in = s.camera == FT_CAMERA_PINHOLE ? s.stereo.u_right : nullptr;
         if (s.last) set_last(j, *s.last);
         j.build_pyr = s.build_pyramids != 0 ? 3 : 0;
+        if (s.pose_out) {
+            j.do_pose = true;
+            j.po = *s.pose_out;
+        }
     }
     return FT_OK;
 }

@@ -43,11 +43,11 @@ __host__ __device__ inline int pyr_vblocks(int w, int h)
     return (int)((t + kPyrThreads - 1) / kPyrThreads);
 }
 
-enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
+enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_POSE = 4, K_KINDS = 5 };
 
 // per-frame counter slots
 enum Ctr { C_GRID_DONE = 0, C_STEREO_DONE = 1, C_STEREO_READY = 2, C_SEARCH_DONE0 = 3,
-           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5 };
+           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5, C_RESOLVED = 6 };
 
 // device status bits (ORed into the context's status word)
 constexpr unsigned kStatusTimeout = 1u;
@@ -63,6 +63,8 @@ struct DevParams {
     float th_last;
     int kb_iters;
     float min_depth;
+    int po_rounds, po_iters, po_huber;
+    float po_chi2_mono, po_chi2_stereo;
     int halo;            // rows a right keypoint's band can reach beyond floor(y), any octave
     int halo_oct[FT_MAX_LEVELS];   // same for the octave window of a left keypoint of octave o
     int halo_c[FT_MAX_LEVELS];     // same for a right keypoint of octave o
@@ -140,6 +142,15 @@ struct FrameDev {
     int fold_resolve;              // 1: the last search item of a camera writes the final tables
     int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]
+    // pose optimization (next row f4): one work item after the frame's final
+    // match tables (C_RESOLVED reaches n_resolve_signals), pinhole frames
+    int do_pose;
+    int n_resolve_signals;         // resolve completions to wait for (0: the matches are inputs)
+    const int *po_mp_kp;           // [nm] matches: map point -> keypoint (cam[0])
+    float *po_Rt;                  // [12] out: R row-major, t
+    int8_t *po_inlier;             // [nm] out: 1 inlier, 0 outlier, -1 unmatched
+    int *po_n;                     // [1] out: inliers
+    float4 *po_list;               // [2 * nm] scratch: observations in map-point order
 };
 
 struct BatchHeader {
