@@ -573,7 +573,8 @@ def fisheye_pairs(frames) -> int:
     return n
 
 
-def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_bytes: int, lasts=None) -> dict:
+def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_bytes: int, lasts=None,
+               pose: bool = False) -> dict:
     """One fused launch per step over `frames` (graph replay, autotuned tiles,
     L2 flushed between steps): launch time, throughput and the HBM roofline."""
     import ctypes as C
@@ -583,7 +584,7 @@ def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_byte
     from paper_2509_10757_gb300 import _lib as L
     from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch, stream_handle
 
-    pb = PackedBatch(frames, device=dev, lasts=lasts)
+    pb = PackedBatch(frames, device=dev, lasts=lasts, pose=pose)
     pb.upload()
     ctx = Context(device=local_rank, arena_bytes=arena_bytes, max_frames=max(len(frames), 1), use_graphs=True)
     stream = torch.cuda.Stream(device=dev)
@@ -960,6 +961,16 @@ def run_gpu(args, rank, world, local_rank):
         plain_ms.append(p0.elapsed_time(p1))
     plain_units = sum(frames[f].left.n + frames[f].map.n for f in range(nplain))
 
+    # the batched workload with pose optimization after the search (next row
+    # f4; the paper switches it off, so it is not part of the headline)
+    clocks.mark("pose", True)
+    pose = time_batch(frames, max(20, min(args.steps, 500)), max(3, args.warmup), dev, local_rank,
+                      512 << 20, pose=True)
+    clocks.mark("pose", False)
+    pose["workload"] = ("batched pinhole + pose optimization: the headline's 64 frames, each followed by "
+                        "4 rounds x 10 Gauss-Newton steps over its matches (single launch, L2 flushed)")
+    pose["without_pose_ms_per_launch"] = statistics.mean(step_ms)
+
     # the other batched workloads of the scope, one fused launch per step:
     # the fisheye batch (popcount roofline) and the 1080p stress batch of 32
     clocks.mark("fisheye", True)
@@ -1045,6 +1056,7 @@ def run_gpu(args, rank, world, local_rank):
                                             "(launches overlap)"}},
         "fisheye": fisheye,
         "stress": stress,
+        "pose_optimization": pose,
         "gpu_launches": launches,
         "clocks": clk,
     }
