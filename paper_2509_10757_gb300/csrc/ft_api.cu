@@ -148,9 +148,10 @@ struct ft_ctx {
     bool have_last = false;
     bool use_graphs = false;
     cudaStream_t capture_stream = nullptr;
-    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM,
-                                                                             //  slot, pyramid frames,
-                                                                             //  pyramid blocks per image)
+    std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM,
+                                                                                  //  slot, pyramid frames,
+                                                                                  //  pyramid blocks per image,
+                                                                                  //  pose frames)
     std::map<Bucket, ft_tuning> tuning;
     uint64_t launches = 0;
     unsigned debug_flags = 0;
@@ -617,7 +618,6 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             }
             F.n_grid_items = F.ncam;
         }
-        int n_pose = 0;
         if (j.do_pose) {
             CamDev &C = F.cam[0];
             if (!j.do_search) {
@@ -641,8 +641,6 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             F.po_inlier = j.po.inlier;
             F.po_n = j.po.n_inliers;
             F.po_list = reinterpret_cast<float4 *>(carve(sizeof(float4) * 2 * (size_t)std::max(F.nm, 1)));
-            F.n_resolve_signals = j.do_search ? (F.fold_resolve ? F.ncam : n_resolve[0] + n_resolve[1]) : 0;
-            n_pose = 1;
         }
         n_index = F.rowsort + F.n_grid_items;
         if (scratch > ctx->arena_bytes)
@@ -653,7 +651,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
         F.n_resolve_items[0] = n_resolve[0];
         F.n_resolve_items[1] = n_resolve[1];
         const int per_kind[K_KINDS] = {n_index, n_stereo, n_search[0] + n_search[1],
-                                       n_resolve[0] + n_resolve[1], n_pose};
+                                       n_resolve[0] + n_resolve[1]};
         for (int k = 0; k < K_KINDS; ++k) {
             prefix[k * (n + 1) + f] = counts[k];
             counts[k] += per_kind[k];
@@ -687,9 +685,9 @@ ft_status finish_call(ft_ctx *ctx, cudaStream_t s)
 }
 
 ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int slot, int grid,
-                    size_t copy_bytes, int pyr_frames, int pyr_blocks, cudaGraphExec_t *out)
+                    size_t copy_bytes, int pyr_frames, int pyr_blocks, int pose_frames, cudaGraphExec_t *out)
 {
-    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames, pyr_blocks);
+    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames, pyr_blocks, pose_frames);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
@@ -701,8 +699,9 @@ ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int sl
     FT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e1 = cudaMemcpyAsync(table_dev, ctx->staging[slot], copy_bytes, cudaMemcpyHostToDevice, cs);
     const cudaError_t e0 = launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_blocks, cs);
-    const cudaError_t e2 = e0 != cudaSuccess ? e0 : launch_fused(reinterpret_cast<const BatchHeader *>(table_dev),
-                                                                 grid, cs);
+    cudaError_t e2 = e0 != cudaSuccess ? e0 : launch_fused(reinterpret_cast<const BatchHeader *>(table_dev),
+                                                           grid, cs);
+    if (e2 == cudaSuccess) e2 = launch_pose(reinterpret_cast<const BatchHeader *>(table_dev), pose_frames, cs);
     const cudaError_t e3 = cudaStreamEndCapture(cs, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -768,27 +767,32 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
             }
         pyr_blocks = most;
     }
-    if (items > 0 || pyr_frames > 0) {
+    // frames that optimize their pose run the pose kernel after the fused
+    // kernel, one block per frame up to the last such frame
+    int pose_frames = 0;
+    for (size_t f = 0; f < jobs.size(); ++f)
+        if (jobs[f].do_pose) pose_frames = (int)f + 1;
+    if (items > 0 || pyr_frames > 0 || pose_frames > 0) {
         if (allow_graph && ctx->use_graphs && items > 0) {
             const int fp2 = bk.frames_p2;
             const size_t copy = std::max(bytes, table_layout(fp2).total);
             cudaGraphExec_t exec = nullptr;
             if ((s = get_graph(ctx, table_dev, fp2, cps, slot, grid_max, std::min(copy, ctx->table_cap),
-                               pyr_frames > 0 ? fp2 : 0, pyr_blocks, &exec)) != FT_OK)
+                               pyr_frames > 0 ? fp2 : 0, pyr_blocks, pose_frames > 0 ? fp2 : 0, &exec)) != FT_OK)
                 return s;
             FT_CUDA(cudaGraphLaunch(exec, stream));
         } else {
             FT_CUDA(cudaMemcpyAsync(table_dev, ctx->staging[slot], bytes, cudaMemcpyHostToDevice, stream));
-            if (pyr_frames > 0) {
+            if (pyr_frames > 0)
                 FT_CUDA(launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_blocks,
                                         stream));
-                ctx->launches += 1;
-            }
             if (items > 0)
                 FT_CUDA(launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), std::min(items, grid_max),
                                      stream));
+            if (pose_frames > 0)
+                FT_CUDA(launch_pose(reinterpret_cast<const BatchHeader *>(table_dev), pose_frames, stream));
         }
-        if (items > 0) ctx->launches += 1;
+        ctx->launches += (items > 0 ? 1 : 0) + (pyr_frames > 0 ? 1 : 0) + (pose_frames > 0 ? 1 : 0);
     }
     FT_CUDA(cudaEventRecord(ctx->slot_done[slot], stream));
     return finish_call(ctx, stream);

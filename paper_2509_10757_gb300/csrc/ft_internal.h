@@ -43,11 +43,11 @@ __host__ __device__ inline int pyr_vblocks(int w, int h)
     return (int)((t + kPyrThreads - 1) / kPyrThreads);
 }
 
-enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_POSE = 4, K_KINDS = 5 };
+enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
 
 // per-frame counter slots
 enum Ctr { C_GRID_DONE = 0, C_STEREO_DONE = 1, C_STEREO_READY = 2, C_SEARCH_DONE0 = 3,
-           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5, C_RESOLVED = 6 };
+           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5 };
 
 // device status bits (ORed into the context's status word)
 constexpr unsigned kStatusTimeout = 1u;
@@ -142,10 +142,9 @@ struct FrameDev {
     int fold_resolve;              // 1: the last search item of a camera writes the final tables
     int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]
-    // pose optimization (next row f4): one work item after the frame's final
-    // match tables (C_RESOLVED reaches n_resolve_signals), pinhole frames
+    // pose optimization (next row f4): the pose kernel, launched after the
+    // fused kernel, takes one block per frame with do_pose (pinhole frames)
     int do_pose;
-    int n_resolve_signals;         // resolve completions to wait for (0: the matches are inputs)
     const int *po_mp_kp;           // [nm] matches: map point -> keypoint (cam[0])
     float *po_Rt;                  // [12] out: R row-major, t
     int8_t *po_inlier;             // [nm] out: 1 inlier, 0 outlier, -1 unmatched
@@ -173,10 +172,15 @@ struct BatchHeader {
 // Launch helpers implemented in ft_kernels.cu (host-callable).
 namespace ft {
 cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stream);
+// pose optimization of the frames with do_pose (one block per frame of the
+// first nframes; after the fused kernel on the same stream)
+cudaError_t launch_pose(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream);
 // levels 1.. of the pyramids of the frames that build them (before the fused
 // launch); blocks_per_image blocks stride over each image's virtual blocks
 cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, int blocks_per_image, cudaStream_t stream);
 int fused_smem_bytes();
+// device set-up of the fused and pose kernels (shared-memory attributes),
+// then the fused kernel's resident CTAs per SM
 cudaError_t fused_occupancy(int *ctas_per_sm);
 const void *fused_kernel_ptr();
 // set the text ft_last_error() returns on this thread (ft_api.cu)

@@ -255,16 +255,6 @@ struct SmemSearch {
     uint4 buf[kSearchStage * 3];
 };
 
-// pose optimization of one frame: per-warp partial sums of the normal
-// equations (21 of H, 6 of g), the pose, and scan / count scratch
-struct SmemPose {
-    float part[kWarps][28];
-    float Rt[12];
-    int warp_sums[kWarps];
-    int n_in;
-    int ok;
-};
-
 union Smem {
     SmemStereo s;
     SmemRows r;
@@ -272,7 +262,6 @@ union Smem {
     SmemFish f;
     SmemMedian m;
     SmemSearch q;
-    SmemPose p;
 };
 // three CTAs per SM: dynamic + static shared memory + the 1 KB the SM
 // reserves per CTA must stay within the SM's 228 KB
@@ -1538,7 +1527,6 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         // the last search item of this camera also writes the final tables
         // (small frames: no separate resolve items wait for the search)
         resolve_range(F.cam[cam], F.nm, 0, max(F.nm, F.cam[cam].nk));
-        if (F.do_pose) signal_count(&F.ctr[C_RESOLVED], (unsigned)F.n_resolve_signals, s_flag);
     }
 }
 
@@ -1599,278 +1587,9 @@ __device__ void resolve_item(const BatchHeader &B, const FrameDev &F, int tile, 
         // the wait ran out (reported in the status word): leave defined outputs
         for (int m = i0 + threadIdx.x; m < min(i1, F.nm); m += kThreads) C.mp_kp[m] = -1;
         for (int k = i0 + threadIdx.x; k < min(i1, C.nk); k += kThreads) C.kp_mp[k] = -1;
-    } else {
-        resolve_range(C, F.nm, i0, i1);
-    }
-    if (F.do_pose) signal_count(&F.ctr[C_RESOLVED], (unsigned)F.n_resolve_signals, s_flag);
-}
-
-// ---------------------------------------------------------------- K_POSE (next row f4)
-// Pose optimization of one pinhole frame over the search's matches: the
-// motion-only refinement the paper's tracking runs with all the map points
-// found in the frame (section II-D; FastTrack switches it off, section
-// IV-F).  The reading (the algorithm family's): observations are the
-// matched keypoints (x, y) and, where stereo gave one, u_right; weight
-// 1/scale[oct]^2; po_rounds rounds of po_iters Gauss-Newton steps over the
-// inliers with Huber weights, the perturbation exp(d) multiplied on the left
-// of the pose, every observation reclassified by its chi2 after each round.
-// FP32; one CTA per frame: each thread accumulates the normal equations of
-// its observations, warps reduce by shuffles, thread 0 sums the warps in a
-// fixed order, solves the 6x6 system (Cholesky) and updates the pose.
-
-// exclusive block scan of one value per thread; *total receives the sum
-__device__ int block_scan1(int v, int *warp_sums, int *total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += t;
-    }
-    if (lane == 31) warp_sums[w] = x;
-    __syncthreads();
-    int before = 0, sum = 0;
-#pragma unroll
-    for (int i = 0; i < kWarps; ++i) {
-        const int ws = warp_sums[i];
-        before += i < w ? ws : 0;
-        sum += ws;
-    }
-    __syncthreads();
-    *total = sum;
-    return before + x - v;
-}
-
-// observation of list entry (a, b) at pose Rt: residual, chi2 and the rows
-// of the Jacobian; false if the point is not in front of the camera
-struct PoseObs {
-    float e[3], J[3][6], chi2;
-    bool stereo;
-};
-
-__device__ __forceinline__ bool pose_obs(const CamDev &C, const float *Rt, float4 a, float4 b, PoseObs &o)
-{
-    const float x = Rt[0] * a.x + Rt[1] * a.y + Rt[2] * a.z + Rt[9];
-    const float y = Rt[3] * a.x + Rt[4] * a.y + Rt[5] * a.z + Rt[10];
-    const float z = Rt[6] * a.x + Rt[7] * a.y + Rt[8] * a.z + Rt[11];
-    if (!(z > 0.0f)) return false;
-    const float iz = 1.0f / z, iz2 = iz * iz;
-    const float u = C.fx * x * iz + C.cx, v = C.fy * y * iz + C.cy;
-    o.stereo = b.z >= 0.0f;
-    o.e[0] = b.x - u;
-    o.e[1] = b.y - v;
-    o.e[2] = o.stereo ? b.z - (u - C.bf * iz) : 0.0f;
-    o.chi2 = a.w * (o.e[0] * o.e[0] + o.e[1] * o.e[1] + o.e[2] * o.e[2]);
-    // d projection / d Pc, times d Pc / d (w, v) = [ -[Pc]x | I ]
-    const float D[3][3] = {{C.fx * iz, 0.0f, -C.fx * x * iz2},
-                           {0.0f, C.fy * iz, -C.fy * y * iz2},
-                           {C.fx * iz, 0.0f, -C.fx * x * iz2 + C.bf * iz2}};
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        o.J[r][0] = -D[r][1] * z + D[r][2] * y;
-        o.J[r][1] = D[r][0] * z - D[r][2] * x;
-        o.J[r][2] = -D[r][0] * y + D[r][1] * x;
-        o.J[r][3] = D[r][0];
-        o.J[r][4] = D[r][1];
-        o.J[r][5] = D[r][2];
-    }
-    return true;
-}
-
-// thread 0: H d = g (H packed upper triangle, 21 values) by Cholesky; false
-// if H is not positive definite
-__device__ __noinline__ bool pose_solve(const float *Hp, const float *g, float *d)
-{
-    float H[6][6], L[6][6];
-    int q = 0;
-    for (int i = 0; i < 6; ++i)
-        for (int j = i; j < 6; ++j) H[i][j] = H[j][i] = Hp[q++];
-    for (int j = 0; j < 6; ++j) {
-        float s = H[j][j];
-        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-        if (!(s > 0.0f)) return false;
-        L[j][j] = sqrtf(s);
-        for (int i = j + 1; i < 6; ++i) {
-            float t = H[i][j];
-            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-            L[i][j] = t / L[j][j];
-        }
-    }
-    float y[6];
-    for (int i = 0; i < 6; ++i) {
-        float s = g[i];
-        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-        y[i] = s / L[i][i];
-    }
-    for (int i = 5; i >= 0; --i) {
-        float s = y[i];
-        for (int k = i + 1; k < 6; ++k) s -= L[k][i] * d[k];
-        d[i] = s / L[i][i];
-    }
-    return true;
-}
-
-// thread 0: (R, t) <- exp(d) (R, t), exp of the twist d = (w, v)
-__device__ __noinline__ void pose_update(float *Rt, const float *d)
-{
-    const float th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const float th = sqrtf(th2);
-    float a, b, c;
-    if (th < 0.01f) {
-        a = 1.0f - th2 / 6.0f;
-        b = 0.5f - th2 / 24.0f;
-        c = 1.0f / 6.0f - th2 / 120.0f;
-    } else {
-        const float sn = sinf(th), cs = cosf(th);
-        a = sn / th;
-        b = (1.0f - cs) / th2;
-        c = (th - sn) / (th2 * th);
-    }
-    const float W[9] = {0.0f, -d[2], d[1], d[2], 0.0f, -d[0], -d[1], d[0], 0.0f};
-    float W2[9], Rd[9], V[9], Rn[12];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
-    for (int i = 0; i < 9; ++i) {
-        const float id = (i % 4 == 0) ? 1.0f : 0.0f;
-        Rd[i] = id + a * W[i] + b * W2[i];
-        V[i] = id + b * W[i] + c * W2[i];
-    }
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j)
-            Rn[3 * i + j] = Rd[3 * i] * Rt[j] + Rd[3 * i + 1] * Rt[3 + j] + Rd[3 * i + 2] * Rt[6 + j];
-        Rn[9 + i] = Rd[3 * i] * Rt[9] + Rd[3 * i + 1] * Rt[10] + Rd[3 * i + 2] * Rt[11] +
-                    V[3 * i] * d[3] + V[3 * i + 1] * d[4] + V[3 * i + 2] * d[5];
-    }
-    for (int i = 0; i < 12; ++i) Rt[i] = Rn[i];
-}
-
-__device__ void pose_item(const BatchHeader &B, const FrameDev &F, SmemPose &S, int *s_flag)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const CamDev &C = F.cam[0];
-    const int M = F.nm;
-    if (tid < 9) S.Rt[tid] = C.R[tid];
-    else if (tid < 12) S.Rt[tid] = C.t[tid - 9];
-    bool ok = F.n_resolve_signals == 0 ||
-              wait_geq(B, &F.ctr[C_RESOLVED], (unsigned)F.n_resolve_signals, s_flag);
-    if (!ok) {
-        // the wait ran out (reported in the status word): the pose as given,
-        // no inliers
-        for (int m = tid; m < M; m += kThreads) F.po_inlier[m] = -1;
-        if (tid < 12) F.po_Rt[tid] = S.Rt[tid];
-        if (tid == 0) *F.po_n = 0;
         return;
     }
-    // observations in map-point order: thread tid takes a contiguous chunk of
-    // map points, counts its matches, and writes them after the chunks before
-    const int per = (M + kThreads - 1) / kThreads;
-    const int m0 = min(M, tid * per), m1 = min(M, m0 + per);
-    int cnt = 0;
-    for (int m = m0; m < m1; ++m) {
-        const int k = __ldcg(F.po_mp_kp + m);
-        cnt += (k >= 0 && k < C.nk) ? 1 : 0;
-    }
-    int total = 0;
-    int pos = block_scan1(cnt, S.warp_sums, &total);
-    for (int m = m0; m < m1; ++m) {
-        const int k = __ldcg(F.po_mp_kp + m);
-        const bool valid = k >= 0 && k < C.nk;
-        F.po_inlier[m] = valid ? 1 : -1;
-        if (!valid) continue;
-        const float4 P = __ldg(F.pos + m);
-        const int oct = __ldg(C.koct + k);
-        const float sc = (oct >= 0 && oct < B.p.nlevels) ? B.p.sc[oct] : 1.0f;
-        const float ur = F.u_right_in ? __ldcg(F.u_right_in + k) : -1.0f;
-        F.po_list[2 * pos] = make_float4(P.x, P.y, P.z, 1.0f / (sc * sc));
-        F.po_list[2 * pos + 1] = make_float4(__ldg(C.kx + k), __ldg(C.ky + k), ur >= 0.0f ? ur : -1.0f,
-                                             __int_as_float(m | (int)0x80000000));
-        ++pos;
-    }
-    if (tid == 0) {
-        S.n_in = total;
-        S.ok = 1;
-    }
-    __syncthreads();
-    const float th_mono = B.p.po_chi2_mono, th_stereo = B.p.po_chi2_stereo;
-    for (int round = 0; round < B.p.po_rounds; ++round) {
-        if (S.n_in < 3) break;
-        for (int it = 0; it < B.p.po_iters; ++it) {
-            float acc[27];
-#pragma unroll
-            for (int q = 0; q < 27; ++q) acc[q] = 0.0f;
-            for (int e = tid; e < total; e += kThreads) {
-                const float4 a = __ldcg(F.po_list + 2 * e), b = __ldcg(F.po_list + 2 * e + 1);
-                if (__float_as_int(b.w) >= 0) continue;            // outlier
-                PoseObs o;
-                if (!pose_obs(C, S.Rt, a, b, o)) continue;
-                const float th = o.stereo ? th_stereo : th_mono;
-                const float h = (!B.p.po_huber || o.chi2 <= th) ? 1.0f : sqrtf(th / o.chi2);
-                const float hw = h * a.w;
-                const int rows = o.stereo ? 3 : 2;
-                for (int r = 0; r < rows; ++r) {
-                    int q = 0;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-#pragma unroll
-                        for (int j = i; j < 6; ++j) acc[q++] += hw * o.J[r][i] * o.J[r][j];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) acc[21 + i] += hw * o.J[r][i] * o.e[r];
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                float v = acc[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-                acc[q] = v;
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < 27; ++q) S.part[warp][q] = acc[q];
-            }
-            __syncthreads();
-            if (tid == 0) {
-                float Hg[27];
-                for (int q = 0; q < 27; ++q) {
-                    float v = 0.0f;
-                    for (int w = 0; w < kWarps; ++w) v += S.part[w][q];
-                    Hg[q] = v;
-                }
-                float d[6];
-                if (pose_solve(Hg, Hg + 21, d)) pose_update(S.Rt, d);
-                else S.ok = 0;
-            }
-            __syncthreads();
-            if (!S.ok) break;
-        }
-        // classify every observation at the new pose
-        int n_in = 0;
-        for (int e = tid; e < total; e += kThreads) {
-            const float4 a = __ldcg(F.po_list + 2 * e);
-            float4 b = __ldcg(F.po_list + 2 * e + 1);
-            PoseObs o;
-            bool in = pose_obs(C, S.Rt, a, b, o);
-            if (in) in = !(o.chi2 > (o.stereo ? th_stereo : th_mono));
-            const int m = __float_as_int(b.w) & 0x7fffffff;
-            b.w = __int_as_float(in ? (m | (int)0x80000000) : m);
-            F.po_list[2 * e + 1] = b;
-            n_in += in ? 1 : 0;
-        }
-        int all = 0;
-        block_scan1(n_in, S.warp_sums, &all);
-        if (tid == 0) S.n_in = all;
-        __syncthreads();
-        if (!S.ok) break;
-    }
-    for (int e = tid; e < total; e += kThreads) {
-        const int w = __float_as_int(__ldcg(F.po_list + 2 * e + 1).w);
-        F.po_inlier[w & 0x7fffffff] = w < 0 ? 1 : 0;
-    }
-    if (tid < 12) F.po_Rt[tid] = S.Rt[tid];
-    if (tid == 0) *F.po_n = S.n_in;
+    resolve_range(C, F.nm, i0, i1);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -1934,8 +1653,7 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
             else stereo_fisheye_item(B, F, tile, U, &s_flag);
             break;
         case K_SEARCH: search_item(B, F, tile, U, &s_flag); break;
-        case K_RESOLVE: resolve_item(B, F, tile, &s_flag); break;
-        default: pose_item(B, F, U.p, &s_flag); break;
+        default: resolve_item(B, F, tile, &s_flag); break;
         }
         if (B.trace != nullptr && threadIdx.x == 0) {
             const unsigned slot = atomicAdd(B.queue + 1, 1u);
@@ -1955,6 +1673,320 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
             }
         }
     }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- f4: pose optimization
+// The refinement of the camera pose with all the map points the search found
+// in the frame (paper section II-D; FastTrack switches it off, section
+// IV-F), as the algorithm family's motion-only optimization (a reading):
+// observations are the matched keypoints (x, y) and, where stereo gave one,
+// u_right; weight 1/scale[oct]^2; po_rounds rounds of po_iters Gauss-Newton
+// steps over the inliers with Huber weights, the update exp(d) multiplied on
+// the left of the pose; every observation reclassified by its chi2 after
+// each round.  FP32.  A kernel of its own, after the fused kernel on the
+// same stream (the matches are final by then): one block of kPoseThreads
+// per frame.  Every thread accumulates the normal equations of its
+// observations, each warp reduce-scatters its 27 sums (lane q ends with sum
+// q), warp 0 adds the warps in a fixed order and lane 0 solves the 6x6
+// system (Cholesky) and updates the pose.  The observations stay in shared
+// memory when they fit; they are read at every step.
+namespace {
+
+constexpr int kPoseThreads = 512;
+constexpr int kPoseWarps = kPoseThreads / 32;
+constexpr int kPoseStage = 2048;                 // observations kept on chip
+constexpr int kPoseSmem = 2 * kPoseStage * (int)sizeof(float4);
+
+struct PoseShared {
+    float part[kPoseWarps][32];
+    float tot[32];
+    float Rt[12];
+    int warp_sums[kPoseWarps];
+    int n_in, ok, total;
+};
+
+// observation (a, b) at pose Rt: residual, chi2 and Jacobian rows (rotation
+// then translation of the left perturbation); false if not in front
+struct PoseObs {
+    float e[3], J[3][6], chi2;
+    bool stereo;
+};
+
+__device__ __forceinline__ bool pose_obs(const CamDev &C, const float *Rt, float4 a, float4 b, PoseObs &o)
+{
+    const float x = Rt[0] * a.x + Rt[1] * a.y + Rt[2] * a.z + Rt[9];
+    const float y = Rt[3] * a.x + Rt[4] * a.y + Rt[5] * a.z + Rt[10];
+    const float z = Rt[6] * a.x + Rt[7] * a.y + Rt[8] * a.z + Rt[11];
+    if (!(z > 0.0f)) return false;
+    const float iz = 1.0f / z, iz2 = iz * iz;
+    const float u = C.fx * x * iz + C.cx, v = C.fy * y * iz + C.cy;
+    o.stereo = b.z >= 0.0f;
+    o.e[0] = b.x - u;
+    o.e[1] = b.y - v;
+    o.e[2] = o.stereo ? b.z - (u - C.bf * iz) : 0.0f;
+    o.chi2 = a.w * (o.e[0] * o.e[0] + o.e[1] * o.e[1] + o.e[2] * o.e[2]);
+    // d projection / d Pc, times d Pc / d (w, v) = [ -[Pc]x | I ]
+    const float D[3][3] = {{C.fx * iz, 0.0f, -C.fx * x * iz2},
+                           {0.0f, C.fy * iz, -C.fy * y * iz2},
+                           {C.fx * iz, 0.0f, -C.fx * x * iz2 + C.bf * iz2}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        o.J[r][0] = -D[r][1] * z + D[r][2] * y;
+        o.J[r][1] = D[r][0] * z - D[r][2] * x;
+        o.J[r][2] = -D[r][0] * y + D[r][1] * x;
+        o.J[r][3] = D[r][0];
+        o.J[r][4] = D[r][1];
+        o.J[r][5] = D[r][2];
+    }
+    return true;
+}
+
+// lane 0 of warp 0: solve H d = g (H as its upper triangle, row by row, in
+// tot[0..20], g in tot[21..26]) by Cholesky with one reciprocal per column,
+// then (R, t) <- exp(d) (R, t); ok = 0 if H is not positive definite
+__device__ void pose_step(PoseShared &S)
+{
+    float H[6][6], L[6][6], inv[6], y[6], d[6];
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) H[i][j] = H[j][i] = S.tot[q++];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float s = H[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0f)) {
+            S.ok = 0;
+            return;
+        }
+        L[j][j] = sqrtf(s);
+        inv[j] = 1.0f / L[j][j];
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            float t = H[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t * inv[j];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float s = S.tot[21 + i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+        y[i] = s * inv[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        float s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) s -= L[k][i] * d[k];
+        d[i] = s * inv[i];
+    }
+    // exp of the twist d = (w, v): R_d = I + a [w]x + b [w]x^2,
+    // V = I + b [w]x + c [w]x^2 (series of a, b, c below theta = 0.01)
+    const float th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float th = sqrtf(th2);
+    float a, b, c;
+    if (th < 0.01f) {
+        a = 1.0f - th2 / 6.0f;
+        b = 0.5f - th2 / 24.0f;
+        c = 1.0f / 6.0f - th2 / 120.0f;
+    } else {
+        const float sn = sinf(th), cs = cosf(th);
+        a = sn / th;
+        b = (1.0f - cs) / th2;
+        c = (th - sn) / (th2 * th);
+    }
+    const float W[9] = {0.0f, -d[2], d[1], d[2], 0.0f, -d[0], -d[1], d[0], 0.0f};
+    float W2[9], Rd[9], V[9], Rn[12];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float id = (i % 4 == 0) ? 1.0f : 0.0f;
+        Rd[i] = id + a * W[i] + b * W2[i];
+        V[i] = id + b * W[i] + c * W2[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Rn[3 * i + j] = Rd[3 * i] * S.Rt[j] + Rd[3 * i + 1] * S.Rt[3 + j] + Rd[3 * i + 2] * S.Rt[6 + j];
+        Rn[9 + i] = Rd[3 * i] * S.Rt[9] + Rd[3 * i + 1] * S.Rt[10] + Rd[3 * i + 2] * S.Rt[11] +
+                    V[3 * i] * d[3] + V[3 * i + 1] * d[4] + V[3 * i + 2] * d[5];
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) S.Rt[i] = Rn[i];
+}
+
+// block-wide sum of one int per thread (all threads get it)
+__device__ int pose_block_sum(int v, PoseShared &S)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = __reduce_add_sync(kFull, v);
+    if (lane == 0) S.warp_sums[w] = v;
+    __syncthreads();
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < kPoseWarps; ++i) sum += S.warp_sums[i];
+    __syncthreads();
+    return sum;
+}
+
+__global__ void __launch_bounds__(kPoseThreads, 1) ft_pose_kernel(const BatchHeader *__restrict__ hdr)
+{
+    extern __shared__ __align__(16) float4 pose_stage[];
+    __shared__ PoseShared S;
+    __shared__ __align__(16) DevParams sP;
+    __shared__ __align__(16) FrameDev sF;
+    const int f = blockIdx.x;
+    if (f >= hdr->nframes || !hdr->frames[f].do_pose) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        const unsigned *a = reinterpret_cast<const unsigned *>(hdr->frames + f);
+        unsigned *b = reinterpret_cast<unsigned *>(&sF);
+        for (int i = tid; i < (int)(sizeof(FrameDev) / 4); i += kPoseThreads) b[i] = __ldg(a + i);
+        const unsigned *pa = reinterpret_cast<const unsigned *>(&hdr->p);
+        unsigned *pb = reinterpret_cast<unsigned *>(&sP);
+        for (int i = tid; i < (int)(sizeof(DevParams) / 4); i += kPoseThreads) pb[i] = __ldg(pa + i);
+    }
+    __syncthreads();
+    const FrameDev &F = sF;
+    const DevParams &P = sP;
+    const CamDev &C = F.cam[0];
+    const int M = F.nm;
+    if (tid < 9) S.Rt[tid] = C.R[tid];
+    else if (tid < 12) S.Rt[tid] = C.t[tid - 9];
+    // observations in map-point order: thread tid takes a contiguous chunk of
+    // map points, counts its matches, and writes them after the chunks before
+    const int per = (M + kPoseThreads - 1) / kPoseThreads;
+    const int m0 = min(M, tid * per), m1 = min(M, m0 + per);
+    int cnt = 0;
+    for (int m = m0; m < m1; ++m) {
+        const int k = __ldg(F.po_mp_kp + m);
+        cnt += (k >= 0 && k < C.nk) ? 1 : 0;
+    }
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) S.warp_sums[warp] = x;
+    __syncthreads();
+    int pos = x - cnt, total = 0;
+#pragma unroll
+    for (int i = 0; i < kPoseWarps; ++i) {
+        const int ws = S.warp_sums[i];
+        pos += i < warp ? ws : 0;
+        total += ws;
+    }
+    __syncthreads();
+    float4 *list = total <= kPoseStage ? pose_stage : F.po_list;
+    for (int m = m0; m < m1; ++m) {
+        const int k = __ldg(F.po_mp_kp + m);
+        const bool valid = k >= 0 && k < C.nk;
+        F.po_inlier[m] = valid ? 1 : -1;
+        if (!valid) continue;
+        const float4 Pw = __ldg(F.pos + m);
+        const int oct = __ldg(C.koct + k);
+        const float sc = (oct >= 0 && oct < P.nlevels) ? P.sc[oct] : 1.0f;
+        const float ur = F.u_right_in ? __ldg(F.u_right_in + k) : -1.0f;
+        list[2 * pos] = make_float4(Pw.x, Pw.y, Pw.z, 1.0f / (sc * sc));
+        list[2 * pos + 1] = make_float4(__ldg(C.kx + k), __ldg(C.ky + k), ur >= 0.0f ? ur : -1.0f,
+                                        __int_as_float(m | (int)0x80000000));
+        ++pos;
+    }
+    if (tid == 0) {
+        S.n_in = total;
+        S.ok = 1;
+    }
+    __syncthreads();
+    const float th_mono = P.po_chi2_mono, th_stereo = P.po_chi2_stereo;
+    for (int round = 0; round < P.po_rounds; ++round) {
+        if (S.n_in < 3) break;
+        for (int it = 0; it < P.po_iters; ++it) {
+            float acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
+            for (int e = tid; e < total; e += kPoseThreads) {
+                const float4 a = list[2 * e], b = list[2 * e + 1];
+                if (__float_as_int(b.w) >= 0) continue;            // outlier
+                PoseObs o;
+                if (!pose_obs(C, S.Rt, a, b, o)) continue;
+                const float th = o.stereo ? th_stereo : th_mono;
+                const float h = (!P.po_huber || o.chi2 <= th) ? 1.0f : sqrtf(th / o.chi2);
+                const float hw = h * a.w;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    if (r == 2 && !o.stereo) break;
+                    int q = 0;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const float wi = hw * o.J[r][i];
+#pragma unroll
+                        for (int j = i; j < 6; ++j) acc[q++] += wi * o.J[r][j];
+                        acc[21 + i] += wi * o.e[r];
+                    }
+                }
+            }
+            // reduce-scatter: after the five butterfly stages lane q holds
+            // the warp's sum of entry q
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const bool upper = (lane & s) != 0;
+#pragma unroll
+                for (int i = 0; i < s; ++i) {
+                    const float send = upper ? acc[i] : acc[i + s];
+                    const float keep = upper ? acc[i + s] : acc[i];
+                    acc[i] = keep + __shfl_xor_sync(kFull, send, s);
+                }
+            }
+            S.part[warp][lane] = acc[0];
+            __syncthreads();
+            if (warp == 0) {
+                float v = 0.0f;
+#pragma unroll
+                for (int w = 0; w < kPoseWarps; ++w) v += S.part[w][lane];
+                S.tot[lane] = v;
+                __syncwarp();
+                if (lane == 0) pose_step(S);
+            }
+            __syncthreads();
+            if (!S.ok) break;
+        }
+        // classify every observation at the new pose
+        int n_in = 0;
+        for (int e = tid; e < total; e += kPoseThreads) {
+            const float4 a = list[2 * e];
+            float4 b = list[2 * e + 1];
+            PoseObs o;
+            bool in = pose_obs(C, S.Rt, a, b, o);
+            if (in) in = !(o.chi2 > (o.stereo ? th_stereo : th_mono));
+            const int m = __float_as_int(b.w) & 0x7fffffff;
+            b.w = __int_as_float(in ? (m | (int)0x80000000) : m);
+            list[2 * e + 1] = b;
+            n_in += in ? 1 : 0;
+        }
+        const int all = pose_block_sum(n_in, S);
+        if (tid == 0) S.n_in = all;
+        __syncthreads();
+        if (!S.ok) break;
+    }
+    for (int e = tid; e < total; e += kPoseThreads) {
+        const int w = __float_as_int(list[2 * e + 1].w);
+        F.po_inlier[w & 0x7fffffff] = w < 0 ? 1 : 0;
+    }
+    if (tid < 12) F.po_Rt[tid] = S.Rt[tid];
+    if (tid == 0) *F.po_n = S.n_in;
 }
 
 }  // namespace
@@ -2204,6 +2236,8 @@ cudaError_t fused_occupancy(int *ctas_per_sm)
 {
     cudaError_t e = cudaFuncSetAttribute(ft_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ft_pose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPoseSmem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, ft_fused_kernel, kThreads,
                                                          sizeof(Smem));
@@ -2212,6 +2246,13 @@ cudaError_t fused_occupancy(int *ctas_per_sm)
 cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stream)
 {
     ft_fused_kernel<<<grid, kThreads, sizeof(Smem), stream>>>(dev_hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pose(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream)
+{
+    if (nframes <= 0) return cudaSuccess;
+    ft_pose_kernel<<<nframes, kPoseThreads, kPoseSmem, stream>>>(dev_hdr);
     return cudaGetLastError();
 }
 
