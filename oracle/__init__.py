@@ -97,6 +97,11 @@ class OrcKeypoints(C.Structure):
     ]
 
 
+class OrcOrbParams(C.Structure):
+    _fields_ = [("fast_th", C.c_int), ("edge", C.c_int), ("max_kp", C.c_int * MAX_LEVELS),
+                ("pattern", C.c_void_p)]
+
+
 def _lib_handle():
     global _lib
     with _lock:
@@ -174,6 +179,14 @@ def _lib_handle():
                                                P(OrcPose), vp, P(OrcKeypoints), vp,
                                                P(OrcKeypoints), vp, C.c_int, vp, vp, vp, vp,
                                                vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_fast_score.restype = C.c_int
+            lib.orc_fast_score.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+            lib.orc_smooth_level.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
+            lib.orc_orientation.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
+            lib.orc_describe.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+            lib.orc_extract_orb.restype = C.c_int
+            lib.orc_extract_orb.argtypes = [P(OrcParams), P(OrcPyramid), P(OrcOrbParams), vp, vp, vp, vp, vp,
+                                            vp, vp]
             lib.orc_se3_exp.argtypes = [vp, vp, vp]
             lib.orc_pose_residual.restype = C.c_int
             lib.orc_pose_residual.argtypes = [P(OrcPinhole), vp, vp, vp, vp, C.c_int, vp, vp]
@@ -689,3 +702,58 @@ def optimize_pose(params: dict, cam, pose, kps, u_right, pos, mp_kp) -> dict:
                                       _ptr(mk), _ptr(Rt), _ptr(inl), _ptr(c2), C.byref(margin), C.byref(rounds))
     return dict(R=Rt[:9].reshape(3, 3).copy(), t=Rt[9:].copy(), inlier=inl, chi2=c2, n_inliers=int(n),
                 min_margin=margin.value, rounds=rounds.value)
+
+
+# --------------------------------------------------------------------------
+# f3: keypoint detection and description
+# --------------------------------------------------------------------------
+def fast_score(img, x: int, y: int, t: int) -> int:
+    """FAST-9 score of pixel (x, y) (-1: not a corner at threshold t)."""
+    a = _c(img, np.uint8)
+    return int(_lib_handle().orc_fast_score(_ptr(a), a.strides[0], x, y, t))
+
+
+def smooth_level(img) -> np.ndarray:
+    a = _c(img, np.uint8)
+    h, w = a.shape
+    out = np.zeros((h, w), np.uint8)
+    _lib_handle().orc_smooth_level(_ptr(a), w, h, a.strides[0], _ptr(out))
+    return out
+
+
+def orientation(img, x: int, y: int) -> np.ndarray:
+    a = _c(img, np.uint8)
+    cs = np.zeros(2, np.float32)
+    _lib_handle().orc_orientation(_ptr(a), a.strides[0], x, y, _ptr(cs))
+    return cs
+
+
+def describe(smooth, x: int, y: int, cs, pattern) -> np.ndarray:
+    a = _c(smooth, np.uint8)
+    c = _c(cs, np.float32)
+    pt = _c(pattern, np.int8).reshape(-1)
+    d = np.zeros(32, np.uint8)
+    _lib_handle().orc_describe(_ptr(a), a.strides[0], x, y, _ptr(c), _ptr(pt), _ptr(d))
+    return d
+
+
+def extract_orb(params: dict, levels, fast_th: int, edge: int, max_kp, pattern) -> dict:
+    """f3 on one image pyramid: fixed slots per level (max_kp[l] each, in
+    level order), padding after each level's keypoints."""
+    keep = _Keep()
+    pyr = pyramid_struct(levels, keep)
+    op = OrcOrbParams()
+    op.fast_th, op.edge = fast_th, edge
+    for l, m in enumerate(max_kp):
+        op.max_kp[l] = int(m)
+    pt = keep.add(_c(pattern, np.int8).reshape(-1))
+    op.pattern = _ptr(pt)
+    n = int(sum(max_kp))
+    out = dict(x=np.zeros(n, np.float32), y=np.zeros(n, np.float32), oct=np.zeros(n, np.int8),
+               score=np.zeros(n, np.int32), cs=np.zeros((n, 2), np.float32), desc=np.zeros((n, 32), np.uint8),
+               n_level=np.zeros(len(levels) + 1, np.int32))
+    p = params_struct(params)
+    _lib_handle().orc_extract_orb(C.byref(p), C.byref(pyr), C.byref(op), *[_ptr(out[k]) for k in
+                                                                          ("x", "y", "oct", "score", "cs", "desc",
+                                                                           "n_level")])
+    return out

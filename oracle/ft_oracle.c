@@ -1278,3 +1278,215 @@ int orc_optimize_pose_pinhole(const orc_params *p, const orc_pinhole *cam, const
     if (rounds_run) *rounds_run = rounds;
     return n_in;
 }
+
+/* ------------------------------------------------------------------------ */
+/* f3: keypoints and descriptors on the pyramid levels.  The paper's ORB     */
+/* extraction builds the pyramid, finds keypoints on every level, describes */
+/* each one and filters them (section II-A), reusing an existing GPU        */
+/* extractor (section IV-B) whose steps it does not give.  The reading      */
+/* follows the published methods the name refers to -- the FAST segment     */
+/* test (Rosten and Drummond), the intensity-centroid orientation and the   */
+/* steered binary tests of ORB (Rublee et al.) -- with these choices:       */
+/*  - FAST-9 on the level image: pixel p with intensity I is a corner if 9  */
+/*    contiguous pixels of the 16 on the radius-3 Bresenham circle are all  */
+/*    brighter than I + t or all darker than I - t; only pixels at least    */
+/*    `edge` pixels from every border are tested;                           */
+/*  - score: the largest threshold at which p is still a corner, i.e. the   */
+/*    best arc's smallest intensity difference minus one;                   */
+/*  - non-maximum suppression: a corner is kept unless one of its 8         */
+/*    neighbours is a corner with a higher score, or an equal score and an  */
+/*    earlier raster position;                                              */
+/*  - filtering: per level the first max_kp[l] kept corners in the order    */
+/*    (score descending, y, x); the level's slots after them are padding    */
+/*    (x = y = -1e9, octave 0, score -1, orientation (1, 0), zero           */
+/*    descriptor);                                                          */
+/*  - orientation: moments m10 = sum u I, m01 = sum v I over the disk       */
+/*    u^2 + v^2 <= 15^2 of the level image; |m| = sqrt(m10^2 + m01^2) in    */
+/*    double, rounded to float; cos = m10/|m|, sin = m01/|m| in FP32 ((1,0)  */
+/*    when both moments are 0);                                             */
+/*  - descriptor: the level smoothed by the 5x5 binomial filter (weights    */
+/*    1 4 6 4 1 in each direction, sum 256, rounded half up, borders        */
+/*    replicated); test i takes the pattern pair (x1, y1, x2, y2), rotates   */
+/*    each point by the orientation in FP32 (u = round(c x - s y),          */
+/*    v = round(s x + c y), products and difference rounded separately) and */
+/*    sets bit i (bit i % 8 of byte i / 8) if S(p1) < S(p2);                */
+/*  - keypoint coordinates in level-0 pixels: x0 = x_l * scale[l] (FP32).    */
+/* ------------------------------------------------------------------------ */
+static const int fast_circle[16][2] = {
+    {0, -3}, {1, -3}, {2, -2}, {3, -1}, {3, 0}, {3, 1}, {2, 2}, {1, 3},
+    {0, 3}, {-1, 3}, {-2, 2}, {-3, 1}, {-3, 0}, {-3, -1}, {-2, -2}, {-1, -3}};
+
+/* score of pixel (x, y) if it passes the segment test at threshold t, else -1 */
+int orc_fast_score(const uint8_t *img, int pitch, int x, int y, int t)
+{
+    const int c = img[(size_t)y * pitch + x];
+    int d[16];
+    for (int i = 0; i < 16; ++i)
+        d[i] = img[(size_t)(y + fast_circle[i][1]) * pitch + (x + fast_circle[i][0])] - c;
+    int best = -1000;
+    for (int start = 0; start < 16; ++start) {
+        int lo_b = 1000, lo_d = 1000;       /* smallest brighter / darker difference over the arc */
+        for (int k = 0; k < 9; ++k) {
+            const int v = d[(start + k) % 16];
+            if (v < lo_b) lo_b = v;
+            if (-v < lo_d) lo_d = -v;
+        }
+        if (lo_b > best) best = lo_b;
+        if (lo_d > best) best = lo_d;
+    }
+    /* a corner at t iff the best arc's smallest difference exceeds t */
+    return best > t ? best - 1 : -1;
+}
+
+void orc_smooth_level(const uint8_t *src, int w, int h, int pitch, uint8_t *dst)
+{
+    static const int wt[5] = {1, 4, 6, 4, 1};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int acc = 0;
+            for (int j = -2; j <= 2; ++j) {
+                int yy = y + j;
+                yy = yy < 0 ? 0 : (yy > h - 1 ? h - 1 : yy);
+                for (int i = -2; i <= 2; ++i) {
+                    int xx = x + i;
+                    xx = xx < 0 ? 0 : (xx > w - 1 ? w - 1 : xx);
+                    acc += wt[j + 2] * wt[i + 2] * src[(size_t)yy * pitch + xx];
+                }
+            }
+            dst[(size_t)y * w + x] = (uint8_t)((acc + 128) >> 8);
+        }
+}
+
+void orc_orientation(const uint8_t *img, int pitch, int x, int y, float *cs2)
+{
+    long long m10 = 0, m01 = 0;
+    for (int v = -15; v <= 15; ++v)
+        for (int u = -15; u <= 15; ++u) {
+            if (u * u + v * v > 15 * 15) continue;
+            const int I = img[(size_t)(y + v) * pitch + (x + u)];
+            m10 += (long long)u * I;
+            m01 += (long long)v * I;
+        }
+    if (m10 == 0 && m01 == 0) {
+        cs2[0] = 1.0f;
+        cs2[1] = 0.0f;
+        return;
+    }
+    const double n2 = (double)m10 * (double)m10 + (double)m01 * (double)m01;
+    const float nm = (float)sqrt(n2);
+    cs2[0] = (float)m10 / nm;
+    cs2[1] = (float)m01 / nm;
+}
+
+void orc_describe(const uint8_t *smooth, int pitch, int x, int y, const float *cs2, const int8_t *pattern,
+                  uint8_t *desc32)
+{
+    const float c = cs2[0], s = cs2[1];
+    memset(desc32, 0, 32);
+    for (int i = 0; i < 256; ++i) {
+        int val[2];
+        for (int q = 0; q < 2; ++q) {
+            const float px = (float)pattern[4 * i + 2 * q], py = (float)pattern[4 * i + 2 * q + 1];
+            const float a = c * px, b = s * py, e = s * px, f = c * py;
+            const int u = (int)roundf(a - b);
+            const int v = (int)roundf(e + f);
+            val[q] = smooth[(size_t)(y + v) * pitch + (x + u)];
+        }
+        if (val[0] < val[1]) desc32[i >> 3] |= (uint8_t)(1u << (i & 7));
+    }
+}
+
+typedef struct {
+    int score, x, y;
+} orc_corner;
+
+/* (score descending, y, x) */
+static int corner_before(const orc_corner *a, const orc_corner *b)
+{
+    if (a->score != b->score) return a->score > b->score;
+    if (a->y != b->y) return a->y < b->y;
+    return a->x < b->x;
+}
+
+int orc_extract_orb(const orc_params *p, const orc_pyramid *pyr, const orc_orb_params *op,
+                    float *x, float *y, int8_t *oct, int32_t *score, float *cs, uint8_t *desc,
+                    int32_t *n_level)
+{
+    float sc[ORC_MAX_LEVELS], isc[ORC_MAX_LEVELS];
+    orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
+    int slot = 0, total = 0;
+    for (int l = 0; l < p->nlevels; ++l) {
+        const uint8_t *img = pyr->data[l];
+        const int w = pyr->width[l], h = pyr->height[l], pitch = pyr->pitch[l];
+        const int e = op->edge;
+        /* scores of every tested pixel (-1: not a corner or not tested) */
+        int *sco = (int *)malloc(sizeof(int) * (size_t)w * (size_t)h);
+        for (int i = 0; i < w * h; ++i) sco[i] = -1;
+        for (int yy = e; yy < h - e; ++yy)
+            for (int xx = e; xx < w - e; ++xx) sco[yy * w + xx] = orc_fast_score(img, pitch, xx, yy, op->fast_th);
+        /* non-maximum suppression, then the kept corners in the filtering order */
+        orc_corner *kept = (orc_corner *)malloc(sizeof(orc_corner) * ((size_t)w * h + 1));
+        int nk = 0;
+        for (int yy = e; yy < h - e; ++yy)
+            for (int xx = e; xx < w - e; ++xx) {
+                const int sp = sco[yy * w + xx];
+                if (sp < 0) continue;
+                int keep = 1;
+                for (int dy = -1; dy <= 1 && keep; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (!dx && !dy) continue;
+                        const int qx = xx + dx, qy = yy + dy;
+                        if (qx < 0 || qy < 0 || qx >= w || qy >= h) continue;
+                        const int sq = sco[qy * w + qx];
+                        if (sq < 0) continue;
+                        const int earlier = qy < yy || (qy == yy && qx < xx);
+                        if (sq > sp || (sq == sp && earlier)) {
+                            keep = 0;
+                            break;
+                        }
+                    }
+                if (keep) kept[nk++] = (orc_corner){sp, xx, yy};
+            }
+        /* insertion sort by (score desc, y, x); levels hold a few thousand */
+        for (int i = 1; i < nk; ++i) {
+            orc_corner v = kept[i];
+            int j = i - 1;
+            while (j >= 0 && corner_before(&v, &kept[j])) {
+                kept[j + 1] = kept[j];
+                --j;
+            }
+            kept[j + 1] = v;
+        }
+        const int cap = op->max_kp[l];
+        const int n = nk < cap ? nk : cap;
+        uint8_t *sm = (uint8_t *)malloc((size_t)w * h);
+        orc_smooth_level(img, w, h, pitch, sm);
+        for (int i = 0; i < cap; ++i) {
+            const int k = slot + i;
+            if (i < n) {
+                const orc_corner *c = &kept[i];
+                x[k] = (float)c->x * sc[l];
+                y[k] = (float)c->y * sc[l];
+                oct[k] = (int8_t)l;
+                score[k] = c->score;
+                orc_orientation(img, pitch, c->x, c->y, cs + 2 * k);
+                orc_describe(sm, w, c->x, c->y, cs + 2 * k, op->pattern, desc + 32 * k);
+            } else {
+                x[k] = y[k] = -1.0e9f;
+                oct[k] = 0;
+                score[k] = -1;
+                cs[2 * k] = 1.0f;
+                cs[2 * k + 1] = 0.0f;
+                memset(desc + 32 * k, 0, 32);
+            }
+        }
+        n_level[l] = n;
+        total += n;
+        slot += cap;
+        free(sm);
+        free(kept);
+        free(sco);
+    }
+    n_level[p->nlevels] = total;
+    return slot;
+}

@@ -205,6 +205,23 @@ void orc_search_last_fisheye(const orc_params *p, const orc_kb8 *camL, const orc
                              int8_t *level_r, float *proj_r, int32_t *mp_kp_r, int32_t *mp_d1_r,
                              int32_t *mp_d2_r, int32_t *kp_mp_r);
 
+/* ---- keypoint detection and description (next row f3) ----------------- */
+typedef struct {
+    int fast_th;                    /* FAST threshold t (20) */
+    int edge;                       /* no corner closer than edge pixels to a border (19) */
+    int max_kp[ORC_MAX_LEVELS];     /* keypoint slots per level */
+    const int8_t *pattern;          /* [256][4] test pairs (x1, y1, x2, y2), |coordinates| <= 13 */
+} orc_orb_params;
+
+int orc_fast_score(const uint8_t *img, int pitch, int x, int y, int t);
+void orc_smooth_level(const uint8_t *src, int w, int h, int pitch, uint8_t *dst);
+void orc_orientation(const uint8_t *img, int pitch, int x, int y, float *cs2);
+void orc_describe(const uint8_t *smooth, int pitch, int x, int y, const float *cs2, const int8_t *pattern,
+                  uint8_t *desc32);
+int orc_extract_orb(const orc_params *p, const orc_pyramid *pyr, const orc_orb_params *op,
+                    float *x, float *y, int8_t *oct, int32_t *score, float *cs, uint8_t *desc,
+                    int32_t *n_level);
+
 /* ---- pose optimization (next row f4), double precision ---------------- */
 void orc_se3_exp(const double *d6, double *R9, double *V9);
 int orc_pose_residual(const orc_pinhole *cam, const double *R9, const double *t3, const float *Pw,

@@ -675,3 +675,36 @@ def last_frame(fr: Frame, seed: int, motion: str = "none", n: int | None = None)
     return LastFrame(pos=np.ascontiguousarray(m.pos[:M]), desc=np.ascontiguousarray(m.desc[:M]),
                      oct=oct_.astype(np.int8), skip=np.ascontiguousarray(m.skip[:M]),
                      pose=make_pose(R, O_last))
+
+
+# --------------------------------------------------------------------------
+# keypoint extraction inputs (next row f3)
+# --------------------------------------------------------------------------
+ORB_FAST_TH = 20
+ORB_EDGE = 19
+
+
+def orb_pattern(seed: int = 2011) -> np.ndarray:
+    """256 test pairs (x1, y1, x2, y2) as int8: points drawn i.i.d. from an
+    isotropic Gaussian of sigma 31/5 around the keypoint, rounded, kept if
+    inside the disk of radius 13; pairs of equal points are drawn again."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((256, 4), np.int8)
+    i = 0
+    while i < 256:
+        p = np.rint(rng.normal(0.0, 31.0 / 5.0, 4))
+        if p[0] ** 2 + p[1] ** 2 > 169 or p[2] ** 2 + p[3] ** 2 > 169 or (p[0] == p[2] and p[1] == p[3]):
+            continue
+        out[i] = p.astype(np.int8)
+        i += 1
+    return out
+
+
+def orb_level_caps(n_features: int, nlevels: int = NLEVELS, s: float = SCALE) -> list:
+    """Keypoint slots per level: a geometric share (1/s)^l of n_features per
+    level, the last level taking what remains."""
+    f = 1.0 / s
+    n0 = n_features * (1.0 - f) / (1.0 - f ** nlevels)
+    caps = [int(round(n0 * f ** l)) for l in range(nlevels - 1)]
+    caps.append(max(0, n_features - sum(caps)))
+    return caps

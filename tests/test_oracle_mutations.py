@@ -88,6 +88,20 @@ MUTANTS = [
     ("last_right_t_dropped",
      "tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2] + t_rl[i];",
      "tr[i] = R_rl[3 * i] * T->t[0] + R_rl[3 * i + 1] * T->t[1] + R_rl[3 * i + 2] * T->t[2];"),
+    # keypoint detection and description (next row f3)
+    ("fast_circle_offset", "{0, -3}, {1, -3}, {2, -2}, {3, -1}, {3, 0},", "{0, -3}, {1, -3}, {2, -2}, {3, -2}, {3, 0},"),
+    ("fast_arc_eight", "for (int k = 0; k < 9; ++k) {", "for (int k = 0; k < 8; ++k) {"),
+    ("fast_score_offset", "return best > t ? best - 1 : -1;", "return best > t ? best : -1;"),
+    ("fast_not_strict", "return best > t ? best - 1 : -1;", "return best >= t ? best - 1 : -1;"),
+    ("nms_tie_later", "if (sq > sp || (sq == sp && earlier)) {", "if (sq > sp || (sq == sp && !earlier)) {"),
+    ("filter_order_x_first", "if (a->y != b->y) return a->y < b->y;\n    return a->x < b->x;",
+     "if (a->x != b->x) return a->x < b->x;\n    return a->y < b->y;"),
+    ("smooth_no_rounding", "dst[(size_t)y * w + x] = (uint8_t)((acc + 128) >> 8);", "dst[(size_t)y * w + x] = (uint8_t)(acc >> 8);"),
+    ("orientation_radius", "if (u * u + v * v > 15 * 15) continue;", "if (u * u + v * v > 14 * 14) continue;"),
+    ("orientation_sign", "cs2[1] = (float)m01 / nm;", "cs2[1] = -(float)m01 / nm;"),
+    ("describe_rotation_sign", "const int u = (int)roundf(a - b);", "const int u = (int)roundf(a + b);"),
+    ("describe_compare", "if (val[0] < val[1]) desc32", "if (val[0] <= val[1]) desc32"),
+    ("keypoint_level_scale", "x[k] = (float)c->x * sc[l];", "x[k] = (float)c->x;"),
     # pose optimization (next row f4)
     ("pose_jacobian_sign", "const double S[18] = {0.0, z, -y, 1.0, 0.0, 0.0,", "const double S[18] = {0.0, -z, y, 1.0, 0.0, 0.0,"),
     ("pose_stereo_bf_sign", "-fx * x * iz2 + bf * iz2};", "-fx * x * iz2 - bf * iz2};"),
@@ -126,7 +140,8 @@ def _run_mutant(tmp, name, old, new):
                         os.path.join(ROOT, "tests", "test_oracle_pyramid.py"),
                         os.path.join(ROOT, "tests", "test_oracle_fisheye_rig.py"),
                         os.path.join(ROOT, "tests", "test_oracle_mirror.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pose.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pose.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_orb.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
