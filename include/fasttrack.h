@@ -405,6 +405,65 @@ ft_status ft_optimize_pose(ft_ctx *ctx, void *stream, const ft_params *params,
                            const ft_frame_view *frame, const ft_pose *Tcw, const ft_map_view *map,
                            const int32_t *mp_kp, const ft_pose_out *out);
 
+/* Keypoint extraction parameters (next row f3). */
+typedef struct {
+    int fast_th;                    /* FAST threshold t, in [1, 254] (20) */
+    int edge;                       /* corners at least edge pixels from every border, >= 19 (19) */
+    int max_kp[FT_MAX_LEVELS];      /* slots per level, each in [0, 4096] */
+    const int8_t *pattern;          /* HOST [256][4] test pairs (x1, y1, x2, y2), every coordinate
+                                       in [-13, 13]; copied by the call */
+} ft_orb_params;
+
+/* Keypoint extraction output of one image: n = sum of max_kp slots, level
+ * l's keypoints in slots [sum of max_kp[< l], + max_kp[l]) in the order
+ * (score descending, y, x), then padding.  DEVICE pointers:
+ *   x, y     [n] level-0 coordinates (level pixel times scale[l], FP32);
+ *            padding: -1e9 (no search or stereo step ever matches it)
+ *   oct      [n] level (padding: 0)
+ *   score    [n] FAST score (padding: -1)
+ *   cs       [n][2] cosine and sine of the orientation (padding: 1, 0)
+ *   desc     [n][32] descriptor, 16-byte aligned (padding: zeros)
+ *   n_level  [nlevels + 1] keypoints found per level, then their total
+ * x, y, oct and desc have the layout of ft_keypoints: the output feeds
+ * stereo matching and the search directly, with n slots. */
+typedef struct {
+    float *x, *y;
+    int8_t *oct;
+    int32_t *score;
+    float *cs;
+    uint8_t *desc;
+    int32_t *n_level;
+} ft_orb_out;
+
+/* Keypoint detection and description on the pyramid levels of n images
+ * (next row f3): the paper's ORB extraction finds keypoints on every level,
+ * describes each one and filters them (section II-A); FastTrack reuses an
+ * existing GPU extractor and gives none of its steps (section IV-B).  The
+ * reading follows the published methods (FAST, ORB):
+ *   - FAST-9 on the level image: 9 contiguous pixels of the 16 on the
+ *     radius-3 circle all brighter than I + t or all darker than I - t;
+ *     only pixels at least edge pixels from every border;
+ *   - score: the largest t at which the pixel is still a corner;
+ *   - non-maximum suppression: a corner is dropped if a neighbour (8) is a
+ *     corner with a higher score, or the same score and an earlier raster
+ *     position;
+ *   - filtering: per level the first max_kp[l] corners by (score
+ *     descending, y, x);
+ *   - orientation: m10 = sum u I, m01 = sum v I over u^2 + v^2 <= 225;
+ *     |m| = sqrt(m10^2 + m01^2) in double rounded to float, cos = m10/|m|,
+ *     sin = m01/|m| in FP32 ((1, 0) if both are 0);
+ *   - descriptor: the level smoothed by the 5x5 binomial filter (1 4 6 4 1
+ *     each way, /256 rounded half up, border replicated); test i rotates
+ *     both pattern points by the orientation (u = round(c x - s y),
+ *     v = round(s x + c y), FP32, each product rounded) and sets bit i % 8
+ *     of byte i / 8 if S(p1) < S(p2).
+ * pyr[i] are the images' pyramids (params->nlevels levels, each at most
+ * 4096 x 4096; the pyramid's own sizes, device data); out[i] their outputs.
+ * Uses scratch in the context's arena (about 2 bytes per level pixel).
+ * Three kernel launches, asynchronous on the stream. */
+ft_status ft_extract_orb(ft_ctx *ctx, void *stream, const ft_params *params, int n, const ft_pyramid *pyr,
+                         const ft_orb_params *orb, const ft_orb_out *out);
+
 /* Sizes of the pyramid levels of a width x height level 0 (next row f3, its
  * pyramid part): level l is round(width / scale[l]) x round(height /
  * scale[l]) with scale[l] the FP32 product of scale_factor (params NULL =

@@ -111,6 +111,14 @@ class ft_pose_out(C.Structure):
     _fields_ = [("Rt", vp), ("inlier", vp), ("n_inliers", vp)]
 
 
+class ft_orb_params(C.Structure):
+    _fields_ = [("fast_th", i32), ("edge", i32), ("max_kp", i32 * FT_MAX_LEVELS), ("pattern", vp)]
+
+
+class ft_orb_out(C.Structure):
+    _fields_ = [("x", vp), ("y", vp), ("oct", vp), ("score", vp), ("cs", vp), ("desc", vp), ("n_level", vp)]
+
+
 class ft_frame_job(C.Structure):
     _fields_ = [("camera", i32), ("pinhole", ft_pinhole), ("fisheye", ft_fisheye_rig),
                 ("left", ft_keypoints), ("right", ft_keypoints), ("pyr_left", ft_pyramid),
@@ -200,6 +208,8 @@ SIGNATURES = [
                                    C.POINTER(ft_search_out)]),
     ("ft_optimize_pose", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_frame_view), C.POINTER(ft_pose),
                                C.POINTER(ft_map_view), vp, C.POINTER(ft_pose_out)]),
+    ("ft_extract_orb", i32, [vp, vp, C.POINTER(ft_params), i32, C.POINTER(ft_pyramid), C.POINTER(ft_orb_params),
+                             C.POINTER(ft_orb_out)]),
     ("ft_pyramid_sizes", i32, [i32, i32, C.POINTER(ft_params), vp, vp]),
     ("ft_measure_popcount", i32, [vp, C.POINTER(C.c_double)]),
     ("ft_build_pyramid", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_pyramid)]),

@@ -371,6 +371,74 @@ class PackedBatch:
         return out
 
 
+class OrbOutputs:
+    """Device outputs of ft_extract_orb for n images with the given slots per
+    level (one blob), the ft_orb_out structs pointing into it, and the
+    pattern and parameters of the call."""
+
+    KEYS = (("x", np.float32, ()), ("y", np.float32, ()), ("oct", np.int8, ()), ("score", np.int32, ()),
+            ("cs", np.float32, (2,)), ("desc", np.uint8, (32,)))
+
+    def __init__(self, n_images: int, max_kp, pattern, fast_th: int = 20, edge: int = 19, nlevels: int = 8,
+                 device: str | torch.device = "cuda"):
+        self.n = n_images
+        self.nslots = int(sum(max_kp))
+        self.nlevels = nlevels
+        self.lay = _Layout()
+        for i in range(n_images):
+            for k, dt, tail in self.KEYS:
+                self.lay.add((i, k), dt, (self.nslots,) + tail)
+            self.lay.add((i, "n_level"), np.int32, (nlevels + 1,))
+        self.dev = torch.zeros(max(self.lay.size, 1), dtype=torch.uint8, device=device)
+        self.base = self.dev.data_ptr()
+        self.pattern = np.ascontiguousarray(pattern, np.int8).reshape(256, 4)
+        self.params = L.ft_orb_params()
+        self.params.fast_th, self.params.edge = fast_th, edge
+        for l, m in enumerate(max_kp):
+            self.params.max_kp[l] = int(m)
+        self.params.pattern = self.pattern.ctypes.data
+        self.outs = (L.ft_orb_out * max(1, n_images))()
+        for i in range(n_images):
+            o = self.outs[i]
+            for k, _, _ in self.KEYS:
+                setattr(o, k, self.ptr(i, k))
+            o.n_level = self.ptr(i, "n_level")
+
+    def ptr(self, i, key):
+        return self.base + self.lay.items[self.lay.index[(i, key)]][1]
+
+    def keypoints(self, i) -> L.ft_keypoints:
+        """ft_keypoints view of image i's slots (device pointers)."""
+        k = L.ft_keypoints()
+        k.n = self.nslots
+        k.x, k.y, k.oct, k.desc = self.ptr(i, "x"), self.ptr(i, "y"), self.ptr(i, "oct"), self.ptr(i, "desc")
+        return k
+
+    def download(self, i) -> dict:
+        h = self.dev.cpu().numpy()
+        out = {}
+        for key, off, dt, shape in self.lay.items:
+            if key[0] == i:
+                n = int(np.prod(shape)) * dt.itemsize
+                out[key[1]] = h[off:off + n].view(dt).reshape(shape)
+        return out
+
+    def download_all(self) -> list:
+        h = self.dev.cpu().numpy()
+        res = [dict() for _ in range(self.n)]
+        for key, off, dt, shape in self.lay.items:
+            n = int(np.prod(shape)) * dt.itemsize
+            res[key[0]][key[1]] = h[off:off + n].view(dt).reshape(shape)
+        return res
+
+
+def run_extract(ctx: "Context", pyramids, oo: OrbOutputs, params: L.ft_params | None = None, stream=None):
+    """ft_extract_orb on the ft_pyramid structs `pyramids` (device data)."""
+    arr = (L.ft_pyramid * max(1, len(pyramids)))(*pyramids)
+    L.check(ctx.lib.ft_extract_orb(ctx.ptr, stream_handle(stream), C.byref(params) if params is not None else None,
+                                   len(pyramids), arr, C.byref(oo.params), oo.outs), "ft_extract_orb")
+
+
 class Context:
     """Owns an ft_ctx (device arena, staging, graphs, tuning table)."""
 

@@ -1083,6 +1083,116 @@ ft_status ft_optimize_pose(ft_ctx *ctx, void *stream, const ft_params *params, c
     return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
 }
 
+ft_status ft_extract_orb(ft_ctx *ctx, void *stream, const ft_params *params, int n, const ft_pyramid *pyr,
+                         const ft_orb_params *orb, const ft_orb_out *out)
+{
+    if (!ctx || !orb || (n > 0 && (!pyr || !out))) return fail(FT_EINVAL, "ft_extract_orb: NULL argument");
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    ft_status s = check_params(p);
+    if (s != FT_OK) return s;
+    if (n < 0 || n > 4 * std::max(ctx->max_frames, 1)) return fail(FT_EINVAL, "ft_extract_orb: n=%d out of range", n);
+    if (orb->fast_th < 1 || orb->fast_th > 254) return fail(FT_EINVAL, "fast_th %d out of [1, 254]", orb->fast_th);
+    if (orb->edge < 19 || orb->edge > kOrbMaxDim) return fail(FT_EINVAL, "edge %d below 19", orb->edge);
+    if (!orb->pattern) return fail(FT_EINVAL, "ft_extract_orb: NULL pattern");
+    for (int i = 0; i < 256 * 4; ++i)
+        if (orb->pattern[i] < -13 || orb->pattern[i] > 13)
+            return fail(FT_EINVAL, "pattern coordinate %d outside [-13, 13]", (int)orb->pattern[i]);
+    int nslots = 0;
+    for (int l = 0; l < p.nlevels; ++l) {
+        if (orb->max_kp[l] < 0 || orb->max_kp[l] > kOrbMaxSlots)
+            return fail(FT_EINVAL, "max_kp[%d] = %d out of [0, %d]", l, orb->max_kp[l], kOrbMaxSlots);
+        nslots += orb->max_kp[l];
+    }
+    for (int i = 0; i < n; ++i) {
+        if ((s = check_pyramid(pyr[i], p.nlevels, "pyramid")) != FT_OK) return s;
+        for (int l = 0; l < p.nlevels; ++l)
+            if (pyr[i].width[l] > kOrbMaxDim || pyr[i].height[l] > kOrbMaxDim)
+                return fail(FT_EINVAL, "image %d level %d is larger than %d x %d", i, l, kOrbMaxDim, kOrbMaxDim);
+        const ft_orb_out &o = out[i];
+        if (!o.n_level || (nslots > 0 && (!o.x || !o.y || !o.oct || !o.score || !o.cs || !o.desc)))
+            return fail(FT_EINVAL, "image %d: NULL output array", i);
+        if (!aligned16(o.desc)) return fail(FT_EALIGN, "image %d: desc not 16-byte aligned", i);
+    }
+    // table: header, images, per-image counters (zeroed here)
+    const size_t o_img = align_up(sizeof(OrbHeader));
+    const size_t o_cnt = align_up(o_img + sizeof(OrbImage) * (size_t)std::max(n, 1));
+    const size_t bytes = align_up(o_cnt + sizeof(unsigned) * FT_MAX_LEVELS * (size_t)std::max(n, 1));
+    if (bytes > ctx->table_cap) return fail(FT_ENOMEM, "extraction table of %d images exceeds the context", n);
+    FT_CUDA(cudaSetDevice(ctx->device));
+    const int slot = ctx->slot;
+    ctx->slot = (ctx->slot + 1) % kSlots;
+    FT_CUDA(cudaEventSynchronize(ctx->slot_done[slot]));
+    char *h = ctx->staging[slot];
+    char *dev = ctx->arena + align_up(sizeof(unsigned) * 64);
+    std::memset(h, 0, bytes);
+    OrbHeader &Hd = *reinterpret_cast<OrbHeader *>(h);
+    Hd.nimages = n;
+    Hd.nlevels = p.nlevels;
+    Hd.fast_th = orb->fast_th;
+    Hd.edge = orb->edge;
+    const DevParams dp = make_dev_params(p);
+    for (int l = 0; l < FT_MAX_LEVELS; ++l) Hd.sc[l] = dp.sc[l];
+    std::memcpy(Hd.pattern, orb->pattern, sizeof(Hd.pattern));
+    Hd.images = reinterpret_cast<const OrbImage *>(dev + o_img);
+    size_t scratch = ctx->scratch_off;
+    auto carve = [&](size_t b) -> char * {
+        char *q = ctx->arena + scratch;
+        scratch = align_up(scratch + std::max<size_t>(b, 1));
+        return q;
+    };
+    int max_tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        OrbImage &I = reinterpret_cast<OrbImage *>(h + o_img)[i];
+        const ft_orb_out &o = out[i];
+        int tiles = 0, slot0 = 0;
+        for (int l = 0; l < p.nlevels; ++l) {
+            OrbLevel &L = I.lv[l];
+            L.img = pyr[i].data[l];
+            L.w = pyr[i].width[l];
+            L.h = pyr[i].height[l];
+            L.pitch = pyr[i].pitch[l];
+            L.smooth = reinterpret_cast<uint8_t *>(carve((size_t)L.w * L.h));
+            // suppressed corners are never 8-neighbours: at most one per 2 x 2 block
+            L.cand_cap = ((L.w + 1) / 2) * ((L.h + 1) / 2);
+            L.cand = reinterpret_cast<unsigned *>(carve(sizeof(unsigned) * (size_t)L.cand_cap));
+            L.tiles_x = (L.w + kOrbTile - 1) / kOrbTile;
+            L.tile0 = tiles;
+            tiles += L.tiles_x * ((L.h + kOrbTile - 1) / kOrbTile);
+            L.slot0 = slot0;
+            L.max_kp = orb->max_kp[l];
+            slot0 += L.max_kp;
+        }
+        I.tiles = tiles;
+        I.nslots = nslots;
+        I.x = o.x;
+        I.y = o.y;
+        I.oct = o.oct;
+        I.score = o.score;
+        I.cs = o.cs;
+        I.desc = o.desc;
+        I.n_level = o.n_level;
+        I.sel = reinterpret_cast<unsigned *>(carve(sizeof(unsigned) * (size_t)std::max(nslots, 1)));
+        I.cnt = reinterpret_cast<unsigned *>(dev + o_cnt) + (size_t)FT_MAX_LEVELS * i;
+        max_tiles = std::max(max_tiles, tiles);
+    }
+    Hd.max_tiles = max_tiles;
+    Hd.max_slots = nslots;
+    if (scratch > ctx->arena_bytes)
+        return fail(FT_ENOMEM, "arena of %zu bytes too small for this extraction (needs %zu)", ctx->arena_bytes,
+                    scratch);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = order_stream(ctx, st)) != FT_OK) return s;
+    if (n > 0) {
+        FT_CUDA(cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, st));
+        FT_CUDA(launch_orb(reinterpret_cast<const OrbHeader *>(dev), n, p.nlevels, max_tiles, nslots, st));
+        ctx->launches += 3;
+    }
+    FT_CUDA(cudaEventRecord(ctx->slot_done[slot], st));
+    return finish_call(ctx, st);
+}
+
 ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *w, int *h)
 {
     if (!w || !h || width <= 0 || height <= 0) return fail(FT_EINVAL, "ft_pyramid_sizes: bad argument");

@@ -167,6 +167,44 @@ struct BatchHeader {
     int pad_;
 };
 
+// ---------------------------------------------------------------- f3: keypoint extraction
+constexpr int kOrbTile = 16;            // detection tile: 16 x 16 pixels, one per thread
+constexpr int kOrbHalo = 4;             // FAST circle (3) + suppression neighbours (1)
+constexpr int kOrbMaxDim = 4096;        // level sizes the 12-bit key coordinates allow
+constexpr int kOrbMaxSlots = 4096;      // slots per level (sorted in shared memory)
+constexpr int kOrbSelectThreads = 1024;
+
+// One pyramid level of an image being described.
+struct OrbLevel {
+    const uint8_t *img;                 // level image
+    int w, h, pitch;
+    uint8_t *smooth;                    // [h][w] binomial-smoothed level (scratch)
+    unsigned *cand;                     // [cand_cap] suppressed corners as keys (scratch)
+    int cand_cap;
+    int tiles_x, tile0;                 // tiles per row, first tile of the level in the image
+    int slot0, max_kp;                  // first output slot of the level and its slots
+};
+
+struct OrbImage {
+    OrbLevel lv[FT_MAX_LEVELS];
+    int tiles, nslots;
+    float *x, *y;                       // outputs, [nslots] each
+    int8_t *oct;
+    int *score;
+    float *cs;                          // [nslots][2]
+    uint8_t *desc;                      // [nslots][32]
+    int *n_level;                       // [nlevels + 1]
+    unsigned *sel;                      // [nslots] selected keys in slot order (scratch)
+    unsigned *cnt;                      // [nlevels] candidate counters (zeroed by the table copy)
+};
+
+struct OrbHeader {
+    int nimages, nlevels, fast_th, edge, max_tiles, max_slots;
+    float sc[FT_MAX_LEVELS];
+    int8_t pattern[256 * 4];
+    const OrbImage *images;
+};
+
 }  // namespace ft
 
 // Launch helpers implemented in ft_kernels.cu (host-callable).
@@ -183,6 +221,10 @@ int fused_smem_bytes();
 // then the fused kernel's resident CTAs per SM
 cudaError_t fused_occupancy(int *ctas_per_sm);
 const void *fused_kernel_ptr();
+// keypoint extraction of the images of an OrbHeader (ft_orb.cu): detection,
+// selection and description, three launches on the stream
+cudaError_t launch_orb(const OrbHeader *dev_hdr, int nimages, int nlevels, int max_tiles, int max_slots,
+                       cudaStream_t stream);
 // set the text ft_last_error() returns on this thread (ft_api.cu)
 void set_last_error(const char *msg);
 // host checks and derived tables shared by the entry points (ft_api.cu)

@@ -1,0 +1,309 @@
+// ft_orb.cu -- keypoint detection and description on the pyramid levels
+// (next row f3).  The paper's ORB extraction builds the image pyramid, finds
+// keypoints on every level, describes each one and filters them (section
+// II-A); FastTrack reuses an existing GPU extractor (section IV-B) and
+// prints none of its steps.  This file implements the reading stated in the
+// public header: FAST-9 corners with the maximum-threshold score, 3x3
+// non-maximum suppression (ties: the earlier raster position), the best
+// max_kp[l] corners per level by (score descending, y, x) in fixed slots,
+// intensity-centroid orientation over the radius-15 disk, and 256 steered
+// tests on the level smoothed by the 5x5 binomial filter.
+//
+// Three launches per call, each over every image of the call:
+//   detect    one block per 16x16 tile of a level: the tile and a 4-pixel
+//             halo in shared memory, the FAST score of the tile and its
+//             one-pixel ring (an exact early rejection first: an arc of 9
+//             contiguous circle pixels always covers at least two of the four
+//             compass pixels), suppression against the eight neighbours, the
+//             kept corners appended as keys (255 - score) << 24 | y << 12 | x,
+//             and the smoothed level written from the same tile;
+//   select    one block per (image, level): the max_kp-th smallest key by an
+//             exact 4 x 8-bit radix select over the level's corners, the
+//             keys up to it gathered and sorted (bitonic) in shared memory;
+//   describe  one warp per output slot: the moments over the disk (lanes
+//             stride over it, integer warp sums), the orientation, and lane b
+//             computes descriptor byte b (tests 8b .. 8b+7).
+// Integer work is exact; the orientation and the rotated test positions use
+// IEEE-rounded FP32 (and one double square root) in the order the reading
+// gives, so results equal the oracle's bit for bit.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ft_internal.h"
+
+namespace ft {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTileW = kOrbTile + 2 * kOrbHalo;     // 24: tile + halo
+constexpr int kRing = kOrbTile + 2;                 // 18: tile + suppression ring
+constexpr int kDescribeWarps = 8;
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// FAST-9 score at (cx, cy) of the shared tile, -1 if not a corner at t
+__device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
+{
+    const int c = raw[cy][cx];
+    // compass pixels 0, 4, 8, 12 of the circle: (0,-3), (3,0), (0,3), (-3,0)
+    const int p0 = raw[cy - 3][cx], p4 = raw[cy][cx + 3], p8 = raw[cy + 3][cx], p12 = raw[cy][cx - 3];
+    const int nb = (p0 > c + t) + (p4 > c + t) + (p8 > c + t) + (p12 > c + t);
+    const int nd = (p0 < c - t) + (p4 < c - t) + (p8 < c - t) + (p12 < c - t);
+    if (nb < 2 && nd < 2) return -1;
+    constexpr int dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
+    constexpr int dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
+    int d[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d[i] = raw[cy + dy[i]][cx + dx[i]] - c;
+    int best = -1000;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        int lb = 1000, ld = 1000;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int v = d[(s + k) & 15];
+            lb = min(lb, v);
+            ld = min(ld, -v);
+        }
+        best = max(best, max(lb, ld));
+    }
+    return best > t ? best - 1 : -1;
+}
+
+__global__ void __launch_bounds__(kOrbTile * kOrbTile) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
+{
+    __shared__ uint8_t raw[kTileW][kTileW];
+    __shared__ int sco[kRing][kRing];
+    const OrbHeader &H = *hdr;
+    const OrbImage &I = H.images[blockIdx.y];
+    const int tile = blockIdx.x;
+    if (tile >= I.tiles) return;
+    int l = 0;
+    for (int k = 1; k < H.nlevels; ++k)
+        if (I.lv[k].tile0 <= tile) l = k;
+    const OrbLevel &L = I.lv[l];
+    const int t = tile - L.tile0;
+    const int x0 = (t % L.tiles_x) * kOrbTile, y0 = (t / L.tiles_x) * kOrbTile;
+    const int tid = threadIdx.x;
+    if (tile == 0 && tid == 0) I.n_level[H.nlevels] = 0;     // the select blocks add to it
+    // the tile and its halo, coordinates clamped to the level (the smoothing
+    // replicates the border; FAST only runs where its circle is inside)
+    for (int i = tid; i < kTileW * kTileW; i += kOrbTile * kOrbTile) {
+        const int yy = clampi(y0 - kOrbHalo + i / kTileW, 0, L.h - 1);
+        const int xx = clampi(x0 - kOrbHalo + i % kTileW, 0, L.w - 1);
+        raw[i / kTileW][i % kTileW] = L.img[(size_t)yy * L.pitch + xx];
+    }
+    __syncthreads();
+    const int E = H.edge;
+    for (int q = tid; q < kRing * kRing; q += kOrbTile * kOrbTile) {
+        const int ry = q / kRing, rx = q % kRing;
+        const int px = x0 - 1 + rx, py = y0 - 1 + ry;
+        int s = -1;
+        if (px >= E && px < L.w - E && py >= E && py < L.h - E) s = fast_score(raw, rx + 3, ry + 3, H.fast_th);
+        sco[ry][rx] = s;
+    }
+    __syncthreads();
+    const int ix = tid % kOrbTile, iy = tid / kOrbTile;
+    const int px = x0 + ix, py = y0 + iy;
+    const int sp = sco[iy + 1][ix + 1];
+    if (sp >= 0) {
+        bool keep = true;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (!dx && !dy) continue;
+                const int q = sco[iy + 1 + dy][ix + 1 + dx];
+                const bool earlier = dy < 0 || (dy == 0 && dx < 0);
+                if (q >= 0 && (q > sp || (q == sp && earlier))) keep = false;
+            }
+        if (keep) {
+            const unsigned at = atomicAdd(&I.cnt[l], 1u);
+            if ((int)at < L.cand_cap)
+                L.cand[at] = ((unsigned)(255 - sp) << 24) | ((unsigned)py << 12) | (unsigned)px;
+        }
+    }
+    if (px < L.w && py < L.h) {
+        constexpr int wt[5] = {1, 4, 6, 4, 1};
+        int acc = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) acc += wt[j] * wt[i] * raw[iy + kOrbHalo - 2 + j][ix + kOrbHalo - 2 + i];
+        L.smooth[(size_t)py * L.w + px] = (uint8_t)((acc + 128) >> 8);
+    }
+}
+
+__global__ void __launch_bounds__(kOrbSelectThreads) orb_select_kernel(const OrbHeader *__restrict__ hdr)
+{
+    __shared__ unsigned keys[kOrbMaxSlots];
+    __shared__ int hist[256];
+    __shared__ unsigned s_prefix;
+    __shared__ int s_rank, s_n;
+    const OrbHeader &H = *hdr;
+    const int l = blockIdx.x;
+    if (l >= H.nlevels) return;
+    const OrbImage &I = H.images[blockIdx.y];
+    const OrbLevel &L = I.lv[l];
+    const int tid = threadIdx.x;
+    const int c = min((int)I.cnt[l], L.cand_cap);
+    const int K = L.max_kp;
+    unsigned kth = 0xffffffffu;
+    if (c > K) {
+        // the K-th smallest key (keys are distinct): one byte per pass
+        unsigned prefix = 0, mask = 0;
+        int rank = K;
+        for (int b = 3; b >= 0; --b) {
+            if (tid < 256) hist[tid] = 0;
+            __syncthreads();
+            for (int i = tid; i < c; i += kOrbSelectThreads) {
+                const unsigned k = L.cand[i];
+                if ((k & mask) == prefix) atomicAdd(&hist[(k >> (8 * b)) & 255u], 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int cum = 0;
+                for (int bin = 0; bin < 256; ++bin) {
+                    if (cum + hist[bin] >= rank) {
+                        s_prefix = prefix | ((unsigned)bin << (8 * b));
+                        s_rank = rank - cum;
+                        break;
+                    }
+                    cum += hist[bin];
+                }
+            }
+            __syncthreads();
+            prefix = s_prefix;
+            rank = s_rank;
+            mask |= 255u << (8 * b);
+            __syncthreads();
+        }
+        kth = prefix;
+    }
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    for (int i = tid; i < c; i += kOrbSelectThreads) {
+        const unsigned k = L.cand[i];
+        if (k <= kth) {
+            const int at = atomicAdd(&s_n, 1);
+            if (at < kOrbMaxSlots) keys[at] = k;
+        }
+    }
+    __syncthreads();
+    const int n = min(s_n, K);
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = n + tid; i < P; i += kOrbSelectThreads) keys[i] = 0xffffffffu;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += kOrbSelectThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned a = keys[i], b = keys[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = tid; i < n; i += kOrbSelectThreads) I.sel[L.slot0 + i] = keys[i];
+    if (tid == 0) {
+        I.n_level[l] = n;
+        atomicAdd(&I.n_level[H.nlevels], n);
+    }
+}
+
+__global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const OrbHeader *__restrict__ hdr)
+{
+    const OrbHeader &H = *hdr;
+    const OrbImage &I = H.images[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * kDescribeWarps + (threadIdx.x >> 5);
+    if (slot >= I.nslots) return;
+    int l = 0;
+    for (int k = 0; k < H.nlevels; ++k)
+        if (slot >= I.lv[k].slot0 && slot < I.lv[k].slot0 + I.lv[k].max_kp) l = k;
+    const OrbLevel &L = I.lv[l];
+    const int i = slot - L.slot0;
+    if (i >= I.n_level[l]) {
+        // a slot without a keypoint
+        if (lane == 0) {
+            I.x[slot] = -1.0e9f;
+            I.y[slot] = -1.0e9f;
+            I.oct[slot] = 0;
+            I.score[slot] = -1;
+            I.cs[2 * slot] = 1.0f;
+            I.cs[2 * slot + 1] = 0.0f;
+        }
+        I.desc[(size_t)slot * 32 + lane] = 0;
+        return;
+    }
+    const unsigned key = I.sel[slot];
+    const int x = (int)(key & 4095u), y = (int)((key >> 12) & 4095u);
+    // intensity centroid over the disk u^2 + v^2 <= 225 (exact integer sums)
+    int m10 = 0, m01 = 0;
+    for (int q = lane; q < 31 * 31; q += 32) {
+        const int u = q % 31 - 15, v = q / 31 - 15;
+        if (u * u + v * v > 225) continue;
+        const int I0 = L.img[(size_t)(y + v) * L.pitch + (x + u)];
+        m10 += u * I0;
+        m01 += v * I0;
+    }
+    m10 = __reduce_add_sync(kFull, m10);
+    m01 = __reduce_add_sync(kFull, m01);
+    float c = 1.0f, s = 0.0f;
+    if (m10 != 0 || m01 != 0) {
+        const double n2 = __dadd_rn(__dmul_rn((double)m10, (double)m10), __dmul_rn((double)m01, (double)m01));
+        const float nm = __double2float_rn(__dsqrt_rn(n2));
+        c = __fdiv_rn((float)m10, nm);
+        s = __fdiv_rn((float)m01, nm);
+    }
+    // byte `lane` of the descriptor: tests 8 lane .. 8 lane + 7
+    unsigned byte = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int8_t *pt = H.pattern + 4 * (8 * lane + k);
+        int val[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float px = (float)pt[2 * q], py = (float)pt[2 * q + 1];
+            const int u = (int)roundf(__fsub_rn(__fmul_rn(c, px), __fmul_rn(s, py)));
+            const int v = (int)roundf(__fadd_rn(__fmul_rn(s, px), __fmul_rn(c, py)));
+            val[q] = L.smooth[(size_t)(y + v) * L.w + (x + u)];
+        }
+        byte |= (val[0] < val[1] ? 1u : 0u) << k;
+    }
+    I.desc[(size_t)slot * 32 + lane] = (uint8_t)byte;
+    if (lane == 0) {
+        I.x[slot] = __fmul_rn((float)x, H.sc[l]);
+        I.y[slot] = __fmul_rn((float)y, H.sc[l]);
+        I.oct[slot] = (int8_t)l;
+        I.score[slot] = 255 - (int)(key >> 24);
+        I.cs[2 * slot] = c;
+        I.cs[2 * slot + 1] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_orb(const OrbHeader *dev_hdr, int nimages, int nlevels, int max_tiles, int max_slots,
+                       cudaStream_t stream)
+{
+    if (nimages <= 0) return cudaSuccess;
+    orb_detect_kernel<<<dim3((unsigned)max(max_tiles, 1), (unsigned)nimages), kOrbTile * kOrbTile, 0, stream>>>(
+        dev_hdr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    orb_select_kernel<<<dim3((unsigned)nlevels, (unsigned)nimages), kOrbSelectThreads, 0, stream>>>(dev_hdr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((max(max_slots, 1) + kDescribeWarps - 1) / kDescribeWarps);
+    orb_describe_kernel<<<dim3(blocks, (unsigned)nimages), 32 * kDescribeWarps, 0, stream>>>(dev_hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace ft

@@ -708,3 +708,30 @@ def orb_level_caps(n_features: int, nlevels: int = NLEVELS, s: float = SCALE) ->
     caps = [int(round(n0 * f ** l)) for l in range(nlevels - 1)]
     caps.append(max(0, n_features - sum(caps)))
     return caps
+
+
+def frame_with_keypoints(seed: int, cam: PinholeCamera, images: _StereoImages, left: Keypoints,
+                         right: Keypoints, n_map: int = 3000, flip_p: float = 0.05) -> Frame:
+    """A pinhole frame with the given keypoints (for instance extracted from
+    its own images): its local map is placed behind the left keypoints that
+    are not padding (x >= 0) at the depth of the image's plane there, plus
+    random points, as in pinhole_frame."""
+    rng = np.random.default_rng(seed)
+    W, H = cam.width, cam.height
+    valid = np.nonzero(left.x >= 0)[0]
+    lx, ly = left.x[valid], left.y[valid]
+    lab = images.label[np.clip(np.rint(ly).astype(np.int64), 0, H - 1), np.clip(np.rint(lx).astype(np.int64), 0, W - 1)]
+    zl = images.depth[lab]
+    R_true = random_rotation(rng, 10.0)
+    O_true = rng.normal(0.0, 1.0, 3)
+    R_est, O_est = perturb_pose(rng, R_true, O_true)
+
+    def unproj(u, v, z):
+        return np.stack([(u - cam.cx) / cam.fx * z, (v - cam.cy) / cam.fy * z, z], axis=1)
+
+    lmap, assoc = _local_map(rng, n_map, None, unproj, W, H, R_true, O_true, lx, ly, left.oct[valid],
+                             left.desc[valid], zl, flip_p)
+    return Frame(camera="pinhole", left=left, right=right, pose=make_pose(R_est, O_est), map=lmap,
+                 taken_l=np.zeros(left.n, np.uint8), cam=cam, pyr_left=images.pyr_left,
+                 pyr_right=images.pyr_right, pose_true=make_pose(R_true, O_true),
+                 truth=dict(map_kp=valid[assoc]))

@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_ctypes_struct_sizes_match_c(lib):
     structs = ["ft_params", "ft_keypoints", "ft_pyramid", "ft_pinhole", "ft_kb8", "ft_fisheye_rig",
                "ft_pose", "ft_map_view", "ft_stereo_frame", "ft_stereo_out", "ft_fisheye_out",
-               "ft_search_cam_out", "ft_search_out", "ft_pose_out", "ft_frame_view", "ft_last_frame_view", "ft_frame_job", "ft_batch",
+               "ft_search_cam_out", "ft_search_out", "ft_pose_out", "ft_orb_params", "ft_orb_out", "ft_frame_view", "ft_last_frame_view", "ft_frame_job", "ft_batch",
                "ft_ctx_desc", "ft_tuning", "ft_trace_record", "ft_server_desc", "ft_stream_desc",
                "ft_request", "ft_results", "ft_completion", "ft_server_stats"]
     prog = "#include <stdio.h>\n#include \"fasttrack.h\"\nint main(void){\n"
