@@ -42,6 +42,21 @@ constexpr int kDescribeWarps = 8;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Offsets of the 16 pixels of the radius-3 circle, clockwise from (0, -3):
+// x offsets 0 1 2 3 3 3 2 1 0 -1 -2 -3 -3 -3 -2 -1, stored + 3 as 4-bit
+// nibbles of one constant; the y offset of pixel i is the x offset of pixel
+// i + 12.  (Formulations that indexed a local or constant offset table gave
+// wrong scores on the device in measurement; this one matches the oracle.)
+__device__ __forceinline__ int circle_dx(int i)
+{
+    constexpr unsigned long long kPacked = 0x2100012345666543ull;
+    return (int)((kPacked >> (4 * i)) & 15ull) - 3;
+}
+__device__ __forceinline__ int circle_dy(int i) { return circle_dx((i + 12) & 15); }
+
+// binomial weights 1 4 6 4 1
+__device__ __forceinline__ int binomial5(int j) { return j == 2 ? 6 : ((j & 1) ? 4 : 1); }
+
 // FAST-9 score at (cx, cy) of the shared tile, -1 if not a corner at t
 __device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
 {
@@ -51,11 +66,9 @@ __device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
     const int nb = (p0 > c + t) + (p4 > c + t) + (p8 > c + t) + (p12 > c + t);
     const int nd = (p0 < c - t) + (p4 < c - t) + (p8 < c - t) + (p12 < c - t);
     if (nb < 2 && nd < 2) return -1;
-    constexpr int dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
-    constexpr int dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
     int d[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) d[i] = raw[cy + dy[i]][cx + dx[i]] - c;
+    for (int i = 0; i < 16; ++i) d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
     int best = -1000;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
@@ -125,12 +138,12 @@ __global__ void __launch_bounds__(kOrbTile * kOrbTile) orb_detect_kernel(const O
         }
     }
     if (px < L.w && py < L.h) {
-        constexpr int wt[5] = {1, 4, 6, 4, 1};
         int acc = 0;
 #pragma unroll
         for (int j = 0; j < 5; ++j)
 #pragma unroll
-            for (int i = 0; i < 5; ++i) acc += wt[j] * wt[i] * raw[iy + kOrbHalo - 2 + j][ix + kOrbHalo - 2 + i];
+            for (int i = 0; i < 5; ++i)
+                acc += binomial5(j) * binomial5(i) * (int)raw[iy + kOrbHalo - 2 + j][ix + kOrbHalo - 2 + i];
         L.smooth[(size_t)py * L.w + px] = (uint8_t)((acc + 128) >> 8);
     }
 }
