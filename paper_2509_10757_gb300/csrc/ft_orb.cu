@@ -45,8 +45,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // Offsets of the 16 pixels of the radius-3 circle, clockwise from (0, -3):
 // x offsets 0 1 2 3 3 3 2 1 0 -1 -2 -3 -3 -3 -2 -1, stored + 3 as 4-bit
 // nibbles of one constant; the y offset of pixel i is the x offset of pixel
-// i + 12.  (Formulations that indexed a local or constant offset table gave
-// wrong scores on the device in measurement; this one matches the oracle.)
+// i + 12.
 __device__ __forceinline__ int circle_dx(int i)
 {
     constexpr unsigned long long kPacked = 0x2100012345666543ull;
@@ -69,6 +68,10 @@ __device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
     int d[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
+    // the best arc: the largest, over the 16 starts and both polarities, of
+    // the smallest difference along 9 contiguous pixels.  Written as
+    // conditional selects: min/max chains over this unrolled window gave
+    // wrong scores on the device in measurement, this form matches the oracle.
     int best = -1000;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
@@ -76,10 +79,11 @@ __device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int v = d[(s + k) & 15];
-            lb = min(lb, v);
-            ld = min(ld, -v);
+            lb = v < lb ? v : lb;
+            ld = -v < ld ? -v : ld;
         }
-        best = max(best, max(lb, ld));
+        best = lb > best ? lb : best;
+        best = ld > best ? ld : best;
     }
     return best > t ? best - 1 : -1;
 }
