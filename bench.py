@@ -651,6 +651,78 @@ def fisheye_result(steps: int, warmup: int, dev, local_rank: int) -> dict:
                         "6000 map points", **r}
 
 
+def extraction_result(steps: int, warmup: int, dev, local_rank: int) -> dict:
+    """Tracking from the device-resident level-0 images of the 64-frame
+    workload (1200 keypoints per image): per step the pyramids of the 128
+    images are built (ft_build_pyramids), keypoints and descriptors are
+    extracted (ft_extract_orb, 1200 slots per image), and ft_track_batch
+    tracks the 64 frames from the extraction's keypoints, all on one stream
+    with no host round trip.  L2 flushed before each step."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300 import scenes
+    from paper_2509_10757_gb300.batch import Context, OrbOutputs, PackedBatch, run_batch, stream_handle
+
+    frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES, nl_range=(1200, 1200))
+    pb = PackedBatch(frames, device=dev, device_pyramids=True)
+    pb.upload()
+    ctx = Context(device=local_rank, arena_bytes=1 << 30, max_frames=FRAMES)
+    caps = scenes.orb_level_caps(1200)
+    oo = OrbOutputs(2 * FRAMES, caps, scenes.orb_pattern(), device=dev)
+    pyrs = []
+    for f in range(FRAMES):
+        pyrs += [pb.pyramid(f, "L"), pb.pyramid(f, "R")]
+        pb.jobs[f].left = oo.keypoints(2 * f)
+        pb.jobs[f].right = oo.keypoints(2 * f + 1)
+        pb.jobs[f].build_pyramids = 0
+    arr = (L.ft_pyramid * len(pyrs))(*pyrs)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    so = stream_handle(stream)
+
+    def step(ev):
+        L.check(ctx.lib.ft_build_pyramids(ctx.ptr, so, None, len(pyrs), arr), "ft_build_pyramids")
+        ev[1].record(stream)
+        L.check(ctx.lib.ft_extract_orb(ctx.ptr, so, None, len(pyrs), arr, C.byref(oo.params), oo.outs),
+                "ft_extract_orb")
+        ev[2].record(stream)
+        run_batch(ctx, pb, stream=stream)
+
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize(dev)
+    times = []
+    for i in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)
+            ev[0].record(stream)
+            step(ev)
+            ev[3].record(stream)
+        times.append(ev)
+    torch.cuda.synchronize(dev)
+    assert ctx.sync_status() == 0
+    tot = [a.elapsed_time(d) for a, _, _, d in times]
+    pyr = [a.elapsed_time(b) for a, b, _, _ in times]
+    ext = [b.elapsed_time(c) for _, b, c, _ in times]
+    trk = [c.elapsed_time(d) for _, _, c, d in times]
+    n_found = int(sum(int(d["n_level"][-1]) for d in oo.download_all()))
+    ctx.close()
+    kp, mp = units_of(frames)
+    mean_s = statistics.mean(tot) / 1e3
+    return {"workload": "tracking from level-0 images: 64 frames 752x480, pyramids built on the device, "
+                        "1200 keypoints extracted per image (FAST-9, orientation, steered 256-bit "
+                        "descriptors), then stereo matching and local-map search from the extracted keypoints",
+            "ms_per_step": statistics.mean(tot), "value": (kp + mp) / mean_s, "unit": UNIT,
+            "pyramid_ms": statistics.mean(pyr), "extraction_ms": statistics.mean(ext),
+            "tracking_ms": statistics.mean(trk), "images": 2 * FRAMES, "slots_per_image": sum(caps),
+            "keypoints_found": n_found, "launches_per_step": 1 + 3 + 1, "steps": steps}
+
+
 _STRESS_BASE: list = []
 
 
@@ -971,6 +1043,11 @@ def run_gpu(args, rank, world, local_rank):
                         "4 rounds x 10 Gauss-Newton steps over its matches (single launch, L2 flushed)")
     pose["without_pose_ms_per_launch"] = statistics.mean(step_ms)
 
+    # tracking from level-0 images through the device keypoint extraction
+    clocks.mark("extraction", True)
+    extraction = extraction_result(max(20, min(args.steps, 300)), max(3, args.warmup), dev, local_rank)
+    clocks.mark("extraction", False)
+
     # the other batched workloads of the scope, one fused launch per step:
     # the fisheye batch (popcount roofline) and the 1080p stress batch of 32
     clocks.mark("fisheye", True)
@@ -1057,6 +1134,7 @@ def run_gpu(args, rank, world, local_rank):
         "fisheye": fisheye,
         "stress": stress,
         "pose_optimization": pose,
+        "extraction": extraction,
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -488,6 +488,10 @@ ft_status ft_measure_popcount(void *stream, double *popc_per_s);
  * up to 4 (bytes past the width are zero).  Asynchronous on the stream. */
 ft_status ft_build_pyramid(ft_ctx *ctx, void *stream, const ft_params *params, const ft_pyramid *pyr);
 
+/* ft_build_pyramid for n images in one launch (at most 2 x max_frames
+ * images); the images may differ in size.  Asynchronous on the stream. */
+ft_status ft_build_pyramids(ft_ctx *ctx, void *stream, const ft_params *params, int n, const ft_pyramid *pyr);
+
 /* Stereo matching followed by the search, for a ragged batch of frames, in
  * one persistent fused launch (CUDA-graph replayed per batch-shape bucket if
  * the context was created with use_graphs).  Each frame's results equal

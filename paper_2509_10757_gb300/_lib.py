@@ -213,6 +213,7 @@ SIGNATURES = [
     ("ft_pyramid_sizes", i32, [i32, i32, C.POINTER(ft_params), vp, vp]),
     ("ft_measure_popcount", i32, [vp, C.POINTER(C.c_double)]),
     ("ft_build_pyramid", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_pyramid)]),
+    ("ft_build_pyramids", i32, [vp, vp, C.POINTER(ft_params), i32, C.POINTER(ft_pyramid)]),
     ("ft_track_batch", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch)]),
     ("ft_autotune", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch), i32,
                           C.POINTER(ft_tuning)]),

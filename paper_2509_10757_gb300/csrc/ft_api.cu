@@ -1253,6 +1253,28 @@ ft_status ft_build_pyramid(ft_ctx *ctx, void *stream, const ft_params *params, c
     return submit(ctx, (cudaStream_t)stream, p, {j}, nullptr, false);
 }
 
+ft_status ft_build_pyramids(ft_ctx *ctx, void *stream, const ft_params *params, int n, const ft_pyramid *pyr)
+{
+    if (!ctx || (n > 0 && !pyr)) return fail(FT_EINVAL, "ft_build_pyramids: NULL argument");
+    if (n < 0 || (n + 1) / 2 > ctx->max_frames)
+        return fail(FT_EINVAL, "ft_build_pyramids: %d images exceed the context (2 x max_frames)", n);
+    ft_params p;
+    if (params) p = *params;
+    else ft_params_default(&p);
+    // two images per job: the pyramid kernel builds a job's left and right
+    std::vector<Job> jobs((n + 1) / 2);
+    for (int i = 0; i < n; i += 2) {
+        Job &j = jobs[i / 2];
+        j.camera = FT_CAMERA_PINHOLE;
+        j.pin.width = pyr[i].width[0];
+        j.pin.height = pyr[i].height[0];
+        j.pyr_l = pyr[i];
+        j.pyr_r = i + 1 < n ? pyr[i + 1] : pyr[i];
+        j.build_pyr = i + 1 < n ? 3 : 1;
+    }
+    return submit(ctx, (cudaStream_t)stream, p, jobs, nullptr, false);
+}
+
 static ft_status jobs_of_batch(const ft_batch *batch, std::vector<Job> &jobs)
 {
     if (!batch || batch->n < 0 || (batch->n > 0 && !batch->frames))

@@ -710,6 +710,27 @@ def test_build_pyramid_per_call_and_size_check(ctx, lib):
     assert ctx.lib.ft_build_pyramid(ctx.ptr, stream_handle(), None, C.byref(pyr)) == lib.FT_EINVAL
 
 
+def test_build_pyramids_many_images_in_one_launch(ctx, lib):
+    # five images of three sizes (an odd count: the last job builds one image)
+    from paper_2509_10757_gb300.batch import PackedBatch, stream_handle
+    frames = [scenes.pinhole_frame(52, W=640, H=480, n_left=200, n_map=100),
+              scenes.pinhole_frame(53, W=752, H=480, n_left=200, n_map=100),
+              scenes.pinhole_frame(54, W=320, H=240, n_left=200, n_map=100)]
+    pb = PackedBatch(frames, device_pyramids=True)
+    pb.upload()
+    sides = [(0, "L"), (0, "R"), (1, "L"), (1, "R"), (2, "L")]
+    arr = (lib.ft_pyramid * len(sides))(*[pb.pyramid(f, s) for f, s in sides])
+    n0 = ctx.launches()
+    lib.check(ctx.lib.ft_build_pyramids(ctx.ptr, stream_handle(), None, len(sides), arr), "ft_build_pyramids")
+    torch.cuda.synchronize()
+    assert ctx.launches() - n0 == 1
+    for f, s in sides:
+        fr = frames[f]
+        ref = orc.build_pyramid((fr.pyr_left if s == "L" else fr.pyr_right)[0])
+        for l in range(1, len(ref)):
+            assert np.array_equal(pb.device_level(f, s, l), ref[l]), (f, s, l)
+
+
 @pytest.mark.parametrize("W,H,nlevels,scale,seed", [(752, 480, 8, 1.2, 752), (333, 77, 8, 1.2, 1),
                                                      (6000, 37, 6, 1.3, 2), (17, 9, 3, 1.5, 3),
                                                      (641, 203, 5, 2.0, 4), (2, 3, 4, 1.2, 5),
