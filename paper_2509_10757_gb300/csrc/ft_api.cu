@@ -80,6 +80,14 @@ TableLayout table_layout(int n)
     return L;
 }
 
+// bytes of an extraction table of n images: header, images, counters
+size_t orb_table_bytes(int n)
+{
+    const size_t o_img = align_up(sizeof(OrbHeader));
+    const size_t o_cnt = align_up(o_img + sizeof(OrbImage) * (size_t)std::max(n, 1));
+    return align_up(o_cnt + sizeof(unsigned) * FT_MAX_LEVELS * (size_t)std::max(n, 1));
+}
+
 struct Bucket {
     int frames_p2, has_pinhole, has_fisheye, nl_p2, m_p2;
     bool operator<(const Bucket &o) const
@@ -881,7 +889,9 @@ ft_status ft_create(ft_ctx **out, const ft_ctx_desc *desc)
     if (e == cudaSuccess) e = fused_occupancy(&c->occ);
     c->sm_count = prop.multiProcessorCount;
     if (c->occ < 1) c->occ = 1;
-    c->table_cap = table_layout(d.max_frames).total;
+    // the table region holds a batch table of max_frames frames or an
+    // extraction table of 4 x max_frames images
+    c->table_cap = std::max(table_layout(d.max_frames).total, orb_table_bytes(4 * d.max_frames));
     const size_t head = align_up(sizeof(unsigned) * 64);
     c->scratch_off = align_up(head + c->table_cap);
     c->arena_bytes = std::max(d.arena_bytes, c->scratch_off + ((size_t)1 << 20));
@@ -1118,7 +1128,7 @@ ft_status ft_extract_orb(ft_ctx *ctx, void *stream, const ft_params *params, int
     // table: header, images, per-image counters (zeroed here)
     const size_t o_img = align_up(sizeof(OrbHeader));
     const size_t o_cnt = align_up(o_img + sizeof(OrbImage) * (size_t)std::max(n, 1));
-    const size_t bytes = align_up(o_cnt + sizeof(unsigned) * FT_MAX_LEVELS * (size_t)std::max(n, 1));
+    const size_t bytes = orb_table_bytes(n);
     if (bytes > ctx->table_cap) return fail(FT_ENOMEM, "extraction table of %d images exceeds the context", n);
     FT_CUDA(cudaSetDevice(ctx->device));
     const int slot = ctx->slot;

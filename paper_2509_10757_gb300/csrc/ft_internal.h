@@ -168,7 +168,7 @@ struct BatchHeader {
 };
 
 // ---------------------------------------------------------------- f3: keypoint extraction
-constexpr int kOrbTile = 16;            // detection tile: 16 x 16 pixels, one per thread
+constexpr int kOrbTile = 32;            // detection tile: 32 x 32 pixels, 4 per thread
 constexpr int kOrbHalo = 4;             // FAST circle (3) + suppression neighbours (1)
 constexpr int kOrbMaxDim = 4096;        // level sizes the 12-bit key coordinates allow
 constexpr int kOrbMaxSlots = 4096;      // slots per level (sorted in shared memory)

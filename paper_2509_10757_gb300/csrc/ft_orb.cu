@@ -10,13 +10,13 @@
 // tests on the level smoothed by the 5x5 binomial filter.
 //
 // Three launches per call, each over every image of the call:
-//   detect    one block per 16x16 tile of a level: the tile and a 4-pixel
-//             halo in shared memory, the FAST score of the tile and its
-//             one-pixel ring (an exact early rejection first: an arc of 9
-//             contiguous circle pixels always covers at least two of the four
-//             compass pixels), suppression against the eight neighbours, the
-//             kept corners appended as keys (255 - score) << 24 | y << 12 | x,
-//             and the smoothed level written from the same tile;
+//   detect    one block of 256 threads per 32x32 tile of a level: the tile
+//             and a 4-pixel halo in shared memory, the FAST score of the tile
+//             and its one-pixel ring (the segment test on bit masks first,
+//             the score for corners only), suppression against the eight
+//             neighbours, the kept corners appended as keys
+//             (255 - score) << 24 | y << 12 | x (one atomic per warp), and
+//             the smoothed level written from the same tile (separable);
 //   select    one block per (image, level): the max_kp-th smallest key by an
 //             exact 4 x 8-bit radix select over the level's corners, the
 //             keys up to it gathered and sorted (bitonic) in shared memory;
@@ -36,11 +36,15 @@ namespace ft {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kTileW = kOrbTile + 2 * kOrbHalo;     // 24: tile + halo
-constexpr int kRing = kOrbTile + 2;                 // 18: tile + suppression ring
+constexpr int kDetThreads = 256;
+constexpr int kTileW = kOrbTile + 2 * kOrbHalo;     // tile + halo
+constexpr int kRing = kOrbTile + 2;                 // tile + suppression ring
+constexpr int kRows = kOrbTile / (kDetThreads / kOrbTile);   // output rows per thread
 constexpr int kDescribeWarps = 8;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+__device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+__device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 
 // Offsets of the 16 pixels of the radius-3 circle, clockwise from (0, -3):
 // x offsets 0 1 2 3 3 3 2 1 0 -1 -2 -3 -3 -3 -2 -1, stored + 3 as 4-bit
@@ -56,42 +60,67 @@ __device__ __forceinline__ int circle_dy(int i) { return circle_dx((i + 12) & 15
 // binomial weights 1 4 6 4 1
 __device__ __forceinline__ int binomial5(int j) { return j == 2 ? 6 : ((j & 1) ? 4 : 1); }
 
-// FAST-9 score at (cx, cy) of the shared tile, -1 if not a corner at t
+// a 16-bit circular mask holds 9 consecutive ones: on the doubled mask, a
+// bit p survives the AND of shifts 1, 2, 4 and 8 iff bits p .. p+8 are set
+__device__ __forceinline__ bool run9(unsigned m)
+{
+    const unsigned d = m | (m << 16);
+    unsigned r = d & (d >> 1);
+    r &= r >> 2;
+    r &= r >> 4;
+    r &= d >> 8;
+    return (r & 0xffffu) != 0;
+}
+
+// FAST-9 score at (cx, cy) of the shared tile, -1 if not a corner at t.
+// The segment test runs on bit masks first; the score (the best arc's
+// smallest difference, minus one) is computed for corners only, as sliding
+// minima (bright) and maxima (dark) over windows of 9 built from windows of
+// 2, 4 and 8 on the circle listed 1.5 times.  Comparisons are written as
+// conditional selects.
 __device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
 {
     const int c = raw[cy][cx];
-    // compass pixels 0, 4, 8, 12 of the circle: (0,-3), (3,0), (0,3), (-3,0)
-    const int p0 = raw[cy - 3][cx], p4 = raw[cy][cx + 3], p8 = raw[cy + 3][cx], p12 = raw[cy][cx - 3];
-    const int nb = (p0 > c + t) + (p4 > c + t) + (p8 > c + t) + (p12 > c + t);
-    const int nd = (p0 < c - t) + (p4 < c - t) + (p8 < c - t) + (p12 < c - t);
-    if (nb < 2 && nd < 2) return -1;
     int d[16];
+    unsigned bright = 0, dark = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
-    // the best arc: the largest, over the 16 starts and both polarities, of
-    // the smallest difference along 9 contiguous pixels.  Written as
-    // conditional selects: min/max chains over this unrolled window gave
-    // wrong scores on the device in measurement, this form matches the oracle.
-    int best = -1000;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        int lb = 1000, ld = 1000;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int v = d[(s + k) & 15];
-            lb = v < lb ? v : lb;
-            ld = -v < ld ? -v : ld;
-        }
-        best = lb > best ? lb : best;
-        best = ld > best ? ld : best;
+    for (int i = 0; i < 16; ++i) {
+        d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
+        bright |= (d[i] > t ? 1u : 0u) << i;
+        dark |= (d[i] < -t ? 1u : 0u) << i;
     }
+    if (!run9(bright) && !run9(dark)) return -1;
+    int lo[23], hi[23];
+#pragma unroll
+    for (int i = 0; i < 23; ++i) {
+        lo[i] = imin(d[i & 15], d[(i + 1) & 15]);
+        hi[i] = imax(d[i & 15], d[(i + 1) & 15]);
+    }
+#pragma unroll
+    for (int i = 0; i < 21; ++i) {
+        lo[i] = imin(lo[i], lo[i + 2]);
+        hi[i] = imax(hi[i], hi[i + 2]);
+    }
+#pragma unroll
+    for (int i = 0; i < 17; ++i) {
+        lo[i] = imin(lo[i], lo[i + 4]);
+        hi[i] = imax(hi[i], hi[i + 4]);
+    }
+    int best_b = -1000, least_hi = 1000;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        best_b = imax(best_b, imin(lo[i], d[(i + 8) & 15]));
+        least_hi = imin(least_hi, imax(hi[i], d[(i + 8) & 15]));
+    }
+    const int best = imax(best_b, -least_hi);
     return best > t ? best - 1 : -1;
 }
 
-__global__ void __launch_bounds__(kOrbTile * kOrbTile) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
+__global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
 {
     __shared__ uint8_t raw[kTileW][kTileW];
-    __shared__ int sco[kRing][kRing];
+    __shared__ short sco[kRing][kRing];
+    __shared__ short hs[kOrbTile + 4][kOrbTile];      // horizontal binomial sums of rows -2 .. T+1
     const OrbHeader &H = *hdr;
     const OrbImage &I = H.images[blockIdx.y];
     const int tile = blockIdx.x;
@@ -102,30 +131,41 @@ __global__ void __launch_bounds__(kOrbTile * kOrbTile) orb_detect_kernel(const O
     const OrbLevel &L = I.lv[l];
     const int t = tile - L.tile0;
     const int x0 = (t % L.tiles_x) * kOrbTile, y0 = (t / L.tiles_x) * kOrbTile;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tile == 0 && tid == 0) I.n_level[H.nlevels] = 0;     // the select blocks add to it
     // the tile and its halo, coordinates clamped to the level (the smoothing
     // replicates the border; FAST only runs where its circle is inside)
-    for (int i = tid; i < kTileW * kTileW; i += kOrbTile * kOrbTile) {
+    for (int i = tid; i < kTileW * kTileW; i += kDetThreads) {
         const int yy = clampi(y0 - kOrbHalo + i / kTileW, 0, L.h - 1);
         const int xx = clampi(x0 - kOrbHalo + i % kTileW, 0, L.w - 1);
         raw[i / kTileW][i % kTileW] = L.img[(size_t)yy * L.pitch + xx];
     }
     __syncthreads();
     const int E = H.edge;
-    for (int q = tid; q < kRing * kRing; q += kOrbTile * kOrbTile) {
+    for (int q = tid; q < kRing * kRing; q += kDetThreads) {
         const int ry = q / kRing, rx = q % kRing;
         const int px = x0 - 1 + rx, py = y0 - 1 + ry;
         int s = -1;
         if (px >= E && px < L.w - E && py >= E && py < L.h - E) s = fast_score(raw, rx + 3, ry + 3, H.fast_th);
-        sco[ry][rx] = s;
+        sco[ry][rx] = (short)s;
+    }
+    for (int q = tid; q < (kOrbTile + 4) * kOrbTile; q += kDetThreads) {
+        const int r = q / kOrbTile, x = q % kOrbTile;
+        int a = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) a += binomial5(i) * (int)raw[r + kOrbHalo - 2][x + kOrbHalo - 2 + i];
+        hs[r][x] = (short)a;
     }
     __syncthreads();
-    const int ix = tid % kOrbTile, iy = tid / kOrbTile;
-    const int px = x0 + ix, py = y0 + iy;
-    const int sp = sco[iy + 1][ix + 1];
-    if (sp >= 0) {
-        bool keep = true;
+    // suppression: thread (ix, iy) owns the pixels of column ix, rows iy + k * (T / kRows)
+    const int ix = tid % kOrbTile, iy0 = tid / kOrbTile;
+    unsigned keys[kRows];
+    int nkeep = 0;
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        const int iy = iy0 + k * (kDetThreads / kOrbTile);
+        const int sp = sco[iy + 1][ix + 1];
+        bool keep = sp >= 0;
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
@@ -135,21 +175,29 @@ __global__ void __launch_bounds__(kOrbTile * kOrbTile) orb_detect_kernel(const O
                 const bool earlier = dy < 0 || (dy == 0 && dx < 0);
                 if (q >= 0 && (q > sp || (q == sp && earlier))) keep = false;
             }
-        if (keep) {
-            const unsigned at = atomicAdd(&I.cnt[l], 1u);
-            if ((int)at < L.cand_cap)
-                L.cand[at] = ((unsigned)(255 - sp) << 24) | ((unsigned)py << 12) | (unsigned)px;
+        if (keep) keys[nkeep++] = ((unsigned)(255 - sp) << 24) | ((unsigned)(y0 + iy) << 12) | (unsigned)(x0 + ix);
+        const int px = x0 + ix, py = y0 + iy;
+        if (px < L.w && py < L.h) {
+            int acc = 0;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc += binomial5(j) * (int)hs[iy + j][ix];
+            L.smooth[(size_t)py * L.w + px] = (uint8_t)((acc + 128) >> 8);
         }
     }
-    if (px < L.w && py < L.h) {
-        int acc = 0;
+    // one atomic per warp reserves the warp's corners
+    int incl = nkeep;
 #pragma unroll
-        for (int j = 0; j < 5; ++j)
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-                acc += binomial5(j) * binomial5(i) * (int)raw[iy + kOrbHalo - 2 + j][ix + kOrbHalo - 2 + i];
-        L.smooth[(size_t)py * L.w + px] = (uint8_t)((acc + 128) >> 8);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
     }
+    const int total = __shfl_sync(kFull, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(&I.cnt[l], (unsigned)total);
+    base = __shfl_sync(kFull, base, 31);
+    int at = (int)base + incl - nkeep;
+    for (int k = 0; k < nkeep; ++k, ++at)
+        if (at < L.cand_cap) L.cand[at] = keys[k];
 }
 
 __global__ void __launch_bounds__(kOrbSelectThreads) orb_select_kernel(const OrbHeader *__restrict__ hdr)
@@ -311,7 +359,7 @@ cudaError_t launch_orb(const OrbHeader *dev_hdr, int nimages, int nlevels, int m
                        cudaStream_t stream)
 {
     if (nimages <= 0) return cudaSuccess;
-    orb_detect_kernel<<<dim3((unsigned)max(max_tiles, 1), (unsigned)nimages), kOrbTile * kOrbTile, 0, stream>>>(
+    orb_detect_kernel<<<dim3((unsigned)max(max_tiles, 1), (unsigned)nimages), kDetThreads, 0, stream>>>(
         dev_hdr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
