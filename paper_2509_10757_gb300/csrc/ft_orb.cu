@@ -72,24 +72,31 @@ __device__ __forceinline__ bool run9(unsigned m)
     return (r & 0xffffu) != 0;
 }
 
-// FAST-9 score at (cx, cy) of the shared tile, -1 if not a corner at t.
-// The segment test runs on bit masks first; the score (the best arc's
-// smallest difference, minus one) is computed for corners only, as sliding
-// minima (bright) and maxima (dark) over windows of 9 built from windows of
-// 2, 4 and 8 on the circle listed 1.5 times.  Comparisons are written as
-// conditional selects.
-__device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
+// FAST-9 segment test at (cx, cy) of the shared tile on bit masks: 9
+// contiguous circle pixels brighter than I + t, or darker than I - t
+__device__ __forceinline__ bool fast_corner(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
 {
     const int c = raw[cy][cx];
-    int d[16];
     unsigned bright = 0, dark = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
-        bright |= (d[i] > t ? 1u : 0u) << i;
-        dark |= (d[i] < -t ? 1u : 0u) << i;
+        const int d = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
+        bright |= (d > t ? 1u : 0u) << i;
+        dark |= (d < -t ? 1u : 0u) << i;
     }
-    if (!run9(bright) && !run9(dark)) return -1;
+    return run9(bright) || run9(dark);
+}
+
+// FAST score of a corner: the best arc's smallest difference minus one,
+// over both polarities.  Sliding minima (bright) and maxima (dark) over
+// windows of 9, built from windows of 2, 4 and 8 on the circle listed 1.5
+// times; comparisons written as conditional selects.
+__device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy)
+{
+    const int c = raw[cy][cx];
+    int d[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
     int lo[23], hi[23];
 #pragma unroll
     for (int i = 0; i < 23; ++i) {
@@ -112,8 +119,7 @@ __device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
         best_b = imax(best_b, imin(lo[i], d[(i + 8) & 15]));
         least_hi = imin(least_hi, imax(hi[i], d[(i + 8) & 15]));
     }
-    const int best = imax(best_b, -least_hi);
-    return best > t ? best - 1 : -1;
+    return imax(best_b, -least_hi) - 1;
 }
 
 __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
@@ -121,6 +127,8 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
     __shared__ uint8_t raw[kTileW][kTileW];
     __shared__ short sco[kRing][kRing];
     __shared__ short hs[kOrbTile + 4][kOrbTile];      // horizontal binomial sums of rows -2 .. T+1
+    __shared__ short clist[kRing * kRing];           // ring pixels that are corners
+    __shared__ int ccount;
     const OrbHeader &H = *hdr;
     const OrbImage &I = H.images[blockIdx.y];
     const int tile = blockIdx.x;
@@ -133,6 +141,7 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
     const int x0 = (t % L.tiles_x) * kOrbTile, y0 = (t / L.tiles_x) * kOrbTile;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tile == 0 && tid == 0) I.n_level[H.nlevels] = 0;     // the select blocks add to it
+    if (tid == 0) ccount = 0;
     // the tile and its halo, coordinates clamped to the level (the smoothing
     // replicates the border; FAST only runs where its circle is inside)
     for (int i = tid; i < kTileW * kTileW; i += kDetThreads) {
@@ -141,13 +150,29 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
         raw[i / kTileW][i % kTileW] = L.img[(size_t)yy * L.pitch + xx];
     }
     __syncthreads();
+    // segment test of the tile and its ring; the corners go to a list so
+    // that their scores are computed with every lane busy
     const int E = H.edge;
-    for (int q = tid; q < kRing * kRing; q += kDetThreads) {
-        const int ry = q / kRing, rx = q % kRing;
-        const int px = x0 - 1 + rx, py = y0 - 1 + ry;
-        int s = -1;
-        if (px >= E && px < L.w - E && py >= E && py < L.h - E) s = fast_score(raw, rx + 3, ry + 3, H.fast_th);
-        sco[ry][rx] = (short)s;
+    for (int base = 0; base < kRing * kRing; base += kDetThreads) {
+        const int q = base + tid;
+        bool corner = false;
+        if (q < kRing * kRing) {
+            const int ry = q / kRing, rx = q % kRing;
+            const int px = x0 - 1 + rx, py = y0 - 1 + ry;
+            if (px >= E && px < L.w - E && py >= E && py < L.h - E) corner = fast_corner(raw, rx + 3, ry + 3, H.fast_th);
+            sco[ry][rx] = -1;
+        }
+        const unsigned b = __ballot_sync(kFull, corner);
+        int wb = 0;
+        if (lane == 0 && b) wb = atomicAdd(&ccount, __popc(b));
+        wb = __shfl_sync(kFull, wb, 0);
+        if (corner) clist[wb + __popc(b & ((1u << lane) - 1u))] = (short)q;
+    }
+    __syncthreads();
+    const int ncorner = ccount;
+    for (int i = tid; i < ncorner; i += kDetThreads) {
+        const int q = clist[i];
+        sco[q / kRing][q % kRing] = (short)fast_score(raw, q % kRing + 3, q / kRing + 3);
     }
     for (int q = tid; q < (kOrbTile + 4) * kOrbTile; q += kDetThreads) {
         const int r = q / kOrbTile, x = q % kOrbTile;
@@ -310,13 +335,20 @@ __global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const
     const unsigned key = I.sel[slot];
     const int x = (int)(key & 4095u), y = (int)((key >> 12) & 4095u);
     // intensity centroid over the disk u^2 + v^2 <= 225 (exact integer sums)
+    // all 31 loads of a lane are issued before any is used (unrolled)
     int m10 = 0, m01 = 0;
-    for (int q = lane; q < 31 * 31; q += 32) {
+    int pix[31];
+#pragma unroll
+    for (int r = 0; r < 31; ++r) {
+        const int q = lane + 32 * r;
         const int u = q % 31 - 15, v = q / 31 - 15;
-        if (u * u + v * v > 225) continue;
-        const int I0 = L.img[(size_t)(y + v) * L.pitch + (x + u)];
-        m10 += u * I0;
-        m01 += v * I0;
+        pix[r] = (q < 31 * 31 && u * u + v * v <= 225) ? (int)L.img[(size_t)(y + v) * L.pitch + (x + u)] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < 31; ++r) {
+        const int q = lane + 32 * r;
+        m10 += (q % 31 - 15) * pix[r];
+        m01 += (q / 31 - 15) * pix[r];
     }
     m10 = __reduce_add_sync(kFull, m10);
     m01 = __reduce_add_sync(kFull, m01);
