@@ -11,9 +11,9 @@
 //
 // Three launches per call, each over every image of the call:
 //   detect    one block of 256 threads per 32x32 tile of a level: the tile
-//             and a 4-pixel halo in shared memory, the FAST score of the tile
-//             and its one-pixel ring (the segment test on bit masks first,
-//             the score for corners only), suppression against the eight
+//             and a 4-pixel halo in shared memory, the FAST score of every
+//             pixel of the tile and its one-pixel ring (two pixels per step
+//             in packed 16-bit lanes), suppression against the eight
 //             neighbours, the kept corners appended as keys
 //             (255 - score) << 24 | y << 12 | x (one atomic per warp), and
 //             the smoothed level written from the same tile (separable);
@@ -43,7 +43,6 @@ constexpr int kRows = kOrbTile / (kDetThreads / kOrbTile);   // output rows per 
 constexpr int kDescribeWarps = 8;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-__device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 
 // Offsets of the 16 pixels of the radius-3 circle, clockwise from (0, -3):
@@ -60,66 +59,41 @@ __device__ __forceinline__ int circle_dy(int i) { return circle_dx((i + 12) & 15
 // binomial weights 1 4 6 4 1
 __device__ __forceinline__ int binomial5(int j) { return j == 2 ? 6 : ((j & 1) ? 4 : 1); }
 
-// a 16-bit circular mask holds 9 consecutive ones: on the doubled mask, a
-// bit p survives the AND of shifts 1, 2, 4 and 8 iff bits p .. p+8 are set
-__device__ __forceinline__ bool run9(unsigned m)
+// FAST-9 scores of the horizontally adjacent pixels (cx, cy) and (cx + 1, cy)
+// of the shared tile, -1 where a pixel is not a corner at t.  The score is
+// the best arc's smallest difference minus one, over both polarities.  The
+// pair's 16 circle differences travel as biased 16-bit lanes (v - c + 256 in
+// [1, 511], the first pixel in the low lane): minima (bright) and maxima
+// (dark) over windows of 3, then of 9, by three-input packed min/max, then
+// the best window.  Every pixel gets its score (no branch on the segment
+// test): a corner is a pixel whose best arc exceeds t.
+__device__ __forceinline__ void fast_score2(const uint8_t (*raw)[kTileW], int cx, int cy, int t, int &s0, int &s1)
 {
-    const unsigned d = m | (m << 16);
-    unsigned r = d & (d >> 1);
-    r &= r >> 2;
-    r &= r >> 4;
-    r &= d >> 8;
-    return (r & 0xffffu) != 0;
-}
-
-// FAST-9 segment test at (cx, cy) of the shared tile on bit masks: 9
-// contiguous circle pixels brighter than I + t, or darker than I - t
-__device__ __forceinline__ bool fast_corner(const uint8_t (*raw)[kTileW], int cx, int cy, int t)
-{
-    const int c = raw[cy][cx];
-    unsigned bright = 0, dark = 0;
+    const unsigned c = (unsigned)raw[cy][cx] | ((unsigned)raw[cy][cx + 1] << 16);
+    unsigned b[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const int d = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
-        bright |= (d > t ? 1u : 0u) << i;
-        dark |= (d < -t ? 1u : 0u) << i;
+        const int yy = cy + circle_dy(i), xx = cx + circle_dx(i);
+        b[i] = ((unsigned)raw[yy][xx] | ((unsigned)raw[yy][xx + 1] << 16)) + 0x01000100u - c;
     }
-    return run9(bright) || run9(dark);
-}
-
-// FAST score of a corner: the best arc's smallest difference minus one,
-// over both polarities.  Sliding minima (bright) and maxima (dark) over
-// windows of 9, built from windows of 2, 4 and 8 on the circle listed 1.5
-// times; comparisons written as conditional selects.
-__device__ int fast_score(const uint8_t (*raw)[kTileW], int cx, int cy)
-{
-    const int c = raw[cy][cx];
-    int d[16];
+    unsigned lo3[22], hi3[22];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) d[i] = (int)raw[cy + circle_dy(i)][cx + circle_dx(i)] - c;
-    int lo[23], hi[23];
-#pragma unroll
-    for (int i = 0; i < 23; ++i) {
-        lo[i] = imin(d[i & 15], d[(i + 1) & 15]);
-        hi[i] = imax(d[i & 15], d[(i + 1) & 15]);
+    for (int i = 0; i < 22; ++i) {
+        lo3[i] = __vimin3_u16x2(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
+        hi3[i] = __vimax3_u16x2(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
     }
-#pragma unroll
-    for (int i = 0; i < 21; ++i) {
-        lo[i] = imin(lo[i], lo[i + 2]);
-        hi[i] = imax(hi[i], hi[i + 2]);
-    }
-#pragma unroll
-    for (int i = 0; i < 17; ++i) {
-        lo[i] = imin(lo[i], lo[i + 4]);
-        hi[i] = imax(hi[i], hi[i + 4]);
-    }
-    int best_b = -1000, least_hi = 1000;
+    unsigned best_lo = 0u, least_hi = 0xffffffffu;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        best_b = imax(best_b, imin(lo[i], d[(i + 8) & 15]));
-        least_hi = imin(least_hi, imax(hi[i], d[(i + 8) & 15]));
+        const unsigned m = __vimin3_u16x2(lo3[i], lo3[i + 3], lo3[i + 6]);
+        const unsigned M = __vimax3_u16x2(hi3[i], hi3[i + 3], hi3[i + 6]);
+        best_lo = __vimax3_u16x2(best_lo, m, m);
+        least_hi = __vimin3_u16x2(least_hi, M, M);
     }
-    return imax(best_b, -least_hi) - 1;
+    const int b0 = imax((int)(best_lo & 0xffffu) - 256, 256 - (int)(least_hi & 0xffffu));
+    const int b1 = imax((int)(best_lo >> 16) - 256, 256 - (int)(least_hi >> 16));
+    s0 = b0 > t ? b0 - 1 : -1;
+    s1 = b1 > t ? b1 - 1 : -1;
 }
 
 __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
@@ -127,8 +101,6 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
     __shared__ uint8_t raw[kTileW][kTileW];
     __shared__ short sco[kRing][kRing];
     __shared__ short hs[kOrbTile + 4][kOrbTile];      // horizontal binomial sums of rows -2 .. T+1
-    __shared__ short clist[kRing * kRing];           // ring pixels that are corners
-    __shared__ int ccount;
     const OrbHeader &H = *hdr;
     const OrbImage &I = H.images[blockIdx.y];
     const int tile = blockIdx.x;
@@ -141,7 +113,6 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
     const int x0 = (t % L.tiles_x) * kOrbTile, y0 = (t / L.tiles_x) * kOrbTile;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tile == 0 && tid == 0) I.n_level[H.nlevels] = 0;     // the select blocks add to it
-    if (tid == 0) ccount = 0;
     // the tile and its halo, coordinates clamped to the level (the smoothing
     // replicates the border; FAST only runs where its circle is inside)
     for (int i = tid; i < kTileW * kTileW; i += kDetThreads) {
@@ -150,29 +121,17 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
         raw[i / kTileW][i % kTileW] = L.img[(size_t)yy * L.pitch + xx];
     }
     __syncthreads();
-    // segment test of the tile and its ring; the corners go to a list so
-    // that their scores are computed with every lane busy
+    // scores of the tile and its one-pixel ring, two adjacent pixels per step
     const int E = H.edge;
-    for (int base = 0; base < kRing * kRing; base += kDetThreads) {
-        const int q = base + tid;
-        bool corner = false;
-        if (q < kRing * kRing) {
-            const int ry = q / kRing, rx = q % kRing;
-            const int px = x0 - 1 + rx, py = y0 - 1 + ry;
-            if (px >= E && px < L.w - E && py >= E && py < L.h - E) corner = fast_corner(raw, rx + 3, ry + 3, H.fast_th);
-            sco[ry][rx] = -1;
-        }
-        const unsigned b = __ballot_sync(kFull, corner);
-        int wb = 0;
-        if (lane == 0 && b) wb = atomicAdd(&ccount, __popc(b));
-        wb = __shfl_sync(kFull, wb, 0);
-        if (corner) clist[wb + __popc(b & ((1u << lane) - 1u))] = (short)q;
-    }
-    __syncthreads();
-    const int ncorner = ccount;
-    for (int i = tid; i < ncorner; i += kDetThreads) {
-        const int q = clist[i];
-        sco[q / kRing][q % kRing] = (short)fast_score(raw, q % kRing + 3, q / kRing + 3);
+    constexpr int kPairs = kRing / 2;
+    for (int q = tid; q < kRing * kPairs; q += kDetThreads) {
+        const int ry = q / kPairs, rx = 2 * (q % kPairs);
+        int s0, s1;
+        fast_score2(raw, rx + 3, ry + 3, H.fast_th, s0, s1);
+        const int px = x0 - 1 + rx, py = y0 - 1 + ry;
+        const bool rows_in = py >= E && py < L.h - E;
+        sco[ry][rx] = (short)((rows_in && px >= E && px < L.w - E) ? s0 : -1);
+        sco[ry][rx + 1] = (short)((rows_in && px + 1 >= E && px + 1 < L.w - E) ? s1 : -1);
     }
     for (int q = tid; q < (kOrbTile + 4) * kOrbTile; q += kDetThreads) {
         const int r = q / kOrbTile, x = q % kOrbTile;
