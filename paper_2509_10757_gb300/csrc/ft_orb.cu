@@ -13,7 +13,7 @@
 //   detect    one block of 256 threads per 32x32 tile of a level: the tile
 //             and a 4-pixel halo in shared memory, the FAST score of every
 //             pixel of the tile and its one-pixel ring (two pixels per step
-//             in packed half-precision lanes), suppression against the eight
+//             in packed 16-bit lanes), suppression against the eight
 //             neighbours, the kept corners appended as keys
 //             (255 - score) << 24 | y << 12 | x (one atomic per warp), and
 //             the smoothed level written from the same tile (separable);
@@ -26,7 +26,6 @@
 // Integer work is exact; the orientation and the rotated test positions use
 // IEEE-rounded FP32 (and one double square root) in the order the reading
 // gives, so results equal the oracle's bit for bit.
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -63,49 +62,36 @@ __device__ __forceinline__ int binomial5(int j) { return j == 2 ? 6 : ((j & 1) ?
 // FAST-9 scores of the horizontally adjacent pixels (cx, cy) and (cx + 1, cy)
 // of the shared tile, -1 where a pixel is not a corner at t.  The score is
 // the best arc's smallest difference minus one, over both polarities.  The
-// pair's 16 circle differences travel as biased lanes k = v - c + 256 in
-// [1, 511], the first pixel in the low lane, turned into half-precision
-// values 1024 + k by setting the exponent bits (exact: every integer up to
-// 2048 is a half): minima (bright) and maxima (dark) over windows of 3, then
-// of 9, by packed half min/max, then the best window; the results decode as
-// bits & 0x3ff.  Every pixel gets its score: a corner is a pixel whose best
-// arc exceeds t.
-union HalfPair {
-    unsigned u;
-    __half2 h;
-};
-__device__ __forceinline__ __half2 hmin3(__half2 a, __half2 b, __half2 c) { return __hmin2(__hmin2(a, b), c); }
-__device__ __forceinline__ __half2 hmax3(__half2 a, __half2 b, __half2 c) { return __hmax2(__hmax2(a, b), c); }
-
+// pair's 16 circle differences travel as biased 16-bit lanes (v - c + 256 in
+// [1, 511], the first pixel in the low lane): minima (bright) and maxima
+// (dark) over windows of 3, then of 9, by three-input packed min/max, then
+// the best window.  Every pixel gets its score (no branch on the segment
+// test): a corner is a pixel whose best arc exceeds t.
 __device__ __forceinline__ void fast_score2(const uint8_t (*raw)[kTileW], int cx, int cy, int t, int &s0, int &s1)
 {
     const unsigned c = (unsigned)raw[cy][cx] | ((unsigned)raw[cy][cx + 1] << 16);
-    __half2 b[16];
+    unsigned b[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int yy = cy + circle_dy(i), xx = cx + circle_dx(i);
-        HalfPair q;
-        q.u = (((unsigned)raw[yy][xx] | ((unsigned)raw[yy][xx + 1] << 16)) + 0x01000100u - c) | 0x64006400u;
-        b[i] = q.h;
+        b[i] = ((unsigned)raw[yy][xx] | ((unsigned)raw[yy][xx + 1] << 16)) + 0x01000100u - c;
     }
-    __half2 lo3[22], hi3[22];
+    unsigned lo3[22], hi3[22];
 #pragma unroll
     for (int i = 0; i < 22; ++i) {
-        lo3[i] = hmin3(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
-        hi3[i] = hmax3(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
+        lo3[i] = __vimin3_u16x2(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
+        hi3[i] = __vimax3_u16x2(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
     }
-    __half2 best_lo = hmin3(lo3[0], lo3[3], lo3[6]);
-    __half2 least_hi = hmax3(hi3[0], hi3[3], hi3[6]);
+    unsigned best_lo = 0u, least_hi = 0xffffffffu;
 #pragma unroll
-    for (int i = 1; i < 16; ++i) {
-        best_lo = __hmax2(best_lo, hmin3(lo3[i], lo3[i + 3], lo3[i + 6]));
-        least_hi = __hmin2(least_hi, hmax3(hi3[i], hi3[i + 3], hi3[i + 6]));
+    for (int i = 0; i < 16; ++i) {
+        const unsigned m = __vimin3_u16x2(lo3[i], lo3[i + 3], lo3[i + 6]);
+        const unsigned M = __vimax3_u16x2(hi3[i], hi3[i + 3], hi3[i + 6]);
+        best_lo = __vimax3_u16x2(best_lo, m, m);
+        least_hi = __vimin3_u16x2(least_hi, M, M);
     }
-    HalfPair lo, hi;
-    lo.h = best_lo;
-    hi.h = least_hi;
-    const int b0 = imax((int)(lo.u & 0x3ffu) - 256, 256 - (int)(hi.u & 0x3ffu));
-    const int b1 = imax((int)((lo.u >> 16) & 0x3ffu) - 256, 256 - (int)((hi.u >> 16) & 0x3ffu));
+    const int b0 = imax((int)(best_lo & 0xffffu) - 256, 256 - (int)(least_hi & 0xffffu));
+    const int b1 = imax((int)(best_lo >> 16) - 256, 256 - (int)(least_hi >> 16));
     s0 = b0 > t ? b0 - 1 : -1;
     s1 = b1 > t ? b1 - 1 : -1;
 }
