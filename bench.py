@@ -621,7 +621,8 @@ def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_byte
            "hbm": {"achieved_gbs": alg / mean_s / 1e9, "frac": alg / mean_s / 1e9 / peaks["hbm_gbs"],
                    "algorithmic_bytes": alg},
            "tuning": {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
-                      "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm}}
+                      "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm,
+                      "search_stage": "L2" if best.search_stage else "on chip if it fits"}}
     ctx.close()
     return out
 
@@ -1071,7 +1072,7 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     def tuning_of(t):
         return {"strip_rows": t.strip_rows, "search_tile": t.search_tile, "fisheye_tile": t.fisheye_tile,
-                "ctas_per_sm": t.ctas_per_sm}
+                "ctas_per_sm": t.ctas_per_sm, "search_stage": "L2" if t.search_stage else "on chip if it fits"}
     ctx_tuning = tuning_of(best_stream)
     ctx.close()
     if rank != 0:

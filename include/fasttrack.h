@@ -321,6 +321,9 @@ typedef struct {
     int fisheye_tile;       /* left keypoints per fisheye work item (64, or 128 for any larger value) */
     int resolve_tile;       /* entries per conflict-resolution item */
     int ctas_per_sm;        /* persistent CTAs per SM (0: occupancy limit) */
+    int search_stage;       /* search candidates: 0 = a camera's keypoint records and descriptors
+                               staged in shared memory when they fit (up to 1536 keypoints), else
+                               read from L2; 1 = always read from L2 */
 } ft_tuning;
 
 /* Fill p with the default readings. */
@@ -501,7 +504,8 @@ ft_status ft_track_batch(ft_ctx *ctx, void *stream, const ft_params *params, con
 /* Time candidate launch shapes on this batch (iters runs each) and keep the
  * fastest for the batch's bucket; *best receives it (may be NULL).  The
  * candidates: strip rows 16/32/64, search tile 256/512/1024, fisheye tile
- * 64/128, every count of CTAs per SM up to the resident maximum. */
+ * 64/128, every count of CTAs per SM up to the resident maximum, and both
+ * search staging modes. */
 ft_status ft_autotune(ft_ctx *ctx, void *stream, const ft_params *params, const ft_batch *batch,
                       int iters, ft_tuning *best);
 

@@ -178,6 +178,7 @@ ft_tuning default_tuning()
     t.fisheye_tile = 128;
     t.resolve_tile = 2048;
     t.ctas_per_sm = 0;
+    t.search_stage = 0;
     return t;
 }
 
@@ -583,6 +584,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
             for (int i = 0; i < 3; ++i) F.last_t[i] = j.last_pose.t[i];
             F.base = j.camera == FT_CAMERA_PINHOLE ? j.pin.b : j.rig.b;
             F.search_tile = std::max(kThreads, tune.search_tile / kThreads * kThreads);
+            F.search_stage = tune.search_stage ? 1 : 0;
             F.resolve_tile = std::max(kThreads, tune.resolve_tile / kThreads * kThreads);
             for (int c = 0; c < F.ncam; ++c) {
                 CamDev &C = F.cam[c];
@@ -1384,14 +1386,16 @@ static std::vector<ft_tuning> tuning_candidates(int occ)
     for (int a : strips)
         for (int b : tiles)
             for (int c : fish)
-                for (int o : occs) {
-                    ft_tuning t = default_tuning();
-                    t.strip_rows = a;
-                    t.search_tile = b;
-                    t.fisheye_tile = c;
-                    t.ctas_per_sm = o;
-                    cand.push_back(t);
-                }
+                for (int o : occs)
+                    for (int st = 0; st < 2; ++st) {
+                        ft_tuning t = default_tuning();
+                        t.strip_rows = a;
+                        t.search_tile = b;
+                        t.fisheye_tile = c;
+                        t.ctas_per_sm = o;
+                        t.search_stage = st;
+                        cand.push_back(t);
+                    }
     return cand;
 }
 
@@ -1569,12 +1573,14 @@ ft_status ft_save_tuning(ft_ctx *ctx, const char *path)
     if (!ctx || !path) return fail(FT_EINVAL, "ft_save_tuning: NULL argument");
     FILE *f = std::fopen(path, "w");
     if (!f) return fail(FT_EINVAL, "cannot write %s", path);
-    std::fprintf(f, "# frames_p2 has_pinhole has_fisheye nl_p2 m_p2 strip_rows search_tile fisheye_tile resolve_tile ctas_per_sm\n");
+    std::fprintf(f, "# frames_p2 has_pinhole has_fisheye nl_p2 m_p2 strip_rows search_tile fisheye_tile resolve_tile "
+                    "ctas_per_sm search_stage\n");
     for (auto &kv : ctx->tuning) {
         const Bucket &b = kv.first;
         const ft_tuning &t = kv.second;
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", b.frames_p2, b.has_pinhole, b.has_fisheye, b.nl_p2,
-                     b.m_p2, t.strip_rows, t.search_tile, t.fisheye_tile, t.resolve_tile, t.ctas_per_sm);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", b.frames_p2, b.has_pinhole, b.has_fisheye, b.nl_p2,
+                     b.m_p2, t.strip_rows, t.search_tile, t.fisheye_tile, t.resolve_tile, t.ctas_per_sm,
+                     t.search_stage);
     }
     std::fclose(f);
     return FT_OK;
@@ -1590,10 +1596,11 @@ ft_status ft_load_tuning(ft_ctx *ctx, const char *path)
         if (line[0] == '#') continue;
         Bucket b{};
         ft_tuning t{};
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &b.frames_p2, &b.has_pinhole, &b.has_fisheye,
-                        &b.nl_p2, &b.m_p2, &t.strip_rows, &t.search_tile, &t.fisheye_tile, &t.resolve_tile,
-                        &t.ctas_per_sm) == 10)
-            ctx->tuning[b] = t;
+        // lines without the last column (search_stage) come from older tables: 0
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d", &b.frames_p2, &b.has_pinhole,
+                                    &b.has_fisheye, &b.nl_p2, &b.m_p2, &t.strip_rows, &t.search_tile,
+                                    &t.fisheye_tile, &t.resolve_tile, &t.ctas_per_sm, &t.search_stage);
+        if (got == 10 || got == 11) ctx->tuning[b] = t;
     }
     std::fclose(f);
     return FT_OK;

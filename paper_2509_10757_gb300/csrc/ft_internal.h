@@ -137,6 +137,7 @@ struct FrameDev {
     // work decomposition
     int strip_rows, n_stereo_items, fisheye_tile;
     int search_tile, resolve_tile;
+    int search_stage;              // 0: stage the camera's records on chip when they fit; 1: read from L2
     int rowsort;                   // row-sort index items (kRowSortItems: the first half the left
                                    // keypoints, the second half the right ones), 0 without stereo
     int fold_resolve;              // 1: the last search item of a camera writes the final tables

@@ -1474,7 +1474,7 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         // by asynchronous copies when they fit (the tail past the placed
         // records is copied but never read)
         const int nk = C.nk;
-        const bool staged = nk <= kSearchStage;
+        const bool staged = F.search_stage == 0 && nk <= kSearchStage;
         // the 16-bit cell starts too when they fit behind the descriptors
         const bool cells = staged && 48 * nk + kCell16Bytes <= (int)sizeof(Q.buf);
         const uint16_t *scell = cells ? reinterpret_cast<const uint16_t *>(Q.buf + 3 * nk) : nullptr;

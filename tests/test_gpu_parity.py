@@ -370,13 +370,15 @@ def test_dense_rows_fall_back_to_scan(ctx, lib):
 
 
 # ---------------------------------------------------------------- launch shapes, graphs, host staging
-@pytest.mark.parametrize("tune", [(1, 256, 512, 256), (7, 1024, 256, 512), (200, 512, 512, 4096)])
+@pytest.mark.parametrize("tune", [(1, 256, 512, 256, 1), (7, 1024, 256, 512, 0), (200, 512, 512, 4096, 1),
+                                  (32, 512, 128, 2048, 1)])
 def test_tuning_variants_same_results(ctx, lib, tune):
+    # strip heights, tiles and both search staging modes (records on chip or in L2)
     from paper_2509_10757_gb300.batch import PackedBatch
     frames = [scenes.single_pinhole(11), scenes.fisheye_frame(11)]
     pb = PackedBatch(frames)
     t = lib.ft_tuning(strip_rows=tune[0], search_tile=tune[1], fisheye_tile=tune[2],
-                      resolve_tile=tune[3], ctas_per_sm=1)
+                      resolve_tile=tune[3], ctas_per_sm=1, search_stage=tune[4])
     b = pb.batch()
     lib.check(lib.ft_set_tuning(ctx.ptr, C.byref(b), C.byref(t)), "ft_set_tuning")
     try:
@@ -419,8 +421,8 @@ def test_autotune_and_table_roundtrip(ctx, lib, tmp_path):
     lib.check(lib.ft_load_tuning(ctx.ptr, path), "load")
     got = lib.ft_tuning()
     lib.check(lib.ft_get_tuning(ctx.ptr, C.byref(b), C.byref(got)), "get")
-    assert (got.strip_rows, got.search_tile, got.fisheye_tile) == (best.strip_rows, best.search_tile,
-                                                                   best.fisheye_tile)
+    assert (got.strip_rows, got.search_tile, got.fisheye_tile, got.search_stage) == \
+        (best.strip_rows, best.search_tile, best.fisheye_tile, best.search_stage)
     out = run_fused(ctx, frames)
     for f in range(len(frames)):
         check_frame(out, f, what="tuned")
