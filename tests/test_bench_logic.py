@@ -37,3 +37,30 @@ def test_clock_summary_reports_median_reasons_and_windows():
     inside = [r for r in c.lines if 1.5 <= r[0] <= 3.5]
     w = c._summary(inside)
     assert w["samples"] == 2 and w["sm_mhz"] == (1900 + 2070) / 2
+
+
+def test_patch_sector_bytes_counts_distinct_sectors():
+    """Two refined matches on level 0 whose left patches share their sectors
+    and whose right strips are far apart: the byte count is 2 x 352, the
+    sector count 11 rows x (2 shared left + 3 right) sectors."""
+    import numpy as np
+    from types import SimpleNamespace as NS
+
+    class Pyr:
+        def __init__(self, base, pitch):
+            self.data = [base] + [0] * 15
+            self.pitch = [pitch] + [0] * 15
+
+    fr = NS(camera="pinhole", pyr_left=[None], pyr_right=[None],
+            left=NS(x=np.array([100.0, 101.0], np.float32), y=np.array([50.0, 50.0], np.float32),
+                    oct=np.array([0, 0], np.int8)),
+            right=NS(x=np.array([60.0, 300.0], np.float32)))
+    out = {"sad_shift": np.array([0, 1], np.int32), "best_r": np.array([0, 1], np.int32)}
+    pb = NS(frames=[fr], outputs=lambda f: out,
+            pyramid=lambda f, side: Pyr(1 << 20 if side == "L" else 1 << 24, 1024))
+    b, s = bench.patch_sector_bytes(pb)
+    assert b == 2 * bench.PATCH_BYTES
+    # left rows: columns 95..105 and 96..106 lie in sector 2 (bytes 64..95) and
+    # sector 3 (96..127): two sectors per row, shared by both patches
+    # right rows: columns 50..70 (sectors 1, 2) and 290..310 (sector 9): 3 per row
+    assert s == 32 * 11 * (2 + 3)
