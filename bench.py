@@ -431,26 +431,48 @@ def run_trace(args, local_rank):
 
 
 def run_profile(args, local_rank):
-    """Small fixed run for ncu: warm-up launches, then `steps` launches of the
-    fused kernel on the batched workload (default tuning, no graphs)."""
+    """Small fixed run for ncu: warm-up, then `steps` calls on the 64-frame
+    batched workload (default tuning, no graphs).  --workload picks what runs:
+    batched (the fused kernel), pose (fused + pose kernels: pose optimization
+    after the search), extraction (pyramids of the 128 images built once,
+    then ft_extract_orb on them: the detect, select and describe kernels)."""
+    import ctypes as C
+
     import torch
 
+    from paper_2509_10757_gb300 import _lib as L
     from paper_2509_10757_gb300 import build as B
     from paper_2509_10757_gb300 import scenes
-    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch
+    from paper_2509_10757_gb300.batch import Context, OrbOutputs, PackedBatch, run_batch, stream_handle
 
     torch.cuda.set_device(local_rank)
     B.build()
-    frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
-    pb = PackedBatch(frames)
-    pb.upload()
-    ctx = Context(device=local_rank, arena_bytes=64 << 20, max_frames=FRAMES)
-    for _ in range(args.warmup + args.steps):
-        run_batch(ctx, pb)
+    n = args.warmup + args.steps
+    if args.workload == "extraction":
+        frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES, nl_range=(1200, 1200))
+        pb = PackedBatch(frames, device_pyramids=True)
+        pb.upload()
+        ctx = Context(device=local_rank, arena_bytes=1 << 30, max_frames=FRAMES)
+        pyrs = []
+        for f in range(FRAMES):
+            pyrs += [pb.pyramid(f, "L"), pb.pyramid(f, "R")]
+        arr = (L.ft_pyramid * len(pyrs))(*pyrs)
+        L.check(ctx.lib.ft_build_pyramids(ctx.ptr, stream_handle(), None, len(pyrs), arr), "ft_build_pyramids")
+        oo = OrbOutputs(len(pyrs), scenes.orb_level_caps(1200), scenes.orb_pattern())
+        for _ in range(n):
+            L.check(ctx.lib.ft_extract_orb(ctx.ptr, stream_handle(), None, len(pyrs), arr, C.byref(oo.params),
+                                           oo.outs), "ft_extract_orb")
+    else:
+        frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
+        pb = PackedBatch(frames, pose=args.workload == "pose")
+        pb.upload()
+        ctx = Context(device=local_rank, arena_bytes=64 << 20, max_frames=FRAMES)
+        for _ in range(n):
+            run_batch(ctx, pb)
     torch.cuda.synchronize()
     assert ctx.sync_status() == 0
     ctx.close()
-    print(json.dumps({"profile_run": "ok", "launches": args.warmup + args.steps}), flush=True)
+    print(json.dumps({"profile_run": "ok", "workload": args.workload, "calls": n}), flush=True)
 
 
 def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batch: int, seed: int = 0,
@@ -1206,8 +1228,9 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served", "configs"])
     ap.add_argument("--trace-out", default=None)
-    ap.add_argument("--workload", default="batched", choices=["batched", "stress", "fisheye"],
-                    help="workload of --mode trace")
+    ap.add_argument("--workload", default="batched", choices=["batched", "stress", "fisheye", "pose", "extraction"],
+                    help="workload of --mode trace (batched, stress, fisheye) or --mode profile (batched, pose, "
+                         "extraction)")
     args = ap.parse_args()
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])
