@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfasttrack.so")
-SOURCES = ["ft_kernels.cu", "ft_orb.cu", "ft_api.cu", "ft_noalloc.cu", "ft_serve.cu"]
+SOURCES = ["ft_kernels.cu", "ft_pyramid.cu", "ft_orb.cu", "ft_api.cu", "ft_noalloc.cu", "ft_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

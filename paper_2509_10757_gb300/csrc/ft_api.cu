@@ -156,10 +156,9 @@ struct ft_ctx {
     bool have_last = false;
     bool use_graphs = false;
     cudaStream_t capture_stream = nullptr;
-    std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;   // (bucket frames, CTAs/SM,
-                                                                                  //  slot, pyramid frames,
-                                                                                  //  pyramid blocks per image,
-                                                                                  //  pose frames)
+    // graphs by (bucket frames, CTAs/SM, slot, pyramid frames, pyramid
+    // blocks per image, pyramid levels, pose frames)
+    std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
     std::map<Bucket, ft_tuning> tuning;
     uint64_t launches = 0;
     unsigned debug_flags = 0;
@@ -267,6 +266,10 @@ ft_status check_job(const Job &j, const ft_params &p)
                 if (py->width[l] != w[l] || py->height[l] != h[l])
                     return fail(FT_EINVAL, "pyramid level %d is %dx%d, a built level is %dx%d", l, py->width[l],
                                 py->height[l], w[l], h[l]);
+            for (int l = 0; l < p.nlevels; ++l)
+                if ((long long)py->pitch[l] * py->height[l] > kPyrMaxLevelBytes)
+                    return fail(FT_EINVAL, "pyramid level %d (%d rows of pitch %d) exceeds 2^31 bytes", l,
+                                py->height[l], py->pitch[l]);
         }
     }
     if (j.camera == FT_CAMERA_PINHOLE) {
@@ -695,9 +698,11 @@ ft_status finish_call(ft_ctx *ctx, cudaStream_t s)
 }
 
 ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int slot, int grid,
-                    size_t copy_bytes, int pyr_frames, int pyr_blocks, int pose_frames, cudaGraphExec_t *out)
+                    size_t copy_bytes, int pyr_frames, int pyr_blocks, int pyr_levels, int pose_frames,
+                    cudaGraphExec_t *out)
 {
-    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames, pyr_blocks, pose_frames);
+    // the pyramid launch's shared memory depends on the level count
+    const auto key = std::make_tuple(frames_p2, cps, slot, pyr_frames, pyr_blocks, pyr_levels, pose_frames);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
@@ -708,7 +713,8 @@ ft_status get_graph(ft_ctx *ctx, char *table_dev, int frames_p2, int cps, int sl
     cudaGraph_t g = nullptr;
     FT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e1 = cudaMemcpyAsync(table_dev, ctx->staging[slot], copy_bytes, cudaMemcpyHostToDevice, cs);
-    const cudaError_t e0 = launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_blocks, cs);
+    const cudaError_t e0 =
+        launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_levels, pyr_blocks, cs);
     cudaError_t e2 = e0 != cudaSuccess ? e0 : launch_fused(reinterpret_cast<const BatchHeader *>(table_dev),
                                                            grid, cs);
     if (e2 == cudaSuccess) e2 = launch_pose(reinterpret_cast<const BatchHeader *>(table_dev), pose_frames, cs);
@@ -760,8 +766,8 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
     const int cps = tune.ctas_per_sm > 0 ? std::min(tune.ctas_per_sm, ctx->occ) : ctx->occ;
     const int grid_max = ctx->sm_count * cps;
     // frames that build their pyramids first run the pyramid kernel, one
-    // block per virtual block of the largest image (the blocks of a smaller
-    // image exit; a graph replayed for larger images strides)
+    // block per level-0 tile of the largest image (the blocks past a smaller
+    // image's tiles exit)
     int pyr_frames = 0, pyr_blocks = 1;
     for (size_t f = 0; f < jobs.size(); ++f)
         if (jobs[f].build_pyr) pyr_frames = (int)f + 1;
@@ -771,9 +777,7 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
             for (int side = 0; side < 2; ++side) {
                 if (!(jobs[f].build_pyr & (1 << side))) continue;
                 const ft_pyramid &py = side ? jobs[f].pyr_r : jobs[f].pyr_l;
-                int n = 0;
-                for (int l = 1; l < params.nlevels; ++l) n += pyr_vblocks(py.width[l], py.height[l]);
-                most = std::max(most, n);
+                most = std::max(most, pyr_tiles(py.width[0], py.height[0]));
             }
         pyr_blocks = most;
     }
@@ -788,13 +792,15 @@ ft_status submit(ft_ctx *ctx, cudaStream_t stream, const ft_params &params, cons
             const size_t copy = std::max(bytes, table_layout(fp2).total);
             cudaGraphExec_t exec = nullptr;
             if ((s = get_graph(ctx, table_dev, fp2, cps, slot, grid_max, std::min(copy, ctx->table_cap),
-                               pyr_frames > 0 ? fp2 : 0, pyr_blocks, pose_frames > 0 ? fp2 : 0, &exec)) != FT_OK)
+                               pyr_frames > 0 ? fp2 : 0, pyr_blocks, params.nlevels, pose_frames > 0 ? fp2 : 0,
+                               &exec)) != FT_OK)
                 return s;
             FT_CUDA(cudaGraphLaunch(exec, stream));
         } else {
             FT_CUDA(cudaMemcpyAsync(table_dev, ctx->staging[slot], bytes, cudaMemcpyHostToDevice, stream));
             if (pyr_frames > 0)
-                FT_CUDA(launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, pyr_blocks,
+                FT_CUDA(launch_pyramids(reinterpret_cast<const BatchHeader *>(table_dev), pyr_frames, params.nlevels,
+                                        pyr_blocks,
                                         stream));
             if (items > 0)
                 FT_CUDA(launch_fused(reinterpret_cast<const BatchHeader *>(table_dev), std::min(items, grid_max),
@@ -889,6 +895,7 @@ ft_status ft_create(ft_ctx **out, const ft_ctx_desc *desc)
     cudaDeviceProp prop{};
     cudaError_t e = cudaGetDeviceProperties(&prop, d.device);
     if (e == cudaSuccess) e = fused_occupancy(&c->occ);
+    if (e == cudaSuccess) e = pyramid_setup();
     c->sm_count = prop.multiProcessorCount;
     if (c->occ < 1) c->occ = 1;
     // the table region holds a batch table of max_frames frames or an

@@ -32,16 +32,19 @@ constexpr int kFishTileMax = 128;                   // left keypoints per fishey
 constexpr int kFoldResolveMax = 8192;               // frames up to this size resolve in their last search item
 constexpr int kCounters = 8;                        // per-frame counters (u32)
 constexpr int kRowSortItems = 4;                    // row-sort work items per pinhole frame (2 per side)
-constexpr int kPyrRows = 16;                        // output rows one pyramid thread walks
 constexpr int kPyrThreads = 256;                    // threads per pyramid block
+constexpr int kPyrTileRows = 16;                    // source rows a pyramid block owns
+constexpr int kPyrTileCols = 752;                   // source columns a pyramid block owns (a multiple of 16)
+constexpr int kPyrStride = kPyrTileCols + 16;       // floats per staged row (owned columns + 16)
+constexpr int kPyrRowsPerLevel = 2 * kPyrTileRows;  // output rows of one level in a tile, at most
 
-// Pyramid work of one level: threads are (band of kPyrRows rows) x (quad of
-// four columns), grouped kPyrThreads to a virtual block.
-__host__ __device__ inline int pyr_vblocks(int w, int h)
+// Tiles of a pyramid's level 0 (one pyramid block each).
+__host__ __device__ inline int pyr_tiles(int W, int H)
 {
-    const long long t = (long long)((w + 3) >> 2) * ((h + kPyrRows - 1) / kPyrRows);
-    return (int)((t + kPyrThreads - 1) / kPyrThreads);
+    return ((H + kPyrTileRows - 1) / kPyrTileRows) * ((W + kPyrTileCols - 1) / kPyrTileCols);
 }
+// Byte offsets within one pyramid image are 32-bit in the pyramid kernel.
+constexpr long long kPyrMaxLevelBytes = 1ll << 31;
 
 enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
 
@@ -216,7 +219,9 @@ cudaError_t launch_fused(const BatchHeader *dev_hdr, int grid, cudaStream_t stre
 cudaError_t launch_pose(const BatchHeader *dev_hdr, int nframes, cudaStream_t stream);
 // levels 1.. of the pyramids of the frames that build them (before the fused
 // launch); blocks_per_image blocks stride over each image's virtual blocks
-cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, int blocks_per_image, cudaStream_t stream);
+cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, int nlevels, int tiles_per_image,
+                            cudaStream_t stream);
+cudaError_t pyramid_setup();   // the pyramid kernel's shared-memory attribute (once per context)
 int fused_smem_bytes();
 // device set-up of the fused and pose kernels (shared-memory attributes),
 // then the fused kernel's resident CTAs per SM

@@ -1991,243 +1991,6 @@ __global__ void __launch_bounds__(kPoseThreads, 1) ft_pose_kernel(const BatchHea
 
 }  // namespace
 
-// ---------------------------------------------------------------- f3: image pyramid
-// Levels 1.. of a pyramid resampled from level 0: bilinear at half-pixel
-// centres, FP32 in the order top = I00 (1-fx) + I01 fx, bottom likewise,
-// value = top (1-fy) + bottom fy, rounded half to even.
-//
-// Block (x, y): y = frame * 2 + side; the x blocks stride over the image's
-// virtual blocks.  A level's threads are (band of kPyrRows output rows) x
-// (quad of four output columns), kPyrThreads per virtual block and one level
-// per virtual block.  A thread walks its band top to bottom keeping the
-// horizontal interpolations of the two source rows it used last, so a source
-// row shared by neighbouring output rows is interpolated once.  Source bytes
-// arrive as aligned 32-bit words, are funnel-shifted into an 8-byte window
-// and picked out with byte permutes.  A byte b becomes the float b exactly by
-// placing it in the mantissa of 2^23 and subtracting 2^23.  The value v lies
-// in [0, 255.5) (a convex combination of bytes, rounded), so adding 1.5 * 2^23
-// rounds it to the nearest integer, ties to even, and the low mantissa byte
-// is the clamped result.  Every step is exact or a single IEEE rounding of
-// the formula's own operation, so levels equal the per-pixel formula bit for
-// bit.  The byte conversion and the final rounding run on pixel pairs with
-// the packed f32x2 add; the formula's products and sums stay scalar with
-// explicit rounding, since a packed multiply feeding a packed add may be
-// fused into one FMA by the compiler (measured: one pixel in ~760k, an exact
-// tie, came out one lower).
-typedef unsigned long long f32x2;        // lane 0 in the low 32 bits
-
-__device__ __forceinline__ f32x2 f2_pack(unsigned lo, unsigned hi)
-{
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_splat(float a) { return f2_pack(__float_as_uint(a), __float_as_uint(a)); }
-__device__ __forceinline__ void f2_unpack(f32x2 a, unsigned &lo, unsigned &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(a));
-}
-__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
-{
-    f32x2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
-constexpr unsigned kExp23 = 0x4B000000u;     // bits of 2^23
-constexpr float kTwo23 = 8388608.0f;         // 2^23
-constexpr float kRound23 = 12582912.0f;      // 1.5 * 2^23
-
-// Columns of one thread's quad.  Pair p (pixels 2p, 2p+1) reads its four
-// source bytes (c0 and c1 of both pixels) from the register pair (L, R) of
-// its window(s); sel[p] places them as bytes 0..3 = c0a, c0b, c1a, c1b.
-// NW windows per quad: 1 (one 8-byte window from c0 of pixel 0), 2 (one per
-// pair) or 4 (one per pixel, 4 bytes each; pair p = pixels' windows 2p, 2p+1).
-template <int NW>
-struct PyrCols {
-    const uint8_t *base[NW]; // the window's first aligned word in source row 0
-    unsigned sh[NW];         // funnel shift (bits) to the window's first byte
-    bool ok1[NW], ok2[NW];   // second / third word inside the row
-    unsigned sel[2];
-    float gx[4], fx[4];
-};
-
-template <int NW>
-__device__ __forceinline__ void pyr_hrow(size_t row_off, const PyrCols<NW> &C, float (&hv)[4])
-{
-    unsigned lo[NW], hi[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-        const unsigned *w = reinterpret_cast<const unsigned *>(C.base[k] + row_off);
-        const unsigned w0 = __ldg(w);
-        const unsigned w1 = C.ok1[k] ? __ldg(w + 1) : 0u;
-        lo[k] = __funnelshift_r(w0, w1, C.sh[k]);
-        if (NW < 4) {
-            const unsigned w2 = C.ok2[k] ? __ldg(w + 2) : 0u;
-            hi[k] = __funnelshift_r(w1, w2, C.sh[k]);
-        }
-    }
-    const f32x2 neg = f2_splat(-kTwo23);
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        unsigned x;
-        if (NW == 1) x = __byte_perm(lo[0], hi[0], C.sel[p]);
-        else if (NW == 2) x = __byte_perm(lo[p], hi[p], C.sel[p]);
-        else x = __byte_perm(lo[2 * p], lo[2 * p + 1], C.sel[p]);
-        unsigned i0a, i0b, i1a, i1b;     // c0 and c1 bytes of pixels 2p, 2p+1 as floats
-        f2_unpack(f2_add(f2_pack(__byte_perm(x, kExp23, 0x7440), __byte_perm(x, kExp23, 0x7441)), neg), i0a, i0b);
-        f2_unpack(f2_add(f2_pack(__byte_perm(x, kExp23, 0x7442), __byte_perm(x, kExp23, 0x7443)), neg), i1a, i1b);
-        const int a = 2 * p, b = a + 1;
-        hv[a] = fadd(fmul(__uint_as_float(i0a), C.gx[a]), fmul(__uint_as_float(i1a), C.fx[a]));
-        hv[b] = fadd(fmul(__uint_as_float(i0b), C.gx[b]), fmul(__uint_as_float(i1b), C.fx[b]));
-    }
-}
-
-// Source rows and weights of output row y (the same operations as the oracle).
-__device__ __forceinline__ void pyr_row(int y, float sy, int H, int &y0, int &y1, float &fy, float &gy)
-{
-    float ys = fsub(fmul(fadd((float)y, 0.5f), sy), 0.5f);
-    ys = fminf(fmaxf(ys, 0.0f), (float)(H - 1));
-    y0 = f2i(floorf(ys));
-    y1 = min(y0 + 1, H - 1);
-    fy = fsub(ys, (float)y0);
-    gy = fsub(1.0f, fy);
-}
-
-// One thread's band: output rows [band * kPyrRows, +kPyrRows) of quad q.
-template <int NW>
-__device__ __forceinline__ void pyr_band(const uint8_t *__restrict__ src, int sp, int H, uint8_t *__restrict__ dst,
-                                         int dp, int w, int h, float sy, int q, int band, const int (&c0)[4],
-                                         const int (&c1)[4], const float (&fx)[4], const float (&gx)[4])
-{
-    PyrCols<NW> C;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-        const int first = c0[k * (4 / NW)];
-        const int off = first & ~3;
-        C.base[k] = src + off;
-        C.sh[k] = 8u * (unsigned)(first & 3);
-        C.ok1[k] = off + 4 < sp;
-        C.ok2[k] = off + 8 < sp;
-    }
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int a = 2 * p, b = a + 1;
-        unsigned s;
-        if (NW == 4) {
-            s = 0u | 4u << 4 | (unsigned)(c1[a] - c0[a]) << 8 | (unsigned)(4 + c1[b] - c0[b]) << 12;
-        } else {
-            const int base = c0[NW == 1 ? 0 : a];
-            s = (unsigned)(c0[a] - base) | (unsigned)(c0[b] - base) << 4 | (unsigned)(c1[a] - base) << 8 |
-                (unsigned)(c1[b] - base) << 12;
-        }
-        C.sel[p] = s;
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        C.gx[j] = gx[j];
-        C.fx[j] = fx[j];
-    }
-    const int left = w - 4 * q;
-    const unsigned mask = left >= 4 ? 0xffffffffu : (1u << (8 * left)) - 1u;
-    const f32x2 rnd = f2_splat(kRound23);
-    // Rows in pairs: the two register arrays swap roles, so the new bottom
-    // row's interpolation always goes into the array whose contents are dead,
-    // and the top row is the previous bottom row unless it was skipped (then
-    // it is interpolated in place): no copies between the arrays.
-    float ha[4], hb[4];
-    int cy1 = -1;
-    const int ya = band * kPyrRows, yb = min(h, ya + kPyrRows);
-    uint8_t *out = dst + 4 * q;
-    auto emit = [&](int y, const float (&top)[4], const float (&bot)[4], float fy, float gy) {
-        float v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = fadd(fmul(top[j], gy), fmul(bot[j], fy));
-        unsigned r0, r1, r2, r3;
-        f2_unpack(f2_add(f2_pack(__float_as_uint(v[0]), __float_as_uint(v[1])), rnd), r0, r1);
-        f2_unpack(f2_add(f2_pack(__float_as_uint(v[2]), __float_as_uint(v[3])), rnd), r2, r3);
-        const unsigned word = __byte_perm(__byte_perm(r0, r1, 0x0040), __byte_perm(r2, r3, 0x0040), 0x5410);
-        *reinterpret_cast<unsigned *>(out + (size_t)y * dp) = word & mask;
-    };
-    for (int y = ya; y < yb; y += 2) {
-        int y0, y1;
-        float fy, gy;
-        // even row: top in ha, bottom into hb
-        pyr_row(y, sy, H, y0, y1, fy, gy);
-        pyr_hrow<NW>((size_t)y1 * sp, C, hb);
-        if (y0 != cy1) pyr_hrow<NW>((size_t)y0 * sp, C, ha);
-        cy1 = y1;
-        emit(y, ha, hb, fy, gy);
-        if (y + 1 >= yb) break;
-        // odd row: top in hb, bottom into ha
-        pyr_row(y + 1, sy, H, y0, y1, fy, gy);
-        pyr_hrow<NW>((size_t)y1 * sp, C, ha);
-        if (y0 != cy1) pyr_hrow<NW>((size_t)y0 * sp, C, hb);
-        cy1 = y1;
-        emit(y + 1, hb, ha, fy, gy);
-    }
-}
-
-__global__ void __launch_bounds__(kPyrThreads, 4) ft_pyramid_kernel(const BatchHeader *__restrict__ hdr)
-{
-    const int f = (int)(blockIdx.y >> 1), side = (int)(blockIdx.y & 1);
-    if (f >= hdr->nframes) return;
-    const FrameDev &F = hdr->frames[f];
-    if (!(F.build_pyr & (1 << side))) return;
-    const int nl = hdr->p.nlevels;
-    const uint8_t *src = side ? F.pyrR[0] : F.pyrL[0];
-    const int *lw = side ? F.rw : F.lw, *lh = side ? F.rh : F.lh, *lp = side ? F.rp : F.lp;
-    const int W = lw[0], H = lh[0], sp = lp[0];
-    int total = 0;
-    for (int l = 1; l < nl; ++l) total += pyr_vblocks(lw[l], lh[l]);
-    for (int vb = (int)blockIdx.x; vb < total; vb += (int)gridDim.x) {
-        int l = 1, b = vb;
-        for (; l < nl - 1; ++l) {
-            const int n = pyr_vblocks(lw[l], lh[l]);
-            if (b < n) break;
-            b -= n;
-        }
-        const int w = lw[l], h = lh[l];
-        const int wq = (w + 3) >> 2;
-        const int v = b * kPyrThreads + (int)threadIdx.x;
-        const int band = v / wq, q = v - band * wq;
-        const bool active = band * kPyrRows < h;
-        const float sx = fdiv((float)W, (float)w), sy = fdiv((float)H, (float)h);
-        int c0[4], c1[4];
-        float fx[4], gx[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float xs = fsub(fmul(fadd((float)(4 * q + j), 0.5f), sx), 0.5f);
-            xs = fminf(fmaxf(xs, 0.0f), (float)(W - 1));
-            c0[j] = f2i(floorf(xs));
-            c1[j] = min(c0[j] + 1, W - 1);
-            fx[j] = fsub(xs, (float)c0[j]);
-            gx[j] = fsub(1.0f, fx[j]);
-        }
-        // windows: one 8-byte window if the quad's bytes span at most 8, else
-        // one per pair if each pair's do, else one per pixel (block-uniform)
-        const bool need2 = c1[3] - c0[0] > 7;
-        const bool need4 = c1[1] - c0[0] > 7 || c1[3] - c0[2] > 7;
-        const int any4 = __syncthreads_or(active && need4);
-        const int any2 = __syncthreads_or(active && need2);
-        if (active) {
-            uint8_t *dst = const_cast<uint8_t *>(side ? F.pyrR[l] : F.pyrL[l]);
-            const int dp = lp[l];
-            if (any4) pyr_band<4>(src, sp, H, dst, dp, w, h, sy, q, band, c0, c1, fx, gx);
-            else if (any2) pyr_band<2>(src, sp, H, dst, dp, w, h, sy, q, band, c0, c1, fx, gx);
-            else pyr_band<1>(src, sp, H, dst, dp, w, h, sy, q, band, c0, c1, fx, gx);
-        }
-    }
-}
-
-cudaError_t launch_pyramids(const BatchHeader *dev_hdr, int nframes, int blocks_per_image, cudaStream_t stream)
-{
-    if (nframes <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)(blocks_per_image > 0 ? blocks_per_image : 1), (unsigned)(nframes * 2));
-    ft_pyramid_kernel<<<grid, kPyrThreads, 0, stream>>>(dev_hdr);
-    return cudaGetLastError();
-}
-
 int fused_smem_bytes() { return (int)sizeof(Smem); }
 
 const void *fused_kernel_ptr() { return (const void *)ft_fused_kernel; }
