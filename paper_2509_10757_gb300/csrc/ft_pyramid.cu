@@ -14,15 +14,19 @@
 //      floats (each source byte is converted once, for every level);
 //   2. finds, for every level, the output rows whose upper source row y0
 //      and the output columns whose left source column c0 lie in the tile
-//      (binary searches over the same FP32 operations as the formula; y0
-//      and c0 never decrease along a level), and tabulates those rows'
+//      (searches over the same FP32 operations as the formula, one lane of
+//      the last warp per level while the tile loads are in flight; y0 and
+//      c0 never decrease along a level), and tabulates those rows'
 //      source-row offsets and vertical weights;
-//   3. gives each thread two output columns (x and x + 32) of one level at
-//      a time (all levels' columns in one list, so few threads idle) and
-//      walks those columns' rows in the tile, keeping the horizontal
-//      interpolations of the last bottom source row for the next output row
-//      when it is the next row's top.  The lanes of a warp take 32
-//      neighbouring columns, so the byte stores of a row coalesce.
+//   3. gives each thread kPyrCols output columns (x, x + 32, ...) of one
+//      level at a time (all levels' columns in one list, so few threads
+//      idle) and walks those columns' rows in the tile, keeping the
+//      horizontal interpolations of the last bottom source row for the next
+//      output row when it is the next row's top.  The lanes of a warp take
+//      32 neighbouring columns, so the byte stores of a row coalesce.
+// The image's last column and row are repeated past the tile's staged ones
+// where the tile reaches the image's edge, so the formula's clamped c1 and y1
+// are always the staged c0 + 1 and y0 + 1.
 // Every tile is independent: no block waits for another.
 //
 // A byte b becomes the float b exactly by placing it in the mantissa of 2^23
