@@ -336,11 +336,11 @@ def sad_vector(params: dict, pyr_left, pyr_right, level: int, ul: int, vl: int, 
     return sad if ok else None
 
 
-def subpixel(sad, L: int, kbest: int, ur0: int, scale: float, xl: float, bf: float, maxD: float):
+def subpixel(sad, L: int, kbest: int, ur0: int, scale: float, xl: float, bf: float, disp_hi: float):
     """a4: (accepted, u_right, depth, delta) for a SAD vector with minimum at kbest."""
     s = _c(sad, np.int32)
     ur, dp, de = C.c_float(-1), C.c_float(-1), C.c_float(0)
-    ok = _lib_handle().orc_subpixel(_ptr(s), L, kbest, ur0, scale, xl, bf, maxD, C.byref(ur),
+    ok = _lib_handle().orc_subpixel(_ptr(s), L, kbest, ur0, scale, xl, bf, disp_hi, C.byref(ur),
                                     C.byref(dp), C.byref(de))
     return bool(ok), ur.value, dp.value, de.value
 

@@ -149,7 +149,7 @@ int orc_row_index(int nr, const float *yr, const int8_t *octr, const float *sc,
 /* ------------------------------------------------------------------------ */
 /* a2: for left keypoint i, scan the row list of row (int)y_i.  A right     */
 /* keypoint j is a candidate if its octave is within one of i's and its x   */
-/* lies in [x_i - maxD, x_i - minD], with minD = 0 and maxD = bf / b (the   */
+/* lies in [x_i - disp_hi, x_i - disp_lo], with disp_lo = 0 and disp_hi = bf / b (the   */
 /* nearest depth is one baseline).  Best = smallest (d, j).  dist[i] is     */
 /* that smallest d (-1 without candidates); best_r[i] = j if d < th_stereo. */
 /* ------------------------------------------------------------------------ */
@@ -158,9 +158,9 @@ void orc_stereo_best(const orc_params *p, const orc_pinhole *cam,
                      const int *row_ptr, const int *row_idx,
                      int32_t *best_r, int32_t *dist)
 {
-    const float minZ = cam->b;
-    const float minD = 0.0f;
-    const float maxD = cam->bf / minZ;
+    const float z_near = cam->b;
+    const float disp_lo = 0.0f;
+    const float disp_hi = cam->bf / z_near;
     for (int i = 0; i < L->n; ++i) {
         best_r[i] = -1;
         dist[i] = -1;
@@ -168,15 +168,15 @@ void orc_stereo_best(const orc_params *p, const orc_pinhole *cam,
         int row = (int)L->y[i];
         if (row >= cam->height) continue;
         if (row_ptr[row + 1] == row_ptr[row]) continue;
-        const float minU = L->x[i] - maxD;
-        const float maxU = L->x[i] - minD;
-        if (maxU < 0.0f) continue;
-        const int levelL = L->oct[i];
+        const float u_lo = L->x[i] - disp_hi;
+        const float u_hi = L->x[i] - disp_lo;
+        if (u_hi < 0.0f) continue;
+        const int oct_l = L->oct[i];
         int bestd = 1 << 30, bestj = -1;
         for (int e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
             int j = row_idx[e];
-            if (R->oct[j] < levelL - 1 || R->oct[j] > levelL + 1) continue;
-            if (R->x[j] < minU || R->x[j] > maxU) continue;
+            if (R->oct[j] < oct_l - 1 || R->oct[j] > oct_l + 1) continue;
+            if (R->x[j] < u_lo || R->x[j] > u_hi) continue;
             int d = orc_hamming(L->desc + (size_t)i * ORC_DESC_BYTES,
                                 R->desc + (size_t)j * ORC_DESC_BYTES);
             if (d < bestd || (d == bestd && j < bestj)) {
@@ -230,28 +230,28 @@ int orc_sad_vector(const orc_params *p, const orc_pyramid *pl, const orc_pyramid
 /* a4: parabola through (k*-1, k*, k*+1) of the SAD curve, vertex offset    */
 /* delta = (S- - S+) / (2 (S- + S+ - 2 S0)); right coordinate              */
 /* uR = scale * (ur0 + k* + delta); disparity = xl - uR must lie in        */
-/* [0, maxD); a disparity of exactly 0 is replaced by 0.01 px; depth =     */
+/* [0, disp_hi); a disparity of exactly 0 is replaced by 0.01 px; depth =     */
 /* bf / disparity.  Returns 1 if accepted.                                  */
 /* ------------------------------------------------------------------------ */
 int orc_subpixel(const int32_t *sad, int L, int kbest, int ur0, float scale, float xl,
-                 float bf, float maxD, float *u_right, float *depth, float *delta)
+                 float bf, float disp_hi, float *u_right, float *depth, float *delta)
 {
-    const float minD = 0.0f;
-    const float dist1 = (float)sad[kbest + L - 1];
-    const float dist2 = (float)sad[kbest + L];
-    const float dist3 = (float)sad[kbest + L + 1];
-    const float deltaR = (dist1 - dist3) / (2.0f * (dist1 + dist3 - 2.0f * dist2));
-    *delta = deltaR;
-    if (deltaR < -1.0f || deltaR > 1.0f) return 0;   /* unreachable: |deltaR| <= 0.5 */
-    float bestuR = scale * ((float)ur0 + (float)kbest + deltaR);
-    float disparity = xl - bestuR;
-    if (!(disparity >= minD && disparity < maxD)) return 0;
+    const float disp_lo = 0.0f;
+    const float sad_m1 = (float)sad[kbest + L - 1];
+    const float sad_0 = (float)sad[kbest + L];
+    const float sad_p1 = (float)sad[kbest + L + 1];
+    const float dk = (sad_m1 - sad_p1) / (2.0f * (sad_m1 + sad_p1 - 2.0f * sad_0));
+    *delta = dk;
+    if (dk < -1.0f || dk > 1.0f) return 0;   /* unreachable: |dk| <= 0.5 */
+    float ur_sub = scale * ((float)ur0 + (float)kbest + dk);
+    float disparity = xl - ur_sub;
+    if (!(disparity >= disp_lo && disparity < disp_hi)) return 0;
     if (disparity <= 0.0f) {
         disparity = 0.01f;
-        bestuR = xl - 0.01f;
+        ur_sub = xl - 0.01f;
     }
     *depth = bf / disparity;
-    *u_right = bestuR;
+    *u_right = ur_sub;
     return 1;
 }
 
@@ -286,9 +286,9 @@ void orc_median_reject(int n_kp, const int32_t *sad_best, float factor, float *u
         if (sad_best[i] >= 0) v[m++] = sad_best[i];
     sort_ints(v, n);
     const int median = v[n / 2];
-    const float thDist = factor * (float)median;
+    const float sad_cut = factor * (float)median;
     for (int i = 0; i < n_kp; ++i) {
-        if (sad_best[i] >= 0 && (float)sad_best[i] >= thDist) {
+        if (sad_best[i] >= 0 && (float)sad_best[i] >= sad_cut) {
             u_right[i] = -1.0f;
             depth[i] = -1.0f;
         }
@@ -320,7 +320,7 @@ void orc_stereo_pinhole(const orc_params *p, const orc_pinhole *cam,
     /* a2 */
     orc_stereo_best(p, cam, L, R, row_ptr, row_idx, best_r, dist);
 
-    const float maxD = cam->bf / cam->b;
+    const float disp_hi = cam->bf / cam->b;
     const int Ls = p->sad_L;
     int32_t sad[2 * 64 + 1];
 
@@ -346,7 +346,7 @@ void orc_stereo_pinhole(const orc_params *p, const orc_pinhole *cam,
 
         /* a4 */
         float delta;
-        if (orc_subpixel(sad, Ls, kbest, ur0, sc[l], L->x[i], cam->bf, maxD, &u_right[i],
+        if (orc_subpixel(sad, Ls, kbest, ur0, sc[l], L->x[i], cam->bf, disp_hi, &u_right[i],
                          &depth[i], &delta))
             sad_best[i] = sad[kbest + Ls];
     }
@@ -435,9 +435,9 @@ static int distance_and_scale(const orc_params *p, const float *O, const float *
     orc_scale_table(p->nlevels, p->scale_factor, sc, isc);
     const float PO[3] = {Pw[0] - O[0], Pw[1] - O[1], Pw[2] - O[2]};
     const float dist = sqrtf(PO[0] * PO[0] + PO[1] * PO[1] + PO[2] * PO[2]);
-    const float maxDistance = p->dist_hi * dmax;
-    const float minDistance = p->dist_lo * dmin;
-    if (dist < minDistance || dist > maxDistance) return 0;
+    const float d_far = p->dist_hi * dmax;
+    const float d_near = p->dist_lo * dmin;
+    if (dist < d_near || dist > d_far) return 0;
     const float vc = (PO[0] * nrm[0] + PO[1] * nrm[1] + PO[2] * nrm[2]) / dist;
     if (vc < p->view_cos_min) return 0;
     const float ratio = dmax / dist;

@@ -125,7 +125,7 @@ void orc_stereo_best(const orc_params *p, const orc_pinhole *cam,
 int orc_sad_vector(const orc_params *p, const orc_pyramid *pl, const orc_pyramid *pr,
                    int level, int ul, int vl, int ur0, int32_t *sad);
 int orc_subpixel(const int32_t *sad, int L, int kbest, int ur0, float scale, float xl,
-                 float bf, float maxD, float *u_right, float *depth, float *delta);
+                 float bf, float disp_hi, float *u_right, float *depth, float *delta);
 void orc_median_reject(int n_kp, const int32_t *sad_best, float factor, float *u_right,
                        float *depth);
 void orc_stereo_pinhole(const orc_params *p, const orc_pinhole *cam,

@@ -574,7 +574,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane & (kGroup - 1), gw = lane / kGroup;
-    const float maxD = fdiv(F.bf, F.b);
+    const float disp_hi = fdiv(F.bf, F.b);
     for (int tb = warp * (32 / kGroup); tb < npass; tb += kGroups) {
         const int t = tb + gw;
         const bool have = t < npass;
@@ -589,9 +589,9 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
             i = __float_as_int(L.z);
             oi = __float_as_int(L.w);
             const int row = f2i(yi);
-            const float minU = fsub(xi, maxD);
-            const float maxU = fsub(xi, 0.0f);
-            if (!(yi < 0.0f) && row < F.H && !(maxU < 0.0f)) {
+            const float u_lo = fsub(xi, disp_hi);
+            const float u_hi = fsub(xi, 0.0f);
+            if (!(yi < 0.0f) && row < F.H && !(u_hi < 0.0f)) {
                 const uint4 a0 = S.u.st.left.ldesc[2 * t], a1 = S.u.st.left.ldesc[2 * t + 1];
                 if (staged) {
                     // candidate octaves oi-1 .. oi+1, each over the rows its band can reach
@@ -606,7 +606,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                             const int oj = rec_octave(g.w);
                             if (oj < oi - 1 || oj > oi + 1) continue;
                             if (!band_has(g.y, row)) continue;
-                            if (g.x < minU || g.x > maxU) continue;
+                            if (g.x < u_lo || g.x > u_hi) continue;
                             const int at = __float_as_int(g.z);
                             const unsigned k = ((unsigned)ham8(a0, a1, S.u.st.sdesc[2 * at], S.u.st.sdesc[2 * at + 1]) << 20) |
                                                (unsigned)rec_index(g.w);
@@ -625,7 +625,7 @@ __device__ void hamming_phase(const DevParams &P, const FrameDev &F, SmemStereo 
                         const int oj = rec_octave(g.w);
                         if (oj < oi - 1 || oj > oi + 1) continue;
                         if (!band_has(g.y, row)) continue;
-                        if (g.x < minU || g.x > maxU) continue;
+                        if (g.x < u_lo || g.x > u_hi) continue;
                         const unsigned k = ((unsigned)ham8(a0, a1, __ldcg(F.rs_desc + 2 * e),
                                                            __ldcg(F.rs_desc + 2 * e + 1)) << 20) |
                                            (unsigned)rec_index(g.w);
@@ -786,16 +786,16 @@ __device__ void refine_round(const DevParams &P, const FrameDev &F, SmemStereo &
             const float d1 = (float)sad[kb - 1], d2 = (float)sad[kb], d3 = (float)sad[kb + 1];
             const float delta = fdiv(fsub(d1, d3), fmul(2.0f, fsub(fadd(d1, d3), fmul(2.0f, d2))));
             if (!(delta < -1.0f || delta > 1.0f)) {
-                float bestuR = fmul(P.sc[J.l], fadd(fadd((float)J.ur0, (float)shift), delta));
-                float disparity = fsub(J.xi, bestuR);
-                const float maxD = fdiv(F.bf, F.b);
-                if (disparity >= 0.0f && disparity < maxD) {
+                float ur_sub = fmul(P.sc[J.l], fadd(fadd((float)J.ur0, (float)shift), delta));
+                float disparity = fsub(J.xi, ur_sub);
+                const float disp_hi = fdiv(F.bf, F.b);
+                if (disparity >= 0.0f && disparity < disp_hi) {
                     if (disparity <= 0.0f) {
                         disparity = 0.01f;
-                        bestuR = fsub(J.xi, 0.01f);
+                        ur_sub = fsub(J.xi, 0.01f);
                     }
                     dep = fdiv(F.bf, disparity);
-                    ur = bestuR;
+                    ur = ur_sub;
                     sadb = sad[kb];
                 }
             }
@@ -1258,9 +1258,9 @@ __device__ __forceinline__ bool distance_scale(const DevParams &P, const float *
 {
     const float px = fsub(pos.x, O[0]), py = fsub(pos.y, O[1]), pz = fsub(pos.z, O[2]);
     const float dist = fsqrt(fadd(fadd(fmul(px, px), fmul(py, py)), fmul(pz, pz)));
-    const float maxDistance = fmul(P.dist_hi, nrm.w);
-    const float minDistance = fmul(P.dist_lo, pos.w);
-    if (dist < minDistance || dist > maxDistance) return false;
+    const float d_far = fmul(P.dist_hi, nrm.w);
+    const float d_near = fmul(P.dist_lo, pos.w);
+    if (dist < d_near || dist > d_far) return false;
     vc = fdiv(fadd(fadd(fmul(px, nrm.x), fmul(py, nrm.y)), fmul(pz, nrm.z)), dist);
     if (vc < P.view_cos_min) return false;
     const float ratio = fdiv(nrm.w, dist);

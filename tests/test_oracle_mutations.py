@@ -17,17 +17,17 @@ MUTANTS = [
     ("hamming_short", "i < ORC_DESC_BYTES; ++i) d +=", "i < ORC_DESC_BYTES - 1; ++i) d +="),
     ("band_ceil", "int b = (int)ceilf(y + r);", "int b = (int)floorf(y + r);"),
     ("tie_last_j", "if (d < bestd || (d == bestd && j < bestj)) {", "if (d <= bestd) {"),
-    ("octave_window", "R->oct[j] > levelL + 1", "R->oct[j] > levelL"),
-    ("disparity_sign", "const float minU = L->x[i] - maxD;", "const float minU = L->x[i] + maxD;"),
+    ("octave_window", "R->oct[j] > oct_l + 1", "R->oct[j] > oct_l"),
+    ("disparity_sign", "const float u_lo = L->x[i] - disp_hi;", "const float u_lo = L->x[i] + disp_hi;"),
     ("threshold_le", "if (bestd < p->th_stereo)", "if (bestd <= p->th_stereo + 10)"),
     ("centre_right", "int b = IR[(size_t)(vl + dy) * sr + (ur0 + k + dx)] - cR;",
      "int b = IR[(size_t)(vl + dy) * sr + (ur0 + k + dx)] - cL;"),
     ("shift_sign", "(ur0 + k + dx)] - cR;", "(ur0 - k + dx)] - cR;"),
     ("sad_bounds", "ur0 + L + w > wr - 1", "ur0 + w > wr - 1"),
-    ("parabola_sign", "(dist1 - dist3) / (2.0f", "(dist3 - dist1) / (2.0f"),
-    ("parabola_factor", "/ (2.0f * (dist1 + dist3 - 2.0f * dist2))", "/ ((dist1 + dist3 - 2.0f * dist2))"),
+    ("parabola_sign", "(sad_m1 - sad_p1) / (2.0f", "(sad_p1 - sad_m1) / (2.0f"),
+    ("parabola_factor", "/ (2.0f * (sad_m1 + sad_p1 - 2.0f * sad_0))", "/ ((sad_m1 + sad_p1 - 2.0f * sad_0))"),
     ("median_index", "const int median = v[n / 2];", "const int median = v[(n - 1) / 2];"),
-    ("median_strict", "(float)sad_best[i] >= thDist", "(float)sad_best[i] > thDist"),
+    ("median_strict", "(float)sad_best[i] >= sad_cut", "(float)sad_best[i] > sad_cut"),
     ("fisheye_overlap", "if (!(R->x[j] >= lap_r0 && R->x[j] <= lap_r1)) continue;", ""),
     ("fisheye_second", "d2[i] = (sj >= 0) ? sd : 256;", "d2[i] = (sj >= 0) ? sd : 255;"),
     ("transpose_R", "Pc[0] = R[0] * P[0] + R[1] * P[1] + R[2] * P[2] + t[0];",

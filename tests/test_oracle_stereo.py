@@ -103,7 +103,7 @@ def test_stereo_best_equals_brute_force(params, seed):
     pool = {6: 1, 7: 2}.get(seed, 3 if seed % 2 else 6)
     cam, L, R = _tiny_pair_scene(seed, pool=pool, flip=0.0 if seed in (4, 6, 7) else 0.15)
     best_r, dist = orc.stereo_best(params, cam, L, R)
-    maxD = float(np.float32(np.float32(cam.bf) / np.float32(cam.b)))
+    disp_hi = float(np.float32(np.float32(cam.bf) / np.float32(cam.b)))
     for i in range(L.n):
         row = int(L.y[i])
         cands = []
@@ -113,7 +113,7 @@ def test_stereo_best_equals_brute_force(params, seed):
                 continue
             if abs(int(R.oct[j]) - int(L.oct[i])) > 1:
                 continue
-            if not (float(L.x[i]) - maxD <= float(R.x[j]) <= float(L.x[i])):
+            if not (float(L.x[i]) - disp_hi <= float(R.x[j]) <= float(L.x[i])):
                 continue
             cands.append((bitcount(L.desc[i], R.desc[j]), j))
         if not cands:
@@ -212,7 +212,7 @@ def test_parabola_disparity_range_and_clamp():
     assert ok and ur == np.float32(100.0 - 0.01) and depth == np.float32(40.0 / np.float32(0.01))
     ok, *_ = orc.subpixel(sad, 5, 0, 100, 1.0, 99.5, 40.0, 60.0)         # negative disparity
     assert not ok
-    ok, *_ = orc.subpixel(sad, 5, 0, 100, 1.0, 160.0, 40.0, 60.0)        # disparity == maxD
+    ok, *_ = orc.subpixel(sad, 5, 0, 100, 1.0, 160.0, 40.0, 60.0)        # disparity == disp_hi
     assert not ok
     ok, ur, depth, _ = orc.subpixel(sad, 5, 0, 100, 1.0, 159.5, 40.0, 60.0)
     assert ok and ur == 100.0 and depth == np.float32(40.0 / 59.5)
