@@ -358,7 +358,7 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
-KIND_NAMES = ("grid", "stereo", "search", "resolve", "pose")
+KIND_NAMES = ("grid", "stereo", "search", "finish", "resolve", "pose")
 
 
 def trace_summary(recs) -> dict:
@@ -686,7 +686,8 @@ def time_batch(frames, steps: int, warmup: int, dev, local_rank: int, arena_byte
                    "algorithmic_bytes": alg},
            "tuning": {"strip_rows": best.strip_rows, "search_tile": best.search_tile,
                       "fisheye_tile": best.fisheye_tile, "ctas_per_sm": best.ctas_per_sm,
-                      "search_stage": "L2" if best.search_stage else "on chip if it fits"}}
+                      "search_stage": "L2" if best.search_stage else "on chip if it fits",
+                      "split_search": {1: "two halves", -1: "one pass"}.get(best.split_search, "automatic")}}
     ctx.close()
     return out
 
@@ -1138,7 +1139,8 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     def tuning_of(t):
         return {"strip_rows": t.strip_rows, "search_tile": t.search_tile, "fisheye_tile": t.fisheye_tile,
-                "ctas_per_sm": t.ctas_per_sm, "search_stage": "L2" if t.search_stage else "on chip if it fits"}
+                "ctas_per_sm": t.ctas_per_sm, "search_stage": "L2" if t.search_stage else "on chip if it fits",
+                "split_search": {1: "two halves", -1: "one pass"}.get(t.split_search, "automatic")}
     ctx_tuning = tuning_of(best_stream)
     ctx.close()
     if rank != 0:

@@ -142,7 +142,7 @@ class ft_ctx_desc(C.Structure):
 
 class ft_tuning(C.Structure):
     _fields_ = [("strip_rows", i32), ("search_tile", i32), ("fisheye_tile", i32),
-                ("resolve_tile", i32), ("ctas_per_sm", i32), ("search_stage", i32)]
+                ("resolve_tile", i32), ("ctas_per_sm", i32), ("search_stage", i32), ("split_search", i32)]
 
 
 class ft_trace_record(C.Structure):

@@ -178,6 +178,7 @@ ft_tuning default_tuning()
     t.resolve_tile = 2048;
     t.ctas_per_sm = 0;
     t.search_stage = 0;
+    t.split_search = 0;
     return t;
 }
 
@@ -487,7 +488,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
         return p;
     };
     const int halo = B.p.halo;
-    int counts[K_KINDS] = {0, 0, 0, 0};
+    int counts[K_KINDS] = {};
     for (int f = 0; f < n; ++f) {
         const Job &j = jobs[f];
         FrameDev &F = frames[f];
@@ -618,6 +619,10 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
                 C.gdesc = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)C.nk));
                 C.gpos = reinterpret_cast<int *>(carve(sizeof(int) * (size_t)C.nk));
                 C.owner = reinterpret_cast<unsigned long long *>(carve(sizeof(unsigned long long) * (size_t)C.nk));
+                // a pinhole frame whose stereo step runs in the same launch splits
+                // its search around it (search items need not wait for it)
+                F.split_search = j.wait_stereo && (tune.split_search > 0 || (tune.split_search == 0 && n <= 32));
+                if (F.split_search) C.scan = reinterpret_cast<uint4 *>(carve(sizeof(uint4) * 2 * (size_t)F.nm));
                 n_search[c] = (F.nm + F.search_tile - 1) / F.search_tile;
                 n_resolve[c] = (std::max(F.nm, C.nk) + F.resolve_tile - 1) / F.resolve_tile;
             }
@@ -663,7 +668,8 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
         F.n_search_items[1] = n_search[1];
         F.n_resolve_items[0] = n_resolve[0];
         F.n_resolve_items[1] = n_resolve[1];
-        const int per_kind[K_KINDS] = {n_index, n_stereo, n_search[0] + n_search[1],
+        const int n_finish = F.split_search ? n_search[0] + n_search[1] : 0;
+        const int per_kind[K_KINDS] = {n_index, n_stereo, n_search[0] + n_search[1], n_finish,
                                        n_resolve[0] + n_resolve[1]};
         for (int k = 0; k < K_KINDS; ++k) {
             prefix[k * (n + 1) + f] = counts[k];
@@ -1380,8 +1386,9 @@ ft_status ft_get_tuning(ft_ctx *ctx, const ft_batch *batch, ft_tuning *t)
 }
 
 // The launch shapes both autotuners try: strip rows 16/32/64, search tile
-// 256/512/1024, fisheye tile 64/128, and every count of CTAs per SM from the
-// resident maximum down to one (fewer leave room for a concurrent launch).
+// 256/512/1024, fisheye tile 64/128, every count of CTAs per SM from the
+// resident maximum down to one (fewer leave room for a concurrent launch),
+// both search staging modes and the search in one pass or two halves.
 static std::vector<ft_tuning> tuning_candidates(int occ)
 {
     const int strips[] = {16, 32, 64};
@@ -1394,15 +1401,17 @@ static std::vector<ft_tuning> tuning_candidates(int occ)
         for (int b : tiles)
             for (int c : fish)
                 for (int o : occs)
-                    for (int st = 0; st < 2; ++st) {
-                        ft_tuning t = default_tuning();
-                        t.strip_rows = a;
-                        t.search_tile = b;
-                        t.fisheye_tile = c;
-                        t.ctas_per_sm = o;
-                        t.search_stage = st;
-                        cand.push_back(t);
-                    }
+                    for (int st = 0; st < 2; ++st)
+                        for (int sp : {1, -1}) {
+                            ft_tuning t = default_tuning();
+                            t.strip_rows = a;
+                            t.search_tile = b;
+                            t.fisheye_tile = c;
+                            t.ctas_per_sm = o;
+                            t.search_stage = st;
+                            t.split_search = sp;
+                            cand.push_back(t);
+                        }
     return cand;
 }
 
@@ -1581,13 +1590,13 @@ ft_status ft_save_tuning(ft_ctx *ctx, const char *path)
     FILE *f = std::fopen(path, "w");
     if (!f) return fail(FT_EINVAL, "cannot write %s", path);
     std::fprintf(f, "# frames_p2 has_pinhole has_fisheye nl_p2 m_p2 strip_rows search_tile fisheye_tile resolve_tile "
-                    "ctas_per_sm search_stage\n");
+                    "ctas_per_sm search_stage split_search\n");
     for (auto &kv : ctx->tuning) {
         const Bucket &b = kv.first;
         const ft_tuning &t = kv.second;
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", b.frames_p2, b.has_pinhole, b.has_fisheye, b.nl_p2,
-                     b.m_p2, t.strip_rows, t.search_tile, t.fisheye_tile, t.resolve_tile, t.ctas_per_sm,
-                     t.search_stage);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d\n", b.frames_p2, b.has_pinhole, b.has_fisheye,
+                     b.nl_p2, b.m_p2, t.strip_rows, t.search_tile, t.fisheye_tile, t.resolve_tile, t.ctas_per_sm,
+                     t.search_stage, t.split_search);
     }
     std::fclose(f);
     return FT_OK;
@@ -1603,11 +1612,13 @@ ft_status ft_load_tuning(ft_ctx *ctx, const char *path)
         if (line[0] == '#') continue;
         Bucket b{};
         ft_tuning t{};
-        // lines without the last column (search_stage) come from older tables: 0
-        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d", &b.frames_p2, &b.has_pinhole,
+        // lines without the last columns (search_stage, split_search) come
+        // from older tables: 0 for each
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d", &b.frames_p2, &b.has_pinhole,
                                     &b.has_fisheye, &b.nl_p2, &b.m_p2, &t.strip_rows, &t.search_tile,
-                                    &t.fisheye_tile, &t.resolve_tile, &t.ctas_per_sm, &t.search_stage);
-        if (got == 10 || got == 11) ctx->tuning[b] = t;
+                                    &t.fisheye_tile, &t.resolve_tile, &t.ctas_per_sm, &t.search_stage,
+                                    &t.split_search);
+        if (got >= 10 && got <= 12) ctx->tuning[b] = t;
     }
     std::fclose(f);
     return FT_OK;

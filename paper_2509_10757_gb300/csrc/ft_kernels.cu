@@ -1322,7 +1322,17 @@ __device__ bool project(const DevParams &P, const CamDev &C, const float *pose, 
 // camera's cell-ordered records and descriptors sit in shared memory.
 // motion: for a last-frame search, +1 / -1 / 0 for a camera that moved
 // forward / backward / neither along its viewing axis (f2).
-template <bool kStaged>
+// kScan: the first half of a search split around the stereo step.  Every
+// test but the stereo consistency is applied; the four smallest keys
+// (distance << 20 | keypoint) that pass, their octaves, the number that
+// passed and the projection's right coordinate and radius go to C.scan for
+// finish_point, which applies the consistency once the stereo step is done.
+// The consistency test drops candidates and keys are unique, so the two
+// smallest consistent keys among the four smallest candidates are the two
+// smallest consistent candidates, unless fewer than two of the four are
+// consistent while more than four passed: only then is the point searched
+// again.
+template <bool kStaged, bool kScan = false>
 __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev &C, const SmemSearch &Q,
                              const uint16_t *scell, float iw, float ih, int m, int motion)
 {
@@ -1332,6 +1342,9 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
     const bool last = F.search_mode != 0;
     int lvl = -1, d1 = -1, d2 = -1, kp = -1;
     float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned sk[4] = {kNoKey, kNoKey, kNoKey, kNoKey};   // kScan: four smallest keys, ascending
+    unsigned soct = 0, scount = 0;                          // their octaves (a byte each), how many passed
+    float sr = 0.0f, sur = 0.0f;
     const int loct = last ? (int)__ldg(F.last_oct + m) : 0;
     const bool skipped = (F.skip != nullptr && __ldg(F.skip + m) != 0) || (last && (loct < 0 || loct >= P.nlevels));
     if (!skipped) {
@@ -1360,6 +1373,8 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
             const int x1 = min(f2i(ceilf(fmul(fadd(du, r), iw))), FT_GRID_COLS - 1);
             const int y0 = max(f2i(floorf(fmul(fsub(dv, r), ih))), 0);
             const int y1 = min(f2i(ceilf(fmul(fadd(dv, r), ih))), FT_GRID_ROWS - 1);
+            sr = r;
+            sur = ur;
             if (!(x0 >= FT_GRID_COLS || x1 < 0 || y0 >= FT_GRID_ROWS || y1 < 0)) {
                 const uint4 q0 = __ldg(F.mdesc + 2 * m), q1 = __ldg(F.mdesc + 2 * m + 1);
                 const bool check_ur = C.model == FT_CAMERA_PINHOLE;
@@ -1396,10 +1411,38 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
                             const float distx = fsub(g.x, u), disty = fsub(g.y, v);
                             if (!(fabsf(distx) < r && fabsf(disty) < r)) continue;
                             if (z >> 28) continue;                         // taken
-                            if (check_ur && g.w > 0.0f && fabsf(fsub(ur, g.w)) > r) continue;
+                            if (!kScan && check_ur && g.w > 0.0f && fabsf(fsub(ur, g.w)) > r) continue;
                             const uint4 b0 = kStaged ? sdesc[2 * e] : __ldcg(C.gdesc + 2 * e);
                             const uint4 b1 = kStaged ? sdesc[2 * e + 1] : __ldcg(C.gdesc + 2 * e + 1);
                             const unsigned key = ((unsigned)ham8(q0, q1, b0, b1) << 20) | (unsigned)k;
+                            if (kScan) {
+                                scount = min(scount + 1u, 255u);
+                                const unsigned ob = (unsigned)oct & 0xffu;
+                                if (key < sk[3]) {
+                                    if (key < sk[2]) {
+                                        sk[3] = sk[2];
+                                        if (key < sk[1]) {
+                                            sk[2] = sk[1];
+                                            if (key < sk[0]) {
+                                                sk[1] = sk[0];
+                                                sk[0] = key;
+                                                soct = (soct << 8) | ob;
+                                            } else {
+                                                sk[1] = key;
+                                                soct = (soct & 0xffu) | ((soct << 8) & 0xff0000u) |
+                                                       ((soct << 8) & 0xff000000u) | ob << 8;
+                                            }
+                                        } else {
+                                            sk[2] = key;
+                                            soct = (soct & 0xffffu) | ((soct << 8) & 0xff000000u) | ob << 16;
+                                        }
+                                    } else {
+                                        sk[3] = key;
+                                        soct = (soct & 0xffffffu) | ob << 24;
+                                    }
+                                }
+                                continue;
+                            }
                             if (key < best) {
                                 second = best;
                                 oct2 = oct1;
@@ -1429,47 +1472,164 @@ __device__ void search_point(const DevParams &P, const FrameDev &F, const CamDev
     }
     C.level[m] = (int8_t)lvl;
     if (C.proj) C.proj[m] = pj;
+    if (kScan) {
+        C.scan[2 * m] = make_uint4(sk[0], sk[1], sk[2], sk[3]);
+        C.scan[2 * m + 1] = make_uint4(__float_as_uint(sur), __float_as_uint(sr), soct, scount);
+        return;
+    }
     C.mp_d1[m] = d1;
     C.mp_d2[m] = d2;
     C.mp_kp[m] = kp;
 }
 
+// The second half of a split search (see search_point): the stereo
+// consistency applied to the four smallest candidates of map point m, then
+// the top-2 rules and the claim, exactly as the unsplit search takes them.
+// A point that needs more than its four smallest candidates is searched
+// again from the device-memory records (whose right coordinates are final).
+__device__ void finish_point(const DevParams &P, const FrameDev &F, const CamDev &C, const SmemSearch &Q, float iw,
+                             float ih, int m, int motion)
+{
+    const uint4 ks = __ldcg(C.scan + 2 * m), aux = __ldcg(C.scan + 2 * m + 1);
+    const unsigned sk[4] = {ks.x, ks.y, ks.z, ks.w};
+    const float ur = __uint_as_float(aux.x), r = __uint_as_float(aux.y);
+    const unsigned count = aux.w;
+    const bool check_ur = C.model == FT_CAMERA_PINHOLE;
+    const bool last = F.search_mode != 0;
+    unsigned best = kNoKey, second = kNoKey;
+    int oct1 = -1, oct2 = -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if ((unsigned)q >= count) break;
+        const unsigned key = sk[q];
+        const int k = (int)(key & 0xfffffu);
+        if (k >= C.nk) continue;                     // never: keys name keypoints of the window
+        if (check_ur) {
+            const int e = __ldcg(C.gpos + k);
+            if (e < 0) continue;                     // never: window keypoints lie in the grid
+            const float w = __ldcg(&C.gkp[e].w);
+            if (w > 0.0f && fabsf(fsub(ur, w)) > r) continue;
+        }
+        const int oct = (int)(int8_t)((aux.z >> (8 * q)) & 0xffu);
+        if (best == kNoKey) {
+            best = key;
+            oct1 = oct;
+        } else {
+            second = key;
+            oct2 = oct;
+            break;
+        }
+    }
+    if (count > 4u && second == kNoKey) {
+        search_point<false>(P, F, C, Q, nullptr, iw, ih, m, motion);
+        return;
+    }
+    int d1 = -1, d2 = -1, kp = -1;
+    if (best != kNoKey) {
+        d1 = (int)(best >> 20);
+        d2 = second != kNoKey ? (int)(second >> 20) : 256;
+        if (d1 <= P.th_search) {
+            const int k1 = (int)(best & 0xfffffu);
+            const bool ratio = !last && (P.ratio_any_octave || oct1 == oct2);
+            if (!(ratio && (float)d1 > fmul(P.nn_ratio, (float)d2))) {
+                atomicMin(C.owner + k1, ((unsigned long long)d1 << 32) | (unsigned)m);
+                kp = k1;
+            }
+        }
+    }
+    C.mp_d1[m] = d1;
+    C.mp_d2[m] = d2;
+    C.mp_kp[m] = kp;
+}
+
+// The camera pose of a search item in shared memory (the right fisheye
+// camera's composed from the rig), the grid scale and the last-frame motion.
+__device__ void search_setup(const FrameDev &F, int cam, SmemSearch &Q, float &iw, float &ih, int &motion)
+{
+    const CamDev &C = F.cam[cam];
+    const int tid = threadIdx.x;
+    if (tid < 12) {
+        const CamDev &L = F.cam[0];
+        float v;
+        if (cam == 0 || F.camera == FT_CAMERA_PINHOLE) {
+            v = tid < 9 ? L.R[tid] : L.t[tid - 9];
+        } else if (tid < 9) {      // right camera: R_rw = R_rl * R_lw
+            const int i = tid / 3, j = tid % 3;
+            v = fadd(fadd(fmul(F.R_rl[3 * i], L.R[j]), fmul(F.R_rl[3 * i + 1], L.R[3 + j])),
+                     fmul(F.R_rl[3 * i + 2], L.R[6 + j]));
+        } else {                   // t_rw = R_rl * t_lw + t_rl
+            const int i = tid - 9;
+            v = fadd(fadd(fadd(fmul(F.R_rl[3 * i], L.t[0]), fmul(F.R_rl[3 * i + 1], L.t[1])),
+                          fmul(F.R_rl[3 * i + 2], L.t[2])),
+                     F.t_rl[i]);
+        }
+        Q.pose[tid] = v;
+    }
+    iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
+    ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
+    motion = 0;
+    if (F.search_mode != 0) {
+        // the current (left) camera centre in the last frame's camera
+        // coordinates; its z against the baseline (f2)
+        const float *O = F.cam[0].O;
+        const float cz = fadd(fadd(fadd(fmul(F.last_R[6], O[0]), fmul(F.last_R[7], O[1])), fmul(F.last_R[8], O[2])),
+                              F.last_t[2]);
+        motion = cz > F.base ? 1 : (-cz > F.base ? -1 : 0);
+    }
+}
+
+// Defined outputs of map points [m0, m1) after a wait ran out (reported in
+// the status word), and an empty first half of a split search.
+__device__ void search_abandon(const CamDev &C, int m0, int m1)
+{
+    for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) {
+        C.level[m] = -1;
+        if (C.proj) C.proj[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+        C.mp_d1[m] = -1;
+        C.mp_d2[m] = -1;
+        C.mp_kp[m] = -1;
+        if (C.scan) {
+            C.scan[2 * m] = make_uint4(kNoKey, kNoKey, kNoKey, kNoKey);
+            C.scan[2 * m + 1] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// The last search (or finish) item of a camera: counts, and for small frames
+// the final tables.
+__device__ void search_done(const FrameDev &F, int cam, int *s_flag)
+{
+    if (signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag) && F.fold_resolve)
+        resolve_range(F.cam[cam], F.nm, 0, max(F.nm, F.cam[cam].nk));
+}
+
+// A tile of map points.  A frame whose search is split around its stereo
+// step (split_search) runs the first half here without waiting for the
+// stereo step; its finish items complete the points.
 __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U, int *s_flag)
 {
     const int cam = tile < F.n_search_items[0] ? 0 : 1;
     const int t = cam ? tile - F.n_search_items[0] : tile;
+    const bool split = F.split_search != 0;
+    const int m0 = t * F.search_tile;
+    const int m1 = min(F.nm, m0 + F.search_tile);
     // the tile's map point records do not depend on the stereo step: ask L2
     // for them before waiting for it
-    for (int m = t * F.search_tile + (int)threadIdx.x; m < min(F.nm, (t + 1) * F.search_tile); m += kThreads) {
+    for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(F.pos + m));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(F.mdesc + 2 * m));
         if (F.search_mode == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(F.nrm + m));
     }
     bool ok = true;
-    if (F.wait_stereo) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
+    if (F.wait_stereo && !split) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
     if (ok) ok = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
+    const CamDev &C = F.cam[cam];
     if (ok) {
-        const CamDev &C = F.cam[cam];
         SmemSearch &Q = U.q;
-        float *pose = Q.pose;
         const int tid = threadIdx.x;
-        if (tid < 12) {
-            const CamDev &L = F.cam[0];
-            float v;
-            if (cam == 0 || F.camera == FT_CAMERA_PINHOLE) {
-                v = tid < 9 ? L.R[tid] : L.t[tid - 9];
-            } else if (tid < 9) {      // right camera: R_rw = R_rl * R_lw
-                const int i = tid / 3, j = tid % 3;
-                v = fadd(fadd(fmul(F.R_rl[3 * i], L.R[j]), fmul(F.R_rl[3 * i + 1], L.R[3 + j])),
-                         fmul(F.R_rl[3 * i + 2], L.R[6 + j]));
-            } else {                   // t_rw = R_rl * t_lw + t_rl
-                const int i = tid - 9;
-                v = fadd(fadd(fadd(fmul(F.R_rl[3 * i], L.t[0]), fmul(F.R_rl[3 * i + 1], L.t[1])),
-                              fmul(F.R_rl[3 * i + 2], L.t[2])),
-                         F.t_rl[i]);
-            }
-            pose[tid] = v;
-        }
+        float iw, ih;
+        int motion;
+        search_setup(F, cam, Q, iw, ih, motion);
         // stage the camera's cell-ordered keypoint records and descriptors
         // by asynchronous copies when they fit (the tail past the placed
         // records is copied but never read)
@@ -1488,21 +1648,15 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         }
         __syncthreads();
         mark(B, 0);
-        const int m0 = t * F.search_tile;
-        const int m1 = min(F.nm, m0 + F.search_tile);
-        const float iw = fdiv((float)FT_GRID_COLS, fsub(C.maxx, C.minx));
-        const float ih = fdiv((float)FT_GRID_ROWS, fsub(C.maxy, C.miny));
-        int motion = 0;
-        if (F.search_mode != 0) {
-            // the current (left) camera centre in the last frame's camera
-            // coordinates; its z against the baseline (f2)
-            const float *O = F.cam[0].O;
-            const float cz =
-                fadd(fadd(fadd(fmul(F.last_R[6], O[0]), fmul(F.last_R[7], O[1])), fmul(F.last_R[8], O[2])),
-                     F.last_t[2]);
-            motion = cz > F.base ? 1 : (-cz > F.base ? -1 : 0);
-        }
-        if (staged) {
+        if (split) {
+            if (staged) {
+                for (int m = m0 + tid; m < m1; m += kThreads)
+                    search_point<true, true>(B.p, F, C, Q, scell, iw, ih, m, motion);
+            } else {
+                for (int m = m0 + tid; m < m1; m += kThreads)
+                    search_point<false, true>(B.p, F, C, Q, nullptr, iw, ih, m, motion);
+            }
+        } else if (staged) {
             for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, scell, iw, ih, m, motion);
         } else {
             for (int m = m0 + tid; m < m1; m += kThreads)
@@ -1510,24 +1664,39 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         }
         mark(B, 1);
     } else {
-        // the wait ran out (reported in the status word): leave defined outputs
-        const CamDev &C = F.cam[cam];
-        const int m0 = t * F.search_tile;
-        const int m1 = min(F.nm, m0 + F.search_tile);
-        for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) {
-            C.level[m] = -1;
-            if (C.proj) C.proj[m] = make_float4(0.f, 0.f, 0.f, 0.f);
-            C.mp_d1[m] = -1;
-            C.mp_d2[m] = -1;
-            C.mp_kp[m] = -1;
-        }
+        search_abandon(C, m0, m1);
     }
-    if (signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag) &&
-        F.fold_resolve) {
-        // the last search item of this camera also writes the final tables
-        // (small frames: no separate resolve items wait for the search)
-        resolve_range(F.cam[cam], F.nm, 0, max(F.nm, F.cam[cam].nk));
+    if (split) signal_count(&F.ctr[C_SCAN_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag);
+    else search_done(F, cam, s_flag);
+}
+
+// The second half of a split search for a tile of map points: waits for the
+// first halves of the camera's tiles (the scan state) and for the frame's
+// stereo step, then finish_point for each point.  The first halves were
+// dequeued before any finish item, so the wait always ends.
+__device__ void finish_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U, int *s_flag)
+{
+    const int cam = tile < F.n_search_items[0] ? 0 : 1;
+    const int t = cam ? tile - F.n_search_items[0] : tile;
+    const int m0 = t * F.search_tile;
+    const int m1 = min(F.nm, m0 + F.search_tile);
+    bool ok = wait_geq(B, &F.ctr[C_SCAN_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag);
+    if (ok) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
+    if (ok) ok = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
+    const CamDev &C = F.cam[cam];
+    if (ok) {
+        SmemSearch &Q = U.q;
+        float iw, ih;
+        int motion;
+        search_setup(F, cam, Q, iw, ih, motion);
+        __syncthreads();
+        mark(B, 0);
+        for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) finish_point(B.p, F, C, Q, iw, ih, m, motion);
+        mark(B, 1);
+    } else {
+        search_abandon(C, m0, m1);
     }
+    search_done(F, cam, s_flag);
 }
 
 // ---------------------------------------------------------------- K_RESOLVE
@@ -1653,6 +1822,7 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
             else stereo_fisheye_item(B, F, tile, U, &s_flag);
             break;
         case K_SEARCH: search_item(B, F, tile, U, &s_flag); break;
+        case K_FINISH: finish_item(B, F, tile, U, &s_flag); break;
         default: resolve_item(B, F, tile, &s_flag); break;
         }
         if (B.trace != nullptr && threadIdx.x == 0) {

@@ -370,15 +370,16 @@ def test_dense_rows_fall_back_to_scan(ctx, lib):
 
 
 # ---------------------------------------------------------------- launch shapes, graphs, host staging
-@pytest.mark.parametrize("tune", [(1, 256, 512, 256, 1), (7, 1024, 256, 512, 0), (200, 512, 512, 4096, 1),
-                                  (32, 512, 128, 2048, 1)])
+@pytest.mark.parametrize("tune", [(1, 256, 512, 256, 1, 1), (7, 1024, 256, 512, 0, -1), (200, 512, 512, 4096, 1, -1),
+                                  (32, 512, 128, 2048, 1, 1), (32, 256, 128, 2048, 0, 0)])
 def test_tuning_variants_same_results(ctx, lib, tune):
-    # strip heights, tiles and both search staging modes (records on chip or in L2)
+    # strip heights, tiles, both search staging modes (records on chip or in
+    # L2) and the search in two halves around the stereo step or in one pass
     from paper_2509_10757_gb300.batch import PackedBatch
     frames = [scenes.single_pinhole(11), scenes.fisheye_frame(11)]
     pb = PackedBatch(frames)
     t = lib.ft_tuning(strip_rows=tune[0], search_tile=tune[1], fisheye_tile=tune[2],
-                      resolve_tile=tune[3], ctas_per_sm=1, search_stage=tune[4])
+                      resolve_tile=tune[3], ctas_per_sm=1, search_stage=tune[4], split_search=tune[5])
     b = pb.batch()
     lib.check(lib.ft_set_tuning(ctx.ptr, C.byref(b), C.byref(t)), "ft_set_tuning")
     try:
@@ -421,8 +422,9 @@ def test_autotune_and_table_roundtrip(ctx, lib, tmp_path):
     lib.check(lib.ft_load_tuning(ctx.ptr, path), "load")
     got = lib.ft_tuning()
     lib.check(lib.ft_get_tuning(ctx.ptr, C.byref(b), C.byref(got)), "get")
-    assert (got.strip_rows, got.search_tile, got.fisheye_tile, got.search_stage) == \
-        (best.strip_rows, best.search_tile, best.fisheye_tile, best.search_stage)
+    assert (got.strip_rows, got.search_tile, got.fisheye_tile, got.search_stage, got.split_search) == \
+        (best.strip_rows, best.search_tile, best.fisheye_tile, best.search_stage, best.split_search)
+    assert best.split_search in (1, -1)
     out = run_fused(ctx, frames)
     for f in range(len(frames)):
         check_frame(out, f, what="tuned")
@@ -773,3 +775,58 @@ def test_build_pyramid_shapes_and_scales(ctx, lib, W, H, nlevels, scale, seed):
         assert len(bad) == 0, (l, len(bad), bad[:4].tolist())
         w4 = (w + 3) // 4 * 4
         assert not got[:, w:w4].any(), l
+
+
+def _split_search_rescans(fr, out, params):
+    """Map points whose split search needs its second pass: more than four
+    keypoints pass every test but the stereo consistency, and fewer than two
+    of the four smallest (Hamming distance, index) keys among them are
+    consistent.  Recomputed here in FP32 from the search's definition."""
+    f32 = np.float32
+    p = _oracle_params(params)
+    sc = scenes.level_scales32(p["nlevels"], p["scale_factor"])
+    cam = fr.cam
+    iw = f32(64) / f32(f32(cam.max_x) - f32(cam.min_x))
+    ih = f32(48) / f32(f32(cam.max_y) - f32(cam.min_y))
+    kx, ky, ko = fr.left.x, fr.left.y, fr.left.oct.astype(np.int64)
+
+    def rnd(v):                                        # roundf: half away from zero
+        return np.sign(v) * np.floor(np.abs(v) + f32(0.5))
+
+    gx = rnd((kx - f32(cam.min_x)).astype(f32) * iw)
+    gy = rnd((ky - f32(cam.min_y)).astype(f32) * ih)
+    in_grid = (gx >= 0) & (gx < 64) & (gy >= 0) & (gy < 48) & (fr.taken_l == 0)
+    kbits = np.unpackbits(fr.left.desc, axis=1)
+    ur_k = out["u_right"]
+    proj, level = out["proj_l"], out["level_l"]
+    n = 0
+    for m in np.nonzero(level >= 0)[0]:
+        lv = int(level[m])
+        u, v, ur, vc = (f32(c) for c in proj[m])
+        r = f32(p["radius_narrow"]) if vc > f32(p["view_cos_narrow"]) else f32(p["radius_wide"])
+        r = f32(f32(r * f32(p["search_th"])) * sc[lv])
+        cand = np.nonzero(in_grid & (ko >= lv - 1) & (ko <= lv) & (np.abs((kx - u).astype(f32)) < r) &
+                          (np.abs((ky - v).astype(f32)) < r))[0]
+        if len(cand) <= 4:
+            continue
+        d = (kbits[cand] != np.unpackbits(fr.map.desc[m])).sum(axis=1)
+        top = cand[np.lexsort((cand, d))[:4]]
+        w = ur_k[top]
+        consistent = ~((w > 0) & (np.abs((f32(ur) - w).astype(f32)) > r))
+        n += int(consistent.sum() < 2)
+    return n
+
+
+def test_split_search_second_pass_on_dense_windows(ctx, lib):
+    # a pinhole frame whose stereo runs in the same launch splits its search:
+    # the first half keeps each map point's four smallest candidates without
+    # the stereo consistency, the second half applies it.  Dense keypoints and
+    # a wide search radius give windows of many candidates whose stereo right
+    # coordinates (other scene points' depths) mostly disagree with the map
+    # point's: those points take the second, full pass.  The frame must equal
+    # the oracle, and the second pass must have been needed.
+    overrides = {"search_th": 3.0}
+    fr = scenes.pinhole_frame(71, n_left=12000, n_map=3000, taken_frac=0.05)
+    out = run_fused(ctx, [fr], params=overrides, lib=lib)
+    check_frame(out, 0, params=overrides, what="dense windows")
+    assert _split_search_rescans(fr, out.outputs(0), overrides) > 0
