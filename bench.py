@@ -435,7 +435,9 @@ def run_profile(args, local_rank):
     batched workload (default tuning, no graphs).  --workload picks what runs:
     batched (the fused kernel), pose (fused + pose kernels: pose optimization
     after the search), extraction (pyramids of the 128 images built once,
-    then ft_extract_orb on them: the detect, select and describe kernels)."""
+    then ft_extract_orb on them: the detect, select and describe kernels),
+    pyramid (levels 1-7 of the 128 images' pyramids built by ft_build_pyramids
+    on every call: the pyramid kernel)."""
     import ctypes as C
 
     import torch
@@ -448,7 +450,18 @@ def run_profile(args, local_rank):
     torch.cuda.set_device(local_rank)
     B.build()
     n = args.warmup + args.steps
-    if args.workload == "extraction":
+    if args.workload == "pyramid":
+        frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
+        pb = PackedBatch(frames, device_pyramids=True)
+        pb.upload()
+        ctx = Context(device=local_rank, arena_bytes=64 << 20, max_frames=FRAMES)
+        pyrs = []
+        for f in range(FRAMES):
+            pyrs += [pb.pyramid(f, "L"), pb.pyramid(f, "R")]
+        arr = (L.ft_pyramid * len(pyrs))(*pyrs)
+        for _ in range(n):
+            L.check(ctx.lib.ft_build_pyramids(ctx.ptr, stream_handle(), None, len(pyrs), arr), "ft_build_pyramids")
+    elif args.workload == "extraction":
         frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES, nl_range=(1200, 1200))
         pb = PackedBatch(frames, device_pyramids=True)
         pb.upload()
@@ -792,6 +805,53 @@ def extraction_result(steps: int, warmup: int, dev, local_rank: int) -> dict:
 _STRESS_BASE: list = []
 
 
+def small_batch_result(steps: int, warmup: int, dev, local_rank: int) -> dict:
+    """Launch time of small batches (1, 8, 16 frames of the headline's
+    workload) with the search in two halves around the stereo step and in
+    one pass after it (ft_tuning.split_search), median of single launches
+    timed alone with L2 flushed: the per-frame latency side of the split."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2509_10757_gb300 import _lib as L
+    from paper_2509_10757_gb300 import scenes
+    from paper_2509_10757_gb300.batch import Context, PackedBatch, run_batch
+
+    frames = scenes.pinhole_batch(seed=0, n_frames=16)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for n in (1, 8, 16):
+        pb = PackedBatch(frames[:n], device=dev)
+        pb.upload()
+        row = {}
+        for name, split in (("two_halves_ms", 1), ("one_pass_ms", -1)):
+            ctx = Context(device=local_rank, arena_bytes=512 << 20, max_frames=16, use_graphs=True)
+            b = pb.batch()
+            t = L.ft_tuning(strip_rows=32, search_tile=512, fisheye_tile=128, resolve_tile=2048, ctas_per_sm=0,
+                            search_stage=0, split_search=split)
+            L.check(ctx.lib.ft_set_tuning(ctx.ptr, C.byref(b), C.byref(t)), "ft_set_tuning")
+            for _ in range(warmup):
+                run_batch(ctx, pb)
+            torch.cuda.synchronize(dev)
+            ev = []
+            for i in range(steps):
+                flush.fill_(i & 0xff)
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                run_batch(ctx, pb)
+                z.record()
+                ev.append((a, z))
+            torch.cuda.synchronize(dev)
+            assert ctx.sync_status() == 0
+            row[name] = statistics.median(a.elapsed_time(z) for a, z in ev)
+            ctx.close()
+        out[str(n)] = row
+    return {"frames": out, "steps": steps,
+            "form": "one context, one stream, CUDA graphs, L2 flushed before each launch, median of launches "
+                    "timed alone; default launch shape with the search in two halves or in one pass"}
+
+
 def stress_result(n: int, steps: int, warmup: int, dev, local_rank: int) -> dict:
     """The 1080p stress batch (8000 keypoints, 100k map points per frame, 8 %
     flips, 40 % distractors) of n frames, 16 distinct frames repeated."""
@@ -1121,6 +1181,9 @@ def run_gpu(args, rank, world, local_rank):
     clocks.mark("fisheye", True)
     fisheye = fisheye_result(max(20, min(args.steps, 300)), max(3, args.warmup), dev, local_rank)
     clocks.mark("fisheye", False)
+    clocks.mark("small", True)
+    small = small_batch_result(max(20, min(args.steps, 200)), max(3, args.warmup), dev, local_rank)
+    clocks.mark("small", False)
     clocks.mark("stress", True)
     stress = stress_result(32, max(10, min(args.steps, 60)), max(3, args.warmup), dev, local_rank)
     clocks.mark("stress", False)
@@ -1207,6 +1270,7 @@ def run_gpu(args, rank, world, local_rank):
                                 "duration": "the headline's timed region divided by its launches "
                                             "(launches overlap)"}},
         "fisheye": fisheye,
+        "small_batches": small,
         "stress": stress,
         "pose_optimization": pose,
         "extraction": extraction,
@@ -1230,9 +1294,10 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served", "configs"])
     ap.add_argument("--trace-out", default=None)
-    ap.add_argument("--workload", default="batched", choices=["batched", "stress", "fisheye", "pose", "extraction"],
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "stress", "fisheye", "pose", "extraction", "pyramid"],
                     help="workload of --mode trace (batched, stress, fisheye) or --mode profile (batched, pose, "
-                         "extraction)")
+                         "extraction, pyramid)")
     args = ap.parse_args()
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])
