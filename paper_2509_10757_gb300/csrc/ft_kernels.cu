@@ -22,6 +22,9 @@
 //   K_SEARCH   one tile of map points, one thread each: frustum test, FP32
 //              projection, predicted level, grid-window gather, top-2 Hamming,
 //              ratio test; accepted claims go to an atomicMin per keypoint.
+//              A frame whose search is split around its stereo step queues
+//              the first halves right after its stereo items (in the K_STEREO
+//              range) and the second halves as K_FINISH items.
 //   K_RESOLVE  one tile: final map-point -> keypoint and keypoint -> map
 //              point tables from the per-keypoint winners.
 // Floating point runs through __fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn /
@@ -1818,7 +1821,8 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
             }
             break;
         case K_STEREO:
-            if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);
+            if (tile >= F.n_stereo_items) search_item(B, F, tile - F.n_stereo_items, U, &s_flag);   // split
+            else if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);
             else stereo_fisheye_item(B, F, tile, U, &s_flag);
             break;
         case K_SEARCH: search_item(B, F, tile, U, &s_flag); break;
@@ -1832,7 +1836,7 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
                 asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
                 ft_trace_record r;
                 r.item = item;
-                r.kind = kind;
+                r.kind = (kind == K_STEREO && tile >= F.n_stereo_items) ? K_SEARCH : kind;
                 r.frame = lo;
                 r.sm = (int)sm;
                 r.t_start = t_start;
