@@ -225,12 +225,14 @@ def algorithmic_bytes(pb) -> int:
     return total
 
 
-def patch_sector_bytes(pb) -> tuple[int, int]:
-    """(byte-granular, sector-granular) bytes of the refined matches' patch
+def patch_sector_bytes(pb, seg: int = 32) -> tuple[int, int]:
+    """(byte-granular, segment-granular) bytes of the refined matches' patch
     rows: an 11-byte left row and a 21-byte right row per patch row touch
-    one or two 32-byte DRAM sectors each, depending on their address; the
-    second figure counts every distinct sector the launch's patches touch
-    once (what the patches must move from DRAM at least)."""
+    one or two aligned seg-byte segments each (32: L2 sectors; 128: the
+    lines DRAM moves), depending on their address; the second figure counts
+    every distinct segment the launch's patches touch once."""
+    sh = seg.bit_length() - 1
+    assert 1 << sh == seg
     sc = np.ones(16, np.float32)
     for l in range(1, 16):
         sc[l] = np.float32(sc[l - 1] * np.float32(1.2))
@@ -260,11 +262,11 @@ def patch_sector_bytes(pb) -> tuple[int, int]:
         pit_r = np.array([pr.pitch[l] for l in range(nl)], np.int64)[lv]
         for dy in range(-5, 6):
             a = base_l + (vl + dy) * pit_l + (ul - 5)
-            sectors += [a >> 5, (a + 10) >> 5]
+            sectors += [a >> sh, (a + 10) >> sh]
             a = base_r + (vl + dy) * pit_r + (ur0 - 10)
-            sectors += [a >> 5, (a + 20) >> 5]
+            sectors += [a >> sh, (a + 20) >> sh]
     n = len(np.unique(np.concatenate(sectors))) if sectors else 0
-    return byte_total, 32 * n
+    return byte_total, seg * n
 
 
 # ---------------------------------------------------------------- CPU oracle arm
@@ -437,7 +439,10 @@ def run_profile(args, local_rank):
     after the search), extraction (pyramids of the 128 images built once,
     then ft_extract_orb on them: the detect, select and describe kernels),
     pyramid (levels 1-7 of the 128 images' pyramids built by ft_build_pyramids
-    on every call: the pyramid kernel)."""
+    on every call: the pyramid kernel), scattered (ft_scattered_reads: one
+    4-byte read every 256 or 1024 bytes of a 1 GiB buffer, alone or with a
+    second read 32, 64 or 128 bytes after it; eight launches, warm-up and
+    steps ignored: the DRAM bytes an isolated read moves)."""
     import ctypes as C
 
     import torch
@@ -450,6 +455,16 @@ def run_profile(args, local_rank):
     torch.cuda.set_device(local_rank)
     B.build()
     n = args.warmup + args.steps
+    if args.workload == "scattered":
+        lib = L.load()
+        cases = []
+        for stride in (256, 1024):
+            for second in (0, 32, 64, 128):
+                acc = C.c_int(0)
+                L.check(lib.ft_scattered_reads(stream_handle(), stride, second, C.byref(acc)), "ft_scattered_reads")
+                cases.append({"stride": stride, "second": second, "accesses": acc.value})
+        print(json.dumps({"profile_run": "ok", "workload": "scattered", "launches": cases}), flush=True)
+        return
     if args.workload == "pyramid":
         frames = scenes.pinhole_batch(seed=0, n_frames=FRAMES)
         pb = PackedBatch(frames, device_pyramids=True)
@@ -1058,6 +1073,8 @@ def run_gpu(args, rank, world, local_rank):
     alg_bytes = algorithmic_bytes(pb)
     patch_b, patch_sec = patch_sector_bytes(pb)
     alg_sector = alg_bytes - patch_b + patch_sec
+    _, patch_line = patch_sector_bytes(pb, 128)
+    alg_line = alg_bytes - patch_b + patch_line
     peaks = measured_peaks()
     avg_launch_s = statistics.mean(step_ms) / 1e3
     achieved = alg_bytes / avg_launch_s / 1e9
@@ -1264,7 +1281,15 @@ def run_gpu(args, rank, world, local_rank):
                          "achieved": alg_sector / avg_launch_s / 1e9,
                          "frac": alg_sector / avg_launch_s / 1e9 / peaks["hbm_gbs"],
                          "note": "the same count with the refined matches' 11- and 21-byte patch rows taken as "
-                                 "the distinct 32-byte DRAM sectors they touch (what they must move at least)"},
+                                 "the distinct 32-byte sectors they touch"},
+                     "line_granular": {
+                         "algorithmic_bytes_per_launch": alg_line,
+                         "achieved": alg_line / avg_launch_s / 1e9,
+                         "frac": alg_line / avg_launch_s / 1e9 / peaks["hbm_gbs"],
+                         "traffic_over_this": (traffic / alg_line) if traffic else None,
+                         "note": "the patch rows taken as the distinct 128-byte lines they touch: on this GPU a "
+                                 "read that misses L2 moves a whole 128-byte line from DRAM (measured with "
+                                 "ft_scattered_reads under ncu), so this is what the launch must move at least"},
                      "stream": {"achieved": alg_bytes / (job_s / args.steps) / 1e9,
                                 "frac": alg_bytes / (job_s / args.steps) / 1e9 / peaks["hbm_gbs"],
                                 "duration": "the headline's timed region divided by its launches "
@@ -1295,9 +1320,9 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "trace", "profile", "served", "configs"])
     ap.add_argument("--trace-out", default=None)
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "stress", "fisheye", "pose", "extraction", "pyramid"],
+                    choices=["batched", "stress", "fisheye", "pose", "extraction", "pyramid", "scattered"],
                     help="workload of --mode trace (batched, stress, fisheye) or --mode profile (batched, pose, "
-                         "extraction, pyramid)")
+                         "extraction, pyramid, scattered)")
     args = ap.parse_args()
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])

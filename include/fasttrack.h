@@ -486,6 +486,16 @@ ft_status ft_pyramid_sizes(int width, int height, const ft_params *params, int *
  * of the paper's method.  Allocates and frees 4 KB of device memory. */
 ft_status ft_measure_popcount(void *stream, double *popc_per_s);
 
+/* Memory diagnostic (not part of the paper's method): one 4-byte read every
+ * stride_bytes (a multiple of 4, at least 256) over a 1 GiB buffer, plus a
+ * second read second_bytes (a multiple of 4, 0: none, less than stride_bytes)
+ * after each; one launch on the stream, waited for.  Read under a profiler's
+ * DRAM counters it shows how many bytes an isolated read moves from DRAM:
+ * the granularity that scattered reads, such as the refinement's patch rows,
+ * pay.  *accesses receives the number of first reads.  Allocates and frees
+ * 1 GiB of device memory. */
+ft_status ft_scattered_reads(void *stream, int stride_bytes, int second_bytes, int *accesses);
+
 /* Build levels 1..nlevels-1 of a pyramid from its level 0 on the device (the
  * paper runs ORB extraction, which produces the pyramid, on the GPU so that
  * the pyramid never crosses the bus; section IV-B).  Level l samples level 0

@@ -212,6 +212,7 @@ SIGNATURES = [
                              C.POINTER(ft_orb_out)]),
     ("ft_pyramid_sizes", i32, [i32, i32, C.POINTER(ft_params), vp, vp]),
     ("ft_measure_popcount", i32, [vp, C.POINTER(C.c_double)]),
+    ("ft_scattered_reads", i32, [vp, i32, i32, C.POINTER(i32)]),
     ("ft_build_pyramid", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_pyramid)]),
     ("ft_build_pyramids", i32, [vp, vp, C.POINTER(ft_params), i32, C.POINTER(ft_pyramid)]),
     ("ft_track_batch", i32, [vp, vp, C.POINTER(ft_params), C.POINTER(ft_batch)]),

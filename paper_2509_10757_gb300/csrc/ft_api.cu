@@ -833,6 +833,21 @@ namespace {
 // value the kernel writes so that nothing is optimised away.
 constexpr int kPopcIters = 4096;
 
+// One 4-byte read every stride_words words (and a second `second` words
+// later), folded into a value the kernel writes only if it is impossible.
+__global__ void __launch_bounds__(256) scattered_read_kernel(const int *a, long long stride_words, int n,
+                                                             int second, int *sink)
+{
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    int s = 0;
+    if (i < n) {
+        const int *p = a + (long long)i * stride_words;
+        s = __ldcg(p);
+        if (second) s += __ldcg(p + second);
+    }
+    if (s == 0x7fffffff) sink[0] = s;
+}
+
 __global__ void __launch_bounds__(256) popcount_rate_kernel(unsigned seed, unsigned *sink)
 {
     unsigned v[8];
@@ -1263,6 +1278,32 @@ ft_status ft_measure_popcount(void *stream, double *popc_per_s)
     cudaFree(sink);
     if (e != cudaSuccess) return fail(FT_ECUDA, "ft_measure_popcount: %s", cudaGetErrorString(e));
     *popc_per_s = (double)blocks * 256.0 * kPopcIters * 8.0 / (best_ms * 1e-3);
+    return FT_OK;
+}
+
+ft_status ft_scattered_reads(void *stream, int stride_bytes, int second_bytes, int *accesses)
+{
+    if (!accesses) return fail(FT_EINVAL, "ft_scattered_reads: NULL argument");
+    if (stride_bytes < 256 || (stride_bytes & 3) || second_bytes < 0 || (second_bytes & 3) ||
+        second_bytes >= stride_bytes)
+        return fail(FT_EINVAL, "ft_scattered_reads: stride %d, second read at %d", stride_bytes, second_bytes);
+    const size_t bytes = (size_t)1 << 30;
+    const int n = (int)(bytes / (size_t)stride_bytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    int *a = nullptr, *sink = nullptr;
+    FT_CUDA(cudaMalloc(&a, bytes));
+    cudaError_t e = cudaMalloc(&sink, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(a, 1, bytes, st);
+    if (e == cudaSuccess) {
+        // the last read: (n - 1) * stride + second + 4 <= n * stride <= 1 GiB
+        scattered_read_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, stride_bytes / 4, n, second_bytes / 4, sink);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(a);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return fail(FT_ECUDA, "ft_scattered_reads: %s", cudaGetErrorString(e));
+    *accesses = n;
     return FT_OK;
 }
 

@@ -98,3 +98,16 @@ def test_noalloc_checks_params_before_any_device_work(lib):
         r = so.ft_stereo_match_pinhole_noalloc(None, C.byref(p), C.byref(cam), C.byref(st), C.byref(out), None)
         assert r == lib.FT_EINVAL, over
         assert lib.last_error(), over
+
+
+def test_scattered_reads_checks_arguments_before_any_device_work(lib):
+    """The memory diagnostic refuses a missing output, a stride below 256 or
+    not a multiple of 4, and a second read outside the stride, before any
+    CUDA call (here on a machine without a GPU)."""
+    so = lib.load()
+    acc = C.c_int(-1)
+    assert so.ft_scattered_reads(None, 1024, 0, None) == lib.FT_EINVAL
+    for stride, second in ((128, 0), (1022, 0), (1024, 1024), (1024, -4), (1024, 6)):
+        assert so.ft_scattered_reads(None, stride, second, C.byref(acc)) == lib.FT_EINVAL, (stride, second)
+        assert lib.last_error()
+    assert acc.value == -1

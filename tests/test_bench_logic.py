@@ -64,3 +64,8 @@ def test_patch_sector_bytes_counts_distinct_sectors():
     # sector 3 (96..127): two sectors per row, shared by both patches
     # right rows: columns 50..70 (sectors 1, 2) and 290..310 (sector 9): 3 per row
     assert s == 32 * 11 * (2 + 3)
+    # 128-byte lines: left rows (bytes 95..105 and 96..106) share line 0;
+    # right rows 50..70 lie in line 0 of the right buffer, 290..310 in line 2
+    b, s = bench.patch_sector_bytes(pb, 128)
+    assert b == 2 * bench.PATCH_BYTES
+    assert s == 128 * 11 * (1 + 2)
