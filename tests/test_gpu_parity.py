@@ -738,11 +738,14 @@ def test_build_pyramids_many_images_in_one_launch(ctx, lib):
 @pytest.mark.parametrize("W,H,nlevels,scale,seed", [(752, 480, 8, 1.2, 752), (333, 77, 8, 1.2, 1),
                                                      (6000, 37, 6, 1.3, 2), (17, 9, 3, 1.5, 3),
                                                      (641, 203, 5, 2.0, 4), (2, 3, 4, 1.2, 5),
-                                                     (1000, 1000, 4, 3.5, 6)])
+                                                     (1000, 1000, 4, 3.5, 6), (753, 17, 8, 1.2, 7),
+                                                     (1504, 33, 6, 1.5, 8)])
 def test_build_pyramid_shapes_and_scales(ctx, lib, W, H, nlevels, scale, seed):
-    # odd widths (ragged last quads), flat and tiny images, a level wider than
-    # 4096, and scale factors whose levels take one 8-byte source window per
-    # four output pixels, one per pair and one per pixel; level 0's row
+    # odd widths, flat and tiny images, a level wider than 4096 (several
+    # column tiles of 752 source columns), level 0 one column and one row past
+    # a whole number of tiles (a last tile of one source column and a last
+    # slab of one source row) or exactly two tiles wide, and scale factors
+    # from 1.2 to 3.5; level 0's row
     # padding holds junk the result must not depend on, levels 1.. start as
     # junk and must come out zero past their width.  The first image has a
     # pixel (level 5, row 9, column 225) whose value is an exact tie, 177.5,
