@@ -360,7 +360,7 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
-KIND_NAMES = ("grid", "stereo", "search", "finish", "resolve", "pose")
+KIND_NAMES = ("grid", "stereo", "search", "resolve", "pose")
 
 
 def trace_summary(recs) -> dict:

@@ -324,12 +324,12 @@ typedef struct {
     int search_stage;       /* search candidates: 0 = a camera's keypoint records and descriptors
                                staged in shared memory when they fit (up to 1536 keypoints), else
                                read from L2; 1 = always read from L2 */
-    int split_search;       /* pinhole frames whose stereo runs in the same call: 1 = the search
-                               runs in two halves around the stereo step (the first, every test but
-                               the stereo consistency, need not wait for it: shorter launches of few
-                               frames), -1 = one pass after the stereo step (fewer work items: more
-                               throughput from overlapping launches), 0 = automatic (two halves for
-                               batches of at most 32 frames); results are the same */
+    int split_search;       /* pinhole frames whose stereo runs in the same call: 1 = a search item
+                               scans its candidates (every test but the stereo consistency) before
+                               it waits for the stereo step and applies the consistency after it,
+                               -1 = it waits for the stereo step first (less work: best for large
+                               batches), 0 = automatic (1 for batches of at most 32 frames); results
+                               are the same */
 } ft_tuning;
 
 /* Fill p with the default readings. */
@@ -556,9 +556,7 @@ ft_status ft_set_debug(ft_ctx *ctx, unsigned flags, uint64_t timeout_ns);
 
 /* Device-side trace of the fused kernel's work items (the tracing
  * subsystem): one record per item of the last call.  kind: 0 grid build,
- * 1 stereo, 2 search, 3 search finish (the stereo consistency and the
- * claims of a pinhole frame whose stereo runs in the same call), 4 conflict
- * resolution.  Times are the GPU global
+ * 1 stereo, 2 search, 3 conflict resolution.  Times are the GPU global
  * timer in ns; wait_ns is the part of [t_start, t_end] spent in bounded
  * waits on other items. */
 typedef struct {

@@ -668,12 +668,7 @@ ft_status build_table(ft_ctx *ctx, const ft_params &params, const std::vector<Jo
         F.n_search_items[1] = n_search[1];
         F.n_resolve_items[0] = n_resolve[0];
         F.n_resolve_items[1] = n_resolve[1];
-        // a split search's first halves follow the frame's stereo items in
-        // the queue (they need no stereo result), its finish items come
-        // after every search item
-        const int n_srch = n_search[0] + n_search[1];
-        const int per_kind[K_KINDS] = {n_index, F.split_search ? n_stereo + n_srch : n_stereo,
-                                       F.split_search ? 0 : n_srch, F.split_search ? n_srch : 0,
+        const int per_kind[K_KINDS] = {n_index, n_stereo, n_search[0] + n_search[1],
                                        n_resolve[0] + n_resolve[1]};
         for (int k = 0; k < K_KINDS; ++k) {
             prefix[k * (n + 1) + f] = counts[k];

@@ -46,13 +46,12 @@ __host__ __device__ inline int pyr_tiles(int W, int H)
 // Byte offsets within one pyramid image are 32-bit in the pyramid kernel.
 constexpr long long kPyrMaxLevelBytes = 1ll << 31;
 
-// work item kinds in queue order (a split search's finish items after every
-// search item, so that they never hold the search items back)
-enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_FINISH = 3, K_RESOLVE = 4, K_KINDS = 5 };
+// work item kinds, in queue order
+enum Kind { K_INDEX = 0, K_STEREO = 1, K_SEARCH = 2, K_RESOLVE = 3, K_KINDS = 4 };
 
 // per-frame counter slots
 enum Ctr { C_GRID_DONE = 0, C_STEREO_DONE = 1, C_STEREO_READY = 2, C_SEARCH_DONE0 = 3,
-           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5, C_SCAN_DONE0 = 6, C_SCAN_DONE1 = 7 };
+           C_SEARCH_DONE1 = 4, C_ROWS_DONE = 5 };
 
 // device status bits (ORed into the context's status word)
 constexpr unsigned kStatusTimeout = 1u;
@@ -148,8 +147,8 @@ struct FrameDev {
     int rowsort;                   // row-sort index items (kRowSortItems: the first half the left
                                    // keypoints, the second half the right ones), 0 without stereo
     int fold_resolve;              // 1: the last search item of a camera writes the final tables
-    int split_search;              // 1: search items skip the stereo consistency and need not wait for the
-                                   // stereo step; finish items (one per search item) apply it after
+    int split_search;              // 1: search items scan their candidates before waiting for the stereo
+                                   // step and apply the stereo consistency after it
     int n_grid_items, n_index_items, n_search_items[2], n_resolve_items[2];
     unsigned *ctr;                 // [kCounters]
     // pose optimization (next row f4): the pose kernel, launched after the

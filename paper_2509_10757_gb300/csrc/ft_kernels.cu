@@ -22,9 +22,9 @@
 //   K_SEARCH   one tile of map points, one thread each: frustum test, FP32
 //              projection, predicted level, grid-window gather, top-2 Hamming,
 //              ratio test; accepted claims go to an atomicMin per keypoint.
-//              A frame whose search is split around its stereo step queues
-//              the first halves right after its stereo items (in the K_STEREO
-//              range) and the second halves as K_FINISH items.
+//              A frame whose search is split around its stereo step scans its
+//              candidates before waiting for the stereo step and applies the
+//              stereo consistency after it, in the same item.
 //   K_RESOLVE  one tile: final map-point -> keypoint and keypoint -> map
 //              point tables from the per-keypoint winners.
 // Floating point runs through __fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn /
@@ -1582,7 +1582,7 @@ __device__ void search_setup(const FrameDev &F, int cam, SmemSearch &Q, float &i
 }
 
 // Defined outputs of map points [m0, m1) after a wait ran out (reported in
-// the status word), and an empty first half of a split search.
+// the status word).
 __device__ void search_abandon(const CamDev &C, int m0, int m1)
 {
     for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) {
@@ -1591,24 +1591,13 @@ __device__ void search_abandon(const CamDev &C, int m0, int m1)
         C.mp_d1[m] = -1;
         C.mp_d2[m] = -1;
         C.mp_kp[m] = -1;
-        if (C.scan) {
-            C.scan[2 * m] = make_uint4(kNoKey, kNoKey, kNoKey, kNoKey);
-            C.scan[2 * m + 1] = make_uint4(0u, 0u, 0u, 0u);
-        }
     }
 }
 
-// The last search (or finish) item of a camera: counts, and for small frames
-// the final tables.
-__device__ void search_done(const FrameDev &F, int cam, int *s_flag)
-{
-    if (signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag) && F.fold_resolve)
-        resolve_range(F.cam[cam], F.nm, 0, max(F.nm, F.cam[cam].nk));
-}
-
 // A tile of map points.  A frame whose search is split around its stereo
-// step (split_search) runs the first half here without waiting for the
-// stereo step; its finish items complete the points.
+// step (split_search) runs the first half of every point without waiting
+// for the stereo step, then waits for it and finishes the points: the first
+// half overlaps the wait.
 __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U, int *s_flag)
 {
     const int cam = tile < F.n_search_items[0] ? 0 : 1;
@@ -1652,6 +1641,9 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
         __syncthreads();
         mark(B, 0);
         if (split) {
+            // first halves (the staged records' right coordinates are not
+            // read: they may not be final yet), then the stereo step, then
+            // the second halves; each thread finishes the points it scanned
             if (staged) {
                 for (int m = m0 + tid; m < m1; m += kThreads)
                     search_point<true, true>(B.p, F, C, Q, scell, iw, ih, m, motion);
@@ -1659,47 +1651,30 @@ __device__ void search_item(const BatchHeader &B, const FrameDev &F, int tile, S
                 for (int m = m0 + tid; m < m1; m += kThreads)
                     search_point<false, true>(B.p, F, C, Q, nullptr, iw, ih, m, motion);
             }
+            mark(B, 1);
+            if (wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag)) {
+                for (int m = m0 + tid; m < m1; m += kThreads) finish_point(B.p, F, C, Q, iw, ih, m, motion);
+            } else {
+                search_abandon(C, m0, m1);
+            }
+            mark(B, 2);
         } else if (staged) {
             for (int m = m0 + tid; m < m1; m += kThreads) search_point<true>(B.p, F, C, Q, scell, iw, ih, m, motion);
+            mark(B, 1);
         } else {
             for (int m = m0 + tid; m < m1; m += kThreads)
                 search_point<false>(B.p, F, C, Q, nullptr, iw, ih, m, motion);
+            mark(B, 1);
         }
-        mark(B, 1);
     } else {
         search_abandon(C, m0, m1);
     }
-    if (split) signal_count(&F.ctr[C_SCAN_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag);
-    else search_done(F, cam, s_flag);
-}
-
-// The second half of a split search for a tile of map points: waits for the
-// first halves of the camera's tiles (the scan state) and for the frame's
-// stereo step, then finish_point for each point.  The first halves were
-// dequeued before any finish item, so the wait always ends.
-__device__ void finish_item(const BatchHeader &B, const FrameDev &F, int tile, Smem &U, int *s_flag)
-{
-    const int cam = tile < F.n_search_items[0] ? 0 : 1;
-    const int t = cam ? tile - F.n_search_items[0] : tile;
-    const int m0 = t * F.search_tile;
-    const int m1 = min(F.nm, m0 + F.search_tile);
-    bool ok = wait_geq(B, &F.ctr[C_SCAN_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag);
-    if (ok) ok = wait_geq(B, &F.ctr[C_STEREO_READY], 1u, s_flag);
-    if (ok) ok = wait_geq(B, &F.ctr[C_GRID_DONE], (unsigned)F.n_grid_items, s_flag);
-    const CamDev &C = F.cam[cam];
-    if (ok) {
-        SmemSearch &Q = U.q;
-        float iw, ih;
-        int motion;
-        search_setup(F, cam, Q, iw, ih, motion);
-        __syncthreads();
-        mark(B, 0);
-        for (int m = m0 + (int)threadIdx.x; m < m1; m += kThreads) finish_point(B.p, F, C, Q, iw, ih, m, motion);
-        mark(B, 1);
-    } else {
-        search_abandon(C, m0, m1);
+    if (signal_count(&F.ctr[C_SEARCH_DONE0 + cam], (unsigned)F.n_search_items[cam], s_flag) &&
+        F.fold_resolve) {
+        // the last search item of this camera also writes the final tables
+        // (small frames: no separate resolve items wait for the search)
+        resolve_range(F.cam[cam], F.nm, 0, max(F.nm, F.cam[cam].nk));
     }
-    search_done(F, cam, s_flag);
 }
 
 // ---------------------------------------------------------------- K_RESOLVE
@@ -1821,12 +1796,10 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
             }
             break;
         case K_STEREO:
-            if (tile >= F.n_stereo_items) search_item(B, F, tile - F.n_stereo_items, U, &s_flag);   // split
-            else if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);
+            if (F.camera == FT_CAMERA_PINHOLE) stereo_pinhole_item(B, F, tile, U, &s_flag);
             else stereo_fisheye_item(B, F, tile, U, &s_flag);
             break;
         case K_SEARCH: search_item(B, F, tile, U, &s_flag); break;
-        case K_FINISH: finish_item(B, F, tile, U, &s_flag); break;
         default: resolve_item(B, F, tile, &s_flag); break;
         }
         if (B.trace != nullptr && threadIdx.x == 0) {
@@ -1836,7 +1809,7 @@ __global__ void __launch_bounds__(kThreads, FT_MIN_CTAS_PER_SM) ft_fused_kernel(
                 asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
                 ft_trace_record r;
                 r.item = item;
-                r.kind = (kind == K_STEREO && tile >= F.n_stereo_items) ? K_SEARCH : kind;
+                r.kind = kind;
                 r.frame = lo;
                 r.sm = (int)sm;
                 r.t_start = t_start;

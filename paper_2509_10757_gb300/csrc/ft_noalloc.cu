@@ -241,7 +241,7 @@ ft_status ft_stereo_match_pinhole_noalloc(void *stream, const ft_params *params,
     F.n_index_items = kRowSortItems;
     F.ctr = reinterpret_cast<unsigned *>(d + o_ctr);
     int *prefix = reinterpret_cast<int *>(host + o_prefix);
-    const int per_kind[K_KINDS] = {kRowSortItems, F.n_stereo_items, 0, 0, 0};
+    const int per_kind[K_KINDS] = {kRowSortItems, F.n_stereo_items, 0, 0};
     int total = 0;
     for (int k = 0; k < K_KINDS; ++k) {
         prefix[2 * k] = 0;
