@@ -751,9 +751,17 @@ def test_build_pyramid_shapes_and_scales(ctx, lib, W, H, nlevels, scale, seed):
     # pixel (level 5, row 9, column 225) whose value is an exact tie, 177.5,
     # only when both products are rounded before the sum: a fused
     # multiply-add there gives 177 instead of 178.
-    from paper_2509_10757_gb300.batch import stream_handle
     rng = np.random.default_rng(seed)
     img = rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+    _check_built_pyramid(ctx, lib, img, nlevels, scale, rng)
+
+
+def _check_built_pyramid(ctx, lib, img, nlevels, scale, rng):
+    """Build levels 1.. of img's pyramid with ft_build_pyramid into buffers
+    whose row padding (level 0) and contents (levels 1..) start as junk, and
+    compare every level with the oracle's; bytes from a level's width to its
+    width rounded up to 4 must come out zero."""
+    from paper_2509_10757_gb300.batch import stream_handle
     ref = orc.build_pyramid(img, nlevels, scale)
     p = _params(lib, {"nlevels": nlevels, "scale_factor": scale})
     pyr = lib.ft_pyramid()
@@ -775,9 +783,33 @@ def test_build_pyramid_shapes_and_scales(ctx, lib, W, H, nlevels, scale, seed):
         h, w = ref[l].shape
         got = bufs[l].cpu().numpy().reshape(h, -1)
         bad = np.argwhere(got[:, :w] != ref[l])
-        assert len(bad) == 0, (l, len(bad), bad[:4].tolist())
+        assert len(bad) == 0, (img.shape, nlevels, scale, l, len(bad), bad[:4].tolist())
         w4 = (w + 3) // 4 * 4
         assert not got[:, w:w4].any(), l
+
+
+def test_build_pyramid_random_shapes(ctx, lib):
+    # seeded random image sizes (2-3000 x 2-600), scale factors (1.05-3.0)
+    # and level counts (as many as keep every level at least one pixel, at
+    # most 8), smooth and noisy content; every level equals the oracle's
+    rng = np.random.default_rng(2024)
+    for case in range(12):
+        W, H = int(rng.integers(2, 3001)), int(rng.integers(2, 601))
+        scale = float(np.float32(rng.uniform(1.05, 3.0)))
+        nl = 1
+        sc = np.float32(1.0)
+        while nl < 8:
+            nxt = np.float32(sc * np.float32(scale))
+            if round(W / float(nxt)) < 1 or round(H / float(nxt)) < 1:
+                break
+            sc, nl = nxt, nl + 1
+        if case % 2:
+            img = rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+        else:
+            yy, xx = np.mgrid[0:H, 0:W]
+            img = (127.5 + 127.5 * np.sin(xx / 7.3 + rng.uniform(0, 6)) * np.cos(yy / 5.1)).astype(np.uint8)
+        if nl >= 2:
+            _check_built_pyramid(ctx, lib, img, nl, scale, rng)
 
 
 def _split_search_rescans(fr, out, params):
