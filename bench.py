@@ -520,6 +520,7 @@ def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batc
     d.hbm_budget = 8 << 30
     d.n_slots, d.max_batch = n_slots, max_batch
     d.slot_arena_bytes = 512 << 20
+    d.queue_depth = SERVE_QUEUE_DEPTH
     srv = C.c_void_p()
     L.check(L.ft_server_create(C.byref(srv), C.byref(d), None), "ft_server_create")
     hosts, sids = [], []
@@ -590,10 +591,11 @@ def serve_load(frames, L, rate_hz: float, seconds: float, n_slots: int, max_batc
     return {"value": served_units / span, "unit": UNIT, "offered_hz": rate_hz * len(frames), "images": images,
             "completed": len(done), "dropped": dropped[0], "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_batch": stats.frames_launched / max(1, stats.batches),
-            "slots": n_slots, "max_batch": max_batch, "seconds": seconds}
+            "slots": n_slots, "max_batch": max_batch, "queue_depth": SERVE_QUEUE_DEPTH, "seconds": seconds}
 
 
 SERVED_RATES_HZ = (30.0, 60.0, 120.0, 240.0)      # per stream, batched server (3 slots, up to 64 frames)
+SERVE_QUEUE_DEPTH = 4    # requests a stream may have waiting in the served sweeps (both forms)
 PLAIN_RATES_HZ = (2.0, 4.0, 8.0, 12.0, 16.0, 30.0)  # per stream, plain form (1 slot, 1 frame per launch)
 P99_BOUNDS_MS = (1.0, 33.0)                         # 1 ms, and one frame period at 30 Hz
 MAX_DROP_FRAC = 0.001

@@ -608,6 +608,8 @@ typedef struct {
     size_t slot_arena_bytes;    /* scratch arena of each slot's context */
     int dry_run;                /* 1: no GPU, fake completions */
     double dry_run_latency_us;  /* fake batch duration */
+    int queue_depth;            /* requests a stream may have waiting (staged at submit), 1-8
+                                   (0: 2); one more is refused with FT_EBUSY */
 } ft_server_desc;
 
 /* A camera stream: its model, pyramid level sizes (pinhole; level pitch =

@@ -153,7 +153,8 @@ class ft_trace_record(C.Structure):
 
 class ft_server_desc(C.Structure):
     _fields_ = [("device", i32), ("hbm_budget", C.c_size_t), ("n_slots", i32), ("max_batch", i32),
-                ("slot_arena_bytes", C.c_size_t), ("dry_run", i32), ("dry_run_latency_us", C.c_double)]
+                ("slot_arena_bytes", C.c_size_t), ("dry_run", i32), ("dry_run_latency_us", C.c_double),
+                ("queue_depth", i32)]
 
 
 class ft_stream_desc(C.Structure):

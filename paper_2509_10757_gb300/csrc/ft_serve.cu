@@ -163,6 +163,8 @@ OutLayout out_layout(int camera, int nl, int nr, int m)
     return L;
 }
 
+constexpr int kMaxQueue = 8;       // waiting requests a stream may be configured for, at most
+
 struct StreamState {
     bool open = false;
     ft_stream_desc desc{};
@@ -171,11 +173,11 @@ struct StreamState {
     size_t o_pyrL[FT_MAX_LEVELS] = {}, o_pyrR[FT_MAX_LEVELS] = {};
     size_t o_pos = 0, o_nrm = 0, o_mdesc = 0, o_skip = 0, o_dyn = 0, o_out = 0;
     int map_n = 0;
-    char *h_dyn[2] = {nullptr, nullptr};   // pinned staging of two requests
-    int dyn_used[2] = {0, 0};
-    char *h_out[2] = {nullptr, nullptr};   // pinned copies of two results
-    char *h_img[2] = {nullptr, nullptr};   // pinned level-0 images of two requests (left, then right;
-                                           // allocated at the first request that carries images)
+    char *h_dyn[kMaxQueue] = {};   // pinned staging of the waiting requests (queue_depth of them)
+    int dyn_used[kMaxQueue] = {};
+    char *h_out[2] = {nullptr, nullptr};   // pinned copies of two results (one request runs at a time)
+    char *h_img[kMaxQueue] = {};   // pinned level-0 images of the waiting requests (left, then right;
+                                   // allocated at the first request that carries images)
     int next_out = 0;
     bool in_flight = false;
     int queued = 0;
@@ -215,6 +217,7 @@ struct ft_server {
     ft_server_desc desc{};
     ft_params params{};
     bool dry = false;
+    int depth = 2;                     // requests a stream may have waiting
     char *pool_mem = nullptr;
     Pool *pool = nullptr;
     std::deque<StreamState> streams;   // a deque: references stay valid while streams open
@@ -231,6 +234,20 @@ struct ft_server {
 };
 
 namespace {
+
+// The pinned staging of a stream (null entries skipped).
+void free_staging(StreamState &S)
+{
+    for (int b = 0; b < kMaxQueue; ++b) {
+        if (S.h_dyn[b]) cudaFreeHost(S.h_dyn[b]);
+        if (S.h_img[b]) cudaFreeHost(S.h_img[b]);
+        S.h_dyn[b] = S.h_img[b] = nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (S.h_out[b]) cudaFreeHost(S.h_out[b]);
+        S.h_out[b] = nullptr;
+    }
+}
 
 void CUDART_CB host_done(void *p)
 {
@@ -479,8 +496,11 @@ ft_status ft_server_create(ft_server **out, const ft_server_desc *desc, const ft
     const ft_server_desc &d = *desc;
     if (d.n_slots < 1 || d.n_slots > 64 || d.max_batch < 1 || d.max_batch > 4096 || d.hbm_budget == 0)
         return fail(FT_EINVAL, "ft_server_create: bad slots / batch / budget");
+    if (d.queue_depth < 0 || d.queue_depth > kMaxQueue)
+        return fail(FT_EINVAL, "ft_server_create: queue depth %d outside 0-%d", d.queue_depth, kMaxQueue);
     ft_server *s = new ft_server();
     s->desc = d;
+    s->depth = d.queue_depth > 0 ? d.queue_depth : 2;
     s->dry = d.dry_run != 0;
     if (params) s->params = *params;
     else ft_params_default(&s->params);
@@ -535,13 +555,7 @@ void ft_server_destroy(ft_server *s)
         if (sl->ctx) ft_destroy(sl->ctx);
         delete sl;
     }
-    for (StreamState &S : s->streams) {
-        for (int b = 0; b < 2; ++b) {
-            if (S.h_dyn[b]) cudaFreeHost(S.h_dyn[b]);
-            if (S.h_out[b]) cudaFreeHost(S.h_out[b]);
-            if (S.h_img[b]) cudaFreeHost(S.h_img[b]);
-        }
-    }
+    for (StreamState &S : s->streams) free_staging(S);
     if (s->pool_mem) cudaFree(s->pool_mem);
     delete s->pool;
     delete s;
@@ -575,15 +589,12 @@ ft_status ft_server_open_stream(ft_server *s, const ft_stream_desc *d, int *stre
         const size_t dynb = dyn_layout(d->max_left, d->max_right).bytes;
         const size_t outb = out_layout(d->camera, d->max_left, d->max_right, d->max_map).bytes;
         bool ok = true;
-        for (int b = 0; b < 2 && ok; ++b) {
-            ok = cudaMallocHost(&S.h_dyn[b], std::max<size_t>(dynb, 16)) == cudaSuccess &&
-                 cudaMallocHost(&S.h_out[b], std::max<size_t>(outb, 16)) == cudaSuccess;
-        }
+        for (int b = 0; b < s->depth && ok; ++b)
+            ok = cudaMallocHost(&S.h_dyn[b], std::max<size_t>(dynb, 16)) == cudaSuccess;
+        for (int b = 0; b < 2 && ok; ++b)
+            ok = cudaMallocHost(&S.h_out[b], std::max<size_t>(outb, 16)) == cudaSuccess;
         if (!ok) {
-            for (int b = 0; b < 2; ++b) {
-                if (S.h_dyn[b]) cudaFreeHost(S.h_dyn[b]);
-                if (S.h_out[b]) cudaFreeHost(S.h_out[b]);
-            }
+            free_staging(S);
             s->pool->release(off, bytes);
             return fail(FT_ENOMEM, "pinned staging for the stream could not be allocated");
         }
@@ -614,11 +625,7 @@ ft_status ft_server_close_stream(ft_server *s, int sid)
     StreamState &S = s->streams[sid];
     if (S.in_flight || S.queued > 0) return fail(FT_EBUSY, "stream %d has requests in flight", sid);
     s->pool->release(S.off, S.bytes);
-    for (int b = 0; b < 2; ++b) {
-        if (S.h_dyn[b]) cudaFreeHost(S.h_dyn[b]);
-        if (S.h_out[b]) cudaFreeHost(S.h_out[b]);
-        if (S.h_img[b]) cudaFreeHost(S.h_img[b]);
-    }
+    free_staging(S);
     S = StreamState();
     s->stats.streams_open -= 1;
     return FT_OK;
@@ -708,12 +715,12 @@ ft_status ft_server_submit(ft_server *s, const ft_request *req)
             lp0 = level_pitch(S.desc, 0);
         }
         r.buf = -1;
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < s->depth; ++b)
             if (!S.dyn_used[b]) {
                 r.buf = b;
                 break;
             }
-        if (r.buf < 0) return fail(FT_EBUSY, "stream %d already has two requests waiting", r.sid);
+        if (r.buf < 0) return fail(FT_EBUSY, "stream %d already has %d requests waiting", r.sid, s->depth);
         if (r.images && !s->dry && !S.h_img[r.buf] &&
             cudaMallocHost(&S.h_img[r.buf], 2 * lp0 * (size_t)H0) != cudaSuccess) {
             S.h_img[r.buf] = nullptr;

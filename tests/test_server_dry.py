@@ -4,7 +4,9 @@ completions instead of GPU work (the failure and timing are made on the
 host).  Checks: admission refuses a stream the budget cannot hold and
 accepts it once another stream closes; a stream's requests complete in
 submit order and never overlap; batches never exceed max_batch and hold at
-most one request per stream; every request completes; requests with level-0
+most one request per stream; a stream holds as many requests as the queue
+depth (two by default) and refuses one more; every request completes;
+requests with level-0
 images are checked at submit (pinhole streams only, both images, a pitch of
 at least the width, stream levels of the sizes the device would build)."""
 import ctypes as C
@@ -24,10 +26,10 @@ def L():
     return _lib
 
 
-def make_server(L, budget=64 << 20, slots=2, max_batch=4, latency_us=300.0):
+def make_server(L, budget=64 << 20, slots=2, max_batch=4, latency_us=300.0, depth=0):
     d = L.ft_server_desc()
     L.ft_server_desc_default(C.byref(d))
-    d.hbm_budget, d.n_slots, d.max_batch = budget, slots, max_batch
+    d.hbm_budget, d.n_slots, d.max_batch, d.queue_depth = budget, slots, max_batch, depth
     d.dry_run, d.dry_run_latency_us = 1, latency_us
     s = C.c_void_p()
     L.check(L.ft_server_create(C.byref(s), C.byref(d), None), "server")
@@ -170,5 +172,29 @@ def test_request_images_are_checked_at_submit(L, frames):
         assert L.ft_server_submit(s, C.byref(hp.request(sb.value, 5))) == L.FT_OK   # no images: accepted
         assert L.ft_server_submit(s, C.byref(hp.request(sp, 6, images=True))) == L.FT_OK
         assert sorted(t for t, *_ in drain(L, s, 2)) == [5, 6]
+    finally:
+        L.ft_server_destroy(s)
+
+
+def test_queue_depth_bounds_the_waiting_requests(L, frames):
+    from paper_2509_10757_gb300.batch import HostFrame
+    d = L.ft_server_desc()
+    L.ft_server_desc_default(C.byref(d))
+    d.dry_run = 1
+    for bad in (-1, 9):
+        d.queue_depth = bad
+        s = C.c_void_p()
+        assert L.ft_server_create(C.byref(s), C.byref(d), None) == L.FT_EINVAL
+        assert not s.value
+    s = make_server(L, latency_us=3000.0, depth=4)
+    try:
+        hf = HostFrame(frames[0])
+        sid = open_stream(L, s, frames[0])[1]
+        for tag in range(4):
+            L.check(L.ft_server_submit(s, C.byref(hf.request(sid, tag))), "submit")
+        assert L.ft_server_submit(s, C.byref(hf.request(sid, 99))) == L.FT_EBUSY
+        assert "4 requests waiting" in L.last_error()
+        done = drain(L, s, 4)
+        assert [x[0] for x in done] == [0, 1, 2, 3]
     finally:
         L.ft_server_destroy(s)
