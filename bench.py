@@ -1216,7 +1216,7 @@ def run_gpu(args, rank, world, local_rank):
     served = None
     if rank == 0 and world == 1 and not args.no_served:
         clocks.mark("served", True)
-        served = run_served(args, local_rank, seconds=2.0)
+        served = run_served(args, local_rank, seconds=4.0)
         clocks.mark("served", False)
     clk = clocks.stop()
     def tuning_of(t):
