@@ -1192,7 +1192,8 @@ ft_status ft_extract_orb(ft_ctx *ctx, void *stream, const ft_params *params, int
             L.w = pyr[i].width[l];
             L.h = pyr[i].height[l];
             L.pitch = pyr[i].pitch[l];
-            L.smooth = reinterpret_cast<uint8_t *>(carve((size_t)L.w * L.h));
+            L.spitch = (L.w + 15) & ~15;
+            L.smooth = reinterpret_cast<uint8_t *>(carve((size_t)L.spitch * L.h));
             // suppressed corners are never 8-neighbours: at most one per 2 x 2 block
             L.cand_cap = ((L.w + 1) / 2) * ((L.h + 1) / 2);
             L.cand = reinterpret_cast<unsigned *>(carve(sizeof(unsigned) * (size_t)L.cand_cap));

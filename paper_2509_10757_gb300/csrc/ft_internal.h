@@ -187,7 +187,8 @@ constexpr int kOrbSelectThreads = 1024;
 struct OrbLevel {
     const uint8_t *img;                 // level image
     int w, h, pitch;
-    uint8_t *smooth;                    // [h][w] binomial-smoothed level (scratch)
+    uint8_t *smooth;                    // [h][spitch] binomial-smoothed level (scratch)
+    int spitch;                         // its row pitch: w rounded up to 16 bytes
     unsigned *cand;                     // [cand_cap] suppressed corners as keys (scratch)
     int cand_cap;
     int tiles_x, tile0;                 // tiles per row, first tile of the level in the image

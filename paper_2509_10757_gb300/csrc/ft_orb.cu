@@ -11,17 +11,23 @@
 //
 // Three launches per call, each over every image of the call:
 //   detect    one block of 256 threads per 32x32 tile of a level: the tile
-//             and a 4-pixel halo in shared memory, the FAST score of every
-//             pixel of the tile and its one-pixel ring (two pixels per step
-//             in packed 16-bit lanes), suppression against the eight
-//             neighbours, the kept corners appended as keys
-//             (255 - score) << 24 | y << 12 | x (one atomic per warp), and
-//             the smoothed level written from the same tile (separable);
+//             and a 4-pixel halo in shared memory as two planes of packed
+//             pixel pairs, the FAST score of every pixel of the tile and its
+//             one-pixel ring (two pixels per step in 16-bit lanes, both
+//             polarities by three-input packed min/max), a 16-bit
+//             suppression key per pixel that orders score and raster
+//             position at once, suppression as one comparison with the
+//             eight neighbours' largest key, the kept corners appended as
+//             keys (255 - score) << 24 | y << 12 | x (one atomic per warp),
+//             and the smoothed level written from the same tile (separable,
+//             two pixels per word);
 //   select    one block per (image, level): the max_kp-th smallest key by an
 //             exact 4 x 8-bit radix select over the level's corners, the
 //             keys up to it gathered and sorted (bitonic) in shared memory;
-//   describe  one warp per output slot: the moments over the disk (lanes
-//             stride over it, integer warp sums), the orientation, and lane b
+//   describe  one warp per output slot: the keypoint's two neighbourhoods
+//             (level and smoothed level) copied to shared memory in one
+//             round trip of 16-byte asynchronous copies, the moments over
+//             the disk (integer warp sums), the orientation, and lane b
 //             computes descriptor byte b (tests 8b .. 8b+7).
 // Integer work is exact; the orientation and the rotated test positions use
 // IEEE-rounded FP32 (and one double square root) in the order the reading
@@ -37,13 +43,15 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kDetThreads = 256;
-constexpr int kTileW = kOrbTile + 2 * kOrbHalo;     // tile + halo
+constexpr int kTileW = kOrbTile + 2 * kOrbHalo;     // tile + halo: 40 columns and rows
+constexpr int kHalfW = kTileW / 2;                  // words per row of a pixel-pair plane
 constexpr int kRing = kOrbTile + 2;                 // tile + suppression ring
-constexpr int kRows = kOrbTile / (kDetThreads / kOrbTile);   // output rows per thread
+constexpr int kPairs = kRing / 2;                   // pixel pairs per ring row (= words per key row)
+constexpr int kHsW = kOrbTile / 2 + 1;              // words per row of horizontal sums (+1: no bank conflicts)
 constexpr int kDescribeWarps = 8;
+static_assert(kDetThreads == 8 * kOrbTile, "suppression: 16 pairs x 2 rows per warp, 2 steps");
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-__device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 
 // Offsets of the 16 pixels of the radius-3 circle, clockwise from (0, -3):
 // x offsets 0 1 2 3 3 3 2 1 0 -1 -2 -3 -3 -3 -2 -1, stored + 3 as 4-bit
@@ -56,51 +64,51 @@ __device__ __forceinline__ int circle_dx(int i)
 }
 __device__ __forceinline__ int circle_dy(int i) { return circle_dx((i + 12) & 15); }
 
-// binomial weights 1 4 6 4 1
-__device__ __forceinline__ int binomial5(int j) { return j == 2 ? 6 : ((j & 1) ? 4 : 1); }
+// lane-wise minimum / maximum of two pixel pairs (16-bit lanes)
+__device__ __forceinline__ unsigned vmin2(unsigned a, unsigned b) { return __vminu2(a, b); }
+__device__ __forceinline__ unsigned vmax2(unsigned a, unsigned b) { return __vmaxu2(a, b); }
 
-// FAST-9 scores of the horizontally adjacent pixels (cx, cy) and (cx + 1, cy)
-// of the shared tile, -1 where a pixel is not a corner at t.  The score is
-// the best arc's smallest difference minus one, over both polarities.  The
-// pair's 16 circle differences travel as biased 16-bit lanes (v - c + 256 in
-// [1, 511], the first pixel in the low lane): minima (bright) and maxima
-// (dark) over windows of 3, then of 9, by three-input packed min/max, then
-// the best window.  Every pixel gets its score (no branch on the segment
-// test): a corner is a pixel whose best arc exceeds t.
-__device__ __forceinline__ void fast_score2(const uint8_t (*raw)[kTileW], int cx, int cy, int t, int &s0, int &s1)
+// The best arc of a pixel pair's 16 circle values v (one pixel per 16-bit
+// lane): for kBright the largest, over the 16 arcs of 9 contiguous circle
+// pixels, of the arc's smallest value; otherwise the smallest of the arcs'
+// largest values.  Three-input packed min/max: the extremes of the 16 arcs
+// of 3, those of the arcs of 9 as three arcs of 3 (i, i + 3, i + 6), then
+// the best of the 16 in a tree (40 operations per polarity; the form with
+// running extremes over blocks of 9, 57 two-input operations, measured 4 %
+// slower over the whole extraction).
+template <bool kBright>
+__device__ __forceinline__ unsigned best_arc(const unsigned (&v)[16])
 {
-    const unsigned c = (unsigned)raw[cy][cx] | ((unsigned)raw[cy][cx + 1] << 16);
-    unsigned b[16];
+    auto in3 = [](unsigned a, unsigned b, unsigned c) { return kBright ? __vimin3_u16x2(a, b, c) : __vimax3_u16x2(a, b, c); };
+    auto out3 = [](unsigned a, unsigned b, unsigned c) { return kBright ? __vimax3_u16x2(a, b, c) : __vimin3_u16x2(a, b, c); };
+    unsigned w3[16], w[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int yy = cy + circle_dy(i), xx = cx + circle_dx(i);
-        b[i] = ((unsigned)raw[yy][xx] | ((unsigned)raw[yy][xx + 1] << 16)) + 0x01000100u - c;
-    }
-    unsigned lo3[22], hi3[22];
+    for (int i = 0; i < 16; ++i) w3[i] = in3(v[i], v[(i + 1) & 15], v[(i + 2) & 15]);
 #pragma unroll
-    for (int i = 0; i < 22; ++i) {
-        lo3[i] = __vimin3_u16x2(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
-        hi3[i] = __vimax3_u16x2(b[i & 15], b[(i + 1) & 15], b[(i + 2) & 15]);
-    }
-    unsigned best_lo = 0u, least_hi = 0xffffffffu;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const unsigned m = __vimin3_u16x2(lo3[i], lo3[i + 3], lo3[i + 6]);
-        const unsigned M = __vimax3_u16x2(hi3[i], hi3[i + 3], hi3[i + 6]);
-        best_lo = __vimax3_u16x2(best_lo, m, m);
-        least_hi = __vimin3_u16x2(least_hi, M, M);
-    }
-    const int b0 = imax((int)(best_lo & 0xffffu) - 256, 256 - (int)(least_hi & 0xffffu));
-    const int b1 = imax((int)(best_lo >> 16) - 256, 256 - (int)(least_hi >> 16));
-    s0 = b0 > t ? b0 - 1 : -1;
-    s1 = b1 > t ? b1 - 1 : -1;
+    for (int i = 0; i < 16; ++i) w[i] = in3(w3[i], w3[(i + 3) & 15], w3[(i + 6) & 15]);
+    const unsigned r0 = out3(w[0], w[1], w[2]), r1 = out3(w[3], w[4], w[5]), r2 = out3(w[6], w[7], w[8]);
+    const unsigned r3 = out3(w[9], w[10], w[11]), r4 = out3(w[12], w[13], w[14]);
+    const unsigned q0 = out3(r0, r1, r2), q1 = out3(r3, r4, w[15]);
+    return kBright ? vmax2(q0, q1) : vmin2(q0, q1);
 }
 
-__global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
+// One block per 32 x 32 tile of a level.  The tile and its 4-pixel halo are
+// held as two planes of pixel pairs: pe[r][k] packs the pixels of halo
+// columns 2k and 2k + 1 of halo row r in its low and high 16-bit lanes,
+// po[r][k] those of columns 2k + 1 and 2k + 2.  Any two horizontally adjacent
+// pixels are then one word, and a warp's pixel pairs read consecutive words.
+// Every pixel of the tile and of its one-pixel ring gets a suppression key:
+// 0 where it is not a corner, else (FAST score + 1) << 8 | (255 - g) with
+// g = 3 * ring row + ring column.  Between 8-neighbours, 3 * dy + dx orders
+// the earlier raster position first, so "the neighbour's score is larger,
+// or equal and the neighbour comes first" is "the neighbour's key is larger"
+// and a corner survives suppression when its key exceeds its 8 neighbours'.
+__global__ void __launch_bounds__(kDetThreads, 5) orb_detect_kernel(const OrbHeader *__restrict__ hdr)
 {
-    __shared__ uint8_t raw[kTileW][kTileW];
-    __shared__ short sco[kRing][kRing];
-    __shared__ short hs[kOrbTile + 4][kOrbTile];      // horizontal binomial sums of rows -2 .. T+1
+    __shared__ __align__(16) unsigned pe[kTileW][kHalfW];
+    __shared__ __align__(16) unsigned po[kTileW][kHalfW];
+    __shared__ unsigned key[kRing][kPairs];             // two 16-bit keys per word
+    __shared__ unsigned hs[kOrbTile + 4][kHsW];         // horizontal binomial sums of rows -2 .. T+1, two per word
     const OrbHeader &H = *hdr;
     const OrbImage &I = H.images[blockIdx.y];
     const int tile = blockIdx.x;
@@ -113,62 +121,105 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
     const int x0 = (t % L.tiles_x) * kOrbTile, y0 = (t / L.tiles_x) * kOrbTile;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tile == 0 && tid == 0) I.n_level[H.nlevels] = 0;     // the select blocks add to it
-    // the tile and its halo, coordinates clamped to the level (the smoothing
-    // replicates the border; FAST only runs where its circle is inside)
-    for (int i = tid; i < kTileW * kTileW; i += kDetThreads) {
-        const int yy = clampi(y0 - kOrbHalo + i / kTileW, 0, L.h - 1);
-        const int xx = clampi(x0 - kOrbHalo + i % kTileW, 0, L.w - 1);
-        raw[i / kTileW][i % kTileW] = L.img[(size_t)yy * L.pitch + xx];
+    // the tile and its halo; coordinates are clamped to the level (the
+    // smoothing replicates the border; FAST only runs where its circle is
+    // inside).  Tiles whose halo lies inside the level read whole words
+    // (level rows are 16-byte aligned: checked on the host).
+    if (x0 >= kOrbHalo && y0 >= kOrbHalo && x0 + kOrbTile + kOrbHalo <= L.w && y0 + kOrbTile + kOrbHalo <= L.h) {
+        constexpr int kWords = kTileW / 4;
+        for (int i = tid; i < kTileW * kWords; i += kDetThreads) {
+            const int r = i / kWords, m = i - r * kWords;
+            const unsigned *row =
+                reinterpret_cast<const unsigned *>(L.img + (size_t)(y0 - kOrbHalo + r) * L.pitch + x0 - kOrbHalo);
+            const unsigned a = __ldg(row + m), b = m + 1 < kWords ? __ldg(row + m + 1) : 0u;
+            *reinterpret_cast<uint2 *>(&pe[r][2 * m]) = make_uint2(__byte_perm(a, 0u, 0x4140), __byte_perm(a, 0u, 0x4342));
+            *reinterpret_cast<uint2 *>(&po[r][2 * m]) =
+                make_uint2(__byte_perm(a, 0u, 0x4241), __byte_perm(__funnelshift_r(a, b, 24), 0u, 0x4140));
+        }
+    } else {
+        for (int i = tid; i < kTileW * kHalfW; i += kDetThreads) {
+            const int r = i / kHalfW, k = i - r * kHalfW;
+            const uint8_t *row = L.img + (size_t)clampi(y0 - kOrbHalo + r, 0, L.h - 1) * L.pitch;
+            const int xa = x0 - kOrbHalo + 2 * k;
+            const unsigned a = row[clampi(xa, 0, L.w - 1)], b = row[clampi(xa + 1, 0, L.w - 1)],
+                           c = row[clampi(xa + 2, 0, L.w - 1)];
+            pe[r][k] = a | (b << 16);
+            po[r][k] = b | (c << 16);
+        }
     }
     __syncthreads();
-    // scores of the tile and its one-pixel ring, two adjacent pixels per step
-    const int E = H.edge;
-    constexpr int kPairs = kRing / 2;
+    // keys of the tile and its ring, two adjacent pixels (ring columns 2h,
+    // 2h + 1) per step; the pair's centre is po[ry + 3][h + 1]
+    const int E = H.edge, th = H.fast_th;
+    const bool ring_in = x0 - 1 >= E && x0 + kOrbTile < L.w - E && y0 - 1 >= E && y0 + kOrbTile < L.h - E;
     for (int q = tid; q < kRing * kPairs; q += kDetThreads) {
-        const int ry = q / kPairs, rx = 2 * (q % kPairs);
-        int s0, s1;
-        fast_score2(raw, rx + 3, ry + 3, H.fast_th, s0, s1);
-        const int px = x0 - 1 + rx, py = y0 - 1 + ry;
-        const bool rows_in = py >= E && py < L.h - E;
-        sco[ry][rx] = (short)((rows_in && px >= E && px < L.w - E) ? s0 : -1);
-        sco[ry][rx + 1] = (short)((rows_in && px + 1 >= E && px + 1 < L.w - E) ? s1 : -1);
-    }
-    for (int q = tid; q < (kOrbTile + 4) * kOrbTile; q += kDetThreads) {
-        const int r = q / kOrbTile, x = q % kOrbTile;
-        int a = 0;
+        const int ry = q / kPairs, h = q - ry * kPairs;
+        const unsigned c = po[ry + 3][h + 1];
+        unsigned v[16];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) a += binomial5(i) * (int)raw[r + kOrbHalo - 2][x + kOrbHalo - 2 + i];
-        hs[r][x] = (short)a;
+        for (int i = 0; i < 16; ++i) {
+            const int dx = circle_dx(i), dy = circle_dy(i);     // halo column of the pair: 2h + 3 + dx
+            v[i] = (dx & 1) ? pe[ry + 3 + dy][h + ((3 + dx) >> 1)] : po[ry + 3 + dy][h + 1 + (dx >> 1)];
+        }
+        // the best arc's smallest difference, over both polarities, + 256
+        // in each lane (bright: arc minimum - centre, dark: centre - arc
+        // maximum; the lanes stay in [1, 511])
+        const unsigned e = vmax2(best_arc<true>(v) + 0x01000100u - c, c + 0x01000100u - best_arc<false>(v));
+        const int b0 = (int)(e & 0xffffu) - 256, b1 = (int)(e >> 16) - 256;
+        const unsigned g = 3u * (unsigned)ry + 2u * (unsigned)h;
+        unsigned k0 = b0 > th ? ((unsigned)b0 << 8) | (255u - g) : 0u;
+        unsigned k1 = b1 > th ? ((unsigned)b1 << 8) | (254u - g) : 0u;
+        if (!ring_in) {
+            const int px = x0 - 1 + 2 * h, py = y0 - 1 + ry;
+            const bool rows_in = py >= E && py < L.h - E;
+            if (!(rows_in && px >= E && px < L.w - E)) k0 = 0u;
+            if (!(rows_in && px + 1 >= E && px + 1 < L.w - E)) k1 = 0u;
+        }
+        key[ry][h] = k0 | (k1 << 16);
+    }
+    // horizontal binomial sums (1 4 6 4 1) of halo rows 2 .. 37, output
+    // columns 2k and 2k + 1 (taps at halo columns 2k + 2 .. 2k + 7)
+    for (int q = (tid + kDetThreads / 2) % kDetThreads; q < (kOrbTile + 4) * (kOrbTile / 2); q += kDetThreads) {
+        const int r = q / (kOrbTile / 2), k = q % (kOrbTile / 2);
+        const unsigned *e = pe[r + 2], *o = po[r + 2];
+        hs[r][k] = e[k + 1] + 4u * o[k + 1] + 6u * e[k + 2] + 4u * o[k + 2] + e[k + 3];
     }
     __syncthreads();
-    // suppression: thread (ix, iy) owns the pixels of column ix, rows iy + k * (T / kRows)
-    const int ix = tid % kOrbTile, iy0 = tid / kOrbTile;
-    unsigned keys[kRows];
-    int nkeep = 0;
+    // suppression and smoothing: thread (h, row) owns tile pixels (2h, iy)
+    // and (2h + 1, iy) for iy = row, row + 8 (a warp: 16 pairs of rows 16
+    // apart, so its key and sum words fall in distinct banks)
+    const int h = tid & 15;
+    const int row0 = (tid >> 5) + 16 * ((tid >> 4) & 1);
+    unsigned kv[4];
+    bool kf[4];
 #pragma unroll
-    for (int k = 0; k < kRows; ++k) {
-        const int iy = iy0 + k * (kDetThreads / kOrbTile);
-        const int sp = sco[iy + 1][ix + 1];
-        bool keep = sp >= 0;
+    for (int s = 0; s < 2; ++s) {
+        const int iy = row0 + 8 * s;
+        const unsigned a0 = key[iy][h], a1 = key[iy][h + 1];
+        const unsigned b0 = key[iy + 1][h], b1 = key[iy + 1][h + 1];
+        const unsigned c0 = key[iy + 2][h], c1 = key[iy + 2][h + 1];
+        const unsigned mid = __byte_perm(b0, b1, 0x5432);      // ring columns 2h + 1, 2h + 2 of ring row iy + 1
+        const unsigned up = vmax2(vmax2(a0, a1), __byte_perm(a0, a1, 0x5432));
+        const unsigned dn = vmax2(vmax2(c0, c1), __byte_perm(c0, c1, 0x5432));
+        const unsigned m = vmax2(vmax2(up, dn), vmax2(b0, b1));
+        const int py = y0 + iy, px = x0 + 2 * h;
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (!dx && !dy) continue;
-                const int q = sco[iy + 1 + dy][ix + 1 + dx];
-                const bool earlier = dy < 0 || (dy == 0 && dx < 0);
-                if (q >= 0 && (q > sp || (q == sp && earlier))) keep = false;
-            }
-        if (keep) keys[nkeep++] = ((unsigned)(255 - sp) << 24) | ((unsigned)(y0 + iy) << 12) | (unsigned)(x0 + ix);
-        const int px = x0 + ix, py = y0 + iy;
-        if (px < L.w && py < L.h) {
-            int acc = 0;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) acc += binomial5(j) * (int)hs[iy + j][ix];
-            L.smooth[(size_t)py * L.w + px] = (uint8_t)((acc + 128) >> 8);
+        for (int j = 0; j < 2; ++j) {
+            const unsigned kp = j ? mid >> 16 : mid & 0xffffu, km = j ? m >> 16 : m & 0xffffu;
+            kf[2 * s + j] = kp > km;
+            kv[2 * s + j] = ((256u - (kp >> 8)) << 24) | ((unsigned)py << 12) | (unsigned)(px + j);
+        }
+        if (py < L.h && px < L.w) {
+            const unsigned acc =
+                hs[iy][h] + 4u * hs[iy + 1][h] + 6u * hs[iy + 2][h] + 4u * hs[iy + 3][h] + hs[iy + 4][h] + 0x00800080u;
+            uint8_t *o = L.smooth + (size_t)py * L.spitch + px;
+            const unsigned sv = __byte_perm(acc, 0u, 0x4431);       // the two lanes' bits 8-15
+            if (px + 1 < L.w) *reinterpret_cast<uint16_t *>(o) = (uint16_t)sv;
+            else o[0] = (uint8_t)sv;
         }
     }
     // one atomic per warp reserves the warp's corners
+    const int nkeep = (int)kf[0] + (int)kf[1] + (int)kf[2] + (int)kf[3];
     int incl = nkeep;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -180,8 +231,12 @@ __global__ void __launch_bounds__(kDetThreads) orb_detect_kernel(const OrbHeader
     if (lane == 31 && total > 0) base = atomicAdd(&I.cnt[l], (unsigned)total);
     base = __shfl_sync(kFull, base, 31);
     int at = (int)base + incl - nkeep;
-    for (int k = 0; k < nkeep; ++k, ++at)
-        if (at < L.cand_cap) L.cand[at] = keys[k];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (kf[s]) {
+            if (at < L.cand_cap) L.cand[at] = kv[s];
+            ++at;
+        }
 }
 
 __global__ void __launch_bounds__(kOrbSelectThreads) orb_select_kernel(const OrbHeader *__restrict__ hdr)
@@ -266,12 +321,32 @@ __global__ void __launch_bounds__(kOrbSelectThreads) orb_select_kernel(const Orb
     }
 }
 
+// Staged neighbourhoods of one keypoint (one warp): rows y - 15 .. y + 15 of
+// the level for the moments and rows y - 18 .. y + 18 of the smoothed level
+// for the tests (rotated pattern points within [-13, 13]^2 land within
+// round(13 sqrt 2) = 18 pixels), each row copied from the 16-byte boundary at
+// or before its first column.
+constexpr int kMomR = 15, kTestR = 18;
+constexpr int kMomRows = 2 * kMomR + 1, kTestRows = 2 * kTestR + 1;
+constexpr int kMomChunks = 3, kTestChunks = 4;      // 16-byte chunks per staged row (31 + 15, 37 + 15 bytes)
+constexpr int kMomStride = 16 * kMomChunks, kTestStride = 16 * kTestChunks;
+constexpr int kStageCopies = kMomRows * kMomChunks + kTestRows * kTestChunks;
+
+__device__ __forceinline__ void copy16_async(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const OrbHeader *__restrict__ hdr)
 {
+    __shared__ __align__(16) uint8_t mom[kDescribeWarps][kMomRows * kMomStride];
+    __shared__ __align__(16) uint8_t tst[kDescribeWarps][kTestRows * kTestStride];
     const OrbHeader &H = *hdr;
     const OrbImage &I = H.images[blockIdx.y];
-    const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * kDescribeWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int slot = blockIdx.x * kDescribeWarps + wv;
     if (slot >= I.nslots) return;
     int l = 0;
     for (int k = 0; k < H.nlevels; ++k)
@@ -293,21 +368,38 @@ __global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const
     }
     const unsigned key = I.sel[slot];
     const int x = (int)(key & 4095u), y = (int)((key >> 12) & 4095u);
+    // both neighbourhoods in one round trip; keypoints lie at least 19
+    // pixels inside the level, and a chunk that holds a column of a row
+    // lies inside the row's 16-byte padded pitch
+    const int a1 = (x - kMomR) & ~15, n1 = ((x + kMomR) >> 4) - (a1 >> 4) + 1;
+    const int a0 = (x - kTestR) & ~15, n0 = ((x + kTestR) >> 4) - (a0 >> 4) + 1;
+    for (int j = lane; j < kStageCopies; j += 32) {
+        if (j < kMomRows * kMomChunks) {
+            const int r = j / kMomChunks, ch = j - r * kMomChunks;
+            if (ch < n1)
+                copy16_async(&mom[wv][r * kMomStride + 16 * ch],
+                             L.img + (size_t)(y - kMomR + r) * L.pitch + a1 + 16 * ch);
+        } else {
+            const int jt = j - kMomRows * kMomChunks, r = jt / kTestChunks, ch = jt - r * kTestChunks;
+            if (ch < n0)
+                copy16_async(&tst[wv][r * kTestStride + 16 * ch],
+                             L.smooth + (size_t)(y - kTestR + r) * L.spitch + a0 + 16 * ch);
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
     // intensity centroid over the disk u^2 + v^2 <= 225 (exact integer sums)
-    // all 31 loads of a lane are issued before any is used (unrolled)
+    const uint8_t *mp = &mom[wv][kMomR * kMomStride + (x - a1)];      // pixel (u, v): mp[v * stride + u]
     int m10 = 0, m01 = 0;
-    int pix[31];
 #pragma unroll
     for (int r = 0; r < 31; ++r) {
         const int q = lane + 32 * r;
         const int u = q % 31 - 15, v = q / 31 - 15;
-        pix[r] = (q < 31 * 31 && u * u + v * v <= 225) ? (int)L.img[(size_t)(y + v) * L.pitch + (x + u)] : 0;
-    }
-#pragma unroll
-    for (int r = 0; r < 31; ++r) {
-        const int q = lane + 32 * r;
-        m10 += (q % 31 - 15) * pix[r];
-        m01 += (q / 31 - 15) * pix[r];
+        if (q < 31 * 31 && u * u + v * v <= 225) {
+            const int p = mp[v * kMomStride + u];
+            m10 += u * p;
+            m01 += v * p;
+        }
     }
     m10 = __reduce_add_sync(kFull, m10);
     m01 = __reduce_add_sync(kFull, m01);
@@ -319,6 +411,7 @@ __global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const
         s = __fdiv_rn((float)m01, nm);
     }
     // byte `lane` of the descriptor: tests 8 lane .. 8 lane + 7
+    const uint8_t *tp = &tst[wv][kTestR * kTestStride + (x - a0)];
     unsigned byte = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -329,7 +422,7 @@ __global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const
             const float px = (float)pt[2 * q], py = (float)pt[2 * q + 1];
             const int u = (int)roundf(__fsub_rn(__fmul_rn(c, px), __fmul_rn(s, py)));
             const int v = (int)roundf(__fadd_rn(__fmul_rn(s, px), __fmul_rn(c, py)));
-            val[q] = L.smooth[(size_t)(y + v) * L.w + (x + u)];
+            val[q] = tp[v * kTestStride + u];
         }
         byte |= (val[0] < val[1] ? 1u : 0u) << k;
     }
