@@ -30,13 +30,16 @@
 //             the disk (integer warp sums), the orientation, and lane b
 //             computes descriptor byte b (tests 8b .. 8b+7).
 // Integer work is exact; the orientation and the rotated test positions use
-// IEEE-rounded FP32 (and one double square root) in the order the reading
-// gives, so results equal the oracle's bit for bit.
+// IEEE-rounded FP32 in the order the reading gives (the moment magnitude,
+// a double square root rounded to float in the reading, is the same value
+// from an FP32 square root settled by integer comparisons: ft_sqrt.h), so
+// results equal the oracle's bit for bit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "ft_internal.h"
+#include "ft_sqrt.h"
 
 namespace ft {
 namespace {
@@ -339,7 +342,7 @@ __device__ __forceinline__ void copy16_async(void *smem, const void *gmem)
                  : "memory");
 }
 
-__global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const OrbHeader *__restrict__ hdr)
+__global__ void __launch_bounds__(32 * kDescribeWarps, 7) orb_describe_kernel(const OrbHeader *__restrict__ hdr)
 {
     __shared__ __align__(16) uint8_t mom[kDescribeWarps][kMomRows * kMomStride];
     __shared__ __align__(16) uint8_t tst[kDescribeWarps][kTestRows * kTestStride];
@@ -388,25 +391,30 @@ __global__ void __launch_bounds__(32 * kDescribeWarps) orb_describe_kernel(const
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncwarp();
-    // intensity centroid over the disk u^2 + v^2 <= 225 (exact integer sums)
-    const uint8_t *mp = &mom[wv][kMomR * kMomStride + (x - a1)];      // pixel (u, v): mp[v * stride + u]
+    // intensity centroid over the disk u^2 + v^2 <= 225 (exact integer
+    // sums): lane u + 15 walks column u (lane 31 idles)
     int m10 = 0, m01 = 0;
+    if (lane < kMomRows) {
+        const int u = lane - kMomR;
+        const uint8_t *col = &mom[wv][x - a1 + u];          // row v + 15 at col[(v + 15) * stride]
+        int sum = 0;
 #pragma unroll
-    for (int r = 0; r < 31; ++r) {
-        const int q = lane + 32 * r;
-        const int u = q % 31 - 15, v = q / 31 - 15;
-        if (q < 31 * 31 && u * u + v * v <= 225) {
-            const int p = mp[v * kMomStride + u];
-            m10 += u * p;
-            m01 += v * p;
-        }
+        for (int v = -kMomR; v <= kMomR; ++v)
+            if (u * u <= kMomR * kMomR - v * v) {
+                const int p = col[(v + kMomR) * kMomStride];
+                sum += p;
+                m01 += v * p;
+            }
+        m10 = u * sum;
     }
     m10 = __reduce_add_sync(kFull, m10);
     m01 = __reduce_add_sync(kFull, m01);
     float c = 1.0f, s = 0.0f;
     if (m10 != 0 || m01 != 0) {
-        const double n2 = __dadd_rn(__dmul_rn((double)m10, (double)m10), __dmul_rn((double)m01, (double)m01));
-        const float nm = __double2float_rn(__dsqrt_rn(n2));
+        // |m| = sqrt(m10^2 + m01^2) as the double square root rounded to
+        // float, which for these integers is the correctly rounded FP32
+        // square root (ft_sqrt.h)
+        const float nm = float_sqrt_rn((uint64_t)((long long)m10 * m10 + (long long)m01 * m01));
         c = __fdiv_rn((float)m10, nm);
         s = __fdiv_rn((float)m01, nm);
     }
