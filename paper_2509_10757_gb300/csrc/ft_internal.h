@@ -211,7 +211,7 @@ struct OrbImage {
 struct OrbHeader {
     int nimages, nlevels, fast_th, edge, max_tiles, max_slots;
     float sc[FT_MAX_LEVELS];
-    int8_t pattern[256 * 4];
+    alignas(16) int8_t pattern[256 * 4];      // test i: x1, y1, x2, y2 at 4 i (16-byte aligned: vector loads)
     const OrbImage *images;
 };
 

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kOrbSelectThreads) orb_select_kernel(const Orb
     const int c = min((int)I.cnt[l], L.cand_cap);
     const int K = L.max_kp;
     unsigned kth = 0xffffffffu;
-    if (c > K) {
+    if (c > K && K > 0) {
         // the K-th smallest key (keys are distinct): one byte per pass
         unsigned prefix = 0, mask = 0;
         int rank = K;
@@ -269,15 +269,30 @@ __global__ void __launch_bounds__(kOrbSelectThreads) orb_select_kernel(const Orb
                 if ((k & mask) == prefix) atomicAdd(&hist[(k >> (8 * b)) & 255u], 1);
             }
             __syncthreads();
-            if (tid == 0) {
-                int cum = 0;
-                for (int bin = 0; bin < 256; ++bin) {
-                    if (cum + hist[bin] >= rank) {
-                        s_prefix = prefix | ((unsigned)bin << (8 * b));
-                        s_rank = rank - cum;
-                        break;
+            if (tid < 32) {
+                // the first bin whose running count reaches the rank: lane t
+                // sums bins 8t .. 8t + 7, a warp scan finds the lane
+                int s8 = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s8 += hist[8 * tid + q];
+                int incl = s8;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(kFull, incl, o);
+                    if (tid >= o) incl += v;
+                }
+                const unsigned hit = __ballot_sync(kFull, incl >= rank);
+                if (tid == __ffs(hit) - 1) {
+                    int cum = incl - s8;
+                    for (int q = 0; q < 8; ++q) {
+                        const int bin = 8 * tid + q;
+                        if (cum + hist[bin] >= rank) {
+                            s_prefix = prefix | ((unsigned)bin << (8 * b));
+                            s_rank = rank - cum;
+                            break;
+                        }
+                        cum += hist[bin];
                     }
-                    cum += hist[bin];
                 }
             }
             __syncthreads();
@@ -418,16 +433,21 @@ __global__ void __launch_bounds__(32 * kDescribeWarps, 7) orb_describe_kernel(co
         c = __fdiv_rn((float)m10, nm);
         s = __fdiv_rn((float)m01, nm);
     }
-    // byte `lane` of the descriptor: tests 8 lane .. 8 lane + 7
+    // byte `lane` of the descriptor: tests 8 lane .. 8 lane + 7 (their 32
+    // pattern coordinates in two 16-byte loads)
     const uint8_t *tp = &tst[wv][kTestR * kTestStride + (x - a0)];
+    const uint4 *pw = reinterpret_cast<const uint4 *>(H.pattern) + 2 * lane;
+    const uint4 pa = __ldg(pw), pb = __ldg(pw + 1);
+    const unsigned pws[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
     unsigned byte = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int8_t *pt = H.pattern + 4 * (8 * lane + k);
         int val[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const float px = (float)pt[2 * q], py = (float)pt[2 * q + 1];
+            // test point q: bytes 2q (x) and 2q + 1 (y) of the test's word, signed
+            const int xi = (int)(pws[k] << (24 - 16 * q)) >> 24, yi = (int)(pws[k] << (16 - 16 * q)) >> 24;
+            const float px = (float)xi, py = (float)yi;
             const int u = (int)roundf(__fsub_rn(__fmul_rn(c, px), __fmul_rn(s, py)));
             const int v = (int)roundf(__fadd_rn(__fmul_rn(s, px), __fmul_rn(c, py)));
             val[q] = tp[v * kTestStride + u];
