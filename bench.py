@@ -90,6 +90,15 @@ def barrier(world: int):
 
 
 # ---------------------------------------------------------------- measurement helpers
+_T0 = time.time()
+
+
+def progress(msg: str):
+    """A progress line on stderr (the result line alone goes to stdout)."""
+    sys.stderr.write(f"bench: {msg} at {time.time() - _T0:.1f} s\n")
+    sys.stderr.flush()
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while running.  The
     sampler runs from before the warm-up to after the last timed form; mark()
@@ -127,6 +136,7 @@ class ClockSampler:
     def mark(self, name: str, begin: bool):
         w = self.windows.setdefault(name, [None, None])
         w[0 if begin else 1] = time.time()
+        progress(f"{name} {'begins' if begin else 'ends'}")
 
     @staticmethod
     def _summary(rows) -> dict:
@@ -987,11 +997,13 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     best = L.ft_tuning()
+    progress("single-launch autotuner begins")
     with torch.cuda.stream(stream):
         b = pb.batch()
         L.check(ctx.lib.ft_autotune(ctx.ptr, stream_handle(stream), None, C.byref(b), 3, C.byref(best)),
                 "ft_autotune")
     torch.cuda.synchronize(dev)
+    progress("stream autotuner begins")
 
     # Headline: a stream of batches.  LANES contexts, each with its own copy
     # of the batch's device buffers and its own stream, take the launches in
@@ -1048,6 +1060,7 @@ def run_gpu(args, rank, world, local_rank):
     value = units / job_s
     ms_per_step = 1e3 * job_s / args.steps
 
+    progress("single launch begins")
     # The single launch (one context, one stream, L2 flushed before each
     # launch, each launch timed alone): the kernel's duration for its
     # roofline and the launch latency.
@@ -1082,6 +1095,7 @@ def run_gpu(args, rank, world, local_rank):
     achieved = alg_bytes / avg_launch_s / 1e9
     traffic = profiled_traffic()
 
+    progress("end to end begins")
     # end to end through the C ABI: host -> device copy of the inputs, the
     # launches, device -> host copy of the outputs, all inside each call.
     # Headline form: the pyramids are built on the device from the uploaded
@@ -1112,6 +1126,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_up_s = max_over_ranks(sum(e2e_up_ms) / 1e3, world, dev)
     e2e_units = sum_over_ranks(float(n_e2e * (kp_units + mp_units)), world, dev)
 
+    progress("pipelined end to end begins")
     # Pipelined end to end: two contexts, each with its own batch buffers
     # and stream, take alternate steps, so one step's host <-> device copies
     # overlap the other's kernels (the copy engines and the SMs work at once).
@@ -1153,6 +1168,7 @@ def run_gpu(args, rank, world, local_rank):
     for c, _, _ in extra:
         c.close()
 
+    progress("device pyramids begins")
     # the device-resident launch with the pyramids built on the device first
     pyr_ms = []
     for i in range(max(3, min(args.steps, 1000))):
@@ -1166,6 +1182,7 @@ def run_gpu(args, rank, world, local_rank):
         pyr_ms.append(s0.elapsed_time(s1))
     pyr_built_bytes = pbd.lpyr.size
 
+    progress("plain form begins")
     # the plain form: one frame per call sequence (stereo, then search), synchronous
     plain_ms = []
     nplain = min(len(frames), 32)
@@ -1211,8 +1228,10 @@ def run_gpu(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        clocks.mark("cpu_baseline", True)
         cpu = time_oracle(frames, budget_s=12.0)
         cpu["all_cores"] = time_oracle_all_cores(frames, budget_s=8.0)
+        clocks.mark("cpu_baseline", False)
     served = None
     if rank == 0 and world == 1 and not args.no_served:
         clocks.mark("served", True)
@@ -1326,6 +1345,11 @@ def main():
                     help="workload of --mode trace (batched, stress, fisheye) or --mode profile (batched, pose, "
                          "extraction, pyramid, scattered)")
     args = ap.parse_args()
+    # a run that takes far longer than it should prints every thread's stack
+    # to stderr (repeatedly), so a stuck step can be named afterwards
+    import faulthandler
+    faulthandler.dump_traceback_later(float(os.environ.get("FT_BENCH_WATCHDOG_S", "900")), repeat=True,
+                                      file=sys.stderr)
     if args.mode == "trace":
         return run_trace(args, dist_env()[2])
     if args.mode == "profile":
