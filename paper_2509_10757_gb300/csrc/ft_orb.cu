@@ -157,26 +157,33 @@ __global__ void __launch_bounds__(kDetThreads, 5) orb_detect_kernel(const OrbHea
     const bool ring_in = x0 - 1 >= E && x0 + kOrbTile < L.w - E && y0 - 1 >= E && y0 + kOrbTile < L.h - E;
     for (int q = tid; q < kRing * kPairs; q += kDetThreads) {
         const int ry = q / kPairs, h = q - ry * kPairs;
-        const unsigned c = po[ry + 3][h + 1];
-        unsigned v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int dx = circle_dx(i), dy = circle_dy(i);     // halo column of the pair: 2h + 3 + dx
-            v[i] = (dx & 1) ? pe[ry + 3 + dy][h + ((3 + dx) >> 1)] : po[ry + 3 + dy][h + 1 + (dx >> 1)];
-        }
-        // the best arc's smallest difference, over both polarities, + 256
-        // in each lane (bright: arc minimum - centre, dark: centre - arc
-        // maximum; the lanes stay in [1, 511])
-        const unsigned e = vmax2(best_arc<true>(v) + 0x01000100u - c, c + 0x01000100u - best_arc<false>(v));
-        const int b0 = (int)(e & 0xffffu) - 256, b1 = (int)(e >> 16) - 256;
-        const unsigned g = 3u * (unsigned)ry + 2u * (unsigned)h;
-        unsigned k0 = b0 > th ? ((unsigned)b0 << 8) | (255u - g) : 0u;
-        unsigned k1 = b1 > th ? ((unsigned)b1 << 8) | (254u - g) : 0u;
+        // pixels closer than E to a border (or outside the level) are not
+        // corners; a pair with neither pixel inside is not scored (a warp of
+        // such pairs, as on a tile that overhangs the level, skips the work)
+        bool in0 = true, in1 = true;
         if (!ring_in) {
             const int px = x0 - 1 + 2 * h, py = y0 - 1 + ry;
             const bool rows_in = py >= E && py < L.h - E;
-            if (!(rows_in && px >= E && px < L.w - E)) k0 = 0u;
-            if (!(rows_in && px + 1 >= E && px + 1 < L.w - E)) k1 = 0u;
+            in0 = rows_in && px >= E && px < L.w - E;
+            in1 = rows_in && px + 1 >= E && px + 1 < L.w - E;
+        }
+        unsigned k0 = 0u, k1 = 0u;
+        if (in0 || in1) {
+            const unsigned c = po[ry + 3][h + 1];
+            unsigned v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int dx = circle_dx(i), dy = circle_dy(i);     // halo column of the pair: 2h + 3 + dx
+                v[i] = (dx & 1) ? pe[ry + 3 + dy][h + ((3 + dx) >> 1)] : po[ry + 3 + dy][h + 1 + (dx >> 1)];
+            }
+            // the best arc's smallest difference, over both polarities, + 256
+            // in each lane (bright: arc minimum - centre, dark: centre - arc
+            // maximum; the lanes stay in [1, 511])
+            const unsigned e = vmax2(best_arc<true>(v) + 0x01000100u - c, c + 0x01000100u - best_arc<false>(v));
+            const int b0 = (int)(e & 0xffffu) - 256, b1 = (int)(e >> 16) - 256;
+            const unsigned g = 3u * (unsigned)ry + 2u * (unsigned)h;
+            if (in0 && b0 > th) k0 = ((unsigned)b0 << 8) | (255u - g);
+            if (in1 && b1 > th) k1 = ((unsigned)b1 << 8) | (254u - g);
         }
         key[ry][h] = k0 | (k1 << 16);
     }
