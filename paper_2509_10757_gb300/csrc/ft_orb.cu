@@ -77,7 +77,7 @@ __device__ __forceinline__ unsigned vmax2(unsigned a, unsigned b) { return __vma
 // largest values.  Three-input packed min/max: the extremes of the 16 arcs
 // of 3, those of the arcs of 9 as three arcs of 3 (i, i + 3, i + 6), then
 // the best of the 16 in a tree (40 operations per polarity; the form with
-// running extremes over blocks of 9, 57 two-input operations, measured 4 %
+// running extremes over blocks of 9, 57 two-input operations, measured 3 %
 // slower over the whole extraction).
 template <bool kBright>
 __device__ __forceinline__ unsigned best_arc(const unsigned (&v)[16])
